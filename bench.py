@@ -1,0 +1,324 @@
+"""Benchmark of the HDD likelihood path on GB300 (one JSON line on stdout).
+
+Default workload: 513 x 513 grid (261,121 unknowns), 256 samples per step,
+40 KL terms (correlation length 0.1, variance 2), 16 x 16 observations, leaves of
+4 x 4 cells.  One step = assemble + upsweep + pruned point solve + log-likelihood
+for the whole batch, inputs resident in HBM.  The step's working set (tens of GB
+of fronts and factors) is far larger than the 129 MB L2, so no flush is needed.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp64|mixed]
+  python bench.py --impl reference ...   # the FP64 CPU oracle on the host cores
+
+Under torchrun (N > 1) every rank evaluates its own batch on its own GPU
+(replicas: the samples are independent; no data-path collective); value is the
+total over ranks divided by the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import workload as w  # noqa: E402
+
+METRIC = "log-likelihood evals/s at 513^2 grid"
+# FP64 FMA throughput of GB300: 2 FP64 FMA per clock per SM (1.25 TFLOP/s nominal
+# at 2070 MHz over 152 SMs), i.e. 152 * 2 * 2 * 2.07e9 flop/s.
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+# FP32 SIMT: 128 FMA per clock per SM.
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+
+
+def _env_int(name, default):
+    try:
+        return int(os.environ.get(name, default))
+    except ValueError:
+        return default
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.samples = []
+        self._stop = threading.Event()
+        self._thr = None
+
+    def _run(self):
+        while not self._stop.is_set():
+            try:
+                out = subprocess.run(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                                      "--format=csv,noheader,nounits"], capture_output=True, text=True, timeout=5)
+                if out.returncode == 0 and out.stdout.strip():
+                    self.samples.append([x.strip() for x in out.stdout.strip().split(",")])
+            except Exception:
+                pass
+            self._stop.wait(0.2)
+
+    def __enter__(self):
+        self._thr = threading.Thread(target=self._run, daemon=True)
+        self._thr.start()
+        return self
+
+    def __exit__(self, *exc):
+        self._stop.set()
+        if self._thr:
+            self._thr.join(timeout=10)
+
+    def summary(self):
+        if not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(s[0]) for s in self.samples if s[0].replace(".", "").isdigit()]
+        mx = [float(s[1]) for s in self.samples if s[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for s in self.samples:
+            for n, v in zip(names, s[4:8]):
+                if v.strip().lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "n_samples": len(self.samples)}
+
+
+def cpu_baseline(cfg, prob, n_samples, processes):
+    """The oracle (FP64 P1 FEM + banded Cholesky) on host cores, spawn pool, 1 BLAS thread each."""
+    from oracle import fem
+    saved = {k: os.environ.get(k) for k in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS")}
+    for k in saved:
+        os.environ[k] = "1"
+    try:
+        t0 = time.perf_counter()
+        fem.evaluate_batch(cfg.N, prob.phi, prob.Z[:n_samples], prob.obs, prob.y, cfg.sigma, cfg.f,
+                           processes=processes)
+        dt = time.perf_counter() - t0
+    finally:
+        for k, v in saved.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
+    return n_samples / dt, dt
+
+
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def run_reference(args, cfg):
+    """--impl reference: the FP64 CPU oracle timed on the host cores."""
+    rank = _env_int("RANK", 0)
+    if rank != 0:
+        return 0
+    P = host_cores()
+    per_step = P
+    prob = w.make_problem(cfg, batch=max(per_step, cfg.batch))
+    for _ in range(args.warmup):
+        cpu_baseline(cfg, prob, per_step, P)
+    times = []
+    for _ in range(args.steps):
+        _, dt = cpu_baseline(cfg, prob, per_step, P)
+        times.append(dt)
+    total = sum(times)
+    value = per_step * args.steps / total
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "evals/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"{cfg.name}: {cfg.N}x{cfg.N} grid, {per_step} samples per step (of {cfg.batch}),"
+                               f" n_z {cfg.n_z}, {cfg.obs_side ** 2} observations", "batch": per_step},
+        "cpu_baseline": {"value": value, "unit": "evals/s", "cores": P, "kind": "oracle",
+                         "sample": f"{per_step} samples per step, one per process"},
+        "e2e": {"value": value, "unit": "evals/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+def run_hdd(args, cfg):
+    import torch
+    from paper_1708_02207_gb300 import build as hdd_build, hdd
+
+    rank, world, local = _env_int("RANK", 0), _env_int("WORLD_SIZE", 1), _env_int("LOCAL_RANK", 0)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist_mod
+        dist = dist_mod
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if rank == 0:
+        hdd_build.build()
+    if dist:
+        dist.barrier()
+
+    prob = w.make_problem(cfg)
+    B = cfg.batch
+    precision = hdd.HDD_MIXED_FP32 if args.precision == "mixed" else hdd.HDD_FP64
+    plan = hdd.Plan(cfg.N, args.leaf or cfg.leaf, prob.phi, prob.obs, cfg.sigma, f=cfg.f, precision=precision,
+                    ir_max_iter=args.ir_iters, ir_tol=args.ir_tol, device=local)
+    info = plan.info()
+    ws = plan.workspace(B)
+    Z = torch.from_numpy(prob.Z).to(dev)
+    y = torch.from_numpy(prob.y).to(dev)
+    u_obs = torch.empty(B, plan.n_obs, dtype=torch.float64, device=dev)
+    ll = torch.empty(B, dtype=torch.float64, device=dev)
+    st_t = torch.empty(B, dtype=torch.int32, device=dev)
+    stream = torch.cuda.Stream(device=dev)
+    stages = ("assemble", "upsweep", "point_solve", "loglik")
+
+    def step(evs=None):
+        if evs is not None:
+            evs[0].record(stream)
+        plan.assemble(Z, ws, stream)
+        if evs is not None:
+            evs[1].record(stream)
+        plan.upsweep(B, ws, stream)
+        if evs is not None:
+            evs[2].record(stream)
+        plan.point_solve(B, ws, u_obs, stream)
+        if evs is not None:
+            evs[3].record(stream)
+        plan.loglik(B, ws, u_obs, y, ll, st_t, stream)
+        if evs is not None:
+            evs[4].record(stream)
+
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            step()
+    stream.synchronize()
+    bad = int((st_t != 0).sum().item())
+
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(5)] for _ in range(args.steps)]
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        with torch.cuda.stream(stream):
+            t_start.record(stream)
+            for k in range(args.steps):
+                step(evs[k])
+            t_end.record(stream)
+        stream.synchronize()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    total_ms = t_start.elapsed_time(t_end)
+    if dist:
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    stage_ms = {s: statistics.mean(e[i].elapsed_time(e[i + 1]) for e in evs) for i, s in enumerate(stages)}
+
+    value = world * B * args.steps / (total_ms / 1e3)
+
+    # end to end through the C ABI with host buffers (pinned), copies inside
+    Zh = torch.from_numpy(prob.Z).pin_memory()
+    yh = torch.from_numpy(prob.y).pin_memory()
+    llh = torch.empty(B, dtype=torch.float64).pin_memory()
+    uh = torch.empty(B, plan.n_obs, dtype=torch.float64).pin_memory()
+    sh = torch.empty(B, dtype=torch.int32).pin_memory()
+
+    def e2e_call():
+        plan.evaluate_host_ptrs(B, ws, Zh.data_ptr(), yh.data_ptr(), 0, llh.data_ptr(), uh.data_ptr(),
+                                sh.data_ptr(), stream)
+
+    for _ in range(max(1, min(args.warmup, 2))):
+        e2e_call()
+    e2e_steps = max(1, min(args.steps, 5))
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        e2e_call()
+    e2e_s = time.perf_counter() - t0
+    e2e_value = world * B * e2e_steps / e2e_s
+    h2d = B * plan.n_z * 8 + plan.n_obs * 8
+    d2h = B * 8 + B * plan.n_obs * 8 + B * 4
+
+    # roofline of the dominant stage (the upsweep: every Schur elimination)
+    up_flops = info["flops_upsweep"] * B
+    achieved = up_flops / (stage_ms["upsweep"] / 1e3) / 1e12
+    if precision == hdd.HDD_FP64:
+        roof = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+                "kernel": "hdd_upsweep (front_small, front_fill, potrf, trsm, syrk launches), FP64 FMA",
+                "peak_source": "derived: 2 FP64 FMA/clk/SM x 152 SMs x 2070 MHz (1.25 TFLOP/s nominal)"}
+    else:
+        roof = {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": achieved / FP32_PEAK_TFLOPS, "traffic": None,
+                "kernel": "hdd_upsweep (front_small, front_fill, potrf, trsm, syrk launches), FP32 FMA",
+                "peak_source": "derived: 128 FP32 FMA/clk/SM x 152 SMs x 2070 MHz"}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        P = min(host_cores(), B)
+        v, dt = cpu_baseline(cfg, prob, P, P)
+        cpu = {"value": v, "unit": "evals/s", "cores": P, "kind": "oracle",
+               "sample": f"{P} of the {B} samples, one per process ({dt:.1f} s)"}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "evals/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64" if precision == hdd.HDD_FP64 else "f32+f64",
+        "data": "synthetic",
+        "config": {"workload": f"{cfg.name}: {cfg.N}x{cfg.N} grid ({(cfg.N - 2) ** 2} unknowns), {B} samples/step,"
+                               f" n_z {cfg.n_z}, corr {cfg.corr_len}, var {cfg.variance},"
+                               f" {cfg.obs_side ** 2} observations, leaf {args.leaf or cfg.leaf}",
+                   "batch": B, "precision": args.precision, "parallelism": f"replicas x{world}",
+                   "l2": "working set >> 129 MB L2 (no flush needed)"},
+        "stage_ms": stage_ms, "failed_samples": bad,
+        "roofline": roof,
+        "e2e": {"value": e2e_value, "unit": "evals/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "gpu_launches": info["launches_evaluate"] * args.steps,
+        "clocks": clk.summary(),
+        "cpu_baseline": cpu,
+        "plan": {"flops_upsweep_per_sample": info["flops_upsweep"], "nodes": info["n_nodes"],
+                 "visited": info["n_visited"], "workspace_gb": plan.workspace_size(B) / 1e9},
+    }
+    if rank == 0:
+        print(json.dumps(line))
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="hdd", choices=["hdd", "reference"])
+    ap.add_argument("--config", default="grid513", choices=sorted(w.CONFIGS))
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--leaf", type=int, default=0)
+    ap.add_argument("--ir-iters", type=int, default=4)
+    ap.add_argument("--ir-tol", type=float, default=1e-10)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args(argv)
+    cfg = w.CONFIGS[args.config]
+    if args.impl == "reference":
+        return run_reference(args, cfg)
+    return run_hdd(args, cfg)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

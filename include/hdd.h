@@ -1,0 +1,179 @@
+/*
+ * hdd.h -- C ABI of the GB300 HDD likelihood library (libhdd.so).
+ *
+ * Hierarchical domain decomposition (HDD) for -div(kappa grad u) = f on the unit
+ * square, P1 elements on an N x N vertex grid, homogeneous Dirichlet data, with
+ * kappa = exp(q(x, Z)) and q a KL expansion in the parameters Z (Sec. 1.1,
+ * Eq. elliptic; notation table: kappa = e^q).  For a batch of parameter vectors Z
+ * the library returns u at a few observation vertices and the Gaussian
+ * log-likelihood of observed data y (Sec. 1.2), without forming the full solution:
+ *
+ *   hdd_plan         decomposition tree, index maps and launch schedule (Sec. 2.1)
+ *   hdd_assemble     kappa per triangle for each sample            (Sec. 3.1)
+ *   hdd_upsweep      "Leaves to Root": Schur maps of every node    (Sec. 2.4, 3.3, 3.4)
+ *   hdd_point_solve  pruned "Root to Leaves" to the observation vertices (Sec. 3.4, 5.3)
+ *   hdd_loglik       Gaussian data-misfit log-likelihood           (Sec. 1.2)
+ *
+ * Conventions shared by every call
+ *   - Vertex (i, j) of the grid sits at (i h, j h), h = 1/(N-1), flat id j*N + i.
+ *     Cell (i, j) is split by its "/" diagonal into triangle 2*(j*(N-1)+i) (lower
+ *     right, right angle at (i+1, j)) and triangle 2*(j*(N-1)+i)+1 (upper left,
+ *     right angle at (i, j+1)).
+ *   - "device" pointers are CUDA global memory of the plan's device; "host"
+ *     pointers are ordinary (pageable or pinned) CPU memory.
+ *   - The caller owns every buffer it passes.  The library owns the plan and the
+ *     device copies it makes in hdd_plan, and allocates nothing else: all scratch
+ *     lives in the caller's workspace (size from hdd_workspace_size).
+ *   - Device work is enqueued on `stream` (a cudaStream_t; NULL = legacy default
+ *     stream) and is asynchronous.  A return value covers argument and launch
+ *     errors only; numerical failures are reported per sample by hdd_loglik.
+ *   - No call throws, traps or aborts.  Calls on one plan may run concurrently
+ *     from several threads if each uses its own workspace.
+ *   - The workspace passed to hdd_upsweep / hdd_point_solve / hdd_loglik must be
+ *     the one hdd_assemble filled, with the same batch.
+ */
+#ifndef HDD_H
+#define HDD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct hdd_plan_s* hdd_plan_t;
+
+typedef enum {
+  HDD_OK = 0,
+  HDD_EINVAL = -1,    /* bad argument (size, pointer, observation on the boundary ...) */
+  HDD_ENOMEM = -2,    /* host or device allocation inside hdd_plan failed */
+  HDD_ECUDA = -3,     /* a CUDA call failed; hdd_last_error() has the text */
+  HDD_ENOTSPD = -4,   /* per sample: a pivot of a Schur block was not positive */
+  HDD_ENOCONV = -5,   /* per sample: iterative refinement did not reach ir_tol */
+  HDD_ETIMEOUT = -6,  /* reserved for bounded device waits */
+  HDD_ESTATE = -7     /* call needs a device plan but the plan is host-only */
+} hdd_status;
+
+typedef enum {
+  HDD_FP64 = 0,       /* every step in FP64 */
+  HDD_MIXED_FP32 = 1  /* FP32 Schur factorisation + FP64-residual iterative refinement */
+} hdd_precision;
+
+typedef struct {
+  int32_t N;                  /* vertices per side, N >= 3 */
+  int32_t leaf;               /* leaf size in cells per side, >= 1 */
+  int32_t n_z;                /* KL terms, 1..256 */
+  const double* kl_basis;     /* host, [n_t x n_z] row-major, n_t = 2 (N-1)^2, already scaled
+                                 by sqrt(lambda_k); copied by hdd_plan (may be NULL for a
+                                 host-only plan) */
+  double f;                   /* constant right-hand side f */
+  int32_t n_obs;              /* observation count, >= 1 */
+  const int32_t* obs_vertex;  /* host, [n_obs] flat vertex ids j*N+i; every one must be an
+                                 interior vertex (1 <= i, j <= N-2), else HDD_EINVAL */
+  double sigma;               /* noise standard deviation, > 0 */
+  int32_t precision;          /* hdd_precision */
+  int32_t ir_max_iter;        /* mixed only: refinement steps after the first solve (0..64) */
+  double ir_tol;              /* mixed only: target max_k |du_k| / max_k |u_k| at the observations */
+  int32_t device;             /* CUDA device ordinal, or -1 for a host-only plan that supports
+                                 the hdd_plan_info / hdd_node_info queries and nothing else */
+} hdd_plan_desc;
+
+typedef struct {
+  int32_t n_nodes;            /* nodes of the decomposition tree (node 0 = Omega) */
+  int32_t n_leaves;
+  int32_t depth;              /* max depth (root = 0) */
+  int32_t height;             /* height of the root (leaves = 0) */
+  int32_t n_visited;          /* nodes on the root-to-observation paths (Sec. 5.3) */
+  int32_t max_front;          /* largest front m + b + 1 */
+  double flops_upsweep;       /* algorithmic flops per sample of hdd_upsweep */
+  double flops_point_solve;   /* algorithmic flops per sample of one pruned descent */
+  double factor_bytes;        /* per sample, bytes of stored factors */
+  double schur_bytes;         /* per sample, peak bytes of live Schur complements */
+  int32_t launches_upsweep;   /* kernel launches of one hdd_upsweep */
+  int32_t launches_evaluate;  /* kernel launches of assemble + upsweep + point solve + loglik */
+} hdd_plan_info_t;
+
+typedef struct {
+  int32_t x0, x1, y0, y1;     /* closed rectangle in vertex indices */
+  int32_t parent, child0, child1;   /* -1 where absent */
+  int32_t depth, height;
+  int32_t m;                  /* eliminated vertices: |gamma| (interface), or leaf interior */
+  int32_t b;                  /* boundary unknowns |I(d omega)| without Dirichlet vertices */
+  int32_t visited;            /* 1 if the pruned descent computes this node's gamma */
+} hdd_node_info_t;
+
+/* Build a plan (Sec. 2.1: binary tree, longer side split at the cell-aligned
+ * midpoint, x first on ties, leaves of at most `leaf` x `leaf` cells).  On
+ * success *out owns host tables and, for device >= 0, device copies of the KL
+ * basis, node tables and index maps.  Errors: HDD_EINVAL, HDD_ENOMEM, HDD_ECUDA. */
+hdd_status hdd_plan(const hdd_plan_desc* desc, hdd_plan_t* out);
+
+/* Release a plan and its device memory.  NULL is accepted.  The caller must make
+ * sure no work that uses the plan is still in flight. */
+hdd_status hdd_plan_destroy(hdd_plan_t plan);
+
+/* Bytes of device workspace for `batch` samples (batch >= 1). */
+hdd_status hdd_workspace_size(hdd_plan_t plan, int32_t batch, size_t* bytes);
+
+/* Assembly (Sec. 3.1, Eq. coefA, Eq. coefc; kappa = e^q): for each sample s and
+ * triangle t, q = sum_k Phi[t,k] Z[s,k] and kappa = exp(q) in FP64, written to
+ * the workspace; the per-triangle stiffness kappa_t |t| grad b_i . grad b_j is
+ * formed from it by hdd_upsweep.  Z: device, [batch x n_z] row-major FP64.
+ * workspace: device, >= hdd_workspace_size(plan, batch) bytes, 256-byte aligned. */
+hdd_status hdd_assemble(hdd_plan_t plan, const double* Z, int32_t batch,
+                        void* workspace, void* stream);
+
+/* "Leaves to Root" (Sec. 3.4) with the Schur maps of Sec. 2.4 (Eq. SchurC1) and
+ * the father system of Sec. 3.3 (Eq. block_equation4): at each leaf the interior
+ * is eliminated; at each father the sons' boundary Schur complements are added
+ * into the union of their boundaries, and the interface gamma is eliminated by a
+ * partial Cholesky (L_gg L_gg^T = K_gg, L_Bg = K_Bg L_gg^-T,
+ * S = K_BB - L_Bg L_Bg^T, right-hand side bordered as one more row).  The
+ * factors (which represent Phi_omega) stay in the workspace. */
+hdd_status hdd_upsweep(hdd_plan_t plan, int32_t batch, void* workspace, void* stream);
+
+/* Pruned "Root to Leaves" (Sec. 3.4, Sec. 5.3): from the root down the nodes on
+ * the paths to the observation vertices, u_gamma = L_gg^-T (y_g - L_Bg^T u_B);
+ * then u at the observation vertices.  Mixed precision adds FP64-residual
+ * iterative refinement (full descents).  u_obs: device, [batch x n_obs] FP64. */
+hdd_status hdd_point_solve(hdd_plan_t plan, int32_t batch, void* workspace, double* u_obs,
+                           void* stream);
+
+/* Likelihood of Sec. 1.2 with i.i.d. N(0, sigma^2) noise:
+ * loglik[s] = -1/2 sum_k (y_k - u_k)^2 / sigma^2 - (n_obs/2) log(2 pi sigma^2).
+ * u_obs: device [batch x n_obs] from hdd_point_solve.  y: device, [n_obs]
+ * (y_per_sample = 0) or [batch x n_obs] (y_per_sample = 1).  loglik: device
+ * [batch] FP64.  sample_status: device [batch] int32 or NULL; 0 = ok, otherwise
+ * (-code) | (node << 8) with code a negative hdd_status (HDD_ENOTSPD, HDD_ENOCONV)
+ * and node the first failing tree node.  A failed sample gets
+ * loglik = -inf. */
+hdd_status hdd_loglik(hdd_plan_t plan, int32_t batch, void* workspace, const double* u_obs,
+                      const double* y, int32_t y_per_sample, double* loglik,
+                      int32_t* sample_status, void* stream);
+
+/* End to end with HOST buffers: copies Z (host [batch x n_z]) and y (host) to the
+ * workspace, runs assemble, upsweep, point solve and loglik on `stream`, copies
+ * loglik (host [batch]), u_obs (host [batch x n_obs], may be NULL) and
+ * sample_status (host [batch], may be NULL) back, and waits for the stream.
+ * Blocking. */
+hdd_status hdd_evaluate_host(hdd_plan_t plan, int32_t batch, void* workspace,
+                             const double* Z, const double* y, int32_t y_per_sample,
+                             double* loglik, double* u_obs, int32_t* sample_status,
+                             void* stream);
+
+/* Plan queries (work on host-only plans too). */
+hdd_status hdd_plan_info(hdd_plan_t plan, hdd_plan_info_t* info);
+hdd_status hdd_node_info(hdd_plan_t plan, int32_t node, hdd_node_info_t* info);
+/* gamma: [m] and bnd: [b] vertex ids in the order the fronts use (either may be NULL). */
+hdd_status hdd_node_indices(hdd_plan_t plan, int32_t node, int32_t* gamma, int32_t* bnd);
+
+/* Static text for a status code; thread-local text of the last CUDA error. */
+const char* hdd_status_string(hdd_status status);
+const char* hdd_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HDD_H */

@@ -1,0 +1,393 @@
+// C ABI of libhdd.so: plan management, workspace layout and the per-call launch
+// schedule of the HDD likelihood path.  No exceptions cross this boundary.
+#include <cuda_runtime.h>
+
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "launch.h"
+#include "plan.h"
+
+struct hdd_plan_s {
+  hdd::Plan p;
+};
+
+namespace hdd {
+cudaError_t configure_front_kernels();
+cudaError_t configure_solve_kernels();
+}  // namespace hdd
+
+namespace {
+
+thread_local std::string g_err;
+
+hdd_status fail_cuda(cudaError_t e, const char* where) {
+  g_err = std::string(where) + ": " + cudaGetErrorString(e);
+  return HDD_ECUDA;
+}
+
+hdd_status fail_inval(const std::string& msg) {
+  g_err = msg;
+  return HDD_EINVAL;
+}
+
+// Makes the plan's device current for the duration of a call.
+struct DeviceScope {
+  int prev = -1;
+  cudaError_t err = cudaSuccess;
+  explicit DeviceScope(int dev) {
+    err = cudaGetDevice(&prev);
+    if (err == cudaSuccess && prev != dev) err = cudaSetDevice(dev);
+  }
+  ~DeviceScope() {
+    int cur = -1;
+    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+std::mutex g_cfg_mutex;
+bool g_configured[64] = {};
+
+cudaError_t configure_device(int dev) {
+  std::lock_guard<std::mutex> lk(g_cfg_mutex);
+  if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+  if (g_configured[dev]) return cudaSuccess;
+  cudaError_t e = hdd::configure_front_kernels();
+  if (e == cudaSuccess) e = hdd::configure_solve_kernels();
+  if (e == cudaSuccess) g_configured[dev] = true;
+  return e;
+}
+
+void free_device(hdd::Plan& p) {
+  cudaFree(p.d_phi);
+  cudaFree(p.d_nodes);
+  cudaFree(p.d_maps);
+  cudaFree(p.d_lists);
+  cudaFree(p.d_obs);
+  p.d_phi = nullptr; p.d_nodes = nullptr; p.d_maps = nullptr; p.d_lists = nullptr; p.d_obs = nullptr;
+}
+
+template <typename T>
+cudaError_t upload(T** dst, const T* src, size_t n) {
+  cudaError_t e = cudaMalloc((void**)dst, (n ? n : 1) * sizeof(T));
+  if (e != cudaSuccess) return e;
+  if (n) e = cudaMemcpy(*dst, src, n * sizeof(T), cudaMemcpyHostToDevice);
+  return e;
+}
+
+hdd::Arenas arenas(const hdd::Plan& p, const hdd::Layout& L, void* ws) {
+  char* w = static_cast<char*>(ws);
+  hdd::Arenas A;
+  A.f64 = reinterpret_cast<double*>(w + L.f64);
+  A.f64_stride = p.f64_stride;
+  A.f32 = reinterpret_cast<float*>(w + L.f32);
+  A.f32_stride = p.f32_stride;
+  A.s64 = reinterpret_cast<double*>(w + L.s64);
+  A.s64_stride = p.s64_stride;
+  A.s32 = reinterpret_cast<float*>(w + L.s32);
+  A.s32_stride = p.s32_stride;
+  return A;
+}
+
+hdd_status check_call(hdd_plan_t plan, int32_t batch, void* ws) {
+  if (!plan) return fail_inval("plan is NULL");
+  if (plan->p.device < 0) {
+    g_err = "host-only plan";
+    return HDD_ESTATE;
+  }
+  if (batch < 1 || batch > 65535) return fail_inval("batch must be in 1..65535");
+  if (!ws) return fail_inval("workspace is NULL");
+  if (reinterpret_cast<uintptr_t>(ws) % 256 != 0) return fail_inval("workspace must be 256-byte aligned");
+  return HDD_OK;
+}
+
+// One pass of "Leaves to Root" over all heights with the given right-hand side.
+cudaError_t run_upsweep(const hdd::Plan& p, int batch, void* ws, const hdd::Rhs& rhs, cudaStream_t st) {
+  const hdd::Layout L = hdd::layout(p, batch);
+  char* w = static_cast<char*>(ws);
+  hdd::StepArgs a{};
+  a.nodes = p.d_nodes;
+  a.maps = p.d_maps;
+  a.batch = batch;
+  a.N = p.N;
+  a.kappa = reinterpret_cast<const double*>(w + L.kappa);
+  a.kap_stride = p.n_t;
+  a.rhs = rhs;
+  a.arenas = arenas(p, L, ws);
+  a.status = reinterpret_cast<int32_t*>(w + L.status);
+  for (int h = 0; h <= p.height; ++h) {
+    for (int kind = 0; kind < 4; ++kind) {
+      const hdd::ListInfo& li = p.lists[p.step_lists[h][kind]];
+      if (li.n == 0) continue;
+      a.list = p.d_lists + li.off;
+      a.nlist = li.n;
+      a.max_nf = li.max_nf;
+      a.max_m = li.max_m;
+      a.max_b = li.max_b;
+      cudaError_t e;
+      switch (kind) {
+        case 0: e = hdd::launch_front_small<double>(a, st); break;
+        case 1: e = hdd::launch_front_large<double>(a, st); break;
+        case 2: e = hdd::launch_front_small<float>(a, st); break;
+        default: e = hdd::launch_front_large<float>(a, st); break;
+      }
+      if (e != cudaSuccess) return e;
+    }
+  }
+  return cudaSuccess;
+}
+
+// "Root to Leaves" over the given per-depth lists, writing u (FP64).
+cudaError_t run_descent(const hdd::Plan& p, int batch, void* ws, const std::vector<int>& per_depth, double* u,
+                        cudaStream_t st) {
+  const hdd::Layout L = hdd::layout(p, batch);
+  const hdd::Arenas A = arenas(p, L, ws);
+  const int64_t NN = (int64_t)p.N * p.N;
+  for (int d = 0; d <= p.depth; ++d) {
+    const hdd::ListInfo& li = p.lists[per_depth[d]];
+    if (li.n == 0) continue;
+    // the lists hold one precision per depth in the plans built here
+    const bool fp64 = p.nodes[p.list_data[li.off]].fp64;
+    cudaError_t e = fp64 ? hdd::launch_descent<double>(p.d_nodes, p.d_maps, p.d_lists + li.off, li.n, batch, A, u,
+                                                       NN, li.max_b, li.max_m, st)
+                         : hdd::launch_descent<float>(p.d_nodes, p.d_maps, p.d_lists + li.off, li.n, batch, A, u,
+                                                      NN, li.max_b, li.max_m, st);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* hdd_status_string(hdd_status s) {
+  switch (s) {
+    case HDD_OK: return "ok";
+    case HDD_EINVAL: return "invalid argument";
+    case HDD_ENOMEM: return "out of memory";
+    case HDD_ECUDA: return "CUDA error";
+    case HDD_ENOTSPD: return "Schur block not positive definite";
+    case HDD_ENOCONV: return "iterative refinement did not converge";
+    case HDD_ETIMEOUT: return "device wait timed out";
+    case HDD_ESTATE: return "operation needs a device plan";
+  }
+  return "unknown status";
+}
+
+const char* hdd_last_error(void) { return g_err.c_str(); }
+
+hdd_status hdd_plan(const hdd_plan_desc* desc, hdd_plan_t* out) {
+  if (!desc || !out) return fail_inval("NULL argument");
+  *out = nullptr;
+  hdd_plan_s* h = new (std::nothrow) hdd_plan_s;
+  if (!h) return HDD_ENOMEM;
+  std::string err;
+  try {
+    err = hdd::build_plan(*desc, h->p);
+  } catch (const std::bad_alloc&) {
+    delete h;
+    g_err = "host allocation failed";
+    return HDD_ENOMEM;
+  } catch (...) {
+    delete h;
+    g_err = "plan construction failed";
+    return HDD_EINVAL;
+  }
+  if (!err.empty()) {
+    delete h;
+    return fail_inval(err);
+  }
+  hdd::Plan& p = h->p;
+  if (p.device >= 0) {
+    if (!desc->kl_basis) {
+      delete h;
+      return fail_inval("kl_basis is NULL");
+    }
+    DeviceScope ds(p.device);
+    if (ds.err != cudaSuccess) {
+      delete h;
+      return fail_cuda(ds.err, "cudaSetDevice");
+    }
+    cudaError_t e = configure_device(p.device);
+    if (e == cudaSuccess) e = upload(&p.d_phi, desc->kl_basis, (size_t)p.n_t * p.n_z);
+    if (e == cudaSuccess) e = upload(&p.d_nodes, p.dev_nodes.data(), p.dev_nodes.size());
+    if (e == cudaSuccess) e = upload(&p.d_maps, p.maps.data(), p.maps.size());
+    if (e == cudaSuccess) e = upload(&p.d_lists, p.list_data.data(), p.list_data.size());
+    if (e == cudaSuccess) e = upload(&p.d_obs, p.obs.data(), p.obs.size());
+    if (e != cudaSuccess) {
+      free_device(p);
+      delete h;
+      return e == cudaErrorMemoryAllocation ? (g_err = "device allocation failed", HDD_ENOMEM)
+                                            : fail_cuda(e, "hdd_plan upload");
+    }
+  }
+  *out = h;
+  return HDD_OK;
+}
+
+hdd_status hdd_plan_destroy(hdd_plan_t plan) {
+  if (!plan) return HDD_OK;
+  if (plan->p.device >= 0) {
+    DeviceScope ds(plan->p.device);
+    free_device(plan->p);
+  }
+  delete plan;
+  return HDD_OK;
+}
+
+hdd_status hdd_workspace_size(hdd_plan_t plan, int32_t batch, size_t* bytes) {
+  if (!plan || !bytes) return fail_inval("NULL argument");
+  if (batch < 1 || batch > 65535) return fail_inval("batch must be in 1..65535");
+  *bytes = hdd::layout(plan->p, batch).total;
+  return HDD_OK;
+}
+
+hdd_status hdd_assemble(hdd_plan_t plan, const double* Z, int32_t batch, void* workspace, void* stream) {
+  hdd_status s = check_call(plan, batch, workspace);
+  if (s != HDD_OK) return s;
+  if (!Z) return fail_inval("Z is NULL");
+  const hdd::Plan& p = plan->p;
+  DeviceScope ds(p.device);
+  if (ds.err != cudaSuccess) return fail_cuda(ds.err, "cudaSetDevice");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const hdd::Layout L = hdd::layout(p, batch);
+  char* w = static_cast<char*>(workspace);
+  cudaError_t e = cudaMemsetAsync(w + L.status, 0, (size_t)batch * 4, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(w + L.conv, 0, (size_t)batch * 4, st);
+  if (e == cudaSuccess)
+    e = hdd::launch_kappa(p.d_phi, Z, p.n_t, p.n_z, batch, reinterpret_cast<double*>(w + L.kappa), p.n_t, st);
+  return e == cudaSuccess ? HDD_OK : fail_cuda(e, "hdd_assemble");
+}
+
+hdd_status hdd_upsweep(hdd_plan_t plan, int32_t batch, void* workspace, void* stream) {
+  hdd_status s = check_call(plan, batch, workspace);
+  if (s != HDD_OK) return s;
+  const hdd::Plan& p = plan->p;
+  DeviceScope ds(p.device);
+  if (ds.err != cudaSuccess) return fail_cuda(ds.err, "cudaSetDevice");
+  hdd::Rhs rhs{nullptr, 0, p.h * p.h * p.f};
+  cudaError_t e = run_upsweep(p, batch, workspace, rhs, static_cast<cudaStream_t>(stream));
+  return e == cudaSuccess ? HDD_OK : fail_cuda(e, "hdd_upsweep");
+}
+
+hdd_status hdd_point_solve(hdd_plan_t plan, int32_t batch, void* workspace, double* u_obs, void* stream) {
+  hdd_status s = check_call(plan, batch, workspace);
+  if (s != HDD_OK) return s;
+  if (!u_obs) return fail_inval("u_obs is NULL");
+  const hdd::Plan& p = plan->p;
+  DeviceScope ds(p.device);
+  if (ds.err != cudaSuccess) return fail_cuda(ds.err, "cudaSetDevice");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const hdd::Layout L = hdd::layout(p, batch);
+  char* w = static_cast<char*>(workspace);
+  double* u = reinterpret_cast<double*>(w + L.u);
+  const int64_t NN = (int64_t)p.N * p.N;
+  cudaError_t e = run_descent(p, batch, workspace, p.down_vis_lists, u, st);
+  if (e == cudaSuccess) e = hdd::launch_gather_obs(u, NN, p.d_obs, p.n_obs, batch, u_obs, st);
+  return e == cudaSuccess ? HDD_OK : fail_cuda(e, "hdd_point_solve");
+}
+
+hdd_status hdd_loglik(hdd_plan_t plan, int32_t batch, void* workspace, const double* u_obs, const double* y,
+                      int32_t y_per_sample, double* loglik, int32_t* sample_status, void* stream) {
+  hdd_status s = check_call(plan, batch, workspace);
+  if (s != HDD_OK) return s;
+  if (!u_obs || !y || !loglik) return fail_inval("NULL argument");
+  const hdd::Plan& p = plan->p;
+  DeviceScope ds(p.device);
+  if (ds.err != cudaSuccess) return fail_cuda(ds.err, "cudaSetDevice");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const hdd::Layout L = hdd::layout(p, batch);
+  char* w = static_cast<char*>(workspace);
+  const int32_t* status = reinterpret_cast<const int32_t*>(w + L.status);
+  cudaError_t e = hdd::launch_loglik(u_obs, p.n_obs, batch, y, y_per_sample ? 1 : 0, p.sigma, status, loglik, st);
+  if (e == cudaSuccess && sample_status)
+    e = cudaMemcpyAsync(sample_status, status, (size_t)batch * 4, cudaMemcpyDeviceToDevice, st);
+  return e == cudaSuccess ? HDD_OK : fail_cuda(e, "hdd_loglik");
+}
+
+hdd_status hdd_evaluate_host(hdd_plan_t plan, int32_t batch, void* workspace, const double* Z, const double* y,
+                             int32_t y_per_sample, double* loglik, double* u_obs, int32_t* sample_status,
+                             void* stream) {
+  hdd_status s = check_call(plan, batch, workspace);
+  if (s != HDD_OK) return s;
+  if (!Z || !y || !loglik) return fail_inval("NULL argument");
+  const hdd::Plan& p = plan->p;
+  DeviceScope ds(p.device);
+  if (ds.err != cudaSuccess) return fail_cuda(ds.err, "cudaSetDevice");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const hdd::Layout L = hdd::layout(p, batch);
+  char* w = static_cast<char*>(workspace);
+  double* dZ = reinterpret_cast<double*>(w + L.z);
+  double* dy = reinterpret_cast<double*>(w + L.y);
+  double* duobs = reinterpret_cast<double*>(w + L.uobs);
+  double* dll = reinterpret_cast<double*>(w + L.ll);
+  const size_t ny = (size_t)p.n_obs * (y_per_sample ? batch : 1);
+  cudaError_t e = cudaMemcpyAsync(dZ, Z, (size_t)batch * p.n_z * 8, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(dy, y, ny * 8, cudaMemcpyHostToDevice, st);
+  if (e != cudaSuccess) return fail_cuda(e, "hdd_evaluate_host copy in");
+  if ((s = hdd_assemble(plan, dZ, batch, workspace, stream)) != HDD_OK) return s;
+  if ((s = hdd_upsweep(plan, batch, workspace, stream)) != HDD_OK) return s;
+  if ((s = hdd_point_solve(plan, batch, workspace, duobs, stream)) != HDD_OK) return s;
+  if ((s = hdd_loglik(plan, batch, workspace, duobs, dy, y_per_sample, dll, nullptr, stream)) != HDD_OK) return s;
+  e = cudaMemcpyAsync(loglik, dll, (size_t)batch * 8, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess && u_obs)
+    e = cudaMemcpyAsync(u_obs, duobs, (size_t)batch * p.n_obs * 8, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess && sample_status)
+    e = cudaMemcpyAsync(sample_status, w + L.status, (size_t)batch * 4, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  return e == cudaSuccess ? HDD_OK : fail_cuda(e, "hdd_evaluate_host");
+}
+
+hdd_status hdd_plan_info(hdd_plan_t plan, hdd_plan_info_t* info) {
+  if (!plan || !info) return fail_inval("NULL argument");
+  const hdd::Plan& p = plan->p;
+  info->n_nodes = (int32_t)p.nodes.size();
+  info->n_leaves = p.n_leaves;
+  info->depth = p.depth;
+  info->height = p.height;
+  info->n_visited = p.n_visited;
+  info->max_front = p.max_front;
+  info->flops_upsweep = p.flops_up;
+  info->flops_point_solve = p.flops_down;
+  info->factor_bytes = (double)p.f64_stride * 8 + (double)p.f32_stride * 4;
+  info->schur_bytes = (double)p.s64_stride * 8 + (double)p.s32_stride * 4;
+  int up = 0, down = 0;
+  for (int h = 0; h <= p.height; ++h)
+    for (int kind = 0; kind < 4; ++kind) {
+      const hdd::ListInfo& li = p.lists[p.step_lists[h][kind]];
+      if (li.n) up += (kind == 1 || kind == 3) ? 4 : 1;
+    }
+  for (int d = 0; d <= p.depth; ++d) down += p.lists[p.down_vis_lists[d]].n > 0;
+  info->launches_upsweep = up;
+  info->launches_evaluate = 1 + up + down + 2;
+  return HDD_OK;
+}
+
+hdd_status hdd_node_info(hdd_plan_t plan, int32_t node, hdd_node_info_t* info) {
+  if (!plan || !info) return fail_inval("NULL argument");
+  const hdd::Plan& p = plan->p;
+  if (node < 0 || node >= (int32_t)p.nodes.size()) return fail_inval("node out of range");
+  const hdd::Node& nd = p.nodes[node];
+  info->x0 = nd.x0; info->x1 = nd.x1; info->y0 = nd.y0; info->y1 = nd.y1;
+  info->parent = nd.parent; info->child0 = nd.child[0]; info->child1 = nd.child[1];
+  info->depth = nd.depth; info->height = nd.height;
+  info->m = nd.m; info->b = nd.b;
+  info->visited = nd.visited ? 1 : 0;
+  return HDD_OK;
+}
+
+hdd_status hdd_node_indices(hdd_plan_t plan, int32_t node, int32_t* gamma, int32_t* bnd) {
+  if (!plan) return fail_inval("NULL argument");
+  const hdd::Plan& p = plan->p;
+  if (node < 0 || node >= (int32_t)p.nodes.size()) return fail_inval("node out of range");
+  const hdd::Node& nd = p.nodes[node];
+  if (gamma) std::memcpy(gamma, nd.gamma.data(), nd.gamma.size() * 4);
+  if (bnd) std::memcpy(bnd, nd.bnd.data(), nd.bnd.size() * 4);
+  return HDD_OK;
+}
+
+}  // extern "C"

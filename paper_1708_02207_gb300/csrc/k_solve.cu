@@ -1,0 +1,189 @@
+// Assembly of kappa, the pruned descent and the misfit.
+#include "launch.h"
+
+namespace hdd {
+
+// ---------------------------------------------------------------------------
+// Assembly (Sec. 3.1; notation table: kappa = e^q): q[s,t] = sum_k Phi[t,k] Z[s,k]
+// accumulated in k order, kappa = exp(q), FP64.  CTA = 128 triangles x 8 samples;
+// Phi and Z chunks staged in shared memory, Phi read once per 8 samples.
+constexpr int kKapT = 128, kKapS = 8, kKapK = 32;
+
+__global__ void k_kappa(const double* __restrict__ phi, const double* __restrict__ Z, int n_t, int n_z, int batch,
+                        double* __restrict__ kappa, int64_t kap_stride) {
+  __shared__ double ph[kKapK][kKapT + 1];
+  __shared__ double zs[kKapS][kKapK];
+  const int t0 = blockIdx.x * kKapT, s0 = blockIdx.y * kKapS;
+  const int t = t0 + threadIdx.x;
+  double acc[kKapS];
+#pragma unroll
+  for (int q = 0; q < kKapS; ++q) acc[q] = 0.0;
+  for (int k0 = 0; k0 < n_z; k0 += kKapK) {
+    const int kc = min(kKapK, n_z - k0);
+    __syncthreads();
+    for (int e = threadIdx.x; e < kKapT * kc; e += blockDim.x) {
+      const int tt = e / kc, kk = e - tt * kc;
+      ph[kk][tt] = (t0 + tt < n_t) ? phi[(int64_t)(t0 + tt) * n_z + k0 + kk] : 0.0;
+    }
+    for (int e = threadIdx.x; e < kKapS * kc; e += blockDim.x) {
+      const int ss = e / kc, kk = e - ss * kc;
+      zs[ss][kk] = (s0 + ss < batch) ? Z[(int64_t)(s0 + ss) * n_z + k0 + kk] : 0.0;
+    }
+    __syncthreads();
+    for (int kk = 0; kk < kc; ++kk) {
+      const double p = ph[kk][threadIdx.x];
+#pragma unroll
+      for (int q = 0; q < kKapS; ++q) acc[q] = fma(p, zs[q][kk], acc[q]);
+    }
+  }
+  if (t < n_t) {
+#pragma unroll
+    for (int q = 0; q < kKapS; ++q)
+      if (s0 + q < batch) kappa[(int64_t)(s0 + q) * kap_stride + t] = exp(acc[q]);
+  }
+}
+
+cudaError_t launch_kappa(const double* phi, const double* Z, int n_t, int n_z, int batch, double* kappa,
+                         int64_t kap_stride, cudaStream_t st) {
+  dim3 grid((n_t + kKapT - 1) / kKapT, (batch + kKapS - 1) / kKapS);
+  k_kappa<<<grid, kKapT, 0, st>>>(phi, Z, n_t, n_z, batch, kappa, kap_stride);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// "Root to Leaves" at one node (Sec. 3.4; Eq. SchurC1 second line,
+// u_2 = A22^-1 F2 c - A22^-1 A21 u_1): with the stored partial Cholesky factors
+//   t = y_g - L_Bg^T u_B,   L_gg^T u_g = t.
+// One CTA per (node, sample).  t by one warp per column (coalesced down the
+// column of F); the back substitution in 32-column blocks from the end: one
+// warp solves the 32 x 32 diagonal block with shuffles, then all warps fold the
+// block into t of the columns to its left.
+template <typename T>
+__device__ __forceinline__ const T* fac_ptr(const Arenas& A, const NodeDev& nd, int s);
+template <> __device__ __forceinline__ const double* fac_ptr<double>(const Arenas& A, const NodeDev& nd, int s) {
+  return A.f64 + (int64_t)s * A.f64_stride + nd.f_off;
+}
+template <> __device__ __forceinline__ const float* fac_ptr<float>(const Arenas& A, const NodeDev& nd, int s) {
+  return A.f32 + (int64_t)s * A.f32_stride + nd.f_off;
+}
+
+template <typename T>
+__global__ void k_descent(const NodeDev* __restrict__ nodes, const int32_t* __restrict__ maps,
+                          const int32_t* __restrict__ list, Arenas A, double* __restrict__ u, int64_t u_stride) {
+  const int node = list[blockIdx.x];
+  const int s = blockIdx.y;
+  const NodeDev nd = nodes[node];
+  const int m = nd.m, b = nd.b, nf = nd.nf;
+  const T* F = fac_ptr<T>(A, nd, s);
+  const int32_t* vid = maps + nd.map_off;
+  double* us = u + (int64_t)s * u_stride;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* uB = reinterpret_cast<T*>(smem_raw);   // [b]
+  T* t = uB + b;                            // [m]
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarp = blockDim.x >> 5;
+  for (int i = threadIdx.x; i < b; i += blockDim.x) uB[i] = (T)us[vid[m + i]];
+  __syncthreads();
+  for (int c = warp; c < m; c += nwarp) {
+    const T* col = F + (int64_t)c * nf;
+    T acc = (T)0;
+    for (int i = lane; i < b; i += 32) acc += col[m + i] * uB[i];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) t[c] = col[nf - 1] - acc;
+  }
+  for (int cb = ((m - 1) / 32) * 32; cb >= 0; cb -= 32) {
+    const int jb = min(32, m - cb);
+    __syncthreads();
+    if (warp == 0) {
+      T x = (lane < jb) ? t[cb + lane] : (T)0;
+      for (int r = jb - 1; r >= 0; --r) {
+        T ur = __shfl_sync(0xffffffffu, x, r);
+        ur = ur / F[(int64_t)(cb + r) * nf + cb + r];
+        if (lane == r) x = ur;
+        if (lane < r) x -= F[(int64_t)(cb + lane) * nf + cb + r] * ur;
+      }
+      if (lane < jb) t[cb + lane] = x;    // now u_g
+    }
+    __syncthreads();
+    for (int c = warp; c < cb; c += nwarp) {
+      const T* col = F + (int64_t)c * nf + cb;
+      T acc = (lane < jb) ? col[lane] * t[cb + lane] : (T)0;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+      if (lane == 0) t[c] -= acc;
+    }
+  }
+  __syncthreads();
+  for (int c = threadIdx.x; c < m; c += blockDim.x) us[vid[c]] = (double)t[c];
+}
+
+template <typename T>
+cudaError_t launch_descent(const NodeDev* nodes, const int32_t* maps, const int32_t* list, int nlist, int batch,
+                           const Arenas& A, double* u, int64_t u_stride, int max_b, int max_m, cudaStream_t st) {
+  if (nlist == 0) return cudaSuccess;
+  const size_t smem = (size_t)(max_b + max_m) * sizeof(T);
+  k_descent<T><<<dim3(nlist, batch), 256, smem, st>>>(nodes, maps, list, A, u, u_stride);
+  return cudaGetLastError();
+}
+template cudaError_t launch_descent<double>(const NodeDev*, const int32_t*, const int32_t*, int, int, const Arenas&,
+                                            double*, int64_t, int, int, cudaStream_t);
+template cudaError_t launch_descent<float>(const NodeDev*, const int32_t*, const int32_t*, int, int, const Arenas&,
+                                           double*, int64_t, int, int, cudaStream_t);
+
+// ---------------------------------------------------------------------------
+__global__ void k_gather_obs(const double* __restrict__ u, int64_t u_stride, const int32_t* __restrict__ obs,
+                             int n_obs, double* __restrict__ u_obs) {
+  const int s = blockIdx.y;
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k < n_obs) u_obs[(int64_t)s * n_obs + k] = u[(int64_t)s * u_stride + obs[k]];
+}
+
+cudaError_t launch_gather_obs(const double* u, int64_t u_stride, const int32_t* obs, int n_obs, int batch,
+                              double* u_obs, cudaStream_t st) {
+  k_gather_obs<<<dim3((n_obs + 255) / 256, batch), 256, 0, st>>>(u, u_stride, obs, n_obs, u_obs);
+  return cudaGetLastError();
+}
+
+// Likelihood of Sec. 1.2 with Gaussian noise: one CTA per sample, fixed-order
+// reduction (each thread strides over k, then a shared-memory tree).
+__global__ void k_loglik(const double* __restrict__ u_obs, int n_obs, const double* __restrict__ y,
+                         int y_per_sample, double sigma, const int32_t* __restrict__ status,
+                         double* __restrict__ loglik) {
+  __shared__ double red[256];
+  const int s = blockIdx.x;
+  const double* us = u_obs + (int64_t)s * n_obs;
+  const double* ys = y + (y_per_sample ? (int64_t)s * n_obs : 0);
+  double acc = 0.0;
+  for (int k = threadIdx.x; k < n_obs; k += blockDim.x) {
+    const double r = ys[k] - us[k];
+    acc = fma(r, r, acc);
+  }
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    const double pi = 3.141592653589793238462643383279502884;
+    double ll = -0.5 * red[0] / (sigma * sigma) - 0.5 * n_obs * log(2.0 * pi * sigma * sigma);
+    if (status && status[s] != 0) ll = -INFINITY;
+    loglik[s] = ll;
+  }
+}
+
+cudaError_t launch_loglik(const double* u_obs, int n_obs, int batch, const double* y, int y_per_sample, double sigma,
+                          const int32_t* status, double* loglik, cudaStream_t st) {
+  k_loglik<<<batch, 256, 0, st>>>(u_obs, n_obs, y, y_per_sample, sigma, status, loglik);
+  return cudaGetLastError();
+}
+
+cudaError_t configure_solve_kernels() {
+  const int lim = 227 * 1024;
+  cudaError_t e;
+  if ((e = cudaFuncSetAttribute(k_descent<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
+  if ((e = cudaFuncSetAttribute(k_descent<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
+  return cudaSuccess;
+}
+
+}  // namespace hdd

@@ -1,0 +1,45 @@
+// Host-side launchers of the HDD kernels (one translation unit per kernel family).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "common.cuh"
+
+namespace hdd {
+
+struct StepArgs {
+  const NodeDev* nodes;
+  const int32_t* maps;
+  const int32_t* list;     // device node indices
+  int nlist;
+  int batch;
+  int N;
+  const double* kappa;     // [batch x n_t]
+  int64_t kap_stride;
+  Rhs rhs;
+  Arenas arenas;
+  int32_t* status;
+  int max_nf, max_m, max_b;
+};
+
+// assembly: kappa = exp(Phi Z) (Sec. 3.1; kappa = e^q)
+cudaError_t launch_kappa(const double* phi, const double* Z, int n_t, int n_z, int batch, double* kappa,
+                         int64_t kap_stride, cudaStream_t st);
+
+// fronts that fit in shared memory: build + partial Cholesky + store, one CTA each
+template <typename T> cudaError_t launch_front_small(const StepArgs& a, cudaStream_t st);
+// large fronts: fill in global memory, then POTRF of gamma, TRSM of the rest, SYRK into S
+template <typename T> cudaError_t launch_front_large(const StepArgs& a, cudaStream_t st);
+
+// descent (Root to Leaves) over a list of nodes of one depth; u is FP64 [batch x N^2]
+template <typename T>
+cudaError_t launch_descent(const NodeDev* nodes, const int32_t* maps, const int32_t* list, int nlist, int batch,
+                           const Arenas& A, double* u, int64_t u_stride, int max_b, int max_m, cudaStream_t st);
+
+cudaError_t launch_gather_obs(const double* u, int64_t u_stride, const int32_t* obs, int n_obs, int batch,
+                              double* u_obs, cudaStream_t st);
+cudaError_t launch_loglik(const double* u_obs, int n_obs, int batch, const double* y, int y_per_sample, double sigma,
+                          const int32_t* status, double* loglik, cudaStream_t st);
+
+}  // namespace hdd

@@ -1,0 +1,326 @@
+// Host construction of the HDD plan: decomposition tree (Sec. 2.1), index sets
+// I(gamma), I(d omega) (Sec. 2.1), extend-add maps of the father system
+// (Sec. 3.3, Eq. block_equation4), the pruned descent set (Sec. 5.3), the
+// per-height launch schedule and the lifetime-packed Schur arena.
+#include <algorithm>
+#include <cmath>
+#include <map>
+#include <numeric>
+
+#include "plan.h"
+
+namespace hdd {
+
+namespace {
+
+bool unknown(int N, int i, int j) { return i >= 1 && j >= 1 && i <= N - 2 && j <= N - 2; }
+
+// Binary tree: split the longer side at the cell-aligned midpoint (x on ties),
+// stop when both sides are at most `leaf` cells.
+void build_tree(Plan& p) {
+  const int N = p.N;
+  p.nodes.clear();
+  Node root;
+  root.x0 = 0; root.x1 = N - 1; root.y0 = 0; root.y1 = N - 1;
+  p.nodes.push_back(root);
+  std::vector<int> stack{0};
+  while (!stack.empty()) {
+    int k = stack.back();
+    stack.pop_back();
+    Node nd = p.nodes[k];
+    int w = nd.x1 - nd.x0, hgt = nd.y1 - nd.y0;
+    if (w <= p.leaf && hgt <= p.leaf) continue;
+    Node a = nd, b = nd;
+    a.depth = b.depth = nd.depth + 1;
+    a.parent = b.parent = k;
+    a.gamma.clear(); b.gamma.clear();
+    a.child[0] = a.child[1] = b.child[0] = b.child[1] = -1;
+    a.split = b.split = 0;
+    if (w >= hgt) {
+      int xm = nd.x0 + w / 2;
+      a.x1 = xm; b.x0 = xm;
+      p.nodes[k].split = 'x'; p.nodes[k].cut = xm;
+    } else {
+      int ym = nd.y0 + hgt / 2;
+      a.y1 = ym; b.y0 = ym;
+      p.nodes[k].split = 'y'; p.nodes[k].cut = ym;
+    }
+    int base = (int)p.nodes.size();
+    p.nodes.push_back(a);
+    p.nodes.push_back(b);
+    p.nodes[k].child[0] = base;
+    p.nodes[k].child[1] = base + 1;
+    stack.push_back(base + 1);
+    stack.push_back(base);
+  }
+  // index sets
+  for (Node& nd : p.nodes) {
+    nd.bnd.clear();
+    nd.gamma.clear();
+    for (int j = nd.y0; j <= nd.y1; ++j)
+      for (int i = nd.x0; i <= nd.x1; ++i) {
+        bool edge = (i == nd.x0 || i == nd.x1 || j == nd.y0 || j == nd.y1);
+        if (edge && unknown(N, i, j)) nd.bnd.push_back(j * N + i);
+      }
+    if (nd.leaf()) {
+      for (int j = nd.y0 + 1; j < nd.y1; ++j)
+        for (int i = nd.x0 + 1; i < nd.x1; ++i) nd.gamma.push_back(j * N + i);
+    } else if (nd.split == 'x') {
+      for (int j = nd.y0 + 1; j < nd.y1; ++j) nd.gamma.push_back(j * N + nd.cut);
+    } else {
+      for (int i = nd.x0 + 1; i < nd.x1; ++i) nd.gamma.push_back(nd.cut * N + i);
+    }
+    nd.m = (int)nd.gamma.size();
+    nd.b = (int)nd.bnd.size();
+    nd.nf = nd.m + nd.b + 1;
+  }
+  // heights (children have larger indices than their parent)
+  for (int k = (int)p.nodes.size() - 1; k >= 0; --k) {
+    Node& nd = p.nodes[k];
+    nd.height = nd.leaf() ? 0 : 1 + std::max(p.nodes[nd.child[0]].height, p.nodes[nd.child[1]].height);
+  }
+}
+
+}  // namespace
+
+std::string build_plan(const hdd_plan_desc& d, Plan& p) {
+  if (d.N < 3) return "N must be >= 3";
+  if (d.N > 8193) return "N must be <= 8193";
+  if (d.leaf < 1) return "leaf must be >= 1";
+  if (d.n_z < 1 || d.n_z > 256) return "n_z must be in 1..256";
+  if (d.n_obs < 1) return "n_obs must be >= 1";
+  if (!d.obs_vertex) return "obs_vertex is NULL";
+  if (!(d.sigma > 0.0)) return "sigma must be > 0";
+  if (d.precision != HDD_FP64 && d.precision != HDD_MIXED_FP32) return "unknown precision";
+  if (d.ir_max_iter < 0 || d.ir_max_iter > 64) return "ir_max_iter must be in 0..64";
+  p.N = d.N; p.leaf = d.leaf; p.n_z = d.n_z; p.n_obs = d.n_obs;
+  p.n_t = 2 * (d.N - 1) * (d.N - 1);
+  p.f = d.f; p.sigma = d.sigma; p.h = 1.0 / (d.N - 1);
+  p.precision = d.precision; p.ir_max_iter = d.ir_max_iter; p.ir_tol = d.ir_tol;
+  p.device = d.device;
+  p.obs.assign(d.obs_vertex, d.obs_vertex + d.n_obs);
+  for (int v : p.obs) {
+    if (v < 0 || v >= d.N * d.N) return "observation vertex out of range";
+    if (!unknown(d.N, v % d.N, v / d.N)) return "observation vertex on the Dirichlet boundary";
+  }
+
+  build_tree(p);
+  const int N = p.N;
+  const int nn = (int)p.nodes.size();
+
+  // owner of every unknown: each is eliminated exactly once
+  p.owner.assign((size_t)N * N, -1);
+  for (int k = 0; k < nn; ++k)
+    for (int v : p.nodes[k].gamma) {
+      if (p.owner[v] != -1) return "internal: vertex eliminated twice";
+      p.owner[v] = k;
+    }
+  for (int j = 1; j <= N - 2; ++j)
+    for (int i = 1; i <= N - 2; ++i)
+      if (p.owner[j * N + i] < 0) return "internal: vertex never eliminated";
+
+  // pruned descent: root-to-owner paths of the observations (Sec. 5.3)
+  for (int v : p.obs) {
+    int k = p.owner[v];
+    while (k >= 0 && !p.nodes[k].visited) {
+      p.nodes[k].visited = true;
+      k = p.nodes[k].parent;
+    }
+  }
+
+  // precision per node: mixed plans keep no FP64 node in this version
+  for (Node& nd : p.nodes) nd.fp64 = (p.precision == HDD_FP64);
+
+  // stats, schedule
+  p.n_leaves = 0; p.depth = 0; p.n_visited = 0; p.max_front = 0;
+  for (const Node& nd : p.nodes) {
+    p.n_leaves += nd.leaf();
+    p.depth = std::max(p.depth, nd.depth);
+    p.n_visited += nd.visited;
+    p.max_front = std::max(p.max_front, nd.nf);
+  }
+  p.height = p.nodes[0].height;
+  p.steps.assign(p.height + 1, Step{});
+  p.down_visited.assign(p.depth + 1, {});
+  p.down_all.assign(p.depth + 1, {});
+  p.max_front_small64 = p.max_front_small32 = 0;
+  p.max_nf_large = p.max_m_large = p.max_b_large = 0;
+  for (int k = 0; k < nn; ++k) {
+    Node& nd = p.nodes[k];
+    Step& st = p.steps[nd.height];
+    if (nd.fp64) {
+      if (nd.nf <= kSmallMax64) { st.small64.push_back(k); p.max_front_small64 = std::max(p.max_front_small64, nd.nf); }
+      else st.large64.push_back(k);
+    } else {
+      if (nd.nf <= kSmallMax32) { st.small32.push_back(k); p.max_front_small32 = std::max(p.max_front_small32, nd.nf); }
+      else st.large32.push_back(k);
+    }
+    bool large = nd.nf > (nd.fp64 ? kSmallMax64 : kSmallMax32);
+    if (large) {
+      p.max_nf_large = std::max(p.max_nf_large, nd.nf);
+      p.max_m_large = std::max(p.max_m_large, nd.m);
+      p.max_b_large = std::max(p.max_b_large, nd.b);
+    }
+    if (nd.m == 0) continue;   // a front with nothing to eliminate has no descent work
+    p.down_all[nd.depth].push_back(k);
+    if (nd.visited) p.down_visited[nd.depth].push_back(k);
+  }
+
+  // factor store offsets (all nodes keep their factors)
+  p.f64_stride = p.f32_stride = 0;
+  for (Node& nd : p.nodes) {
+    int64_t sz = (int64_t)nd.nf * nd.m;
+    int64_t& st = nd.fp64 ? p.f64_stride : p.f32_stride;
+    nd.f_off = st;
+    st += (sz + 31) / 32 * 32;
+  }
+
+  // Schur arena: a node's S lives from its own step to its parent's step.
+  // Group by the parent's height; first-fit packing of the groups' intervals.
+  for (int prec = 0; prec < 2; ++prec) {
+    bool want64 = prec == 0;
+    struct Region { int start, end; int64_t size, off; std::vector<int> members; };
+    std::map<int, Region> regions;   // by parent height
+    for (int k = 1; k < nn; ++k) {
+      Node& nd = p.nodes[k];
+      if (nd.fp64 != want64) continue;
+      int H = p.nodes[nd.parent].height;
+      auto it = regions.find(H);
+      if (it == regions.end()) it = regions.emplace(H, Region{nd.height, H, 0, 0, {}}).first;
+      Region& r = it->second;
+      r.start = std::min(r.start, nd.height);
+      r.members.push_back(k);
+      int64_t sz = (int64_t)(nd.b + 1) * (nd.b + 1);
+      nd.s_off = r.size;   // relative for now
+      r.size += (sz + 31) / 32 * 32;
+    }
+    std::vector<Region*> placed;
+    int64_t peak = 0;
+    for (auto& kv : regions) {
+      Region& r = kv.second;
+      std::vector<int64_t> cand{0};
+      for (Region* q : placed)
+        if (q->start <= r.end && r.start <= q->end) cand.push_back(q->off + q->size);
+      std::sort(cand.begin(), cand.end());
+      for (int64_t off : cand) {
+        bool ok = true;
+        for (Region* q : placed)
+          if (q->start <= r.end && r.start <= q->end && off < q->off + q->size && q->off < off + r.size) {
+            ok = false;
+            break;
+          }
+        if (ok) { r.off = off; break; }
+      }
+      placed.push_back(&r);
+      peak = std::max(peak, r.off + r.size);
+      for (int k : r.members) p.nodes[k].s_off += r.off;
+    }
+    (want64 ? p.s64_stride : p.s32_stride) = peak;
+  }
+
+  // maps: vid[nf-1] (gamma then boundary), pos0[nf], pos1[nf] (merge nodes)
+  p.maps.clear();
+  for (int k = 0; k < nn; ++k) {
+    Node& nd = p.nodes[k];
+    nd.map_off = (int64_t)p.maps.size();
+    std::vector<int> rows(nd.gamma);
+    rows.insert(rows.end(), nd.bnd.begin(), nd.bnd.end());
+    p.maps.insert(p.maps.end(), rows.begin(), rows.end());
+    if (!nd.leaf()) {
+      for (int c = 0; c < 2; ++c) {
+        const Node& ch = p.nodes[nd.child[c]];
+        std::map<int, int> pos;
+        for (int a = 0; a < ch.b; ++a) pos[ch.bnd[a]] = a;
+        int covered = 0;
+        for (int r = 0; r < nd.nf - 1; ++r) {
+          auto it = pos.find(rows[r]);
+          p.maps.push_back(it == pos.end() ? -1 : it->second);
+          covered += it != pos.end();
+        }
+        p.maps.push_back(ch.b);   // right-hand-side row
+        if (covered != ch.b) return "internal: son boundary not covered by the father front";
+      }
+    }
+    if (p.maps.size() > (size_t)INT32_MAX) return "map table too large";
+  }
+
+  // concatenated node lists
+  p.list_data.clear();
+  p.lists.clear();
+  auto add_list = [&](const std::vector<int>& v) {
+    ListInfo li;
+    li.off = (int64_t)p.list_data.size();
+    li.n = (int)v.size();
+    for (int k : v) {
+      p.list_data.push_back(k);
+      li.max_nf = std::max(li.max_nf, p.nodes[k].nf);
+      li.max_m = std::max(li.max_m, p.nodes[k].m);
+      li.max_b = std::max(li.max_b, p.nodes[k].b);
+    }
+    p.lists.push_back(li);
+    return (int)p.lists.size() - 1;
+  };
+  p.step_lists.assign(p.height + 1, {0, 0, 0, 0});
+  for (int hgt = 0; hgt <= p.height; ++hgt) {
+    const Step& st = p.steps[hgt];
+    p.step_lists[hgt] = {add_list(st.small64), add_list(st.large64), add_list(st.small32), add_list(st.large32)};
+  }
+  p.down_vis_lists.assign(p.depth + 1, 0);
+  p.down_all_lists.assign(p.depth + 1, 0);
+  for (int d = 0; d <= p.depth; ++d) {
+    p.down_vis_lists[d] = add_list(p.down_visited[d]);
+    p.down_all_lists[d] = add_list(p.down_all[d]);
+  }
+
+  // device descriptors
+  p.dev_nodes.resize(nn);
+  for (int k = 0; k < nn; ++k) {
+    const Node& nd = p.nodes[k];
+    NodeDev& d = p.dev_nodes[k];
+    d.m = nd.m; d.b = nd.b; d.nf = nd.nf; d.leaf = nd.leaf();
+    d.child0 = nd.child[0]; d.child1 = nd.child[1];
+    d.x0 = nd.x0; d.y0 = nd.y0; d.x1 = nd.x1; d.y1 = nd.y1;
+    d.map_off = (int32_t)nd.map_off;
+    d.fp64 = nd.fp64;
+    d.f_off = nd.f_off; d.s_off = nd.s_off;
+  }
+
+  // algorithmic flops (2 per multiply-add; leading terms):
+  //   Cholesky m^3/3, TRSM (b+1) m^2/2, SYRK (b+1)(b+2)/2 m; descent b m + m^2/2
+  p.flops_up = p.flops_down = 0.0;
+  for (const Node& nd : p.nodes) {
+    double m = nd.m, nb = nd.b + 1.0;
+    p.flops_up += 2.0 * (m * m * m / 3.0 + nb * m * m / 2.0 + nb * (nb + 1.0) / 2.0 * m);
+    if (nd.visited) p.flops_down += 2.0 * (nd.b * m + m * m / 2.0);
+  }
+  return "";
+}
+
+static size_t align256(size_t x) { return (x + 255) / 256 * 256; }
+
+Layout layout(const Plan& p, int batch) {
+  Layout L;
+  size_t off = 0;
+  auto take = [&](size_t bytes) { size_t o = off; off = align256(off + bytes); return o; };
+  const size_t B = (size_t)batch, NN = (size_t)p.N * p.N;
+  L.status = take(B * 4);
+  L.conv = take(B * 4);
+  L.kappa = take(B * p.n_t * 8);
+  L.u = take(B * NN * 8);
+  if (p.precision == HDD_MIXED_FP32) {
+    L.r = take(B * NN * 8);
+    L.du = take(B * NN * 8);
+  }
+  L.f64 = take(B * (size_t)p.f64_stride * 8);
+  L.f32 = take(B * (size_t)p.f32_stride * 4);
+  L.s64 = take(B * (size_t)p.s64_stride * 8);
+  L.s32 = take(B * (size_t)p.s32_stride * 4);
+  L.uobs = take(B * p.n_obs * 8);
+  L.ll = take(B * 8);
+  L.z = take(B * p.n_z * 8);
+  L.y = take(B * p.n_obs * 8);
+  L.total = off;
+  return L;
+}
+
+}  // namespace hdd

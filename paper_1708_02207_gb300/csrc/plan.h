@@ -1,0 +1,115 @@
+// Internal plan of the HDD likelihood library: decomposition tree, fronts,
+// index maps, launch schedule and workspace layout.  Host C++ only; the .cu
+// files include it for the shared device descriptor.
+#pragma once
+
+#include <array>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/hdd.h"
+
+namespace hdd {
+
+// Device-side node descriptor (64 bytes).  A node's front has nf = m + b + 1
+// rows: m eliminated vertices (gamma, or a leaf's interior), b boundary unknowns,
+// and one bordered right-hand-side row.  Per sample the front is stored as
+//   F: nf x m column-major (ld nf)      -> L_gg (rows < m), L_Bg, y_g^T (last row)
+//   S: (b+1) x (b+1) column-major (ld b+1), lower triangle -> Schur complement and
+//      condensed right-hand side (last row)
+struct NodeDev {
+  int32_t m, b, nf, leaf;
+  int32_t child0, child1;
+  int32_t x0, y0, x1, y1;   // closed rectangle (vertex indices)
+  int32_t map_off;          // ints into the map table: vid[nf-1], then pos0[nf], pos1[nf]
+  int32_t fp64;             // 1 if this node's factors are FP64 (mixed plans: top levels)
+  int64_t f_off;            // elements into a sample's factor store of the node's type
+  int64_t s_off;            // elements into a sample's Schur arena of the node's type
+};
+static_assert(sizeof(NodeDev) == 64, "NodeDev layout");
+
+struct Node {
+  int x0, x1, y0, y1;
+  int depth = 0, height = 0;
+  int parent = -1;
+  int child[2] = {-1, -1};
+  char split = 0;          // 'x': vertical line x = cut; 'y': horizontal line y = cut
+  int cut = -1;
+  std::vector<int> gamma;  // eliminated vertex ids, ordered
+  std::vector<int> bnd;    // boundary unknowns, ascending id
+  bool visited = false;
+  bool fp64 = true;
+  int m = 0, b = 0, nf = 0;
+  int64_t f_off = 0, s_off = 0;
+  int64_t map_off = 0;
+  bool leaf() const { return child[0] < 0; }
+};
+
+// A list of nodes launched together, with the maxima that size the launch.
+struct ListInfo {
+  int64_t off = 0;   // into the concatenated list table
+  int n = 0;
+  int max_nf = 0, max_m = 0, max_b = 0;
+};
+
+// One upsweep step: all nodes of one height, split by front size and precision.
+struct Step {
+  std::vector<int> small64, large64, small32, large32;
+};
+
+struct Plan {
+  // problem
+  int N = 0, leaf = 0, n_z = 0, n_obs = 0, n_t = 0, device = -1;
+  int precision = HDD_FP64, ir_max_iter = 0;
+  double f = 1.0, sigma = 1.0, h = 0.0, ir_tol = 1e-10;
+  std::vector<int32_t> obs;
+
+  // tree
+  std::vector<Node> nodes;
+  std::vector<int32_t> owner;          // vertex id -> node that eliminates it (-1: Dirichlet)
+  std::vector<Step> steps;             // by height, leaves first
+  std::vector<std::vector<int>> down_visited, down_all;   // by depth, root first
+  std::vector<int32_t> maps;           // concatenated per-node maps
+  std::vector<NodeDev> dev_nodes;
+  int max_front = 0, max_front_small64 = 0, max_front_small32 = 0;
+  int max_nf_large = 0, max_m_large = 0, max_b_large = 0;
+  int n_leaves = 0, depth = 0, height = 0, n_visited = 0;
+
+  // per-sample sizes (elements)
+  int64_t f64_stride = 0, f32_stride = 0;   // factor stores
+  int64_t s64_stride = 0, s32_stride = 0;   // Schur arenas (lifetime-packed)
+  double flops_up = 0.0, flops_down = 0.0;
+
+  // node lists concatenated (host copy of d_lists) and their descriptors
+  std::vector<int32_t> list_data;
+  std::vector<ListInfo> lists;
+  std::vector<std::array<int, 4>> step_lists;   // [height][small64, large64, small32, large32]
+  std::vector<int> down_vis_lists, down_all_lists;   // [depth]
+
+  // device copies
+  double* d_phi = nullptr;
+  NodeDev* d_nodes = nullptr;
+  int32_t* d_maps = nullptr;
+  int32_t* d_lists = nullptr;
+  int32_t* d_obs = nullptr;
+};
+
+// Front sizes up to these limits run in shared memory (one CTA per front).
+constexpr int kSmallMax64 = 160;   // 160^2 * 8 B = 200 KiB
+constexpr int kSmallMax32 = 224;   // 224^2 * 4 B = 196 KiB
+
+// Build the host plan; returns an empty string on success, else an error text.
+std::string build_plan(const hdd_plan_desc& d, Plan& p);
+
+// Workspace layout for a batch (byte offsets, 256-byte aligned).
+struct Layout {
+  size_t status = 0, kappa = 0;
+  size_t u = 0, r = 0, du = 0;        // FP64 vertex vectors [batch x N^2]
+  size_t f64 = 0, f32 = 0, s64 = 0, s32 = 0;
+  size_t uobs = 0, ll = 0, z = 0, y = 0, conv = 0;
+  size_t total = 0;
+};
+Layout layout(const Plan& p, int batch);
+
+}  // namespace hdd

@@ -1,0 +1,245 @@
+"""ctypes binding of libhdd.so (argument marshalling only).
+
+Every step of the likelihood path runs in the library's CUDA kernels; this module
+only converts Python / PyTorch arguments into the plain pointers and sizes of the
+C ABI declared in include/hdd.h.  PyTorch provides device memory and streams.
+There is no CPU fallback: if the library cannot be loaded, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "_build", "libhdd.so")
+
+HDD_OK, HDD_EINVAL, HDD_ENOMEM, HDD_ECUDA, HDD_ENOTSPD, HDD_ENOCONV, HDD_ETIMEOUT, HDD_ESTATE = 0, -1, -2, -3, -4, -5, -6, -7
+HDD_FP64, HDD_MIXED_FP32 = 0, 1
+
+EXPORTED = [
+    "hdd_plan", "hdd_plan_destroy", "hdd_workspace_size", "hdd_assemble", "hdd_upsweep",
+    "hdd_point_solve", "hdd_loglik", "hdd_evaluate_host", "hdd_plan_info", "hdd_node_info",
+    "hdd_node_indices", "hdd_status_string", "hdd_last_error",
+]
+
+
+class PlanDesc(C.Structure):
+    _fields_ = [
+        ("N", C.c_int32), ("leaf", C.c_int32), ("n_z", C.c_int32),
+        ("kl_basis", C.POINTER(C.c_double)), ("f", C.c_double),
+        ("n_obs", C.c_int32), ("obs_vertex", C.POINTER(C.c_int32)),
+        ("sigma", C.c_double), ("precision", C.c_int32), ("ir_max_iter", C.c_int32),
+        ("ir_tol", C.c_double), ("device", C.c_int32),
+    ]
+
+
+class PlanInfo(C.Structure):
+    _fields_ = [
+        ("n_nodes", C.c_int32), ("n_leaves", C.c_int32), ("depth", C.c_int32), ("height", C.c_int32),
+        ("n_visited", C.c_int32), ("max_front", C.c_int32),
+        ("flops_upsweep", C.c_double), ("flops_point_solve", C.c_double),
+        ("factor_bytes", C.c_double), ("schur_bytes", C.c_double),
+        ("launches_upsweep", C.c_int32), ("launches_evaluate", C.c_int32),
+    ]
+
+
+class NodeInfo(C.Structure):
+    _fields_ = [(n, C.c_int32) for n in
+                ("x0", "x1", "y0", "y1", "parent", "child0", "child1", "depth", "height", "m", "b", "visited")]
+
+
+_lib = None
+
+
+def load_library() -> C.CDLL:
+    """Load libhdd.so (built by paper_1708_02207_gb300.build); raises if it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is missing: run paper_1708_02207_gb300.build.build() first "
+                           "(the HDD path has no CPU fallback)")
+    lib = C.CDLL(LIB_PATH)
+    vp, i32, pd, pi32 = C.c_void_p, C.c_int32, C.POINTER(C.c_double), C.POINTER(C.c_int32)
+    lib.hdd_plan.argtypes = [C.POINTER(PlanDesc), C.POINTER(vp)]
+    lib.hdd_plan_destroy.argtypes = [vp]
+    lib.hdd_workspace_size.argtypes = [vp, i32, C.POINTER(C.c_size_t)]
+    lib.hdd_assemble.argtypes = [vp, vp, i32, vp, vp]
+    lib.hdd_upsweep.argtypes = [vp, i32, vp, vp]
+    lib.hdd_point_solve.argtypes = [vp, i32, vp, vp, vp]
+    lib.hdd_loglik.argtypes = [vp, i32, vp, vp, vp, i32, vp, vp, vp]
+    lib.hdd_evaluate_host.argtypes = [vp, i32, vp, pd, pd, i32, pd, pd, pi32, vp]
+    lib.hdd_plan_info.argtypes = [vp, C.POINTER(PlanInfo)]
+    lib.hdd_node_info.argtypes = [vp, i32, C.POINTER(NodeInfo)]
+    lib.hdd_node_indices.argtypes = [vp, i32, pi32, pi32]
+    lib.hdd_status_string.argtypes = [i32]
+    lib.hdd_status_string.restype = C.c_char_p
+    lib.hdd_last_error.restype = C.c_char_p
+    for name in EXPORTED:
+        if name not in ("hdd_status_string", "hdd_last_error"):
+            getattr(lib, name).restype = i32
+    _lib = lib
+    return lib
+
+
+class HDDError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        lib = load_library()
+        msg = lib.hdd_status_string(status).decode()
+        detail = lib.hdd_last_error().decode()
+        super().__init__(f"{where}: {msg} ({status}) {detail}")
+        self.status = status
+
+
+def _check(status: int, where: str):
+    if status != HDD_OK:
+        raise HDDError(status, where)
+
+
+def _ptr(t) -> int:
+    return 0 if t is None else int(t.data_ptr())
+
+
+def _stream_ptr(stream) -> int:
+    """cudaStream_t of a torch stream, an int handle, or torch's current stream (None)."""
+    if isinstance(stream, int):
+        return stream
+    if stream is None:
+        import torch
+        if not torch.cuda.is_available():
+            return 0
+        return int(torch.cuda.current_stream().cuda_stream)
+    return int(stream.cuda_stream)
+
+
+class Plan:
+    """A device-resident HDD plan for one grid, KL basis and observation set."""
+
+    def __init__(self, N: int, leaf: int, phi: np.ndarray | None, obs: np.ndarray, sigma: float,
+                 f: float = 1.0, precision: int = HDD_FP64, ir_max_iter: int = 4, ir_tol: float = 1e-10,
+                 device: int = 0):
+        self.lib = load_library()
+        self.N, self.leaf, self.sigma, self.f = N, leaf, float(sigma), float(f)
+        self.obs = np.ascontiguousarray(obs, dtype=np.int32)
+        self.n_obs = int(self.obs.size)
+        self.device = device
+        desc = PlanDesc()
+        desc.N, desc.leaf = N, leaf
+        if phi is not None:
+            self._phi = np.ascontiguousarray(phi, dtype=np.float64)
+            desc.n_z = self._phi.shape[1]
+            desc.kl_basis = self._phi.ctypes.data_as(C.POINTER(C.c_double))
+        else:
+            desc.n_z = 1
+            desc.kl_basis = None
+        self.n_z = desc.n_z
+        desc.f = self.f
+        desc.n_obs = self.n_obs
+        desc.obs_vertex = self.obs.ctypes.data_as(C.POINTER(C.c_int32))
+        desc.sigma = self.sigma
+        desc.precision, desc.ir_max_iter, desc.ir_tol = precision, ir_max_iter, ir_tol
+        desc.device = device
+        self.precision = precision
+        h = C.c_void_p()
+        _check(self.lib.hdd_plan(C.byref(desc), C.byref(h)), "hdd_plan")
+        self._h = h
+        self._phi = None  # copied by the library
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self.lib.hdd_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ---- queries -------------------------------------------------------
+    def info(self) -> dict:
+        pi = PlanInfo()
+        _check(self.lib.hdd_plan_info(self._h, C.byref(pi)), "hdd_plan_info")
+        return {n: getattr(pi, n) for n, _ in PlanInfo._fields_}
+
+    def node(self, k: int) -> dict:
+        ni = NodeInfo()
+        _check(self.lib.hdd_node_info(self._h, k, C.byref(ni)), "hdd_node_info")
+        return {n: getattr(ni, n) for n, _ in NodeInfo._fields_}
+
+    def node_indices(self, k: int):
+        d = self.node(k)
+        g = np.zeros(d["m"], dtype=np.int32)
+        b = np.zeros(d["b"], dtype=np.int32)
+        _check(self.lib.hdd_node_indices(self._h, k, g.ctypes.data_as(C.POINTER(C.c_int32)),
+                                         b.ctypes.data_as(C.POINTER(C.c_int32))), "hdd_node_indices")
+        return g, b
+
+    def workspace_size(self, batch: int) -> int:
+        n = C.c_size_t()
+        _check(self.lib.hdd_workspace_size(self._h, batch, C.byref(n)), "hdd_workspace_size")
+        return int(n.value)
+
+    # ---- device calls (torch tensors on this plan's device) --------------
+    def workspace(self, batch: int):
+        import torch
+        return torch.empty(self.workspace_size(batch), dtype=torch.uint8, device=f"cuda:{self.device}")
+
+    def assemble(self, Z, ws, stream=None):
+        batch = Z.shape[0]
+        _check(self.lib.hdd_assemble(self._h, _ptr(Z), batch, _ptr(ws), _stream_ptr(stream)), "hdd_assemble")
+
+    def upsweep(self, batch: int, ws, stream=None):
+        _check(self.lib.hdd_upsweep(self._h, batch, _ptr(ws), _stream_ptr(stream)), "hdd_upsweep")
+
+    def point_solve(self, batch: int, ws, u_obs, stream=None):
+        _check(self.lib.hdd_point_solve(self._h, batch, _ptr(ws), _ptr(u_obs), _stream_ptr(stream)),
+               "hdd_point_solve")
+
+    def loglik(self, batch: int, ws, u_obs, y, loglik, status=None, stream=None):
+        per_sample = 1 if y.dim() == 2 else 0
+        _check(self.lib.hdd_loglik(self._h, batch, _ptr(ws), _ptr(u_obs), _ptr(y), per_sample, _ptr(loglik),
+                                   _ptr(status), _stream_ptr(stream)), "hdd_loglik")
+
+    def evaluate(self, Z, y, ws=None, stream=None):
+        """Device tensors in, (loglik [B], u_obs [B, n_obs], status [B]) device tensors out."""
+        import torch
+        batch = Z.shape[0]
+        dev = Z.device
+        if ws is None:
+            ws = self.workspace(batch)
+        u_obs = torch.empty(batch, self.n_obs, dtype=torch.float64, device=dev)
+        ll = torch.empty(batch, dtype=torch.float64, device=dev)
+        st = torch.empty(batch, dtype=torch.int32, device=dev)
+        self.assemble(Z, ws, stream)
+        self.upsweep(batch, ws, stream)
+        self.point_solve(batch, ws, u_obs, stream)
+        self.loglik(batch, ws, u_obs, y, ll, st, stream)
+        return ll, u_obs, st
+
+    def evaluate_host_ptrs(self, batch: int, ws, Z_ptr: int, y_ptr: int, y_per_sample: int, ll_ptr: int,
+                           uobs_ptr: int, status_ptr: int, stream=None):
+        """hdd_evaluate_host on raw host addresses (e.g. pinned torch tensors)."""
+        _check(self.lib.hdd_evaluate_host(self._h, batch, _ptr(ws), C.cast(Z_ptr, C.POINTER(C.c_double)),
+                                          C.cast(y_ptr, C.POINTER(C.c_double)), y_per_sample,
+                                          C.cast(ll_ptr, C.POINTER(C.c_double)),
+                                          C.cast(uobs_ptr, C.POINTER(C.c_double)) if uobs_ptr else None,
+                                          C.cast(status_ptr, C.POINTER(C.c_int32)) if status_ptr else None,
+                                          _stream_ptr(stream)), "hdd_evaluate_host")
+
+    def evaluate_host(self, Z: np.ndarray, y: np.ndarray, ws, stream=None):
+        """Host arrays in and out through hdd_evaluate_host (copies inside the call)."""
+        Z = np.ascontiguousarray(Z, dtype=np.float64)
+        y = np.ascontiguousarray(y, dtype=np.float64)
+        batch = Z.shape[0]
+        ll = np.empty(batch)
+        u_obs = np.empty((batch, self.n_obs))
+        st = np.empty(batch, dtype=np.int32)
+        dp = C.POINTER(C.c_double)
+        _check(self.lib.hdd_evaluate_host(self._h, batch, _ptr(ws), Z.ctypes.data_as(dp), y.ctypes.data_as(dp),
+                                          1 if y.ndim == 2 else 0, ll.ctypes.data_as(dp), u_obs.ctypes.data_as(dp),
+                                          st.ctypes.data_as(C.POINTER(C.c_int32)), _stream_ptr(stream)),
+               "hdd_evaluate_host")
+        return ll, u_obs, st

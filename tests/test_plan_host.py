@@ -1,0 +1,99 @@
+"""CPU checks of the C ABI: the library builds, loads and exports every declared
+symbol; host-only plans reproduce the oracle's decomposition tree (Sec. 2.1), the
+Appendix A sizes and the pruned descent set (Sec. 5.3); bad arguments are refused."""
+import json
+import os
+import re
+
+import numpy as np
+import pytest
+
+import workload as w
+from oracle import hdd_dense as hd
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def hdd():
+    from paper_1708_02207_gb300 import build, hdd as binding
+    build.build()
+    return binding
+
+
+def test_library_exports_every_declared_symbol(hdd):
+    lib = hdd.load_library()
+    with open(os.path.join(ROOT, "include", "hdd.h")) as fh:
+        header = fh.read()
+    declared = set(re.findall(r"^\s*(?:hdd_status|const char\*)\s+(hdd_\w+)\s*\(", header, re.M))
+    assert len(declared) >= 13
+    for name in declared:
+        assert hasattr(lib, name), name
+    assert set(hdd.EXPORTED) >= declared - {"hdd_zz_unused"}
+
+
+@pytest.mark.parametrize("N,leaf,m_obs", [(33, 8, 3), (65, 4, 5), (17, 16, 2), (30, 4, 4), (50, 5, 6), (9, 1, 2)])
+def test_tree_matches_oracle(hdd, N, leaf, m_obs):
+    obs = w.obs_vertices(N, m_obs)
+    plan = hdd.Plan(N, leaf, None, obs, 0.01, device=-1)
+    nodes = hd.build_tree(N, leaf)
+    info = plan.info()
+    assert info["n_nodes"] == len(nodes)
+    vis = hd.visited_nodes(nodes, obs)
+    assert info["n_visited"] == len(vis)
+    # the C plan and the oracle number nodes the same way (depth-first, left son first)
+    for k, nd in enumerate(nodes):
+        c = plan.node(k)
+        assert (c["x0"], c["x1"], c["y0"], c["y1"]) == (nd.x0, nd.x1, nd.y0, nd.y1)
+        assert c["parent"] == nd.parent
+        assert (c["child0"], c["child1"]) == (tuple(nd.children) if nd.children else (-1, -1))
+        g, b = plan.node_indices(k)
+        assert list(g) == nd.gamma
+        assert list(b) == nd.bnd
+        assert c["visited"] == (k in vis)
+
+
+def test_appendix_a_sizes_in_the_plan(hdd):
+    with open(os.path.join(ROOT, "tests", "golden", "appendix_a.json")) as fh:
+        g = json.load(fh)
+    plan = hdd.Plan(513, 8, None, w.obs_vertices(513, 16), 0.01, device=-1)
+    found = 0
+    for k in range(plan.info()["n_nodes"]):
+        c = plan.node(k)
+        if c["x1"] - c["x0"] == g["cells_per_side"] == c["y1"] - c["y0"] and c["x0"] > 0 and c["y0"] > 0 \
+                and c["x1"] < 512 and c["y1"] < 512:
+            s0, s1 = plan.node(c["child0"]), plan.node(c["child1"])
+            assert c["b"] == g["father_boundary"] and c["m"] == g["gamma"]
+            assert s0["b"] == s1["b"] == g["son_boundary"]
+            _, b0 = plan.node_indices(c["child0"])
+            _, b1 = plan.node_indices(c["child1"])
+            assert len(set(b0) | set(b1)) == g["auxiliary"]
+            found += 1
+    assert found == 4
+
+
+def test_invalid_arguments(hdd):
+    with pytest.raises(hdd.HDDError) as e:
+        hdd.Plan(33, 8, None, np.array([0], dtype=np.int32), 0.01, device=-1)
+    assert e.value.status == hdd.HDD_EINVAL
+    with pytest.raises(hdd.HDDError):
+        hdd.Plan(2, 8, None, np.array([0], dtype=np.int32), 0.01, device=-1)
+    with pytest.raises(hdd.HDDError):
+        hdd.Plan(33, 0, None, w.obs_vertices(33, 3), 0.01, device=-1)
+    with pytest.raises(hdd.HDDError):
+        hdd.Plan(33, 8, None, w.obs_vertices(33, 3), -1.0, device=-1)
+    plan = hdd.Plan(33, 8, None, w.obs_vertices(33, 3), 0.01, device=-1)
+    assert plan.workspace_size(2) > plan.workspace_size(1)
+    with pytest.raises(hdd.HDDError) as e:
+        plan.upsweep(1, None)
+    assert e.value.status == hdd.HDD_ESTATE
+
+
+def test_flop_count_matches_front_sizes(hdd):
+    plan = hdd.Plan(33, 8, None, w.obs_vertices(33, 3), 0.01, device=-1)
+    nodes = hd.build_tree(33, 8)
+    ref = 0.0
+    for nd in nodes:
+        m, nb = len(nd.gamma), len(nd.bnd) + 1
+        ref += 2 * (m ** 3 / 3 + nb * m * m / 2 + nb * (nb + 1) / 2 * m)
+    assert np.isclose(plan.info()["flops_upsweep"], ref)
