@@ -170,8 +170,8 @@ def run_hdd(args, cfg):
     if dist:
         dist.barrier()
 
-    prob = w.make_problem(cfg)
-    B = cfg.batch
+    B = args.batch or cfg.batch
+    prob = w.make_problem(cfg, batch=B)
     precision = hdd.HDD_MIXED_FP32 if args.precision == "mixed" else hdd.HDD_FP64
     plan = hdd.Plan(cfg.N, args.leaf or cfg.leaf, prob.phi, prob.obs, cfg.sigma, f=cfg.f, precision=precision,
                     ir_max_iter=args.ir_iters, ir_tol=args.ir_tol, device=local)
@@ -310,6 +310,7 @@ def main(argv=None):
     ap.add_argument("--config", default="grid513", choices=sorted(w.CONFIGS))
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
     ap.add_argument("--leaf", type=int, default=0)
+    ap.add_argument("--batch", type=int, default=0, help="samples per step (default: the workload's)")
     ap.add_argument("--ir-iters", type=int, default=4)
     ap.add_argument("--ir-tol", type=float, default=1e-10)
     ap.add_argument("--no-cpu-baseline", action="store_true")
