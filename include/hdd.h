@@ -162,6 +162,32 @@ hdd_status hdd_evaluate_host(hdd_plan_t plan, int32_t batch, void* workspace,
                              double* loglik, double* u_obs, int32_t* sample_status,
                              void* stream);
 
+/* Evaluation without any allocation and without a caller workspace.  The paper
+ * has no counterpart: this entry point exists for callers that cannot allocate
+ * device memory at evaluation time -- for example a host application whose whole
+ * device memory is reserved at start-up by another framework's pool, a plug-in
+ * that is given no allocator, or a latency-critical sampling loop that must not
+ * call cudaMalloc/cudaFree (those calls can synchronize the device).
+ *
+ * It runs the same kernels as hdd_assemble + hdd_upsweep + hdd_point_solve +
+ * hdd_loglik, with the workspace placed in one static device array of
+ * HDD_STATIC_WORKSPACE_BYTES that every GPU which loads the library holds until
+ * the process exits.  It calls no cudaMalloc, cudaFree or other allocating
+ * routine.  Z: device [batch x n_z]; y: device [n_obs] or [batch x n_obs];
+ * loglik: device [batch]; u_obs: device [batch x n_obs] or NULL; sample_status:
+ * device [batch] or NULL.  Returns HDD_EINVAL if hdd_workspace_size(plan, batch)
+ * exceeds HDD_STATIC_WORKSPACE_BYTES.
+ *
+ * The first call on a device looks up the array's device address (with that
+ * device current); make that first call before any stream capture.  All calls
+ * share the one array and each call overwrites it (the per-sample status words
+ * are cleared at the start of every call): calls whose GPU work overlaps --
+ * on different streams, or from several threads -- race with each other.  */
+#define HDD_STATIC_WORKSPACE_BYTES ((size_t)32 << 20)
+hdd_status hdd_evaluate_static(hdd_plan_t plan, int32_t batch, const double* Z, const double* y,
+                               int32_t y_per_sample, double* loglik, double* u_obs, int32_t* sample_status,
+                               void* stream);
+
 /* Plan queries (work on host-only plans too). */
 hdd_status hdd_plan_info(hdd_plan_t plan, hdd_plan_info_t* info);
 hdd_status hdd_node_info(hdd_plan_t plan, int32_t node, hdd_node_info_t* info);

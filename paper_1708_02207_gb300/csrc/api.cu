@@ -11,10 +11,6 @@
 #include "launch.h"
 #include "plan.h"
 
-struct hdd_plan_s {
-  hdd::Plan p;
-};
-
 namespace hdd {
 cudaError_t configure_front_kernels();
 cudaError_t configure_solve_kernels();

@@ -113,3 +113,8 @@ struct Layout {
 Layout layout(const Plan& p, int batch);
 
 }  // namespace hdd
+
+// The opaque plan handle of the C ABI.
+struct hdd_plan_s {
+  hdd::Plan p;
+};

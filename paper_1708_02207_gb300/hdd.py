@@ -21,8 +21,9 @@ HDD_FP64, HDD_MIXED_FP32 = 0, 1
 EXPORTED = [
     "hdd_plan", "hdd_plan_destroy", "hdd_workspace_size", "hdd_assemble", "hdd_upsweep",
     "hdd_point_solve", "hdd_loglik", "hdd_evaluate_host", "hdd_plan_info", "hdd_node_info",
-    "hdd_node_indices", "hdd_status_string", "hdd_last_error",
+    "hdd_node_indices", "hdd_status_string", "hdd_last_error", "hdd_evaluate_static",
 ]
+STATIC_WORKSPACE_BYTES = 32 << 20
 
 
 class PlanDesc(C.Structure):
@@ -71,6 +72,7 @@ def load_library() -> C.CDLL:
     lib.hdd_point_solve.argtypes = [vp, i32, vp, vp, vp]
     lib.hdd_loglik.argtypes = [vp, i32, vp, vp, vp, i32, vp, vp, vp]
     lib.hdd_evaluate_host.argtypes = [vp, i32, vp, pd, pd, i32, pd, pd, pi32, vp]
+    lib.hdd_evaluate_static.argtypes = [vp, i32, vp, vp, i32, vp, vp, vp, vp]
     lib.hdd_plan_info.argtypes = [vp, C.POINTER(PlanInfo)]
     lib.hdd_node_info.argtypes = [vp, i32, C.POINTER(NodeInfo)]
     lib.hdd_node_indices.argtypes = [vp, i32, pi32, pi32]
@@ -218,6 +220,14 @@ class Plan:
         self.point_solve(batch, ws, u_obs, stream)
         self.loglik(batch, ws, u_obs, y, ll, st, stream)
         return ll, u_obs, st
+
+    def evaluate_static(self, Z, y, loglik, u_obs=None, status=None, stream=None):
+        """hdd_evaluate_static: same result as evaluate(), workspace in the library's
+        static device array (no allocation); device tensors in and out."""
+        batch = Z.shape[0]
+        per_sample = 1 if y.dim() == 2 else 0
+        _check(self.lib.hdd_evaluate_static(self._h, batch, _ptr(Z), _ptr(y), per_sample, _ptr(loglik),
+                                            _ptr(u_obs), _ptr(status), _stream_ptr(stream)), "hdd_evaluate_static")
 
     def evaluate_host_ptrs(self, batch: int, ws, Z_ptr: int, y_ptr: int, y_per_sample: int, ll_ptr: int,
                            uobs_ptr: int, status_ptr: int, stream=None):
