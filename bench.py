@@ -311,8 +311,8 @@ def main(argv=None):
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
     ap.add_argument("--leaf", type=int, default=0)
     ap.add_argument("--batch", type=int, default=0, help="samples per step (default: the workload's)")
-    ap.add_argument("--ir-iters", type=int, default=4)
-    ap.add_argument("--ir-tol", type=float, default=1e-10)
+    ap.add_argument("--ir-iters", type=int, default=2)
+    ap.add_argument("--ir-tol", type=float, default=1e-8)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args(argv)
     cfg = w.CONFIGS[args.config]

@@ -74,7 +74,10 @@ typedef struct {
   double sigma;               /* noise standard deviation, > 0 */
   int32_t precision;          /* hdd_precision */
   int32_t ir_max_iter;        /* mixed only: refinement steps after the first solve (0..64) */
-  double ir_tol;              /* mixed only: target max_k |du_k| / max_k |u_k| at the observations */
+  double ir_tol;              /* mixed only: target relative error at the observations, estimated
+                                 after the last step as d_K min(1, d_K / d_{K-1}) / max_k |u_k|
+                                 with d = max_k |du_k| over the observations */
+  int32_t fp64_top_levels;    /* mixed only: tree depths 0..fp64_top_levels-1 are factorised in FP64 */
   int32_t device;             /* CUDA device ordinal, or -1 for a host-only plan that supports
                                  the hdd_plan_info / hdd_node_info queries and nothing else */
 } hdd_plan_desc;

@@ -14,6 +14,7 @@
 namespace hdd {
 cudaError_t configure_front_kernels();
 cudaError_t configure_solve_kernels();
+cudaError_t configure_refine_kernels();
 }  // namespace hdd
 
 namespace {
@@ -53,6 +54,7 @@ cudaError_t configure_device(int dev) {
   if (g_configured[dev]) return cudaSuccess;
   cudaError_t e = hdd::configure_front_kernels();
   if (e == cudaSuccess) e = hdd::configure_solve_kernels();
+  if (e == cudaSuccess) e = hdd::configure_refine_kernels();
   if (e == cudaSuccess) g_configured[dev] = true;
   return e;
 }
@@ -156,6 +158,53 @@ cudaError_t run_descent(const hdd::Plan& p, int batch, void* ws, const std::vect
   return cudaSuccess;
 }
 
+// Right-hand-side sweep (leaves to root) through the stored factors.
+cudaError_t run_forward(const hdd::Plan& p, int batch, void* ws, const hdd::Rhs& rhs, cudaStream_t st) {
+  const hdd::Layout L = hdd::layout(p, batch);
+  const hdd::Arenas A = arenas(p, L, ws);
+  for (int h = 0; h <= p.height; ++h)
+    for (int k = 0; k < 2; ++k) {
+      const hdd::ListInfo& li = p.lists[p.fwd_lists[h][k]];
+      if (li.n == 0) continue;
+      cudaError_t e = k == 0 ? hdd::launch_forward<double>(p.d_nodes, p.d_maps, p.d_lists + li.off, li.n, batch, A,
+                                                           rhs, li.max_nf, st)
+                             : hdd::launch_forward<float>(p.d_nodes, p.d_maps, p.d_lists + li.off, li.n, batch, A,
+                                                          rhs, li.max_nf, st);
+      if (e != cudaSuccess) return e;
+    }
+  return cudaSuccess;
+}
+
+// Mixed precision point solve: full descent, then ir_max_iter refinement steps
+// (FP64 residual, sweep through the FP32/FP64 factors, update); the last step's
+// descent is pruned to the observation paths and checked against ir_tol.
+cudaError_t run_refined_solve(const hdd::Plan& p, int batch, void* ws, double* u_obs, cudaStream_t st) {
+  const hdd::Layout L = hdd::layout(p, batch);
+  char* w = static_cast<char*>(ws);
+  double* u = reinterpret_cast<double*>(w + L.u);
+  double* r = reinterpret_cast<double*>(w + L.r);
+  double* du = reinterpret_cast<double*>(w + L.du);
+  const double* kappa = reinterpret_cast<const double*>(w + L.kappa);
+  int32_t* status = reinterpret_cast<int32_t*>(w + L.status);
+  double* dprev = reinterpret_cast<double*>(w + L.conv);   // zeroed by hdd_assemble
+  const int64_t NN = (int64_t)p.N * p.N;
+  const double load = p.h * p.h * p.f;
+  const int K = p.ir_max_iter;
+  cudaError_t e = run_descent(p, batch, ws, K > 0 ? p.down_all_lists : p.down_vis_lists, u, st);
+  for (int it = 1; it <= K && e == cudaSuccess; ++it) {
+    const bool last = it == K;
+    e = hdd::launch_residual(kappa, p.n_t, u, NN, p.N, load, r, batch, st);
+    if (e == cudaSuccess) e = run_forward(p, batch, ws, hdd::Rhs{r, NN, 0.0}, st);
+    if (e == cudaSuccess) e = run_descent(p, batch, ws, last ? p.down_vis_lists : p.down_all_lists, du, st);
+    if (e == cudaSuccess && !last) e = hdd::launch_delta_obs(du, NN, p.d_obs, p.n_obs, dprev, batch, st);
+    if (e == cudaSuccess && !last) e = hdd::launch_update(u, du, NN, p.N, batch, st);
+  }
+  if (e == cudaSuccess)
+    e = hdd::launch_final_obs(u, K > 0 ? du : nullptr, NN, p.d_obs, p.n_obs, K > 0 ? p.ir_tol : -1.0, dprev, u_obs,
+                              status, batch, st);
+  return e;
+}
+
 }  // namespace
 
 extern "C" {
@@ -253,7 +302,7 @@ hdd_status hdd_assemble(hdd_plan_t plan, const double* Z, int32_t batch, void* w
   const hdd::Layout L = hdd::layout(p, batch);
   char* w = static_cast<char*>(workspace);
   cudaError_t e = cudaMemsetAsync(w + L.status, 0, (size_t)batch * 4, st);
-  if (e == cudaSuccess) e = cudaMemsetAsync(w + L.conv, 0, (size_t)batch * 4, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(w + L.conv, 0, (size_t)batch * 8, st);
   if (e == cudaSuccess)
     e = hdd::launch_kappa(p.d_phi, Z, p.n_t, p.n_z, batch, reinterpret_cast<double*>(w + L.kappa), p.n_t, st);
   return e == cudaSuccess ? HDD_OK : fail_cuda(e, "hdd_assemble");
@@ -282,8 +331,13 @@ hdd_status hdd_point_solve(hdd_plan_t plan, int32_t batch, void* workspace, doub
   char* w = static_cast<char*>(workspace);
   double* u = reinterpret_cast<double*>(w + L.u);
   const int64_t NN = (int64_t)p.N * p.N;
-  cudaError_t e = run_descent(p, batch, workspace, p.down_vis_lists, u, st);
-  if (e == cudaSuccess) e = hdd::launch_gather_obs(u, NN, p.d_obs, p.n_obs, batch, u_obs, st);
+  cudaError_t e;
+  if (p.precision == HDD_MIXED_FP32) {
+    e = run_refined_solve(p, batch, workspace, u_obs, st);
+  } else {
+    e = run_descent(p, batch, workspace, p.down_vis_lists, u, st);
+    if (e == cudaSuccess) e = hdd::launch_gather_obs(u, NN, p.d_obs, p.n_obs, batch, u_obs, st);
+  }
   return e == cudaSuccess ? HDD_OK : fail_cuda(e, "hdd_point_solve");
 }
 
@@ -357,9 +411,20 @@ hdd_status hdd_plan_info(hdd_plan_t plan, hdd_plan_info_t* info) {
       const hdd::ListInfo& li = p.lists[p.step_lists[h][kind]];
       if (li.n) up += (kind == 1 || kind == 3) ? 4 : 1;
     }
-  for (int d = 0; d <= p.depth; ++d) down += p.lists[p.down_vis_lists[d]].n > 0;
+  int down_all = 0, fwd = 0;
+  for (int d = 0; d <= p.depth; ++d) {
+    down += p.lists[p.down_vis_lists[d]].n > 0;
+    down_all += p.lists[p.down_all_lists[d]].n > 0;
+  }
+  for (int h = 0; h <= p.height; ++h) fwd += (p.lists[p.fwd_lists[h][0]].n > 0) + (p.lists[p.fwd_lists[h][1]].n > 0);
+  int solve = down + 1;
+  if (p.precision == HDD_MIXED_FP32) {
+    const int K = p.ir_max_iter;
+    solve = (K > 0 ? down_all : down) + 1;
+    for (int it = 1; it <= K; ++it) solve += 1 + fwd + (it == K ? down : down_all) + (it == K ? 0 : 2);
+  }
   info->launches_upsweep = up;
-  info->launches_evaluate = 1 + up + down + 2;
+  info->launches_evaluate = 1 + up + solve + 1;
   return HDD_OK;
 }
 

@@ -1,0 +1,226 @@
+// Iterative refinement of the mixed-precision path: FP64 residual of the global
+// FE system, a right-hand-side-only sweep through the stored factors, update.
+//
+// With factors L (the partial Cholesky factors of every node, FP32 below the
+// top levels) the HDD solve of A x = r is: leaves to root, z_g = sum of the sons'
+// condensed right-hand sides + r_g, y_g = L_gg^-1 z_g, condensed z_B - L_Bg y_g
+// (the bordered row of the upsweep, Eq. SchurC1 applied to a new F c); then the
+// unchanged descent (Root to Leaves).  The residual r = b - A u uses the FP64
+// stiffness of Eq. coefA (5-point edge weights of the "/" mesh) and the FP64 u.
+#include "launch.h"
+
+namespace hdd {
+
+template <typename T> __device__ __forceinline__ T* fwd_F(const Arenas& A, const NodeDev& nd, int s);
+template <> __device__ __forceinline__ double* fwd_F<double>(const Arenas& A, const NodeDev& nd, int s) {
+  return A.f64 + (int64_t)s * A.f64_stride + nd.f_off;
+}
+template <> __device__ __forceinline__ float* fwd_F<float>(const Arenas& A, const NodeDev& nd, int s) {
+  return A.f32 + (int64_t)s * A.f32_stride + nd.f_off;
+}
+template <typename T> __device__ __forceinline__ T* fwd_S(const Arenas& A, const NodeDev& nd, int s);
+template <> __device__ __forceinline__ double* fwd_S<double>(const Arenas& A, const NodeDev& nd, int s) {
+  return A.s64 + (int64_t)s * A.s64_stride + nd.s_off;
+}
+template <> __device__ __forceinline__ float* fwd_S<float>(const Arenas& A, const NodeDev& nd, int s) {
+  return A.s32 + (int64_t)s * A.s32_stride + nd.s_off;
+}
+
+// condensed right-hand side entry p of a son (last row of its Schur block)
+__device__ __forceinline__ double son_rhs(const Arenas& A, const NodeDev& ch, int s, int p) {
+  const int64_t idx = (int64_t)p * (ch.b + 1) + ch.b + ch.s_off;
+  return ch.fp64 ? A.s64[(int64_t)s * A.s64_stride + idx] : (double)A.s32[(int64_t)s * A.s32_stride + idx];
+}
+
+// Right-hand-side sweep at one node: one CTA per (node, sample).  Forward
+// substitution with L_gg in 32-column blocks (one warp, shuffles), each block
+// folded into every row below it (one thread per row, coalesced down columns).
+template <typename T>
+__global__ void k_forward(const NodeDev* __restrict__ nodes, const int32_t* __restrict__ maps,
+                          const int32_t* __restrict__ list, Arenas A, Rhs rhs) {
+  const int node = list[blockIdx.x];
+  const int s = blockIdx.y;
+  const NodeDev nd = nodes[node];
+  const int m = nd.m, b = nd.b, nf = nd.nf;
+  T* F = fwd_F<T>(A, nd, s);
+  const int32_t* vid = maps + nd.map_off;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* z = reinterpret_cast<T*>(smem_raw);   // [nf - 1]
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (nd.leaf) {
+    for (int r = threadIdx.x; r < nf - 1; r += blockDim.x) z[r] = (r < m) ? (T)rhs(s, vid[r]) : (T)0;
+  } else {
+    const NodeDev c0 = nodes[nd.child0], c1 = nodes[nd.child1];
+    const int32_t* pos0 = vid + (nf - 1);
+    const int32_t* pos1 = pos0 + nf;
+    for (int r = threadIdx.x; r < nf - 1; r += blockDim.x) {
+      double v = (r < m) ? rhs(s, vid[r]) : 0.0;
+      if (pos0[r] >= 0) v += son_rhs(A, c0, s, pos0[r]);
+      if (pos1[r] >= 0) v += son_rhs(A, c1, s, pos1[r]);
+      z[r] = (T)v;
+    }
+  }
+  for (int cb = 0; cb < m; cb += 32) {
+    const int jb = min(32, m - cb);
+    __syncthreads();
+    if (warp == 0) {
+      T x = (lane < jb) ? z[cb + lane] : (T)0;
+      for (int c = 0; c < jb; ++c) {
+        T yc = __shfl_sync(0xffffffffu, x, c);
+        yc = yc / F[(int64_t)(cb + c) * nf + cb + c];
+        if (lane == c) x = yc;
+        if (lane > c && lane < jb) x -= F[(int64_t)(cb + c) * nf + cb + lane] * yc;
+      }
+      if (lane < jb) z[cb + lane] = x;
+    }
+    __syncthreads();
+    for (int i = cb + jb + threadIdx.x; i < nf - 1; i += blockDim.x) {
+      T acc = (T)0;
+      for (int c = 0; c < jb; ++c) acc += F[(int64_t)(cb + c) * nf + i] * z[cb + c];
+      z[i] -= acc;
+    }
+  }
+  __syncthreads();
+  for (int c = threadIdx.x; c < m; c += blockDim.x) F[(int64_t)c * nf + nf - 1] = z[c];
+  if (b > 0) {
+    T* S = fwd_S<T>(A, nd, s);
+    for (int r = threadIdx.x; r < b; r += blockDim.x) S[(int64_t)r * (b + 1) + b] = z[m + r];
+  }
+}
+
+template <typename T>
+cudaError_t launch_forward(const NodeDev* nodes, const int32_t* maps, const int32_t* list, int nlist, int batch,
+                           const Arenas& A, const Rhs& rhs, int max_nf, cudaStream_t st) {
+  if (nlist == 0) return cudaSuccess;
+  k_forward<T><<<dim3(nlist, batch), 256, (size_t)max_nf * sizeof(T), st>>>(nodes, maps, list, A, rhs);
+  return cudaGetLastError();
+}
+template cudaError_t launch_forward<double>(const NodeDev*, const int32_t*, const int32_t*, int, int, const Arenas&,
+                                            const Rhs&, int, cudaStream_t);
+template cudaError_t launch_forward<float>(const NodeDev*, const int32_t*, const int32_t*, int, int, const Arenas&,
+                                           const Rhs&, int, cudaStream_t);
+
+// r = b - A u over the unknowns (FP64).  (A u)_v = sum over the four axis edges of
+// w_e (u_v - u_w), w_e = mean kappa of the two triangles having e as a leg;
+// Dirichlet neighbours contribute u_w = 0.  Boundary entries of r are set to 0.
+__global__ void k_residual(const double* __restrict__ kappa, int64_t kap_stride, const double* __restrict__ u,
+                           int64_t u_stride, int N, double load, double* __restrict__ r) {
+  const int s = blockIdx.y;
+  const int v = blockIdx.x * blockDim.x + threadIdx.x;
+  if (v >= N * N) return;
+  const int i = v % N, j = v / N;
+  double* rs = r + (int64_t)s * u_stride;
+  if (i < 1 || j < 1 || i > N - 2 || j > N - 2) {
+    rs[v] = 0.0;
+    return;
+  }
+  const double* k = kappa + (int64_t)s * kap_stride;
+  const double* us = u + (int64_t)s * u_stride;
+  auto kt = [&](int ci, int cj, int t) { return k[2 * ((int64_t)cj * (N - 1) + ci) + t]; };
+  auto uu = [&](int a, int c) { return (a < 1 || c < 1 || a > N - 2 || c > N - 2) ? 0.0 : us[c * N + a]; };
+  const double uv = us[v];
+  const double wr = 0.5 * (kt(i, j, 0) + kt(i, j - 1, 1));          // (i,j)-(i+1,j)
+  const double wl = 0.5 * (kt(i - 1, j, 0) + kt(i - 1, j - 1, 1));  // (i-1,j)-(i,j)
+  const double wu = 0.5 * (kt(i, j, 1) + kt(i - 1, j, 0));          // (i,j)-(i,j+1)
+  const double wd = 0.5 * (kt(i, j - 1, 1) + kt(i - 1, j - 1, 0));  // (i,j-1)-(i,j)
+  const double Au = wr * (uv - uu(i + 1, j)) + wl * (uv - uu(i - 1, j)) + wu * (uv - uu(i, j + 1)) +
+                    wd * (uv - uu(i, j - 1));
+  rs[v] = load - Au;
+}
+
+cudaError_t launch_residual(const double* kappa, int64_t kap_stride, const double* u, int64_t u_stride, int N,
+                            double load, double* r, int batch, cudaStream_t st) {
+  const int NN = N * N;
+  k_residual<<<dim3((NN + 255) / 256, batch), 256, 0, st>>>(kappa, kap_stride, u, u_stride, N, load, r);
+  return cudaGetLastError();
+}
+
+// u += du at every interior vertex
+__global__ void k_update(double* __restrict__ u, const double* __restrict__ du, int64_t stride, int N) {
+  const int s = blockIdx.y;
+  const int v = blockIdx.x * blockDim.x + threadIdx.x;
+  if (v >= N * N) return;
+  const int i = v % N, j = v / N;
+  if (i < 1 || j < 1 || i > N - 2 || j > N - 2) return;
+  u[(int64_t)s * stride + v] += du[(int64_t)s * stride + v];
+}
+
+cudaError_t launch_update(double* u, const double* du, int64_t stride, int N, int batch, cudaStream_t st) {
+  const int NN = N * N;
+  k_update<<<dim3((NN + 255) / 256, batch), 256, 0, st>>>(u, du, stride, N);
+  return cudaGetLastError();
+}
+
+// max_k |du[obs_k]| per sample (the size of a refinement correction), kept for
+// the contraction estimate of the last step.
+__global__ void k_delta_obs(const double* __restrict__ du, int64_t stride, const int32_t* __restrict__ obs,
+                            int n_obs, double* __restrict__ dprev) {
+  __shared__ double red[256];
+  const int s = blockIdx.x;
+  double md = 0.0;
+  for (int k = threadIdx.x; k < n_obs; k += blockDim.x) md = fmax(md, fabs(du[(int64_t)s * stride + obs[k]]));
+  red[threadIdx.x] = md;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) red[threadIdx.x] = fmax(red[threadIdx.x], red[threadIdx.x + w]);
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) dprev[s] = red[0];
+}
+
+cudaError_t launch_delta_obs(const double* du, int64_t stride, const int32_t* obs, int n_obs, double* dprev,
+                             int batch, cudaStream_t st) {
+  k_delta_obs<<<batch, 256, 0, st>>>(du, stride, obs, n_obs, dprev);
+  return cudaGetLastError();
+}
+
+// Last refinement step: u_obs = u[obs] + du[obs].  The error left after this
+// update is estimated from the observed contraction, d_K * min(1, d_K / d_{K-1})
+// with d = max_k |du_k| (d_{K-1} = 0, i.e. no contraction credit, after a single
+// step); a sample whose estimate exceeds tol * max_k |u_obs_k| is marked HDD_ENOCONV.
+__global__ void k_final_obs(const double* __restrict__ u, const double* __restrict__ du, int64_t stride,
+                            const int32_t* __restrict__ obs, int n_obs, double tol, const double* __restrict__ dprev,
+                            double* __restrict__ u_obs, int32_t* status) {
+  __shared__ double red_d[256], red_u[256];
+  const int s = blockIdx.x;
+  double md = 0.0, mu = 0.0;
+  for (int k = threadIdx.x; k < n_obs; k += blockDim.x) {
+    const double d = du ? du[(int64_t)s * stride + obs[k]] : 0.0;
+    const double v = u[(int64_t)s * stride + obs[k]] + d;
+    u_obs[(int64_t)s * n_obs + k] = v;
+    md = fmax(md, fabs(d));
+    mu = fmax(mu, fabs(v));
+  }
+  red_d[threadIdx.x] = md;
+  red_u[threadIdx.x] = mu;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) {
+      red_d[threadIdx.x] = fmax(red_d[threadIdx.x], red_d[threadIdx.x + w]);
+      red_u[threadIdx.x] = fmax(red_u[threadIdx.x], red_u[threadIdx.x + w]);
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0 && tol >= 0.0) {
+    const double dK = red_d[0], dp = dprev ? dprev[s] : 0.0;
+    const double est = (dp > 0.0) ? dK * fmin(1.0, dK / dp) : dK;
+    if (!(est <= tol * red_u[0])) flag_status(status, s, -HDD_ENOCONV, 0);
+  }
+}
+
+cudaError_t launch_final_obs(const double* u, const double* du, int64_t stride, const int32_t* obs, int n_obs,
+                             double tol, const double* dprev, double* u_obs, int32_t* status, int batch,
+                             cudaStream_t st) {
+  k_final_obs<<<batch, 256, 0, st>>>(u, du, stride, obs, n_obs, tol, dprev, u_obs, status);
+  return cudaGetLastError();
+}
+
+cudaError_t configure_refine_kernels() {
+  const int lim = 227 * 1024;
+  cudaError_t e;
+  if ((e = cudaFuncSetAttribute(k_forward<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
+  if ((e = cudaFuncSetAttribute(k_forward<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
+  return cudaSuccess;
+}
+
+}  // namespace hdd

@@ -37,6 +37,19 @@ template <typename T>
 cudaError_t launch_descent(const NodeDev* nodes, const int32_t* maps, const int32_t* list, int nlist, int batch,
                            const Arenas& A, double* u, int64_t u_stride, int max_b, int max_m, cudaStream_t st);
 
+// iterative refinement (mixed precision)
+template <typename T>
+cudaError_t launch_forward(const NodeDev* nodes, const int32_t* maps, const int32_t* list, int nlist, int batch,
+                           const Arenas& A, const Rhs& rhs, int max_nf, cudaStream_t st);
+cudaError_t launch_residual(const double* kappa, int64_t kap_stride, const double* u, int64_t u_stride, int N,
+                            double load, double* r, int batch, cudaStream_t st);
+cudaError_t launch_update(double* u, const double* du, int64_t stride, int N, int batch, cudaStream_t st);
+cudaError_t launch_delta_obs(const double* du, int64_t stride, const int32_t* obs, int n_obs, double* dprev,
+                             int batch, cudaStream_t st);
+cudaError_t launch_final_obs(const double* u, const double* du, int64_t stride, const int32_t* obs, int n_obs,
+                             double tol, const double* dprev, double* u_obs, int32_t* status, int batch,
+                             cudaStream_t st);
+
 cudaError_t launch_gather_obs(const double* u, int64_t u_stride, const int32_t* obs, int n_obs, int batch,
                               double* u_obs, cudaStream_t st);
 cudaError_t launch_loglik(const double* u_obs, int n_obs, int batch, const double* y, int y_per_sample, double sigma,

@@ -93,10 +93,12 @@ std::string build_plan(const hdd_plan_desc& d, Plan& p) {
   if (!(d.sigma > 0.0)) return "sigma must be > 0";
   if (d.precision != HDD_FP64 && d.precision != HDD_MIXED_FP32) return "unknown precision";
   if (d.ir_max_iter < 0 || d.ir_max_iter > 64) return "ir_max_iter must be in 0..64";
+  if (d.fp64_top_levels < 0 || d.fp64_top_levels > 64) return "fp64_top_levels must be in 0..64";
   p.N = d.N; p.leaf = d.leaf; p.n_z = d.n_z; p.n_obs = d.n_obs;
   p.n_t = 2 * (d.N - 1) * (d.N - 1);
   p.f = d.f; p.sigma = d.sigma; p.h = 1.0 / (d.N - 1);
   p.precision = d.precision; p.ir_max_iter = d.ir_max_iter; p.ir_tol = d.ir_tol;
+  p.fp64_top_levels = d.fp64_top_levels;
   p.device = d.device;
   p.obs.assign(d.obs_vertex, d.obs_vertex + d.n_obs);
   for (int v : p.obs) {
@@ -128,8 +130,8 @@ std::string build_plan(const hdd_plan_desc& d, Plan& p) {
     }
   }
 
-  // precision per node: mixed plans keep no FP64 node in this version
-  for (Node& nd : p.nodes) nd.fp64 = (p.precision == HDD_FP64);
+  // precision per node: mixed plans factorise the top fp64_top_levels depths in FP64
+  for (Node& nd : p.nodes) nd.fp64 = (p.precision == HDD_FP64) || nd.depth < p.fp64_top_levels;
 
   // stats, schedule
   p.n_leaves = 0; p.depth = 0; p.n_visited = 0; p.max_front = 0;
@@ -265,6 +267,14 @@ std::string build_plan(const hdd_plan_desc& d, Plan& p) {
     const Step& st = p.steps[hgt];
     p.step_lists[hgt] = {add_list(st.small64), add_list(st.large64), add_list(st.small32), add_list(st.large32)};
   }
+  p.fwd_lists.assign(p.height + 1, {0, 0});
+  for (int hgt = 0; hgt <= p.height; ++hgt) {
+    const Step& st = p.steps[hgt];
+    std::vector<int> l64(st.small64), l32(st.small32);
+    l64.insert(l64.end(), st.large64.begin(), st.large64.end());
+    l32.insert(l32.end(), st.large32.begin(), st.large32.end());
+    p.fwd_lists[hgt] = {add_list(l64), add_list(l32)};
+  }
   p.down_vis_lists.assign(p.depth + 1, 0);
   p.down_all_lists.assign(p.depth + 1, 0);
   for (int d = 0; d <= p.depth; ++d) {
@@ -304,7 +314,7 @@ Layout layout(const Plan& p, int batch) {
   auto take = [&](size_t bytes) { size_t o = off; off = align256(off + bytes); return o; };
   const size_t B = (size_t)batch, NN = (size_t)p.N * p.N;
   L.status = take(B * 4);
-  L.conv = take(B * 4);
+  L.conv = take(B * 8);
   L.kappa = take(B * p.n_t * 8);
   L.u = take(B * NN * 8);
   if (p.precision == HDD_MIXED_FP32) {

@@ -61,7 +61,7 @@ struct Step {
 struct Plan {
   // problem
   int N = 0, leaf = 0, n_z = 0, n_obs = 0, n_t = 0, device = -1;
-  int precision = HDD_FP64, ir_max_iter = 0;
+  int precision = HDD_FP64, ir_max_iter = 0, fp64_top_levels = 0;
   double f = 1.0, sigma = 1.0, h = 0.0, ir_tol = 1e-10;
   std::vector<int32_t> obs;
 
@@ -86,6 +86,7 @@ struct Plan {
   std::vector<ListInfo> lists;
   std::vector<std::array<int, 4>> step_lists;   // [height][small64, large64, small32, large32]
   std::vector<int> down_vis_lists, down_all_lists;   // [depth]
+  std::vector<std::array<int, 2>> fwd_lists;         // [height][fp64, fp32]: right-hand-side sweep
 
   // device copies
   double* d_phi = nullptr;

@@ -1,0 +1,91 @@
+"""GPU parity of the mixed-precision path (FP32 Schur factorisation, FP64 residual,
+iterative refinement) against the FP64 oracle.
+
+Tolerance after refinement (stated by the target of this path): 1e-8 relative
+per result, max_k |u_k - u_k^oracle| / max_k |u_k^oracle| and
+|loglik - loglik^oracle| / |loglik^oracle|.
+"""
+import numpy as np
+import pytest
+
+import workload as w
+from tests.gpu_common import interior, oracle_eval, oracle_full, rel_err_field, rel_err_scalar, small_problem
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-8
+
+
+@pytest.fixture(scope="module")
+def hdd():
+    from paper_1708_02207_gb300 import build, hdd as binding
+    build.build()
+    return binding
+
+
+def gpu_eval(hdd, N, leaf, phi, obs, Z, y, sigma, **kw):
+    kw.setdefault("precision", hdd.HDD_MIXED_FP32)
+    plan = hdd.Plan(N, leaf, phi, obs, sigma, **kw)
+    ll, u_obs, st = plan.evaluate(torch.from_numpy(np.ascontiguousarray(Z)).cuda(),
+                                  torch.from_numpy(np.ascontiguousarray(y)).cuda())
+    torch.cuda.synchronize()
+    return ll.cpu().numpy(), u_obs.cpu().numpy(), st.cpu().numpy()
+
+
+def test_grid33_mixed(hdd):
+    cfg = w.CONFIGS["grid33"]
+    prob = w.make_problem(cfg, batch=4)
+    ll, u, st = gpu_eval(hdd, cfg.N, cfg.leaf, prob.phi, prob.obs, prob.Z, prob.y, cfg.sigma, ir_max_iter=2)
+    u_ref, ll_ref = oracle_eval(cfg.N, prob.phi, prob.Z, prob.obs, prob.y, cfg.sigma)
+    assert (st == 0).all()
+    assert rel_err_field(u, u_ref).max() <= TOL
+    assert rel_err_scalar(ll, ll_ref).max() <= TOL
+
+
+@pytest.mark.parametrize("N,leaf,top", [(65, 4, 0), (129, 8, 0), (129, 8, 2), (50, 5, 1)])
+def test_full_field_mixed(hdd, N, leaf, top):
+    phi, Z = small_problem(N, n_z=20, corr_len=0.2, variance=2.0, batch=3, seed=N + top)
+    obs = interior(N)
+    _, u, st = gpu_eval(hdd, N, leaf, phi, obs, Z, np.zeros(obs.size), 0.1, ir_max_iter=3, fp64_top_levels=top)
+    ref = oracle_full(N, phi, Z)[:, obs]
+    assert (st == 0).all()
+    assert rel_err_field(u, ref).max() <= TOL
+
+
+def test_refinement_contracts(hdd):
+    # each refinement step multiplies the error by the contraction factor of the
+    # FP32 factorisation; no refinement leaves an FP32-sized error
+    N = 129
+    phi, Z = small_problem(N, n_z=20, corr_len=0.2, variance=2.0, batch=2, seed=7)
+    obs = w.obs_vertices(N, 8)
+    ref, _ = oracle_eval(N, phi, Z, obs, np.zeros(obs.size), 0.1)
+    errs = []
+    for K in (0, 1, 2, 3):
+        _, u, _ = gpu_eval(hdd, N, 8, phi, obs, Z, np.zeros(obs.size), 0.1, ir_max_iter=K, ir_tol=1.0)
+        errs.append(rel_err_field(u, ref).max())
+    assert 1e-9 < errs[0] < 1e-3
+    assert errs[1] < 0.1 * errs[0] and errs[2] < 0.1 * errs[1]
+    assert errs[3] <= TOL
+
+
+def test_no_convergence_is_flagged(hdd):
+    N = 33
+    phi, Z = small_problem(N, batch=2, seed=9)
+    obs = w.obs_vertices(N, 3)
+    ll, _, st = gpu_eval(hdd, N, 8, phi, obs, Z, np.zeros(obs.size), 0.1, ir_max_iter=1, ir_tol=0.0)
+    assert ((st & 0xFF) == -hdd.HDD_ENOCONV).all() and np.isneginf(ll).all()
+
+
+def test_grid513_full_batch_mixed_sampled(hdd):
+    cfg = w.CONFIGS["grid513"]
+    prob = w.make_problem(cfg)
+    plan = hdd.Plan(cfg.N, cfg.leaf, prob.phi, prob.obs, cfg.sigma, precision=hdd.HDD_MIXED_FP32, ir_max_iter=2)
+    ll, u, st = plan.evaluate(torch.from_numpy(prob.Z).cuda(), torch.from_numpy(prob.y).cuda())
+    ll, u, st = ll.cpu().numpy(), u.cpu().numpy(), st.cpu().numpy()
+    torch.cuda.empty_cache()
+    assert (st == 0).all()
+    samples = [0, 128, 255]
+    u_ref, ll_ref = oracle_eval(cfg.N, prob.phi, prob.Z[samples], prob.obs, prob.y, cfg.sigma)
+    assert rel_err_field(u[samples], u_ref).max() <= TOL
+    assert rel_err_scalar(ll[samples], ll_ref).max() <= TOL
