@@ -15,6 +15,7 @@ namespace hdd {
 cudaError_t configure_front_kernels();
 cudaError_t configure_solve_kernels();
 cudaError_t configure_refine_kernels();
+cudaError_t configure_warp_kernels();
 }  // namespace hdd
 
 namespace {
@@ -55,6 +56,7 @@ cudaError_t configure_device(int dev) {
   cudaError_t e = hdd::configure_front_kernels();
   if (e == cudaSuccess) e = hdd::configure_solve_kernels();
   if (e == cudaSuccess) e = hdd::configure_refine_kernels();
+  if (e == cudaSuccess) e = hdd::configure_warp_kernels();
   if (e == cudaSuccess) g_configured[dev] = true;
   return e;
 }
@@ -117,7 +119,7 @@ cudaError_t run_upsweep(const hdd::Plan& p, int batch, void* ws, const hdd::Rhs&
   a.arenas = arenas(p, L, ws);
   a.status = reinterpret_cast<int32_t*>(w + L.status);
   for (int h = 0; h <= p.height; ++h) {
-    for (int kind = 0; kind < 4; ++kind) {
+    for (int kind = 0; kind < 6; ++kind) {
       const hdd::ListInfo& li = p.lists[p.step_lists[h][kind]];
       if (li.n == 0) continue;
       a.list = p.d_lists + li.off;
@@ -127,9 +129,11 @@ cudaError_t run_upsweep(const hdd::Plan& p, int batch, void* ws, const hdd::Rhs&
       a.max_b = li.max_b;
       cudaError_t e;
       switch (kind) {
-        case 0: e = hdd::launch_front_small<double>(a, st); break;
-        case 1: e = hdd::launch_front_large<double>(a, st); break;
-        case 2: e = hdd::launch_front_small<float>(a, st); break;
+        case 0: e = hdd::launch_front_warp<double>(a, st); break;
+        case 1: e = hdd::launch_front_small<double>(a, st); break;
+        case 2: e = hdd::launch_front_large<double>(a, st); break;
+        case 3: e = hdd::launch_front_warp<float>(a, st); break;
+        case 4: e = hdd::launch_front_small<float>(a, st); break;
         default: e = hdd::launch_front_large<float>(a, st); break;
       }
       if (e != cudaSuccess) return e;
@@ -149,10 +153,10 @@ cudaError_t run_descent(const hdd::Plan& p, int batch, void* ws, const std::vect
     if (li.n == 0) continue;
     // the lists hold one precision per depth in the plans built here
     const bool fp64 = p.nodes[p.list_data[li.off]].fp64;
-    cudaError_t e = fp64 ? hdd::launch_descent<double>(p.d_nodes, p.d_maps, p.d_lists + li.off, li.n, batch, A, u,
-                                                       NN, li.max_b, li.max_m, st)
-                         : hdd::launch_descent<float>(p.d_nodes, p.d_maps, p.d_lists + li.off, li.n, batch, A, u,
-                                                      NN, li.max_b, li.max_m, st);
+    cudaError_t e = fp64 ? hdd::launch_descent_warp<double>(p.d_nodes, p.d_maps, p.d_lists + li.off, li.n, batch, A,
+                                                            u, NN, li.max_nf, st)
+                         : hdd::launch_descent_warp<float>(p.d_nodes, p.d_maps, p.d_lists + li.off, li.n, batch, A,
+                                                           u, NN, li.max_nf, st);
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;
@@ -166,10 +170,10 @@ cudaError_t run_forward(const hdd::Plan& p, int batch, void* ws, const hdd::Rhs&
     for (int k = 0; k < 2; ++k) {
       const hdd::ListInfo& li = p.lists[p.fwd_lists[h][k]];
       if (li.n == 0) continue;
-      cudaError_t e = k == 0 ? hdd::launch_forward<double>(p.d_nodes, p.d_maps, p.d_lists + li.off, li.n, batch, A,
-                                                           rhs, li.max_nf, st)
-                             : hdd::launch_forward<float>(p.d_nodes, p.d_maps, p.d_lists + li.off, li.n, batch, A,
-                                                          rhs, li.max_nf, st);
+      cudaError_t e = k == 0 ? hdd::launch_forward_warp<double>(p.d_nodes, p.d_maps, p.d_lists + li.off, li.n, batch,
+                                                                A, rhs, li.max_nf, st)
+                             : hdd::launch_forward_warp<float>(p.d_nodes, p.d_maps, p.d_lists + li.off, li.n, batch,
+                                                               A, rhs, li.max_nf, st);
       if (e != cudaSuccess) return e;
     }
   return cudaSuccess;
@@ -407,9 +411,9 @@ hdd_status hdd_plan_info(hdd_plan_t plan, hdd_plan_info_t* info) {
   info->schur_bytes = (double)p.s64_stride * 8 + (double)p.s32_stride * 4;
   int up = 0, down = 0;
   for (int h = 0; h <= p.height; ++h)
-    for (int kind = 0; kind < 4; ++kind) {
+    for (int kind = 0; kind < 6; ++kind) {
       const hdd::ListInfo& li = p.lists[p.step_lists[h][kind]];
-      if (li.n) up += (kind == 1 || kind == 3) ? 4 : 1;
+      if (li.n) up += (kind == 2 || kind == 5) ? 4 : 1;
     }
   int down_all = 0, fwd = 0;
   for (int d = 0; d <= p.depth; ++d) {

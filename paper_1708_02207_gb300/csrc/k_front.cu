@@ -37,11 +37,31 @@ __device__ __forceinline__ double front_entry(int r, int c, int s, int node, con
 }
 
 // ---------------------------------------------------------------------------
-// Small fronts: the whole front lives in shared memory (column-major, ld nf).
-// One CTA per (node, sample).  Right-looking partial Cholesky of the first m
-// columns with one barrier per column: step k updates the trailing lower
-// triangle with the unscaled column k divided by the pivot and, in the same
-// phase, scales column k-1 (which no thread reads any more).
+// Fronts of 33..kSmallMax rows: the whole front lives in shared memory
+// (column-major, ld nf), one CTA per (node, sample).  Fathers are assembled by
+// scattering each son's lower Schur triangle (read column by column, coalesced)
+// through the son's up map; sons one after the other, then the gamma loads.
+// Partial Cholesky: per column k, scale column k, then one warp per trailing
+// column j updates rows j..nf-1 (contiguous, conflict-free) with l_j.
+template <typename T>
+__device__ __forceinline__ void scatter_son(T* K, int nf, const NodeDev& ch, const int32_t* maps, const Arenas& A,
+                                            int s) {
+  const int ldc = ch.b + 1;
+  const int32_t* up = maps + ch.up_off;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarp = blockDim.x >> 5;
+  const int64_t base = (int64_t)s * (ch.fp64 ? A.s64_stride : A.s32_stride) + ch.s_off;
+  for (int cc = warp; cc < ldc; cc += nwarp) {
+    const int pc = up[cc];
+    for (int aa = cc + lane; aa < ldc; aa += 32) {
+      const int64_t idx = base + (int64_t)cc * ldc + aa;
+      const T val = ch.fp64 ? (T)A.s64[idx] : (T)A.s32[idx];
+      const int pr = up[aa];
+      const int r = max(pr, pc), c = min(pr, pc);
+      K[c * nf + r] += val;
+    }
+  }
+}
+
 template <typename T>
 __global__ void k_front_small(StepArgs a) {
   const int node = a.list[blockIdx.x];
@@ -50,13 +70,23 @@ __global__ void k_front_small(StepArgs a) {
   const int nf = nd.nf, m = nd.m;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* K = reinterpret_cast<T*>(smem_raw);
-  T* piv = K + nf * nf;     // sqrt of the pivots (diagonal of L)
   const int32_t* map = a.maps + nd.map_off;
-  const double* kap = a.kappa + (int64_t)s * a.kap_stride;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarp = blockDim.x >> 5;
 
-  for (int idx = threadIdx.x; idx < nf * nf; idx += blockDim.x) {
-    const int c = idx / nf, r = idx - c * nf;
-    K[idx] = (r >= c) ? (T)front_entry(r, c, s, node, nd, a.nodes, map, kap, a.N, a.rhs, a.arenas) : (T)0;
+  if (nd.leaf) {
+    const double* kap = a.kappa + (int64_t)s * a.kap_stride;
+    for (int idx = threadIdx.x; idx < nf * nf; idx += blockDim.x) {
+      const int c = idx / nf, r = idx - c * nf;
+      K[idx] = (r >= c) ? (T)leaf_entry(r, c, s, nd, map, kap, a.N, a.rhs) : (T)0;
+    }
+  } else {
+    for (int idx = threadIdx.x; idx < nf * nf; idx += blockDim.x) K[idx] = (T)0;
+    __syncthreads();
+    scatter_son<T>(K, nf, a.nodes[nd.child0], a.maps, a.arenas, s);
+    __syncthreads();
+    scatter_son<T>(K, nf, a.nodes[nd.child1], a.maps, a.arenas, s);
+    __syncthreads();
+    for (int c = threadIdx.x; c < m; c += blockDim.x) K[c * nf + nf - 1] += (T)a.rhs(s, map[c]);
   }
   for (int k = 0; k < m; ++k) {
     __syncthreads();
@@ -65,45 +95,32 @@ __global__ void k_front_small(StepArgs a) {
       if (threadIdx.x == 0) flag_status(a.status, s, -HDD_ENOTSPD, node);
       p = (T)1;
     }
-    if (threadIdx.x == 0) piv[k] = sqrt(p);
-    const T rp = (T)1 / p;
-    const T* colk = K + k * nf;
-    const int n = nf - k - 1;
-    for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
-      const int jj = idx / n, ii = idx - jj * n;
-      if (ii < jj) continue;
-      const int i = k + 1 + ii, j = k + 1 + jj;
-      K[j * nf + i] -= colk[i] * (colk[j] * rp);
+    const T d = sqrt(p), inv = (T)1 / d;
+    T* colk = K + k * nf;
+    for (int i = k + 1 + threadIdx.x; i < nf; i += blockDim.x) colk[i] *= inv;
+    __syncthreads();
+    if (threadIdx.x == 0) colk[k] = d;
+    for (int j = k + 1 + warp; j < nf; j += nwarp) {
+      const T lj = colk[j];
+      T* colj = K + j * nf;
+      for (int i = j + lane; i < nf; i += 32) colj[i] -= colk[i] * lj;
     }
-    if (k > 0) {
-      const int c = k - 1;
-      const T d = piv[c], rd = (T)1 / d;
-      for (int i = c + threadIdx.x; i < nf; i += blockDim.x) K[c * nf + i] = (i == c) ? d : K[c * nf + i] * rd;
-    }
-  }
-  __syncthreads();
-  if (m > 0) {
-    const int c = m - 1;
-    const T d = piv[c], rd = (T)1 / d;
-    for (int i = c + threadIdx.x; i < nf; i += blockDim.x) K[c * nf + i] = (i == c) ? d : K[c * nf + i] * rd;
   }
   __syncthreads();
   T* F = node_F<T>(a.arenas, nd, s);
   for (int idx = threadIdx.x; idx < m * nf; idx += blockDim.x) F[idx] = K[idx];
   const int nb = nd.b + 1;
   T* S = node_S<T>(a.arenas, nd, s);
-  for (int idx = threadIdx.x; idx < nb * nb; idx += blockDim.x) {
-    const int c = idx / nb, r = idx - c * nb;
-    S[idx] = K[(m + c) * nf + m + r];
-  }
+  for (int c = warp; c < nb; c += nwarp)
+    for (int r = c + lane; r < nb; r += 32) S[c * nb + r] = K[(m + c) * nf + m + r];
 }
 
-static int small_threads(int nf) { return nf <= 40 ? 64 : (nf <= 96 ? 128 : 256); }
+static int small_threads(int nf) { return nf <= 64 ? 128 : 256; }
 
 template <typename T>
 cudaError_t launch_front_small(const StepArgs& a, cudaStream_t st) {
   if (a.nlist == 0) return cudaSuccess;
-  const size_t smem = ((size_t)a.max_nf * a.max_nf + a.max_nf) * sizeof(T);
+  const size_t smem = (size_t)a.max_nf * a.max_nf * sizeof(T);
   dim3 grid(a.nlist, a.batch);
   k_front_small<T><<<grid, small_threads(a.max_nf), smem, st>>>(a);
   return cudaGetLastError();

@@ -1,0 +1,283 @@
+// Warp-per-front kernels: fronts of at most 32 rows held in registers (one row
+// per lane), and the right-hand-side / descent sweeps with one warp per
+// (node, sample).  A CTA of 8 warps serves 8 samples of the same node, which
+// share the node's index maps.
+#include "launch.h"
+
+namespace hdd {
+
+constexpr unsigned kFull = 0xffffffffu;
+
+template <typename T> __device__ __forceinline__ T* warp_F(const Arenas& A, const NodeDev& nd, int s);
+template <> __device__ __forceinline__ double* warp_F<double>(const Arenas& A, const NodeDev& nd, int s) {
+  return A.f64 + (int64_t)s * A.f64_stride + nd.f_off;
+}
+template <> __device__ __forceinline__ float* warp_F<float>(const Arenas& A, const NodeDev& nd, int s) {
+  return A.f32 + (int64_t)s * A.f32_stride + nd.f_off;
+}
+template <typename T> __device__ __forceinline__ T* warp_S(const Arenas& A, const NodeDev& nd, int s);
+template <> __device__ __forceinline__ double* warp_S<double>(const Arenas& A, const NodeDev& nd, int s) {
+  return A.s64 + (int64_t)s * A.s64_stride + nd.s_off;
+}
+template <> __device__ __forceinline__ float* warp_S<float>(const Arenas& A, const NodeDev& nd, int s) {
+  return A.s32 + (int64_t)s * A.s32_stride + nd.s_off;
+}
+
+// ---------------------------------------------------------------------------
+// Fronts with nf <= 32: lane r holds row r of the (symmetric) front.  Build
+// (leaf stiffness, or the sons' Schur complements through the gather maps),
+// partial Cholesky of the first m columns with shuffles (column k of L is
+// broadcast entry by entry), then the factor columns and the Schur block are
+// written with coalesced stores.
+template <typename T>
+__global__ void __launch_bounds__(256) k_front_warp(StepArgs a) {
+  const int node = a.list[blockIdx.x];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int s = blockIdx.y * 8 + warp;
+  if (s >= a.batch) return;
+  const NodeDev nd = a.nodes[node];
+  const int nf = nd.nf, m = nd.m, nb = nd.b + 1;
+  const int N = a.N;
+  const int32_t* map = a.maps + nd.map_off;
+  const int v = (lane < nf - 1) ? map[lane] : -1;
+  const double rv = (lane < m) ? a.rhs(s, v) : 0.0;   // load of this lane's vertex if it is eliminated here
+  T row[32];
+#pragma unroll
+  for (int c = 0; c < 32; ++c) row[c] = (T)0;
+  if (nd.leaf) {
+    const double* kap = a.kappa + (int64_t)s * a.kap_stride;
+    int vi = -7, vj = -7;
+    double wl = 0.0, wr = 0.0, wd = 0.0, wu = 0.0;
+    if (v >= 0) {
+      vi = v % N;
+      vj = v / N;
+      wl = w_horizontal(kap, N, nd, vi - 1, vj);
+      wr = w_horizontal(kap, N, nd, vi, vj);
+      wd = w_vertical(kap, N, nd, vi, vj - 1);
+      wu = w_vertical(kap, N, nd, vi, vj);
+    }
+#pragma unroll
+    for (int c = 0; c < 32; ++c) {
+      const int ci = __shfl_sync(kFull, vi, c), cj = __shfl_sync(kFull, vj, c);
+      const double rc = __shfl_sync(kFull, rv, c);
+      double val = 0.0;
+      if (c < nf && lane < nf) {
+        if (lane == nf - 1) {
+          val = (c < m) ? rc : 0.0;
+        } else if (c == nf - 1) {
+          val = rv;
+        } else if (c == lane) {
+          val = wl + wr + wd + wu;
+        } else if (cj == vj && ci == vi - 1) {
+          val = -wl;
+        } else if (cj == vj && ci == vi + 1) {
+          val = -wr;
+        } else if (ci == vi && cj == vj - 1) {
+          val = -wd;
+        } else if (ci == vi && cj == vj + 1) {
+          val = -wu;
+        }
+      }
+      row[c] = (T)val;
+    }
+  } else {
+    const int32_t* pos0 = map + (nf - 1);
+    const int32_t* pos1 = pos0 + nf;
+    const NodeDev c0 = a.nodes[nd.child0], c1 = a.nodes[nd.child1];
+    const int p0 = (lane < nf) ? pos0[lane] : -1, p1 = (lane < nf) ? pos1[lane] : -1;
+#pragma unroll
+    for (int c = 0; c < 32; ++c) {
+      const int q0 = __shfl_sync(kFull, p0, c), q1 = __shfl_sync(kFull, p1, c);
+      const double rc = __shfl_sync(kFull, rv, c);
+      double val = 0.0;
+      if (p0 >= 0 && q0 >= 0) val += son_entry(a.arenas, c0, s, p0, q0);
+      if (p1 >= 0 && q1 >= 0) val += son_entry(a.arenas, c1, s, p1, q1);
+      if (lane == nf - 1 && c < m) val += rc;
+      if (c == nf - 1 && lane < m) val += rv;
+      row[c] = (T)val;
+    }
+  }
+  bool bad = false;
+#pragma unroll
+  for (int k = 0; k < 32; ++k) {
+    if (k < m) {
+      T pk = __shfl_sync(kFull, row[k], k);
+      if (!(pk > (T)0) || !isfinite(pk)) {
+        bad = true;
+        pk = (T)1;
+      }
+      const T d = sqrt(pk), inv = (T)1 / d;
+      T lk = (lane == k) ? d : row[k] * inv;
+      if (lane < k) lk = (T)0;
+#pragma unroll
+      for (int j = k + 1; j < 32; ++j) {
+        const T lj = __shfl_sync(kFull, lk, j);
+        if (lane > k) row[j] -= lk * lj;
+      }
+      row[k] = lk;
+    }
+  }
+  if (bad && lane == 0) flag_status(a.status, s, -HDD_ENOTSPD, node);
+  T* F = warp_F<T>(a.arenas, nd, s);
+#pragma unroll
+  for (int c = 0; c < 32; ++c)
+    if (c < m && lane < nf) F[c * nf + lane] = row[c];
+  T* S = warp_S<T>(a.arenas, nd, s);
+#pragma unroll
+  for (int c = 0; c < 32; ++c)
+    if (c >= m && c < nf && lane >= m && lane < nf) S[(c - m) * nb + (lane - m)] = row[c];
+}
+
+template <typename T>
+cudaError_t launch_front_warp(const StepArgs& a, cudaStream_t st) {
+  if (a.nlist == 0) return cudaSuccess;
+  k_front_warp<T><<<dim3(a.nlist, (a.batch + 7) / 8), 256, 0, st>>>(a);
+  return cudaGetLastError();
+}
+template cudaError_t launch_front_warp<double>(const StepArgs&, cudaStream_t);
+template cudaError_t launch_front_warp<float>(const StepArgs&, cudaStream_t);
+
+// Warps per CTA of the sweeps: 8, or fewer when a warp's vector of nf entries
+// would not fit the shared memory of 8 warps.
+static int sweep_warps(size_t bytes_per_warp) {
+  const size_t lim = 227 * 1024;
+  int w = 8;
+  while (w > 1 && (size_t)w * bytes_per_warp > lim) --w;
+  return w;
+}
+
+// ---------------------------------------------------------------------------
+// Right-hand-side sweep at one node (leaves to root), one warp per sample:
+// z = sons' condensed right-hand sides + r at gamma; y = L_gg^-1 z_g column by
+// column (coalesced down each column of F), folding every column into the rows
+// below it, which leaves z_B - L_Bg y_g.
+template <typename T>
+__device__ __forceinline__ double son_cond(const Arenas& A, const NodeDev& ch, int s, int p) {
+  const int64_t idx = (int64_t)p * (ch.b + 1) + ch.b + ch.s_off;
+  return ch.fp64 ? A.s64[(int64_t)s * A.s64_stride + idx] : (double)A.s32[(int64_t)s * A.s32_stride + idx];
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_forward_warp(const NodeDev* __restrict__ nodes,
+                                                      const int32_t* __restrict__ maps,
+                                                      const int32_t* __restrict__ list, int batch, int zstride,
+                                                      Arenas A, Rhs rhs) {
+  const int node = list[blockIdx.x];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int s = blockIdx.y * (blockDim.x >> 5) + warp;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* z = reinterpret_cast<T*>(smem_raw) + warp * zstride;
+  if (s >= batch) return;
+  const NodeDev nd = nodes[node];
+  const int m = nd.m, b = nd.b, nf = nd.nf;
+  const int32_t* vid = maps + nd.map_off;
+  T* F = warp_F<T>(A, nd, s);
+  if (nd.leaf) {
+    for (int r = lane; r < nf - 1; r += 32) z[r] = (r < m) ? (T)rhs(s, vid[r]) : (T)0;
+  } else {
+    const NodeDev c0 = nodes[nd.child0], c1 = nodes[nd.child1];
+    const int32_t* pos0 = vid + (nf - 1);
+    const int32_t* pos1 = pos0 + nf;
+    for (int r = lane; r < nf - 1; r += 32) {
+      double val = (r < m) ? rhs(s, vid[r]) : 0.0;
+      const int q0 = pos0[r], q1 = pos1[r];
+      if (q0 >= 0) val += son_cond<T>(A, c0, s, q0);
+      if (q1 >= 0) val += son_cond<T>(A, c1, s, q1);
+      z[r] = (T)val;
+    }
+  }
+  __syncwarp();
+  for (int c = 0; c < m; ++c) {
+    const T* col = F + (int64_t)c * nf;
+    const T yc = z[c] / col[c];
+    for (int i = c + 1 + lane; i < nf - 1; i += 32) z[i] -= col[i] * yc;
+    __syncwarp();
+    if (lane == 0) z[c] = yc;
+    __syncwarp();
+  }
+  for (int c = lane; c < m; c += 32) F[(int64_t)c * nf + nf - 1] = z[c];
+  if (b > 0) {
+    T* S = warp_S<T>(A, nd, s);
+    for (int r = lane; r < b; r += 32) S[(int64_t)r * (b + 1) + b] = z[m + r];
+  }
+}
+
+template <typename T>
+cudaError_t launch_forward_warp(const NodeDev* nodes, const int32_t* maps, const int32_t* list, int nlist, int batch,
+                                const Arenas& A, const Rhs& rhs, int max_nf, cudaStream_t st) {
+  if (nlist == 0) return cudaSuccess;
+  const int zs = (max_nf + 1) & ~1;
+  const int wpb = sweep_warps(zs * sizeof(T));
+  k_forward_warp<T><<<dim3(nlist, (batch + wpb - 1) / wpb), 32 * wpb, (size_t)wpb * zs * sizeof(T), st>>>(
+      nodes, maps, list, batch, zs, A, rhs);
+  return cudaGetLastError();
+}
+template cudaError_t launch_forward_warp<double>(const NodeDev*, const int32_t*, const int32_t*, int, int,
+                                                 const Arenas&, const Rhs&, int, cudaStream_t);
+template cudaError_t launch_forward_warp<float>(const NodeDev*, const int32_t*, const int32_t*, int, int,
+                                                const Arenas&, const Rhs&, int, cudaStream_t);
+
+// ---------------------------------------------------------------------------
+// Descent at one node (Root to Leaves), one warp per sample: with w = [u_g; u_B]
+// (u_B gathered from the vertex vector), for c = m-1 .. 0
+//   u_c = (y_c - sum_{r > c} F[r, c] w_r) / F[c, c],
+// i.e. L_gg^T u_g = y_g - L_Bg^T u_B, each column of F read once, coalesced.
+template <typename T>
+__global__ void __launch_bounds__(256) k_descent_warp(const NodeDev* __restrict__ nodes,
+                                                      const int32_t* __restrict__ maps,
+                                                      const int32_t* __restrict__ list, int batch, int wstride,
+                                                      Arenas A, double* __restrict__ u, int64_t u_stride) {
+  const int node = list[blockIdx.x];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int s = blockIdx.y * (blockDim.x >> 5) + warp;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* wv = reinterpret_cast<T*>(smem_raw) + warp * wstride;
+  if (s >= batch) return;
+  const NodeDev nd = nodes[node];
+  const int m = nd.m, b = nd.b, nf = nd.nf;
+  const int32_t* vid = maps + nd.map_off;
+  const T* F = warp_F<T>(A, nd, s);
+  double* us = u + (int64_t)s * u_stride;
+  for (int i = lane; i < b; i += 32) wv[m + i] = (T)us[vid[m + i]];
+  __syncwarp();
+  for (int c = m - 1; c >= 0; --c) {
+    const T* col = F + (int64_t)c * nf;
+    T acc = (T)0;
+    for (int r = c + 1 + lane; r < nf - 1; r += 32) acc += col[r] * wv[r];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(kFull, acc, o);
+    const T uc = (col[nf - 1] - acc) / col[c];
+    if (lane == 0) wv[c] = uc;
+    __syncwarp();
+  }
+  for (int c = lane; c < m; c += 32) us[vid[c]] = (double)wv[c];
+}
+
+template <typename T>
+cudaError_t launch_descent_warp(const NodeDev* nodes, const int32_t* maps, const int32_t* list, int nlist, int batch,
+                                const Arenas& A, double* u, int64_t u_stride, int max_nf, cudaStream_t st) {
+  if (nlist == 0) return cudaSuccess;
+  const int ws = (max_nf + 1) & ~1;
+  const int wpb = sweep_warps(ws * sizeof(T));
+  k_descent_warp<T><<<dim3(nlist, (batch + wpb - 1) / wpb), 32 * wpb, (size_t)wpb * ws * sizeof(T), st>>>(
+      nodes, maps, list, batch, ws, A, u, u_stride);
+  return cudaGetLastError();
+}
+template cudaError_t launch_descent_warp<double>(const NodeDev*, const int32_t*, const int32_t*, int, int,
+                                                 const Arenas&, double*, int64_t, int, cudaStream_t);
+template cudaError_t launch_descent_warp<float>(const NodeDev*, const int32_t*, const int32_t*, int, int,
+                                                const Arenas&, double*, int64_t, int, cudaStream_t);
+
+}  // namespace hdd
+
+namespace hdd {
+cudaError_t configure_warp_kernels() {
+  const int lim = 227 * 1024;
+  cudaError_t e;
+  if ((e = cudaFuncSetAttribute(k_forward_warp<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
+  if ((e = cudaFuncSetAttribute(k_forward_warp<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
+  if ((e = cudaFuncSetAttribute(k_descent_warp<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
+  if ((e = cudaFuncSetAttribute(k_descent_warp<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
+  return cudaSuccess;
+}
+}  // namespace hdd

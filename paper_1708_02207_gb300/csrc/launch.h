@@ -27,6 +27,15 @@ struct StepArgs {
 cudaError_t launch_kappa(const double* phi, const double* Z, int n_t, int n_z, int batch, double* kappa,
                          int64_t kap_stride, cudaStream_t st);
 
+// fronts of at most 32 rows: one warp each, in registers
+template <typename T> cudaError_t launch_front_warp(const StepArgs& a, cudaStream_t st);
+// sweeps with one warp per (node, sample)
+template <typename T>
+cudaError_t launch_forward_warp(const NodeDev* nodes, const int32_t* maps, const int32_t* list, int nlist, int batch,
+                                const Arenas& A, const Rhs& rhs, int max_nf, cudaStream_t st);
+template <typename T>
+cudaError_t launch_descent_warp(const NodeDev* nodes, const int32_t* maps, const int32_t* list, int nlist, int batch,
+                                const Arenas& A, double* u, int64_t u_stride, int max_nf, cudaStream_t st);
 // fronts that fit in shared memory: build + partial Cholesky + store, one CTA each
 template <typename T> cudaError_t launch_front_small(const StepArgs& a, cudaStream_t st);
 // large fronts: fill in global memory, then POTRF of gamma, TRSM of the rest, SYRK into S

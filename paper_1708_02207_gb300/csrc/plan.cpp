@@ -151,10 +151,12 @@ std::string build_plan(const hdd_plan_desc& d, Plan& p) {
     Node& nd = p.nodes[k];
     Step& st = p.steps[nd.height];
     if (nd.fp64) {
-      if (nd.nf <= kSmallMax64) { st.small64.push_back(k); p.max_front_small64 = std::max(p.max_front_small64, nd.nf); }
+      if (nd.nf <= kTinyMax) st.tiny64.push_back(k);
+      else if (nd.nf <= kSmallMax64) { st.small64.push_back(k); p.max_front_small64 = std::max(p.max_front_small64, nd.nf); }
       else st.large64.push_back(k);
     } else {
-      if (nd.nf <= kSmallMax32) { st.small32.push_back(k); p.max_front_small32 = std::max(p.max_front_small32, nd.nf); }
+      if (nd.nf <= kTinyMax) st.tiny32.push_back(k);
+      else if (nd.nf <= kSmallMax32) { st.small32.push_back(k); p.max_front_small32 = std::max(p.max_front_small32, nd.nf); }
       else st.large32.push_back(k);
     }
     bool large = nd.nf > (nd.fp64 ? kSmallMax64 : kSmallMax32);
@@ -245,6 +247,24 @@ std::string build_plan(const hdd_plan_desc& d, Plan& p) {
     }
     if (p.maps.size() > (size_t)INT32_MAX) return "map table too large";
   }
+  // up maps: for every non-root node, the father-front row of each of its Schur
+  // rows (boundary unknowns, then the right-hand side)
+  for (int k = 0; k < nn; ++k) {
+    Node& nd = p.nodes[k];
+    nd.up_off = (int64_t)p.maps.size();
+    if (nd.parent < 0) continue;
+    const Node& pa = p.nodes[nd.parent];
+    std::map<int, int> prow;
+    for (int r = 0; r < pa.m; ++r) prow[pa.gamma[r]] = r;
+    for (int r = 0; r < pa.b; ++r) prow[pa.bnd[r]] = pa.m + r;
+    for (int a = 0; a < nd.b; ++a) {
+      auto it = prow.find(nd.bnd[a]);
+      if (it == prow.end()) return "internal: son boundary vertex missing in the father front";
+      p.maps.push_back(it->second);
+    }
+    p.maps.push_back(pa.nf - 1);
+    if (p.maps.size() > (size_t)INT32_MAX) return "map table too large";
+  }
 
   // concatenated node lists
   p.list_data.clear();
@@ -262,16 +282,19 @@ std::string build_plan(const hdd_plan_desc& d, Plan& p) {
     p.lists.push_back(li);
     return (int)p.lists.size() - 1;
   };
-  p.step_lists.assign(p.height + 1, {0, 0, 0, 0});
+  p.step_lists.assign(p.height + 1, {0, 0, 0, 0, 0, 0});
   for (int hgt = 0; hgt <= p.height; ++hgt) {
     const Step& st = p.steps[hgt];
-    p.step_lists[hgt] = {add_list(st.small64), add_list(st.large64), add_list(st.small32), add_list(st.large32)};
+    p.step_lists[hgt] = {add_list(st.tiny64), add_list(st.small64), add_list(st.large64),
+                         add_list(st.tiny32), add_list(st.small32), add_list(st.large32)};
   }
   p.fwd_lists.assign(p.height + 1, {0, 0});
   for (int hgt = 0; hgt <= p.height; ++hgt) {
     const Step& st = p.steps[hgt];
-    std::vector<int> l64(st.small64), l32(st.small32);
+    std::vector<int> l64(st.tiny64), l32(st.tiny32);
+    l64.insert(l64.end(), st.small64.begin(), st.small64.end());
     l64.insert(l64.end(), st.large64.begin(), st.large64.end());
+    l32.insert(l32.end(), st.small32.begin(), st.small32.end());
     l32.insert(l32.end(), st.large32.begin(), st.large32.end());
     p.fwd_lists[hgt] = {add_list(l64), add_list(l32)};
   }
@@ -291,6 +314,7 @@ std::string build_plan(const hdd_plan_desc& d, Plan& p) {
     d.child0 = nd.child[0]; d.child1 = nd.child[1];
     d.x0 = nd.x0; d.y0 = nd.y0; d.x1 = nd.x1; d.y1 = nd.y1;
     d.map_off = (int32_t)nd.map_off;
+    d.up_off = (int32_t)nd.up_off;
     d.fp64 = nd.fp64;
     d.f_off = nd.f_off; d.s_off = nd.s_off;
   }

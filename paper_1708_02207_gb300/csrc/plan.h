@@ -12,7 +12,7 @@
 
 namespace hdd {
 
-// Device-side node descriptor (64 bytes).  A node's front has nf = m + b + 1
+// Device-side node descriptor (72 bytes).  A node's front has nf = m + b + 1
 // rows: m eliminated vertices (gamma, or a leaf's interior), b boundary unknowns,
 // and one bordered right-hand-side row.  Per sample the front is stored as
 //   F: nf x m column-major (ld nf)      -> L_gg (rows < m), L_Bg, y_g^T (last row)
@@ -23,11 +23,13 @@ struct NodeDev {
   int32_t child0, child1;
   int32_t x0, y0, x1, y1;   // closed rectangle (vertex indices)
   int32_t map_off;          // ints into the map table: vid[nf-1], then pos0[nf], pos1[nf]
+  int32_t up_off;           // ints into the map table: father-front row of each Schur row [b+1]
   int32_t fp64;             // 1 if this node's factors are FP64 (mixed plans: top levels)
+  int32_t pad_;
   int64_t f_off;            // elements into a sample's factor store of the node's type
   int64_t s_off;            // elements into a sample's Schur arena of the node's type
 };
-static_assert(sizeof(NodeDev) == 64, "NodeDev layout");
+static_assert(sizeof(NodeDev) == 72, "NodeDev layout");
 
 struct Node {
   int x0, x1, y0, y1;
@@ -43,6 +45,7 @@ struct Node {
   int m = 0, b = 0, nf = 0;
   int64_t f_off = 0, s_off = 0;
   int64_t map_off = 0;
+  int64_t up_off = 0;
   bool leaf() const { return child[0] < 0; }
 };
 
@@ -55,7 +58,7 @@ struct ListInfo {
 
 // One upsweep step: all nodes of one height, split by front size and precision.
 struct Step {
-  std::vector<int> small64, large64, small32, large32;
+  std::vector<int> tiny64, small64, large64, tiny32, small32, large32;
 };
 
 struct Plan {
@@ -84,7 +87,7 @@ struct Plan {
   // node lists concatenated (host copy of d_lists) and their descriptors
   std::vector<int32_t> list_data;
   std::vector<ListInfo> lists;
-  std::vector<std::array<int, 4>> step_lists;   // [height][small64, large64, small32, large32]
+  std::vector<std::array<int, 6>> step_lists;   // [height][tiny64, small64, large64, tiny32, small32, large32]
   std::vector<int> down_vis_lists, down_all_lists;   // [depth]
   std::vector<std::array<int, 2>> fwd_lists;         // [height][fp64, fp32]: right-hand-side sweep
 
@@ -96,7 +99,9 @@ struct Plan {
   int32_t* d_obs = nullptr;
 };
 
-// Front sizes up to these limits run in shared memory (one CTA per front).
+// Fronts of at most kTinyMax rows run one per warp in registers; up to the
+// kSmallMax limits one per CTA in shared memory; larger ones in global memory.
+constexpr int kTinyMax = 32;
 constexpr int kSmallMax64 = 160;   // 160^2 * 8 B = 200 KiB
 constexpr int kSmallMax32 = 224;   // 224^2 * 4 B = 196 KiB
 
