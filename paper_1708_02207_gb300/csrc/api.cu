@@ -22,6 +22,10 @@ namespace {
 
 thread_local std::string g_err;
 
+// Sweeps over nodes whose interface has at least this many vertices use one CTA
+// per (node, sample) with blocked substitution; smaller nodes one warp each.
+constexpr int kSweepCtaMinM = 64;
+
 hdd_status fail_cuda(cudaError_t e, const char* where) {
   g_err = std::string(where) + ": " + cudaGetErrorString(e);
   return HDD_ECUDA;
@@ -114,6 +118,7 @@ cudaError_t run_upsweep(const hdd::Plan& p, int batch, void* ws, const hdd::Rhs&
   a.batch = batch;
   a.N = p.N;
   a.kappa = reinterpret_cast<const double*>(w + L.kappa);
+  a.kappa32 = L.kappa32 ? reinterpret_cast<const float*>(w + L.kappa32) : nullptr;
   a.kap_stride = p.n_t;
   a.rhs = rhs;
   a.arenas = arenas(p, L, ws);
@@ -153,10 +158,20 @@ cudaError_t run_descent(const hdd::Plan& p, int batch, void* ws, const std::vect
     if (li.n == 0) continue;
     // the lists hold one precision per depth in the plans built here
     const bool fp64 = p.nodes[p.list_data[li.off]].fp64;
-    cudaError_t e = fp64 ? hdd::launch_descent_warp<double>(p.d_nodes, p.d_maps, p.d_lists + li.off, li.n, batch, A,
-                                                            u, NN, li.max_nf, st)
-                         : hdd::launch_descent_warp<float>(p.d_nodes, p.d_maps, p.d_lists + li.off, li.n, batch, A,
-                                                           u, NN, li.max_nf, st);
+    // nodes with long interfaces: one CTA per (node, sample), blocked back substitution;
+    // otherwise one warp per (node, sample)
+    const bool cta = li.max_m >= kSweepCtaMinM;
+    cudaError_t e;
+    if (cta)
+      e = fp64 ? hdd::launch_descent<double>(p.d_nodes, p.d_maps, p.d_lists + li.off, li.n, batch, A, u, NN,
+                                             li.max_b, li.max_m, st)
+               : hdd::launch_descent<float>(p.d_nodes, p.d_maps, p.d_lists + li.off, li.n, batch, A, u, NN,
+                                            li.max_b, li.max_m, st);
+    else
+      e = fp64 ? hdd::launch_descent_warp<double>(p.d_nodes, p.d_maps, p.d_lists + li.off, li.n, batch, A, u, NN,
+                                                  li.max_nf, st)
+               : hdd::launch_descent_warp<float>(p.d_nodes, p.d_maps, p.d_lists + li.off, li.n, batch, A, u, NN,
+                                                 li.max_nf, st);
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;
@@ -170,10 +185,18 @@ cudaError_t run_forward(const hdd::Plan& p, int batch, void* ws, const hdd::Rhs&
     for (int k = 0; k < 2; ++k) {
       const hdd::ListInfo& li = p.lists[p.fwd_lists[h][k]];
       if (li.n == 0) continue;
-      cudaError_t e = k == 0 ? hdd::launch_forward_warp<double>(p.d_nodes, p.d_maps, p.d_lists + li.off, li.n, batch,
-                                                                A, rhs, li.max_nf, st)
-                             : hdd::launch_forward_warp<float>(p.d_nodes, p.d_maps, p.d_lists + li.off, li.n, batch,
-                                                               A, rhs, li.max_nf, st);
+      const bool cta = li.max_m >= kSweepCtaMinM;
+      cudaError_t e;
+      if (cta)
+        e = k == 0 ? hdd::launch_forward<double>(p.d_nodes, p.d_maps, p.d_lists + li.off, li.n, batch, A, rhs,
+                                                 li.max_nf, st)
+                   : hdd::launch_forward<float>(p.d_nodes, p.d_maps, p.d_lists + li.off, li.n, batch, A, rhs,
+                                                li.max_nf, st);
+      else
+        e = k == 0 ? hdd::launch_forward_warp<double>(p.d_nodes, p.d_maps, p.d_lists + li.off, li.n, batch, A, rhs,
+                                                      li.max_nf, st)
+                   : hdd::launch_forward_warp<float>(p.d_nodes, p.d_maps, p.d_lists + li.off, li.n, batch, A, rhs,
+                                                     li.max_nf, st);
       if (e != cudaSuccess) return e;
     }
   return cudaSuccess;
@@ -308,7 +331,8 @@ hdd_status hdd_assemble(hdd_plan_t plan, const double* Z, int32_t batch, void* w
   cudaError_t e = cudaMemsetAsync(w + L.status, 0, (size_t)batch * 4, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(w + L.conv, 0, (size_t)batch * 8, st);
   if (e == cudaSuccess)
-    e = hdd::launch_kappa(p.d_phi, Z, p.n_t, p.n_z, batch, reinterpret_cast<double*>(w + L.kappa), p.n_t, st);
+    e = hdd::launch_kappa(p.d_phi, Z, p.n_t, p.n_z, batch, reinterpret_cast<double*>(w + L.kappa),
+                          L.kappa32 ? reinterpret_cast<float*>(w + L.kappa32) : nullptr, p.n_t, st);
   return e == cudaSuccess ? HDD_OK : fail_cuda(e, "hdd_assemble");
 }
 

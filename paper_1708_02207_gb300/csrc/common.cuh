@@ -27,8 +27,9 @@ struct Rhs {
 };
 
 // kappa of triangle (cell (i, j), half t) if the cell lies in the rectangle.
-__device__ __forceinline__ double kap_in(const double* kap, int N, const NodeDev& nd, int i, int j, int t) {
-  if (i < nd.x0 || i >= nd.x1 || j < nd.y0 || j >= nd.y1) return 0.0;
+template <typename KT>
+__device__ __forceinline__ KT kap_in(const KT* kap, int N, const NodeDev& nd, int i, int j, int t) {
+  if (i < nd.x0 || i >= nd.x1 || j < nd.y0 || j >= nd.y1) return (KT)0;
   return kap[2 * ((int64_t)j * (N - 1) + i) + t];
 }
 // Stiffness weight of an axis edge from the triangles inside the rectangle.  For
@@ -37,23 +38,26 @@ __device__ __forceinline__ double kap_in(const double* kap, int N, const NodeDev
 // vertex in the middle): each leg couples its ends by -kappa_t/2, the hypotenuse
 // by 0.  The horizontal edge (i,j)-(i+1,j) is a leg of the lower-right triangle
 // of cell (i,j) and of the upper-left triangle of cell (i,j-1).
-__device__ __forceinline__ double w_horizontal(const double* kap, int N, const NodeDev& nd, int i, int j) {
-  return 0.5 * (kap_in(kap, N, nd, i, j, 0) + kap_in(kap, N, nd, i, j - 1, 1));
+template <typename KT>
+__device__ __forceinline__ KT w_horizontal(const KT* kap, int N, const NodeDev& nd, int i, int j) {
+  return (KT)0.5 * (kap_in(kap, N, nd, i, j, 0) + kap_in(kap, N, nd, i, j - 1, 1));
 }
 // The vertical edge (i,j)-(i,j+1) is a leg of the upper-left triangle of cell
 // (i,j) and of the lower-right triangle of cell (i-1,j).
-__device__ __forceinline__ double w_vertical(const double* kap, int N, const NodeDev& nd, int i, int j) {
-  return 0.5 * (kap_in(kap, N, nd, i, j, 1) + kap_in(kap, N, nd, i - 1, j, 0));
+template <typename KT>
+__device__ __forceinline__ KT w_vertical(const KT* kap, int N, const NodeDev& nd, int i, int j) {
+  return (KT)0.5 * (kap_in(kap, N, nd, i, j, 1) + kap_in(kap, N, nd, i - 1, j, 0));
 }
 
 // Entry (r, c), r >= c, of a leaf front: the stiffness of the leaf's own
 // triangles over [interior, boundary, rhs] (Leaves to Root, step 1).  The load
 // enters at the interior rows only; boundary rows receive theirs at the node
-// that eliminates them.
-__device__ __forceinline__ double leaf_entry(int r, int c, int s, const NodeDev& nd, const int32_t* vid,
-                                             const double* kap, int N, const Rhs& rhs) {
+// that eliminates them.  Computed in the front's precision KT.
+template <typename KT>
+__device__ __forceinline__ KT leaf_entry(int r, int c, int s, const NodeDev& nd, const int32_t* vid,
+                                         const KT* kap, int N, const Rhs& rhs) {
   const int nf = nd.nf;
-  if (r == nf - 1) return (c < nd.m) ? rhs(s, vid[c]) : 0.0;
+  if (r == nf - 1) return (c < nd.m) ? (KT)rhs(s, vid[c]) : (KT)0;
   const int v = vid[r], u = vid[c];
   const int vi = v % N, vj = v / N;
   if (v == u) {
@@ -63,7 +67,7 @@ __device__ __forceinline__ double leaf_entry(int r, int c, int s, const NodeDev&
   const int ui = u % N, uj = u / N;
   if (vj == uj && (vi - ui == 1 || ui - vi == 1)) return -w_horizontal(kap, N, nd, min(vi, ui), vj);
   if (vi == ui && (vj - uj == 1 || uj - vj == 1)) return -w_vertical(kap, N, nd, vi, min(vj, uj));
-  return 0.0;
+  return (KT)0;
 }
 
 // Workspace arenas of one precision pair (per-sample strides in elements).
@@ -74,31 +78,39 @@ struct Arenas {
   float* s32; int64_t s32_stride;
 };
 
-// Entry (a, b) of a son's Schur complement (lower triangle is stored).
-__device__ __forceinline__ double son_entry(const Arenas& A, const NodeDev& ch, int s, int a, int b) {
+// Entry (a, b) of a son's Schur complement (lower triangle is stored), returned
+// in the caller's precision T; the son's own precision is read directly.
+template <typename T>
+__device__ __forceinline__ T son_entry(const Arenas& A, const NodeDev& ch, int s, int a, int b) {
   const int lo = min(a, b), hi = max(a, b);
   const int64_t idx = (int64_t)lo * (ch.b + 1) + hi + ch.s_off;
-  return ch.fp64 ? A.s64[(int64_t)s * A.s64_stride + idx] : (double)A.s32[(int64_t)s * A.s32_stride + idx];
+  return ch.fp64 ? (T)A.s64[(int64_t)s * A.s64_stride + idx] : (T)A.s32[(int64_t)s * A.s32_stride + idx];
 }
 
 // Entry (r, c), r >= c, of a father front (Sec. 3.3, Eq. block_equation4): the
 // sons' Schur complements embedded into the union of their boundaries and added
 // (the shared interface block receives both), plus the load of the father's own
 // gamma vertices in the right-hand-side row.
-__device__ __forceinline__ double father_entry(int r, int c, int s, const NodeDev& nd, const int32_t* map,
-                                               const NodeDev& ch0, const NodeDev& ch1, const Arenas& A,
-                                               const Rhs& rhs) {
+template <typename T>
+__device__ __forceinline__ T father_entry(int r, int c, int s, const NodeDev& nd, const int32_t* map,
+                                          const NodeDev& ch0, const NodeDev& ch1, const Arenas& A,
+                                          const Rhs& rhs) {
   const int nf = nd.nf;
   const int32_t* pos0 = map + (nf - 1);
   const int32_t* pos1 = pos0 + nf;
-  double v = 0.0;
+  T v = (T)0;
   int a = pos0[r], b = pos0[c];
-  if (a >= 0 && b >= 0) v += son_entry(A, ch0, s, a, b);
+  if (a >= 0 && b >= 0) v += son_entry<T>(A, ch0, s, a, b);
   a = pos1[r]; b = pos1[c];
-  if (a >= 0 && b >= 0) v += son_entry(A, ch1, s, a, b);
-  if (r == nf - 1 && c < nd.m) v += rhs(s, map[c]);
+  if (a >= 0 && b >= 0) v += son_entry<T>(A, ch1, s, a, b);
+  if (r == nf - 1 && c < nd.m) v += (T)rhs(s, map[c]);
   return v;
 }
+
+// kappa per triangle in the front's precision (FP64 array, or its FP32 copy).
+template <typename T> __device__ __forceinline__ const T* kappa_of(const double* k64, const float* k32);
+template <> __device__ __forceinline__ const double* kappa_of<double>(const double* k64, const float*) { return k64; }
+template <> __device__ __forceinline__ const float* kappa_of<float>(const double*, const float* k32) { return k32; }
 
 template <typename T> struct Prec;
 template <> struct Prec<double> { static constexpr bool is64 = true; };

@@ -29,11 +29,12 @@ template <> __device__ __forceinline__ float* node_S<float>(const Arenas& A, con
   return A.s32 + (int64_t)s * A.s32_stride + nd.s_off;
 }
 
-__device__ __forceinline__ double front_entry(int r, int c, int s, int node, const NodeDev& nd,
-                                              const NodeDev* nodes, const int32_t* map, const double* kap,
-                                              int N, const Rhs& rhs, const Arenas& A) {
-  if (nd.leaf) return leaf_entry(r, c, s, nd, map, kap, N, rhs);
-  return father_entry(r, c, s, nd, map, nodes[nd.child0], nodes[nd.child1], A, rhs);
+template <typename T>
+__device__ __forceinline__ T front_entry(int r, int c, int s, int node, const NodeDev& nd, const NodeDev* nodes,
+                                         const int32_t* map, const T* kap, int N, const Rhs& rhs,
+                                         const Arenas& A) {
+  if (nd.leaf) return leaf_entry<T>(r, c, s, nd, map, kap, N, rhs);
+  return father_entry<T>(r, c, s, nd, map, nodes[nd.child0], nodes[nd.child1], A, rhs);
 }
 
 // ---------------------------------------------------------------------------
@@ -44,7 +45,7 @@ __device__ __forceinline__ double front_entry(int r, int c, int s, int node, con
 // Partial Cholesky: per column k, scale column k, then one warp per trailing
 // column j updates rows j..nf-1 (contiguous, conflict-free) with l_j.
 template <typename T>
-__device__ __forceinline__ void scatter_son(T* K, int nf, const NodeDev& ch, const int32_t* maps, const Arenas& A,
+__device__ __forceinline__ void scatter_son(T* K, int ld, const NodeDev& ch, const int32_t* maps, const Arenas& A,
                                             int s) {
   const int ldc = ch.b + 1;
   const int32_t* up = maps + ch.up_off;
@@ -57,70 +58,139 @@ __device__ __forceinline__ void scatter_son(T* K, int nf, const NodeDev& ch, con
       const T val = ch.fp64 ? (T)A.s64[idx] : (T)A.s32[idx];
       const int pr = up[aa];
       const int r = max(pr, pc), c = min(pr, pc);
-      K[c * nf + r] += val;
+      K[c * ld + r] += val;
     }
   }
 }
 
+// POTRF of K_gg (m x m, in F with ld nf): one CTA per (node, sample), blocked
+// right-looking with 32-column panels staged in shared memory; the trailing
+// update uses 4 x 4 register tiles over the lower triangle.
+constexpr int kPanel = 32;
+
+__device__ __forceinline__ void tri_index(int idx, int& ti, int& tj) {
+  int t = (int)((sqrtf(8.0f * (float)idx + 1.0f) - 1.0f) * 0.5f);
+  while (t * (t + 1) / 2 > idx) --t;
+  while ((t + 1) * (t + 2) / 2 <= idx) ++t;
+  ti = t;
+  tj = idx - t * (t + 1) / 2;
+}
+
+// Panel width of the blocked factorisation of shared-memory fronts.
+constexpr int kSmallPanel = 8;
+
+// Leading dimension of a shared-memory front: a multiple of 4, congruent to 4
+// modulo 8, so that column-varying accesses spread over 8 banks.
+__host__ __device__ __forceinline__ int front_ld(int nf) {
+  int ld = (nf + 3) & ~3;
+  if ((ld & 7) == 0) ld += 4;
+  return ld;
+}
+
 template <typename T>
-__global__ void k_front_small(StepArgs a) {
+__global__ void __launch_bounds__(512) k_front_small(StepArgs a) {
   const int node = a.list[blockIdx.x];
   const int s = blockIdx.y;
   const NodeDev nd = a.nodes[node];
-  const int nf = nd.nf, m = nd.m;
+  const int nf = nd.nf, m = nd.m, ld = front_ld(nf);
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* K = reinterpret_cast<T*>(smem_raw);
   const int32_t* map = a.maps + nd.map_off;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarp = blockDim.x >> 5;
 
   if (nd.leaf) {
-    const double* kap = a.kappa + (int64_t)s * a.kap_stride;
-    for (int idx = threadIdx.x; idx < nf * nf; idx += blockDim.x) {
-      const int c = idx / nf, r = idx - c * nf;
-      K[idx] = (r >= c) ? (T)leaf_entry(r, c, s, nd, map, kap, a.N, a.rhs) : (T)0;
-    }
+    const T* kap = kappa_of<T>(a.kappa, a.kappa32) + (int64_t)s * a.kap_stride;
+    for (int c = warp; c < nf; c += nwarp)
+      for (int r = lane; r < nf; r += 32)
+        K[c * ld + r] = (r >= c) ? leaf_entry<T>(r, c, s, nd, map, kap, a.N, a.rhs) : (T)0;
   } else {
-    for (int idx = threadIdx.x; idx < nf * nf; idx += blockDim.x) K[idx] = (T)0;
+    for (int idx = threadIdx.x; idx < nf * ld; idx += blockDim.x) K[idx] = (T)0;
     __syncthreads();
-    scatter_son<T>(K, nf, a.nodes[nd.child0], a.maps, a.arenas, s);
+    scatter_son<T>(K, ld, a.nodes[nd.child0], a.maps, a.arenas, s);
     __syncthreads();
-    scatter_son<T>(K, nf, a.nodes[nd.child1], a.maps, a.arenas, s);
+    scatter_son<T>(K, ld, a.nodes[nd.child1], a.maps, a.arenas, s);
     __syncthreads();
-    for (int c = threadIdx.x; c < m; c += blockDim.x) K[c * nf + nf - 1] += (T)a.rhs(s, map[c]);
+    for (int c = threadIdx.x; c < m; c += blockDim.x) K[c * ld + nf - 1] += (T)a.rhs(s, map[c]);
   }
-  for (int k = 0; k < m; ++k) {
-    __syncthreads();
-    T p = K[k * nf + k];
-    if (!(p > (T)0) || !isfinite(p)) {   // not SPD: record, continue with a unit pivot
-      if (threadIdx.x == 0) flag_status(a.status, s, -HDD_ENOTSPD, node);
-      p = (T)1;
+  // Blocked right-looking partial Cholesky: factor a panel of kSmallPanel columns
+  // (rank-1 steps restricted to the panel), then one rank-kb update of the
+  // trailing lower triangle with 4 x 4 register tiles; one warp walks a column
+  // of tiles, its lanes down the rows (conflict-free, no index division).
+  for (int k0 = 0; k0 < m; k0 += kSmallPanel) {
+    const int kb = min(kSmallPanel, m - k0), kend = k0 + kb;
+    for (int k = k0; k < kend; ++k) {
+      __syncthreads();
+      T p = K[k * ld + k];
+      if (!(p > (T)0) || !isfinite(p)) {   // not SPD: record, continue with a unit pivot
+        if (threadIdx.x == 0) flag_status(a.status, s, -HDD_ENOTSPD, node);
+        p = (T)1;
+      }
+      const T d = sqrt(p), inv = (T)1 / d;
+      T* colk = K + k * ld;
+      for (int i = k + 1 + threadIdx.x; i < nf; i += blockDim.x) colk[i] *= inv;
+      __syncthreads();
+      if (threadIdx.x == 0) colk[k] = d;
+      for (int j = k + 1 + warp; j < kend; j += nwarp) {
+        const T lj = colk[j];
+        T* colj = K + j * ld;
+        for (int i = j + lane; i < nf; i += 32) colj[i] -= colk[i] * lj;
+      }
     }
-    const T d = sqrt(p), inv = (T)1 / d;
-    T* colk = K + k * nf;
-    for (int i = k + 1 + threadIdx.x; i < nf; i += blockDim.x) colk[i] *= inv;
     __syncthreads();
-    if (threadIdx.x == 0) colk[k] = d;
-    for (int j = k + 1 + warp; j < nf; j += nwarp) {
-      const T lj = colk[j];
-      T* colj = K + j * nf;
-      for (int i = j + lane; i < nf; i += 32) colj[i] -= colk[i] * lj;
+    if (kend >= nf) continue;
+    const int t0 = kend & ~3;                    // tiles aligned to multiples of 4
+    const int nt = (nf - t0 + 3) >> 2;
+    for (int tj = warp; tj < nt; tj += nwarp) {
+      const int j0 = t0 + 4 * tj;
+      for (int ti = tj + lane; ti < nt; ti += 32) {
+        const int i0 = t0 + 4 * ti;
+        T acc[4][4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+#pragma unroll
+          for (int w = 0; w < 4; ++w) acc[q][w] = (T)0;
+        for (int l = k0; l < kend; ++l) {
+          const T* col = K + l * ld;
+          T x[4], y[4];
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            x[q] = col[i0 + q];
+            y[q] = col[j0 + q];
+          }
+#pragma unroll
+          for (int q = 0; q < 4; ++q)
+#pragma unroll
+            for (int w = 0; w < 4; ++w) acc[q][w] += x[q] * y[w];
+        }
+#pragma unroll
+        for (int w = 0; w < 4; ++w) {
+          const int j = j0 + w;
+          if (j < kend || j >= nf) continue;
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            const int i = i0 + q;
+            if (i < nf && i >= j) K[j * ld + i] -= acc[q][w];
+          }
+        }
+      }
     }
   }
   __syncthreads();
   T* F = node_F<T>(a.arenas, nd, s);
-  for (int idx = threadIdx.x; idx < m * nf; idx += blockDim.x) F[idx] = K[idx];
+  for (int c = warp; c < m; c += nwarp)
+    for (int r = lane; r < nf; r += 32) F[c * nf + r] = K[c * ld + r];
   const int nb = nd.b + 1;
   T* S = node_S<T>(a.arenas, nd, s);
   for (int c = warp; c < nb; c += nwarp)
-    for (int r = c + lane; r < nb; r += 32) S[c * nb + r] = K[(m + c) * nf + m + r];
+    for (int r = c + lane; r < nb; r += 32) S[c * nb + r] = K[(m + c) * ld + m + r];
 }
 
-static int small_threads(int nf) { return nf <= 64 ? 128 : 256; }
+static int small_threads(int nf) { return nf <= 64 ? 128 : (nf <= 128 ? 256 : 512); }
 
 template <typename T>
 cudaError_t launch_front_small(const StepArgs& a, cudaStream_t st) {
   if (a.nlist == 0) return cudaSuccess;
-  const size_t smem = (size_t)a.max_nf * a.max_nf * sizeof(T);
+  const size_t smem = (size_t)a.max_nf * front_ld(a.max_nf) * sizeof(T) + 4 * 4 * sizeof(T);
   dim3 grid(a.nlist, a.batch);
   k_front_small<T><<<grid, small_threads(a.max_nf), smem, st>>>(a);
   return cudaGetLastError();
@@ -138,27 +208,14 @@ __global__ void k_front_fill(StepArgs a) {
   const int nf = nd.nf, m = nd.m, nb = nd.b + 1;
   if (c >= nf) return;
   const int32_t* map = a.maps + nd.map_off;
-  const double* kap = a.kappa + (int64_t)s * a.kap_stride;
+  const T* kap = kappa_of<T>(a.kappa, a.kappa32) + (int64_t)s * a.kap_stride;
   T* F = node_F<T>(a.arenas, nd, s);
   T* S = node_S<T>(a.arenas, nd, s);
   for (int r = lane; r < nf; r += 32) {
-    const T v = (r >= c) ? (T)front_entry(r, c, s, node, nd, a.nodes, map, kap, a.N, a.rhs, a.arenas) : (T)0;
+    const T v = (r >= c) ? front_entry<T>(r, c, s, node, nd, a.nodes, map, kap, a.N, a.rhs, a.arenas) : (T)0;
     if (c < m) F[(int64_t)c * nf + r] = v;
     else if (r >= m) S[(int64_t)(c - m) * nb + (r - m)] = v;
   }
-}
-
-// POTRF of K_gg (m x m, in F with ld nf): one CTA per (node, sample), blocked
-// right-looking with 32-column panels staged in shared memory; the trailing
-// update uses 4 x 4 register tiles over the lower triangle.
-constexpr int kPanel = 32;
-
-__device__ __forceinline__ void tri_index(int idx, int& ti, int& tj) {
-  int t = (int)((sqrt(8.0 * idx + 1.0) - 1.0) * 0.5);
-  while (t * (t + 1) / 2 > idx) --t;
-  while ((t + 1) * (t + 2) / 2 <= idx) ++t;
-  ti = t;
-  tj = idx - t * (t + 1) / 2;
 }
 
 // Rows of a panel (POTRF) or of a row block (TRSM) kept in shared memory; larger
@@ -168,7 +225,7 @@ template <> struct SmemCap<double> { static constexpr int rows = 800; };
 template <> struct SmemCap<float> { static constexpr int rows = 1600; };
 
 template <typename T>
-__global__ void k_potrf(StepArgs a) {
+__global__ void __launch_bounds__(256) k_potrf(StepArgs a) {
   const int node = a.list[blockIdx.x];
   const int s = blockIdx.y;
   const NodeDev nd = a.nodes[node];
@@ -188,7 +245,9 @@ __global__ void k_potrf(StepArgs a) {
         const int l = idx / rows, i = idx - l * rows;
         Ps[idx] = A[(int64_t)(k0 + l) * nf + k0 + i];
       }
-    // factor the panel (rows k0..m-1, columns k0..k0+kb-1)
+    // factor the panel (rows k0..m-1, columns k0..k0+kb-1): per column, scale it,
+    // then one warp per remaining panel column applies the rank-1 update
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarp = blockDim.x >> 5;
     for (int kk = 0; kk < kb; ++kk) {
       __syncthreads();
       T p = P[(int64_t)kk * ld + kk];
@@ -196,30 +255,16 @@ __global__ void k_potrf(StepArgs a) {
         if (threadIdx.x == 0) flag_status(a.status, s, -HDD_ENOTSPD, node);
         p = (T)1;
       }
-      if (threadIdx.x == 0) piv[kk] = sqrt(p);
-      const T rp = (T)1 / p;
-      const T* colk = P + (int64_t)kk * ld;
-      const int ncol = kb - kk - 1;                 // panel columns right of kk
-      const int nrow = rows - kk - 1;               // rows below kk
-      for (int idx = threadIdx.x; idx < ncol * nrow; idx += blockDim.x) {
-        const int jj = idx / nrow, ii = idx - jj * nrow;
-        if (ii < jj) continue;
-        const int i = kk + 1 + ii, j = kk + 1 + jj;
-        P[(int64_t)j * ld + i] -= colk[i] * (colk[j] * rp);
+      const T d = sqrt(p), inv = (T)1 / d;
+      T* colk = P + (int64_t)kk * ld;
+      for (int i = kk + 1 + threadIdx.x; i < rows; i += blockDim.x) colk[i] *= inv;
+      __syncthreads();
+      if (threadIdx.x == 0) colk[kk] = d;
+      for (int j = kk + 1 + warp; j < kb; j += nwarp) {
+        const T lj = colk[j];
+        T* colj = P + (int64_t)j * ld;
+        for (int i = j + lane; i < rows; i += 32) colj[i] -= colk[i] * lj;
       }
-      if (kk > 0) {
-        const int c = kk - 1;
-        const T d = piv[c], rd = (T)1 / d;
-        for (int i = c + threadIdx.x; i < rows; i += blockDim.x)
-          P[(int64_t)c * ld + i] = (i == c) ? d : P[(int64_t)c * ld + i] * rd;
-      }
-    }
-    __syncthreads();
-    {
-      const int c = kb - 1;
-      const T d = piv[c], rd = (T)1 / d;
-      for (int i = c + threadIdx.x; i < rows; i += blockDim.x)
-        P[(int64_t)c * ld + i] = (i == c) ? d : P[(int64_t)c * ld + i] * rd;
     }
     __syncthreads();
     if (in_smem)
@@ -227,74 +272,85 @@ __global__ void k_potrf(StepArgs a) {
         const int l = idx / rows, i = idx - l * rows;
         if (i >= l) A[(int64_t)(k0 + l) * nf + k0 + i] = Ps[idx];
       }
-    // trailing update of K_gg[k0+kb:m, k0+kb:m] (lower)
+    // trailing update of K_gg[k0+kb:m, k0+kb:m] (lower): 4 x 4 register tiles,
+    // one warp per column of tiles, lanes down the rows (coalesced in global memory)
     const int n = rows - kb;
     if (n <= 0) continue;
-    const int nt = (n + 3) / 4;
-    const int ntiles = nt * (nt + 1) / 2;
-    for (int idx = threadIdx.x; idx < ntiles; idx += blockDim.x) {
-      int ti, tj;
-      tri_index(idx, ti, tj);
-      const int i0 = kb + 4 * ti, j0 = kb + 4 * tj;   // panel-relative rows
-      T acc[4][4];
-#pragma unroll
-      for (int q = 0; q < 4; ++q)
-#pragma unroll
-        for (int w = 0; w < 4; ++w) acc[q][w] = (T)0;
-      for (int l = 0; l < kb; ++l) {
-        T x[4], y[4];
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          x[q] = (i0 + q < rows) ? P[(int64_t)l * ld + i0 + q] : (T)0;
-          y[q] = (j0 + q < rows) ? P[(int64_t)l * ld + j0 + q] : (T)0;
-        }
+    const int nt = (n + 3) >> 2;
+    for (int tj = warp; tj < nt; tj += nwarp) {
+      const int j0 = kb + 4 * tj;
+      for (int ti = tj + lane; ti < nt; ti += 32) {
+        const int i0 = kb + 4 * ti;
+        T acc[4][4];
 #pragma unroll
         for (int q = 0; q < 4; ++q)
 #pragma unroll
-          for (int w = 0; w < 4; ++w) acc[q][w] += x[q] * y[w];
-      }
+          for (int w = 0; w < 4; ++w) acc[q][w] = (T)0;
+        for (int l = 0; l < kb; ++l) {
+          T x[4], y[4];
 #pragma unroll
-      for (int w = 0; w < 4; ++w) {
-        const int j = j0 + w;
-        if (j >= rows) break;
+          for (int q = 0; q < 4; ++q) {
+            x[q] = (i0 + q < rows) ? P[(int64_t)l * ld + i0 + q] : (T)0;
+            y[q] = (j0 + q < rows) ? P[(int64_t)l * ld + j0 + q] : (T)0;
+          }
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          const int i = i0 + q;
-          if (i < rows && i >= j) A[(int64_t)(k0 + j) * nf + k0 + i] -= acc[q][w];
+          for (int q = 0; q < 4; ++q)
+#pragma unroll
+            for (int w = 0; w < 4; ++w) acc[q][w] += x[q] * y[w];
+        }
+#pragma unroll
+        for (int w = 0; w < 4; ++w) {
+          const int j = j0 + w;
+          if (j >= rows) break;
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            const int i = i0 + q;
+            if (i < rows && i >= j) A[(int64_t)(k0 + j) * nf + k0 + i] -= acc[q][w];
+          }
         }
       }
     }
   }
 }
 
-// TRSM: rows m..nf-1 of F times L_gg^-T.  One CTA per (32-row block, node, sample);
-// the block's rows stay in shared memory across the column sweep.
-constexpr int kTrsmRows = 32;
+// TRSM: rows m..nf-1 of F times L_gg^-T.  One CTA per (row block, node, sample);
+// the row block X stays in shared memory across the column sweep (or is updated
+// in place in global memory when m is too large).  Per 32-column block of L_gg:
+// the diagonal triangle is solved one thread per row, then the remaining columns
+// are updated in 64-column chunks of L staged in shared memory, with register
+// micro-tiles (4 rows x kTrsmCols columns per thread).
+template <typename T> struct TrsmShape;
+template <> struct TrsmShape<float> { static constexpr int rows = 64, cap = 760; };
+template <> struct TrsmShape<double> { static constexpr int rows = 32, cap = 760; };
 
 template <typename T>
-__global__ void k_trsm(StepArgs a) {
+__global__ void __launch_bounds__(256) k_trsm(StepArgs a) {
+  constexpr int R = TrsmShape<T>::rows;     // rows per CTA
+  constexpr int RG = R / 4;                 // row groups of 4
+  constexpr int CG = 256 / RG;              // column groups
+  constexpr int CPT = 64 / CG;              // columns per thread in a 64-column chunk
   const int node = a.list[blockIdx.y];
   const int s = blockIdx.z;
   const NodeDev nd = a.nodes[node];
   const int nf = nd.nf, m = nd.m;
-  const int r0 = m + blockIdx.x * kTrsmRows;
+  const int r0 = m + blockIdx.x * R;
   if (r0 >= nf || m == 0) return;
-  const int nr = min(kTrsmRows, nf - r0);
+  const int nr = min(R, nf - r0);
   T* A = node_F<T>(a.arenas, nd, s);
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* L = reinterpret_cast<T*>(smem_raw);        // [32][33]
-  T* Xs = L + 32 * 33;                          // [m][kTrsmRows]
-  const bool in_smem = m <= SmemCap<T>::rows;
-  // X(r, c) = X[c * ldx + r]: the row block in shared memory, or in place in F
+  T* L = reinterpret_cast<T*>(smem_raw);    // [32][33] diagonal block
+  T* Lc = L + 32 * 33 + 3;                  // [32][64] chunk of the panel below it
+  Lc = reinterpret_cast<T*>((reinterpret_cast<uintptr_t>(Lc) + 15) & ~uintptr_t(15));
+  T* Xs = Lc + 32 * 64;                     // [m][R]
+  const bool in_smem = m <= TrsmShape<T>::cap;
   T* X = in_smem ? Xs : A + r0;
-  const int64_t ldx = in_smem ? kTrsmRows : nf;
+  const int64_t ldx = in_smem ? R : nf;
   if (in_smem)
-    for (int idx = threadIdx.x; idx < m * kTrsmRows; idx += blockDim.x) {
-      const int c = idx / kTrsmRows, r = idx - c * kTrsmRows;
+    for (int idx = threadIdx.x; idx < m * R; idx += blockDim.x) {
+      const int c = idx / R, r = idx - c * R;
       Xs[idx] = (r < nr) ? A[(int64_t)c * nf + r0 + r] : (T)0;
     }
-  const int r = threadIdx.x % kTrsmRows, grp = threadIdx.x / kTrsmRows, ngrp = blockDim.x / kTrsmRows;
-  const bool row_ok = r < nr;
+  const int rg = threadIdx.x % RG, cg = threadIdx.x / RG;
   for (int j0 = 0; j0 < m; j0 += 32) {
     const int jb = min(32, m - j0);
     __syncthreads();
@@ -303,25 +359,56 @@ __global__ void k_trsm(StepArgs a) {
       L[l * 33 + q] = (q >= l) ? A[(int64_t)(j0 + l) * nf + j0 + q] : (T)0;
     }
     __syncthreads();
-    if (threadIdx.x < kTrsmRows && row_ok) {
+    if (threadIdx.x < nr) {
+      const int r = threadIdx.x;
       for (int cc = 0; cc < jb; ++cc) {
         T x = X[(j0 + cc) * ldx + r];
         for (int l = 0; l < cc; ++l) x -= X[(j0 + l) * ldx + r] * L[l * 33 + cc];
         X[(j0 + cc) * ldx + r] = x / L[cc * 33 + cc];
       }
     }
-    __syncthreads();
-    if (row_ok)
-      for (int c2 = j0 + jb + grp; c2 < m; c2 += ngrp) {
-        T acc = (T)0;
-        for (int l = 0; l < jb; ++l) acc += X[(j0 + l) * ldx + r] * A[(int64_t)(j0 + l) * nf + c2];
-        X[c2 * ldx + r] -= acc;
+    for (int c0 = j0 + jb; c0 < m; c0 += 64) {
+      const int nc = min(64, m - c0);
+      __syncthreads();
+      for (int idx = threadIdx.x; idx < jb * 64; idx += blockDim.x) {
+        const int l = idx >> 6, cc = idx & 63;
+        Lc[idx] = (cc < nc) ? A[(int64_t)(j0 + l) * nf + c0 + cc] : (T)0;
       }
+      __syncthreads();
+      T acc[4][CPT];
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+#pragma unroll
+        for (int w = 0; w < CPT; ++w) acc[q][w] = (T)0;
+      const int rr = rg * 4, cc0 = cg * CPT;
+      for (int l = 0; l < jb; ++l) {
+        const T* xc = X + (j0 + l) * ldx + rr;
+        const T* lc = Lc + l * 64 + cc0;
+        T x[4], y[CPT];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) x[q] = xc[q];
+#pragma unroll
+        for (int w = 0; w < CPT; ++w) y[w] = lc[w];
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+#pragma unroll
+          for (int w = 0; w < CPT; ++w) acc[q][w] += x[q] * y[w];
+      }
+#pragma unroll
+      for (int w = 0; w < CPT; ++w) {
+        const int c = c0 + cc0 + w;
+        if (c < m) {
+#pragma unroll
+          for (int q = 0; q < 4; ++q)
+            if (rr + q < nr) X[c * ldx + rr + q] -= acc[q][w];
+        }
+      }
+    }
   }
   __syncthreads();
   if (in_smem)
-    for (int idx = threadIdx.x; idx < m * kTrsmRows; idx += blockDim.x) {
-      const int c = idx / kTrsmRows, rr = idx - c * kTrsmRows;
+    for (int idx = threadIdx.x; idx < m * R; idx += blockDim.x) {
+      const int c = idx / R, rr = idx - c * R;
       if (rr < nr) A[(int64_t)c * nf + r0 + rr] = Xs[idx];
     }
 }
@@ -393,8 +480,10 @@ cudaError_t launch_front_large(const StepArgs& a, cudaStream_t st) {
     k_potrf<T><<<dim3(a.nlist, a.batch), 256, smem, st>>>(a);
   }
   {
-    const size_t smem = (rows_smem * kTrsmRows + 32 * 33) * sizeof(T);
-    dim3 grid((a.max_b + 1 + kTrsmRows - 1) / kTrsmRows, a.nlist, a.batch);
+    constexpr int R = TrsmShape<T>::rows;
+    const size_t xrows = (size_t)min(a.max_m, TrsmShape<T>::cap);
+    const size_t smem = (xrows * R + 32 * 33 + 3 + 32 * 64) * sizeof(T) + 16;
+    dim3 grid((a.max_b + 1 + R - 1) / R, a.nlist, a.batch);
     k_trsm<T><<<grid, 256, smem, st>>>(a);
   }
   {

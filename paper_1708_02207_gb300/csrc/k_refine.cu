@@ -54,10 +54,10 @@ __global__ void k_forward(const NodeDev* __restrict__ nodes, const int32_t* __re
     const int32_t* pos0 = vid + (nf - 1);
     const int32_t* pos1 = pos0 + nf;
     for (int r = threadIdx.x; r < nf - 1; r += blockDim.x) {
-      double v = (r < m) ? rhs(s, vid[r]) : 0.0;
-      if (pos0[r] >= 0) v += son_rhs(A, c0, s, pos0[r]);
-      if (pos1[r] >= 0) v += son_rhs(A, c1, s, pos1[r]);
-      z[r] = (T)v;
+      T v = (r < m) ? (T)rhs(s, vid[r]) : (T)0;
+      if (pos0[r] >= 0) v += (T)son_rhs(A, c0, s, pos0[r]);
+      if (pos1[r] >= 0) v += (T)son_rhs(A, c1, s, pos1[r]);
+      z[r] = v;
     }
   }
   for (int cb = 0; cb < m; cb += 32) {

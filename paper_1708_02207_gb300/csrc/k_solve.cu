@@ -10,7 +10,7 @@ namespace hdd {
 constexpr int kKapT = 128, kKapS = 8, kKapK = 32;
 
 __global__ void k_kappa(const double* __restrict__ phi, const double* __restrict__ Z, int n_t, int n_z, int batch,
-                        double* __restrict__ kappa, int64_t kap_stride) {
+                        double* __restrict__ kappa, float* __restrict__ kappa32, int64_t kap_stride) {
   __shared__ double ph[kKapK][kKapT + 1];
   __shared__ double zs[kKapS][kKapK];
   const int t0 = blockIdx.x * kKapT, s0 = blockIdx.y * kKapS;
@@ -39,14 +39,18 @@ __global__ void k_kappa(const double* __restrict__ phi, const double* __restrict
   if (t < n_t) {
 #pragma unroll
     for (int q = 0; q < kKapS; ++q)
-      if (s0 + q < batch) kappa[(int64_t)(s0 + q) * kap_stride + t] = exp(acc[q]);
+      if (s0 + q < batch) {
+        const double kv = exp(acc[q]);
+        kappa[(int64_t)(s0 + q) * kap_stride + t] = kv;
+        if (kappa32) kappa32[(int64_t)(s0 + q) * kap_stride + t] = (float)kv;
+      }
   }
 }
 
 cudaError_t launch_kappa(const double* phi, const double* Z, int n_t, int n_z, int batch, double* kappa,
-                         int64_t kap_stride, cudaStream_t st) {
+                         float* kappa32, int64_t kap_stride, cudaStream_t st) {
   dim3 grid((n_t + kKapT - 1) / kKapT, (batch + kKapS - 1) / kKapS);
-  k_kappa<<<grid, kKapT, 0, st>>>(phi, Z, n_t, n_z, batch, kappa, kap_stride);
+  k_kappa<<<grid, kKapT, 0, st>>>(phi, Z, n_t, n_z, batch, kappa, kappa32, kap_stride);
   return cudaGetLastError();
 }
 

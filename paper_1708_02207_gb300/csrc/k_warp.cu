@@ -40,14 +40,14 @@ __global__ void __launch_bounds__(256) k_front_warp(StepArgs a) {
   const int N = a.N;
   const int32_t* map = a.maps + nd.map_off;
   const int v = (lane < nf - 1) ? map[lane] : -1;
-  const double rv = (lane < m) ? a.rhs(s, v) : 0.0;   // load of this lane's vertex if it is eliminated here
+  const T rv = (lane < m) ? (T)a.rhs(s, v) : (T)0;   // load of this lane's vertex if it is eliminated here
   T row[32];
 #pragma unroll
   for (int c = 0; c < 32; ++c) row[c] = (T)0;
   if (nd.leaf) {
-    const double* kap = a.kappa + (int64_t)s * a.kap_stride;
+    const T* kap = kappa_of<T>(a.kappa, a.kappa32) + (int64_t)s * a.kap_stride;
     int vi = -7, vj = -7;
-    double wl = 0.0, wr = 0.0, wd = 0.0, wu = 0.0;
+    T wl = (T)0, wr = (T)0, wd = (T)0, wu = (T)0;
     if (v >= 0) {
       vi = v % N;
       vj = v / N;
@@ -59,11 +59,11 @@ __global__ void __launch_bounds__(256) k_front_warp(StepArgs a) {
 #pragma unroll
     for (int c = 0; c < 32; ++c) {
       const int ci = __shfl_sync(kFull, vi, c), cj = __shfl_sync(kFull, vj, c);
-      const double rc = __shfl_sync(kFull, rv, c);
-      double val = 0.0;
+      const T rc = __shfl_sync(kFull, rv, c);
+      T val = (T)0;
       if (c < nf && lane < nf) {
         if (lane == nf - 1) {
-          val = (c < m) ? rc : 0.0;
+          val = (c < m) ? rc : (T)0;
         } else if (c == nf - 1) {
           val = rv;
         } else if (c == lane) {
@@ -78,7 +78,7 @@ __global__ void __launch_bounds__(256) k_front_warp(StepArgs a) {
           val = -wu;
         }
       }
-      row[c] = (T)val;
+      row[c] = val;
     }
   } else {
     const int32_t* pos0 = map + (nf - 1);
@@ -88,13 +88,13 @@ __global__ void __launch_bounds__(256) k_front_warp(StepArgs a) {
 #pragma unroll
     for (int c = 0; c < 32; ++c) {
       const int q0 = __shfl_sync(kFull, p0, c), q1 = __shfl_sync(kFull, p1, c);
-      const double rc = __shfl_sync(kFull, rv, c);
-      double val = 0.0;
-      if (p0 >= 0 && q0 >= 0) val += son_entry(a.arenas, c0, s, p0, q0);
-      if (p1 >= 0 && q1 >= 0) val += son_entry(a.arenas, c1, s, p1, q1);
+      const T rc = __shfl_sync(kFull, rv, c);
+      T val = (T)0;
+      if (p0 >= 0 && q0 >= 0) val += son_entry<T>(a.arenas, c0, s, p0, q0);
+      if (p1 >= 0 && q1 >= 0) val += son_entry<T>(a.arenas, c1, s, p1, q1);
       if (lane == nf - 1 && c < m) val += rc;
       if (c == nf - 1 && lane < m) val += rv;
-      row[c] = (T)val;
+      row[c] = val;
     }
   }
   bool bad = false;
@@ -152,9 +152,9 @@ static int sweep_warps(size_t bytes_per_warp) {
 // column (coalesced down each column of F), folding every column into the rows
 // below it, which leaves z_B - L_Bg y_g.
 template <typename T>
-__device__ __forceinline__ double son_cond(const Arenas& A, const NodeDev& ch, int s, int p) {
+__device__ __forceinline__ T son_cond(const Arenas& A, const NodeDev& ch, int s, int p) {
   const int64_t idx = (int64_t)p * (ch.b + 1) + ch.b + ch.s_off;
-  return ch.fp64 ? A.s64[(int64_t)s * A.s64_stride + idx] : (double)A.s32[(int64_t)s * A.s32_stride + idx];
+  return ch.fp64 ? (T)A.s64[(int64_t)s * A.s64_stride + idx] : (T)A.s32[(int64_t)s * A.s32_stride + idx];
 }
 
 template <typename T>
@@ -179,11 +179,11 @@ __global__ void __launch_bounds__(256) k_forward_warp(const NodeDev* __restrict_
     const int32_t* pos0 = vid + (nf - 1);
     const int32_t* pos1 = pos0 + nf;
     for (int r = lane; r < nf - 1; r += 32) {
-      double val = (r < m) ? rhs(s, vid[r]) : 0.0;
+      T val = (r < m) ? (T)rhs(s, vid[r]) : (T)0;
       const int q0 = pos0[r], q1 = pos1[r];
       if (q0 >= 0) val += son_cond<T>(A, c0, s, q0);
       if (q1 >= 0) val += son_cond<T>(A, c1, s, q1);
-      z[r] = (T)val;
+      z[r] = val;
     }
   }
   __syncwarp();

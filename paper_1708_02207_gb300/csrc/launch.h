@@ -16,6 +16,7 @@ struct StepArgs {
   int batch;
   int N;
   const double* kappa;     // [batch x n_t]
+  const float* kappa32;    // FP32 copy (mixed plans) or nullptr
   int64_t kap_stride;
   Rhs rhs;
   Arenas arenas;
@@ -25,7 +26,7 @@ struct StepArgs {
 
 // assembly: kappa = exp(Phi Z) (Sec. 3.1; kappa = e^q)
 cudaError_t launch_kappa(const double* phi, const double* Z, int n_t, int n_z, int batch, double* kappa,
-                         int64_t kap_stride, cudaStream_t st);
+                         float* kappa32, int64_t kap_stride, cudaStream_t st);
 
 // fronts of at most 32 rows: one warp each, in registers
 template <typename T> cudaError_t launch_front_warp(const StepArgs& a, cudaStream_t st);

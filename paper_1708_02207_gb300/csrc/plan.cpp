@@ -340,6 +340,7 @@ Layout layout(const Plan& p, int batch) {
   L.status = take(B * 4);
   L.conv = take(B * 8);
   L.kappa = take(B * p.n_t * 8);
+  if (p.precision == HDD_MIXED_FP32) L.kappa32 = take(B * p.n_t * 4);
   L.u = take(B * NN * 8);
   if (p.precision == HDD_MIXED_FP32) {
     L.r = take(B * NN * 8);

@@ -110,7 +110,7 @@ std::string build_plan(const hdd_plan_desc& d, Plan& p);
 
 // Workspace layout for a batch (byte offsets, 256-byte aligned).
 struct Layout {
-  size_t status = 0, kappa = 0;
+  size_t status = 0, kappa = 0, kappa32 = 0;
   size_t u = 0, r = 0, du = 0;        // FP64 vertex vectors [batch x N^2]
   size_t f64 = 0, f32 = 0, s64 = 0, s32 = 0;
   size_t uobs = 0, ll = 0, z = 0, y = 0, conv = 0;
