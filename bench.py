@@ -229,6 +229,10 @@ def run_hdd(args, cfg):
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         total_ms = float(t.item())
     stage_ms = {s: statistics.mean(e[i].elapsed_time(e[i + 1]) for e in evs) for i, s in enumerate(stages)}
+    step_ms = sorted(e[0].elapsed_time(e[4]) for e in evs)
+
+    def pct(q):
+        return step_ms[min(len(step_ms) - 1, int(round(q * (len(step_ms) - 1))))]
 
     value = world * B * args.steps / (total_ms / 1e3)
 
@@ -268,6 +272,39 @@ def run_hdd(args, cfg):
                 "kernel": "hdd_upsweep (front_small, front_fill, potrf, trsm, syrk launches), FP32 FMA",
                 "peak_source": "derived: 128 FP32 FMA/clk/SM x 152 SMs x 2070 MHz"}
 
+    # the plain FP64 path on the same inputs (the speedup of the mixed path is over it)
+    fp64 = None
+    if precision != hdd.HDD_FP64 and args.fp64_steps > 0:
+        del ws
+        torch.cuda.empty_cache()
+        plan64 = hdd.Plan(cfg.N, args.leaf or cfg.leaf, prob.phi, prob.obs, cfg.sigma, f=cfg.f,
+                          precision=hdd.HDD_FP64, device=local)
+        ws64 = plan64.workspace(B)
+        u64 = torch.empty(B, plan.n_obs, dtype=torch.float64, device=dev)
+        ll64 = torch.empty(B, dtype=torch.float64, device=dev)
+        with torch.cuda.stream(stream):
+            plan64.assemble(Z, ws64, stream)
+            plan64.upsweep(B, ws64, stream)
+            plan64.point_solve(B, ws64, u64, stream)
+            plan64.loglik(B, ws64, u64, y, ll64, None, stream)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(args.fp64_steps):
+                plan64.assemble(Z, ws64, stream)
+                plan64.upsweep(B, ws64, stream)
+                plan64.point_solve(B, ws64, u64, stream)
+                plan64.loglik(B, ws64, u64, y, ll64, None, stream)
+            e1.record(stream)
+        stream.synchronize()
+        t64 = e0.elapsed_time(e1) / args.fp64_steps
+        rel = ((u_obs - u64).abs().max(dim=1).values / u64.abs().max(dim=1).values).max().item()
+        fp64 = {"value": world * B / (t64 / 1e3), "unit": "evals/s", "ms_per_step": t64,
+                "speedup_of_mixed": (world * B / (t64 / 1e3)) and value / (world * B / (t64 / 1e3)),
+                "max_rel_diff_u_obs_mixed_vs_fp64": rel, "steps": args.fp64_steps}
+        del ws64
+        torch.cuda.empty_cache()
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         P = min(host_cores(), B)
@@ -286,6 +323,8 @@ def run_hdd(args, cfg):
                    "batch": B, "precision": args.precision, "parallelism": f"replicas x{world}",
                    "l2": "working set >> 129 MB L2 (no flush needed)"},
         "stage_ms": stage_ms, "failed_samples": bad,
+        "latency_ms": {"p50": pct(0.5), "p99": pct(0.99), "note": "per step (one batch of samples)"},
+        "fp64_path": fp64,
         "roofline": roof,
         "e2e": {"value": e2e_value, "unit": "evals/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": info["launches_evaluate"] * args.steps,
@@ -308,7 +347,9 @@ def main(argv=None):
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="hdd", choices=["hdd", "reference"])
     ap.add_argument("--config", default="grid513", choices=sorted(w.CONFIGS))
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--precision", default="mixed", choices=["fp64", "mixed"])
+    ap.add_argument("--fp64-steps", type=int, default=2,
+                    help="timed steps of the plain FP64 path reported beside the mixed one (0: skip)")
     ap.add_argument("--leaf", type=int, default=0)
     ap.add_argument("--batch", type=int, default=0, help="samples per step (default: the workload's)")
     ap.add_argument("--ir-iters", type=int, default=2)

@@ -16,6 +16,7 @@ cudaError_t configure_front_kernels();
 cudaError_t configure_solve_kernels();
 cudaError_t configure_refine_kernels();
 cudaError_t configure_warp_kernels();
+cudaError_t configure_tc_kernels();
 }  // namespace hdd
 
 namespace {
@@ -24,7 +25,7 @@ thread_local std::string g_err;
 
 // Sweeps over nodes whose interface has at least this many vertices use one CTA
 // per (node, sample) with blocked substitution; smaller nodes one warp each.
-constexpr int kSweepCtaMinM = 64;
+constexpr int kSweepCtaMinM = 32;
 
 hdd_status fail_cuda(cudaError_t e, const char* where) {
   g_err = std::string(where) + ": " + cudaGetErrorString(e);
@@ -61,6 +62,7 @@ cudaError_t configure_device(int dev) {
   if (e == cudaSuccess) e = hdd::configure_solve_kernels();
   if (e == cudaSuccess) e = hdd::configure_refine_kernels();
   if (e == cudaSuccess) e = hdd::configure_warp_kernels();
+  if (e == cudaSuccess) e = hdd::configure_tc_kernels();
   if (e == cudaSuccess) g_configured[dev] = true;
   return e;
 }
@@ -93,6 +95,12 @@ hdd::Arenas arenas(const hdd::Plan& p, const hdd::Layout& L, void* ws) {
   A.s64_stride = p.s64_stride;
   A.s32 = reinterpret_cast<float*>(w + L.s32);
   A.s32_stride = p.s32_stride;
+  A.y64 = reinterpret_cast<double*>(w + L.y64);
+  A.y64_stride = p.y64_stride;
+  A.y32 = reinterpret_cast<float*>(w + L.y32);
+  A.y32_stride = p.y32_stride;
+  A.tc = reinterpret_cast<unsigned char*>(w + L.tc);
+  A.tc_stride = p.tc_stride;
   return A;
 }
 
@@ -169,9 +177,9 @@ cudaError_t run_descent(const hdd::Plan& p, int batch, void* ws, const std::vect
                                             li.max_b, li.max_m, st);
     else
       e = fp64 ? hdd::launch_descent_warp<double>(p.d_nodes, p.d_maps, p.d_lists + li.off, li.n, batch, A, u, NN,
-                                                  li.max_nf, st)
+                                                  li.max_nf, li.max_m, st)
                : hdd::launch_descent_warp<float>(p.d_nodes, p.d_maps, p.d_lists + li.off, li.n, batch, A, u, NN,
-                                                 li.max_nf, st);
+                                                 li.max_nf, li.max_m, st);
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;
@@ -194,9 +202,9 @@ cudaError_t run_forward(const hdd::Plan& p, int batch, void* ws, const hdd::Rhs&
                                                 li.max_nf, st);
       else
         e = k == 0 ? hdd::launch_forward_warp<double>(p.d_nodes, p.d_maps, p.d_lists + li.off, li.n, batch, A, rhs,
-                                                      li.max_nf, st)
+                                                      li.max_nf, li.max_m, st)
                    : hdd::launch_forward_warp<float>(p.d_nodes, p.d_maps, p.d_lists + li.off, li.n, batch, A, rhs,
-                                                     li.max_nf, st);
+                                                     li.max_nf, li.max_m, st);
       if (e != cudaSuccess) return e;
     }
   return cudaSuccess;
@@ -437,7 +445,7 @@ hdd_status hdd_plan_info(hdd_plan_t plan, hdd_plan_info_t* info) {
   for (int h = 0; h <= p.height; ++h)
     for (int kind = 0; kind < 6; ++kind) {
       const hdd::ListInfo& li = p.lists[p.step_lists[h][kind]];
-      if (li.n) up += (kind == 2 || kind == 5) ? 4 : 1;
+      if (li.n) up += kind == 2 ? 4 : (kind == 5 ? 5 : 1);
     }
   int down_all = 0, fwd = 0;
   for (int d = 0; d <= p.depth; ++d) {

@@ -76,7 +76,20 @@ struct Arenas {
   float* f32; int64_t f32_stride;
   double* s64; int64_t s64_stride;
   float* s32; int64_t s32_stride;
+  double* y64; int64_t y64_stride;
+  float* y32; int64_t y32_stride;
+  unsigned char* tc; int64_t tc_stride;   // split TF32 tiles for the tensor-core SYRK
 };
+
+// y_g of a node (the bordered row of its front): written by the upsweep and by
+// every right-hand-side sweep, read by the descent.
+template <typename T> __device__ __forceinline__ T* node_Y(const Arenas& A, const NodeDev& nd, int s);
+template <> __device__ __forceinline__ double* node_Y<double>(const Arenas& A, const NodeDev& nd, int s) {
+  return A.y64 + (int64_t)s * A.y64_stride + nd.y_off;
+}
+template <> __device__ __forceinline__ float* node_Y<float>(const Arenas& A, const NodeDev& nd, int s) {
+  return A.y32 + (int64_t)s * A.y32_stride + nd.y_off;
+}
 
 // Entry (a, b) of a son's Schur complement (lower triangle is stored), returned
 // in the caller's precision T; the son's own precision is read directly.

@@ -10,6 +10,8 @@
 // (Eq. SchurC1): L_gg L_gg^T = K_gg, L_Bg = K_Bg L_gg^-T, S = K_BB - L_Bg L_Bg^T;
 // the bordered right-hand-side row turns into y_g^T = (L_gg^-1 b_g)^T and the
 // condensed load b_B - L_Bg y_g, i.e. Psi^f c of the paper.
+#include <type_traits>
+
 #include "launch.h"
 
 namespace hdd {
@@ -179,6 +181,8 @@ __global__ void __launch_bounds__(512) k_front_small(StepArgs a) {
   T* F = node_F<T>(a.arenas, nd, s);
   for (int c = warp; c < m; c += nwarp)
     for (int r = lane; r < nf; r += 32) F[c * nf + r] = K[c * ld + r];
+  T* Y = node_Y<T>(a.arenas, nd, s);
+  for (int c = threadIdx.x; c < m; c += blockDim.x) Y[c] = K[c * ld + nf - 1];
   const int nb = nd.b + 1;
   T* S = node_S<T>(a.arenas, nd, s);
   for (int c = warp; c < nb; c += nwarp)
@@ -313,6 +317,49 @@ __global__ void __launch_bounds__(256) k_potrf(StepArgs a) {
   }
 }
 
+// Staging for the tensor-core SYRK (k_syrk_tc): rows [row0, row0 + nr) of X
+// (= F[m:nf, 0:m], relative row numbers; the bordered right-hand-side row is
+// excluded, k_syrk_rhs handles it) split into TF32 hi and lo parts and written in
+// 128-row x kTcChunk-column tiles, K-major core-matrix layout (8 rows x 16 bytes
+// per core matrix, cores along K 128 bytes apart).  The block holding the last
+// boundary row also zero-fills the rest of its tile.
+__device__ __forceinline__ float tf32_rna(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return __uint_as_float(r);
+}
+
+__device__ __forceinline__ void write_tc_tiles(const float* X, int64_t ldx, const NodeDev& nd, const Arenas& A, int s,
+                                               int row0, int nr, bool last) {
+  if (nd.b == 0) return;
+  const int m = nd.m;
+  const int nchunks = (m + kTcChunk - 1) / kTcChunk;
+  if (last) --nr;                      // the right-hand-side row
+  if (last && nr == 0 && row0 % kTcTile == 0) return;   // nothing of this tile is a boundary row
+  const int rows = last ? ((row0 / kTcTile) + 1) * kTcTile - row0 : nr;   // zero-fill to the tile end
+  unsigned char* base = A.tc + (int64_t)s * A.tc_stride + nd.tc_off;
+  const int items = rows * nchunks * (kTcChunk / 4);
+  for (int idx = threadIdx.x; idx < items; idx += blockDim.x) {
+    const int rr = idx % rows;
+    const int rest = idx / rows;
+    const int kq = rest % (kTcChunk / 4), c = rest / (kTcChunk / 4);
+    const int row = row0 + rr, T = row / kTcTile, tr = row % kTcTile;
+    float v[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int k = c * kTcChunk + 4 * kq + q;
+      v[q] = (rr < nr && k < m) ? X[(int64_t)k * ldx + rr] : 0.0f;
+    }
+    float4 hi, lo;
+    hi.x = tf32_rna(v[0]); hi.y = tf32_rna(v[1]); hi.z = tf32_rna(v[2]); hi.w = tf32_rna(v[3]);
+    lo.x = tf32_rna(v[0] - hi.x); lo.y = tf32_rna(v[1] - hi.y); lo.z = tf32_rna(v[2] - hi.z); lo.w = tf32_rna(v[3] - hi.w);
+    const int64_t blk = ((int64_t)T * nchunks + c) * 2 * kTcBlockBytes;
+    const int off = (tr >> 3) * (kTcChunk / 4) * 128 + kq * 128 + (tr & 7) * 16;
+    *reinterpret_cast<float4*>(base + blk + off) = hi;
+    *reinterpret_cast<float4*>(base + blk + kTcBlockBytes + off) = lo;
+  }
+}
+
 // TRSM: rows m..nf-1 of F times L_gg^-T.  One CTA per (row block, node, sample);
 // the row block X stays in shared memory across the column sweep (or is updated
 // in place in global memory when m is too large).  Per 32-column block of L_gg:
@@ -411,6 +458,12 @@ __global__ void __launch_bounds__(256) k_trsm(StepArgs a) {
       const int c = idx / R, rr = idx - c * R;
       if (rr < nr) A[(int64_t)c * nf + r0 + rr] = Xs[idx];
     }
+  if (r0 + nr == nf) {   // this block holds the bordered row: y_g
+    T* Y = node_Y<T>(a.arenas, nd, s);
+    for (int c = threadIdx.x; c < m; c += blockDim.x) Y[c] = X[c * ldx + (nr - 1)];
+  }
+  if (std::is_same<T, float>::value && nd.tc_off >= 0)
+    write_tc_tiles(reinterpret_cast<const float*>(X), ldx, nd, a.arenas, s, blockIdx.x * R, nr, r0 + nr == nf);
 }
 
 // SYRK: S -= X X^T with X = F[m:nf, 0:m] (b+1 rows incl. the right-hand side).
@@ -467,6 +520,28 @@ __global__ void k_syrk(StepArgs a) {
   }
 }
 
+// The bordered right-hand-side row of S for fronts whose SYRK runs on the tensor
+// cores: S[b, j] -= sum_k y_k X[j, k] for j = 0..b (y = the last row of X), one
+// CTA per (node, sample), threads over j (coalesced down the columns of F).
+__global__ void k_syrk_rhs(StepArgs a) {
+  const int node = a.list[blockIdx.x];
+  const int s = blockIdx.y;
+  const NodeDev nd = a.nodes[node];
+  const int nf = nd.nf, m = nd.m, b = nd.b, nb = b + 1;
+  if (m == 0) return;
+  const float* X = a.arenas.f32 + (int64_t)s * a.arenas.f32_stride + nd.f_off + m;
+  float* S = a.arenas.s32 + (int64_t)s * a.arenas.s32_stride + nd.s_off;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float* y = reinterpret_cast<float*>(smem_raw);
+  for (int k = threadIdx.x; k < m; k += blockDim.x) y[k] = X[(int64_t)k * nf + b];
+  __syncthreads();
+  for (int j = threadIdx.x; j <= b; j += blockDim.x) {
+    float acc = 0.0f;
+    for (int k = 0; k < m; ++k) acc += y[k] * X[(int64_t)k * nf + j];
+    S[(int64_t)j * nb + b] -= acc;
+  }
+}
+
 template <typename T>
 cudaError_t launch_front_large(const StepArgs& a, cudaStream_t st) {
   if (a.nlist == 0) return cudaSuccess;
@@ -485,6 +560,13 @@ cudaError_t launch_front_large(const StepArgs& a, cudaStream_t st) {
     const size_t smem = (xrows * R + 32 * 33 + 3 + 32 * 64) * sizeof(T) + 16;
     dim3 grid((a.max_b + 1 + R - 1) / R, a.nlist, a.batch);
     k_trsm<T><<<grid, 256, smem, st>>>(a);
+  }
+  if (std::is_same<T, float>::value) {
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    if ((e = launch_syrk_tc(a, st)) != cudaSuccess) return e;   // tensor cores, 3xTF32, boundary rows
+    k_syrk_rhs<<<dim3(a.nlist, a.batch), 256, (size_t)a.max_m * sizeof(float), st>>>(a);
+    return cudaGetLastError();
   }
   {
     const int nt = (a.max_b + 1 + kSyrkTile - 1) / kSyrkTile;

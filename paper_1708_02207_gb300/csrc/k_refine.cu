@@ -26,9 +26,10 @@ template <> __device__ __forceinline__ float* fwd_S<float>(const Arenas& A, cons
   return A.s32 + (int64_t)s * A.s32_stride + nd.s_off;
 }
 
-// condensed right-hand side entry p of a son (last row of its Schur block)
+// condensed right-hand side entry p of a son, stored contiguously at the start
+// of the son's Schur block by the son's own right-hand-side sweep
 __device__ __forceinline__ double son_rhs(const Arenas& A, const NodeDev& ch, int s, int p) {
-  const int64_t idx = (int64_t)p * (ch.b + 1) + ch.b + ch.s_off;
+  const int64_t idx = (int64_t)p + ch.s_off;
   return ch.fp64 ? A.s64[(int64_t)s * A.s64_stride + idx] : (double)A.s32[(int64_t)s * A.s32_stride + idx];
 }
 
@@ -81,10 +82,11 @@ __global__ void k_forward(const NodeDev* __restrict__ nodes, const int32_t* __re
     }
   }
   __syncthreads();
-  for (int c = threadIdx.x; c < m; c += blockDim.x) F[(int64_t)c * nf + nf - 1] = z[c];
+  T* Y = node_Y<T>(A, nd, s);
+  for (int c = threadIdx.x; c < m; c += blockDim.x) Y[c] = z[c];
   if (b > 0) {
     T* S = fwd_S<T>(A, nd, s);
-    for (int r = threadIdx.x; r < b; r += blockDim.x) S[(int64_t)r * (b + 1) + b] = z[m + r];
+    for (int r = threadIdx.x; r < b; r += blockDim.x) S[r] = z[m + r];
   }
 }
 

@@ -72,6 +72,11 @@ template <> __device__ __forceinline__ const float* fac_ptr<float>(const Arenas&
 }
 
 template <typename T>
+__device__ __forceinline__ const T* fac_Y(const Arenas& A, const NodeDev& nd, int s) {
+  return node_Y<T>(A, nd, s);
+}
+
+template <typename T>
 __global__ void k_descent(const NodeDev* __restrict__ nodes, const int32_t* __restrict__ maps,
                           const int32_t* __restrict__ list, Arenas A, double* __restrict__ u, int64_t u_stride) {
   const int node = list[blockIdx.x];
@@ -87,13 +92,14 @@ __global__ void k_descent(const NodeDev* __restrict__ nodes, const int32_t* __re
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarp = blockDim.x >> 5;
   for (int i = threadIdx.x; i < b; i += blockDim.x) uB[i] = (T)us[vid[m + i]];
   __syncthreads();
+  const T* Y = fac_Y<T>(A, nd, s);
   for (int c = warp; c < m; c += nwarp) {
     const T* col = F + (int64_t)c * nf;
     T acc = (T)0;
     for (int i = lane; i < b; i += 32) acc += col[m + i] * uB[i];
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-    if (lane == 0) t[c] = col[nf - 1] - acc;
+    if (lane == 0) t[c] = Y[c] - acc;
   }
   for (int cb = ((m - 1) / 32) * 32; cb >= 0; cb -= 32) {
     const int jb = min(32, m - cb);

@@ -1,0 +1,216 @@
+// Schur-complement update on the 5th-generation tensor cores (tcgen05, sm_103a).
+//
+// S -= X X^T over the b boundary rows of the large FP32 fronts (X = F[m:nf, 0:m];
+// the bordered right-hand-side row is done by k_syrk_rhs), i.e. the SYRK of the
+// partial Cholesky of Sec. 2.4
+// (Eq. SchurC1: A11 - A12 A22^-1 A21 = K_BB - L_Bg L_Bg^T).  One CTA of 128
+// threads computes one 128 x 128 lower tile pair of one (node, sample):
+//   * the TRSM that produced X also wrote it split into TF32 hi and lo parts,
+//     in 128-row x 16-column tiles in the K-major, no-swizzle core-matrix layout
+//     (8-row x 16-byte core matrices) that the MMA reads from shared memory;
+//   * one thread runs the pipeline: cp.async.bulk copies (completion counted in
+//     bytes on an mbarrier) fill kStages shared-memory stages, and for each
+//     16-column chunk it issues tcgen05.mma kind::tf32 (M = N = 128, K = 8)
+//     three times per step, hi*hi + hi*lo + lo*hi ("3xTF32", about FP32
+//     accuracy), with the accumulator in tensor memory (128 lanes x 128 columns);
+//     tcgen05.commit frees a stage for the next copy;
+//   * every wait is bounded; a timeout marks the sample HDD_ETIMEOUT;
+//   * the four warps read their 32 accumulator lanes with tcgen05.ld and subtract
+//     them from S (coalesced along the rows of S).
+#include "launch.h"
+
+namespace hdd {
+
+namespace {
+
+constexpr int kTile = kTcTile;        // M = N of the MMA and of the output tile
+constexpr int kChunk = kTcChunk;      // contraction columns staged per buffer
+constexpr int kTileBytes = (int)kTcBlockBytes;          // one operand part (8 KiB)
+constexpr int kStageBytes = 4 * kTileBytes;             // A hi/lo, B hi/lo (32 KiB)
+constexpr int kStages = 2;                              // pipeline depth: 64 KiB, 3 CTAs per SM
+constexpr uint32_t kWaitLimit = 1u << 24;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// Shared-memory matrix descriptor: K-major, no swizzle.  lbo = bytes between
+// core matrices along K, sbo = bytes between 8-row groups; bit 46 = descriptor
+// version of tcgen05.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+  return (uint64_t)((saddr >> 4) & 0x3FFF) | ((uint64_t)((lbo >> 4) & 0x3FFF) << 16) |
+         ((uint64_t)((sbo >> 4) & 0x3FFF) << 32) | ((uint64_t)1 << 46);
+}
+
+// Instruction descriptor: D = F32, A = B = TF32, both K-major, N = M = 128.
+__device__ __forceinline__ uint32_t idesc_tf32() {
+  return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(kTile >> 3) << 17) | ((uint32_t)(kTile >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_tf32(uint32_t tmem, uint64_t da, uint64_t db, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n.reg .pred p;\nsetp.ne.u32 p, %4, 0;\n"
+      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}" ::"r"(tmem),
+      "l"(da), "l"(db), "r"(idesc), "r"(acc));
+}
+
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t phase) {
+  for (uint32_t it = 0; it < kWaitLimit; ++it) {
+    uint32_t done;
+    asm volatile(
+        "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}"
+        : "=r"(done)
+        : "r"(mbar), "r"(phase));
+    if (done) return true;
+  }
+  return false;
+}
+
+}  // namespace
+
+__global__ void __launch_bounds__(128, 3) k_syrk_tc(StepArgs a) {
+  const int node = a.list[blockIdx.y];
+  const int s = blockIdx.z;
+  const NodeDev nd = a.nodes[node];
+  const int m = nd.m, nb = nd.b + 1, nbt = nd.b;   // tiles cover the b boundary rows
+  const int nt = (nbt + kTile - 1) / kTile;
+  if ((int)blockIdx.x >= nt * (nt + 1) / 2 || m == 0 || nd.tc_off < 0) return;
+  int TI = (int)((sqrtf(8.0f * (float)blockIdx.x + 1.0f) - 1.0f) * 0.5f);
+  while (TI * (TI + 1) / 2 > (int)blockIdx.x) --TI;
+  while ((TI + 1) * (TI + 2) / 2 <= (int)blockIdx.x) ++TI;
+  const int TJ = blockIdx.x - TI * (TI + 1) / 2;
+
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  unsigned char* stage =
+      reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  __shared__ __align__(8) uint64_t full[kStages], empty[kStages];
+  __shared__ uint32_t tmem_slot;
+  __shared__ int timed_out;
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
+                 "r"(kTile));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  if (tid == 0) {
+    for (int b = 0; b < kStages; ++b) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&full[b])));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&empty[b])));
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;");
+    timed_out = 0;
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  const uint32_t tmem = tmem_slot;
+
+  if (tid == 0) {
+    // one thread runs the pipeline: bulk copies of the split tiles (TI: A, TJ: B)
+    // into kStages shared-memory stages, tensor-core MMAs out of them
+    const int nchunks = (m + kChunk - 1) / kChunk;
+    const unsigned char* base = a.arenas.tc + (int64_t)s * a.arenas.tc_stride + nd.tc_off;
+    const uint32_t idesc = idesc_tf32();
+    const uint32_t sbo = (kChunk / 4) * 128;
+    uint32_t ph_full[kStages] = {}, ph_empty[kStages] = {};
+    bool ok = true;
+    auto load = [&](int c) {
+      const int b = c % kStages;
+      const uint32_t dst = smem_u32(stage + b * kStageBytes);
+      const uint32_t bar = smem_u32(&full[b]);
+      const unsigned char* srcA = base + ((int64_t)TI * nchunks + c) * 2 * kTileBytes;
+      const unsigned char* srcB = base + ((int64_t)TJ * nchunks + c) * 2 * kTileBytes;
+      asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(kStageBytes));
+      asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+                   "l"(srcA), "r"(2 * kTileBytes), "r"(bar)
+                   : "memory");
+      asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                       dst + 2 * kTileBytes),
+                   "l"(srcB), "r"(2 * kTileBytes), "r"(bar)
+                   : "memory");
+    };
+    for (int c = 0; c < nchunks && c < kStages; ++c) load(c);
+    for (int c = 0; c < nchunks; ++c) {
+      const int b = c % kStages;
+      if (!mbar_wait(smem_u32(&full[b]), ph_full[b])) { ok = false; break; }
+      ph_full[b] ^= 1u;
+      asm volatile("tcgen05.fence::after_thread_sync;");
+      const uint32_t Ah = smem_u32(stage + b * kStageBytes);
+      const uint32_t Al = Ah + kTileBytes, Bh = Ah + 2 * kTileBytes, Bl = Ah + 3 * kTileBytes;
+#pragma unroll
+      for (int t = 0; t < kChunk / 8; ++t) {
+        const uint32_t o = t * 256;   // two core matrices (128 bytes apart along K) per MMA
+        const uint64_t dah = smem_desc(Ah + o, 128, sbo), dal = smem_desc(Al + o, 128, sbo);
+        const uint64_t dbh = smem_desc(Bh + o, 128, sbo), dbl = smem_desc(Bl + o, 128, sbo);
+        mma_tf32(tmem, dah, dbh, idesc, (c > 0 || t > 0) ? 1u : 0u);
+        mma_tf32(tmem, dah, dbl, idesc, 1u);
+        mma_tf32(tmem, dal, dbh, idesc, 1u);
+      }
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+          smem_u32(&empty[b])));
+      if (c + kStages < nchunks) {   // refill this stage once its MMAs are done
+        if (!mbar_wait(smem_u32(&empty[b]), ph_empty[b])) { ok = false; break; }
+        ph_empty[b] ^= 1u;
+        load(c + kStages);
+      }
+    }
+    // the MMAs of the last chunks: their commits have not been waited for yet
+    if (ok)
+      for (int c = max(0, nchunks - kStages); c < nchunks; ++c) {
+        const int b = c % kStages;
+        if (!mbar_wait(smem_u32(&empty[b]), ph_empty[b])) { ok = false; break; }
+        ph_empty[b] ^= 1u;
+      }
+    if (!ok) timed_out = 1;
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  if (timed_out) {
+    if (tid == 0) flag_status(a.status, s, -HDD_ETIMEOUT, node);
+  } else {
+    float* S = a.arenas.s32 + (int64_t)s * a.arenas.s32_stride + nd.s_off;
+    const int i = TI * kTile + warp * 32 + lane;   // accumulator lane = tile row
+#pragma unroll 1
+    for (int c0 = 0; c0 < kTile; c0 += 32) {
+      if (TI == TJ && c0 > warp * 32 + 31) break;   // strictly above the diagonal of this warp's rows
+      uint32_t r[32];
+      const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0;
+      asm volatile(
+          "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+          "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+          : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+            "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+            "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+            "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+          : "r"(taddr));
+      asm volatile("tcgen05.wait::ld.sync.aligned;");
+      if (i < nbt) {
+#pragma unroll
+        for (int q = 0; q < 32; ++q) {
+          const int j = TJ * kTile + c0 + q;
+          if (j < nbt && i >= j) S[(int64_t)j * nb + i] -= __uint_as_float(r[q]);
+        }
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTile));
+}
+
+constexpr size_t kSyrkTcSmem = kStages * (size_t)kStageBytes + 1024;
+
+cudaError_t launch_syrk_tc(const StepArgs& a, cudaStream_t st) {
+  if (a.nlist == 0) return cudaSuccess;
+  const int nt = (a.max_b + kTile - 1) / kTile;
+  if (nt == 0) return cudaSuccess;
+  dim3 grid(nt * (nt + 1) / 2, a.nlist, a.batch);
+  k_syrk_tc<<<grid, 128, kSyrkTcSmem, st>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t configure_tc_kernels() {
+  return cudaFuncSetAttribute(k_syrk_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSyrkTcSmem);
+}
+
+}  // namespace hdd

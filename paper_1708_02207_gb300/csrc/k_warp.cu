@@ -122,6 +122,12 @@ __global__ void __launch_bounds__(256) k_front_warp(StepArgs a) {
 #pragma unroll
   for (int c = 0; c < 32; ++c)
     if (c < m && lane < nf) F[c * nf + lane] = row[c];
+  if (lane == nf - 1) {
+    T* Y = node_Y<T>(a.arenas, nd, s);
+#pragma unroll
+    for (int c = 0; c < 32; ++c)
+      if (c < m) Y[c] = row[c];
+  }
   T* S = warp_S<T>(a.arenas, nd, s);
 #pragma unroll
   for (int c = 0; c < 32; ++c)
@@ -149,29 +155,38 @@ static int sweep_warps(size_t bytes_per_warp) {
 // ---------------------------------------------------------------------------
 // Right-hand-side sweep at one node (leaves to root), one warp per sample:
 // z = sons' condensed right-hand sides + r at gamma; y = L_gg^-1 z_g column by
-// column (coalesced down each column of F), folding every column into the rows
-// below it, which leaves z_B - L_Bg y_g.
+// column, folding every column into the rows below it, which leaves z_B - L_Bg y_g.
+// The node's factor block is first staged in shared memory with coalesced loads
+// (all in flight at once), so the sequential solve runs on shared memory.
+// Outputs: y_g into the y arena, the condensed right-hand side (b entries)
+// contiguously at the start of the node's (now unused) Schur block.
 template <typename T>
 __device__ __forceinline__ T son_cond(const Arenas& A, const NodeDev& ch, int s, int p) {
-  const int64_t idx = (int64_t)p * (ch.b + 1) + ch.b + ch.s_off;
+  const int64_t idx = (int64_t)p + ch.s_off;
   return ch.fp64 ? (T)A.s64[(int64_t)s * A.s64_stride + idx] : (T)A.s32[(int64_t)s * A.s32_stride + idx];
 }
 
 template <typename T>
 __global__ void __launch_bounds__(256) k_forward_warp(const NodeDev* __restrict__ nodes,
                                                       const int32_t* __restrict__ maps,
-                                                      const int32_t* __restrict__ list, int batch, int zstride,
-                                                      Arenas A, Rhs rhs) {
+                                                      const int32_t* __restrict__ list, int batch, int wstride,
+                                                      int stage, Arenas A, Rhs rhs) {
   const int node = list[blockIdx.x];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int s = blockIdx.y * (blockDim.x >> 5) + warp;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* z = reinterpret_cast<T*>(smem_raw) + warp * zstride;
+  T* z = reinterpret_cast<T*>(smem_raw) + warp * wstride;
   if (s >= batch) return;
   const NodeDev nd = nodes[node];
   const int m = nd.m, b = nd.b, nf = nd.nf;
   const int32_t* vid = maps + nd.map_off;
-  T* F = warp_F<T>(A, nd, s);
+  const T* Fg = warp_F<T>(A, nd, s);
+  const T* F = Fg;
+  if (stage) {
+    T* Fs = z + ((nf + 3) & ~3);
+    for (int idx = lane; idx < nf * m; idx += 32) Fs[idx] = Fg[idx];
+    F = Fs;
+  }
   if (nd.leaf) {
     for (int r = lane; r < nf - 1; r += 32) z[r] = (r < m) ? (T)rhs(s, vid[r]) : (T)0;
   } else {
@@ -195,38 +210,50 @@ __global__ void __launch_bounds__(256) k_forward_warp(const NodeDev* __restrict_
     if (lane == 0) z[c] = yc;
     __syncwarp();
   }
-  for (int c = lane; c < m; c += 32) F[(int64_t)c * nf + nf - 1] = z[c];
+  T* Y = node_Y<T>(A, nd, s);
+  for (int c = lane; c < m; c += 32) Y[c] = z[c];
   if (b > 0) {
     T* S = warp_S<T>(A, nd, s);
-    for (int r = lane; r < b; r += 32) S[(int64_t)r * (b + 1) + b] = z[m + r];
+    for (int r = lane; r < b; r += 32) S[r] = z[m + r];
   }
+}
+
+// Bytes of shared memory per warp of a sweep: the vector, plus the staged
+// factor block when it fits in 64 KiB.
+template <typename T>
+static int sweep_stride(int max_nf, int max_m, int* stage) {
+  const size_t vec = (size_t)((max_nf + 3) & ~3);
+  const size_t fac = (size_t)max_nf * max_m;
+  *stage = (vec + fac) * sizeof(T) <= 64 * 1024;
+  return (int)(*stage ? vec + fac : vec);
 }
 
 template <typename T>
 cudaError_t launch_forward_warp(const NodeDev* nodes, const int32_t* maps, const int32_t* list, int nlist, int batch,
-                                const Arenas& A, const Rhs& rhs, int max_nf, cudaStream_t st) {
+                                const Arenas& A, const Rhs& rhs, int max_nf, int max_m, cudaStream_t st) {
   if (nlist == 0) return cudaSuccess;
-  const int zs = (max_nf + 1) & ~1;
-  const int wpb = sweep_warps(zs * sizeof(T));
-  k_forward_warp<T><<<dim3(nlist, (batch + wpb - 1) / wpb), 32 * wpb, (size_t)wpb * zs * sizeof(T), st>>>(
-      nodes, maps, list, batch, zs, A, rhs);
+  int stage = 0;
+  const int ws = sweep_stride<T>(max_nf, max_m, &stage);
+  const int wpb = sweep_warps((size_t)ws * sizeof(T));
+  k_forward_warp<T><<<dim3(nlist, (batch + wpb - 1) / wpb), 32 * wpb, (size_t)wpb * ws * sizeof(T), st>>>(
+      nodes, maps, list, batch, ws, stage, A, rhs);
   return cudaGetLastError();
 }
 template cudaError_t launch_forward_warp<double>(const NodeDev*, const int32_t*, const int32_t*, int, int,
-                                                 const Arenas&, const Rhs&, int, cudaStream_t);
+                                                 const Arenas&, const Rhs&, int, int, cudaStream_t);
 template cudaError_t launch_forward_warp<float>(const NodeDev*, const int32_t*, const int32_t*, int, int,
-                                                const Arenas&, const Rhs&, int, cudaStream_t);
+                                                const Arenas&, const Rhs&, int, int, cudaStream_t);
 
 // ---------------------------------------------------------------------------
 // Descent at one node (Root to Leaves), one warp per sample: with w = [u_g; u_B]
 // (u_B gathered from the vertex vector), for c = m-1 .. 0
 //   u_c = (y_c - sum_{r > c} F[r, c] w_r) / F[c, c],
-// i.e. L_gg^T u_g = y_g - L_Bg^T u_B, each column of F read once, coalesced.
+// i.e. L_gg^T u_g = y_g - L_Bg^T u_B; the factor block is staged first.
 template <typename T>
 __global__ void __launch_bounds__(256) k_descent_warp(const NodeDev* __restrict__ nodes,
                                                       const int32_t* __restrict__ maps,
                                                       const int32_t* __restrict__ list, int batch, int wstride,
-                                                      Arenas A, double* __restrict__ u, int64_t u_stride) {
+                                                      int stage, Arenas A, double* __restrict__ u, int64_t u_stride) {
   const int node = list[blockIdx.x];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int s = blockIdx.y * (blockDim.x >> 5) + warp;
@@ -236,7 +263,14 @@ __global__ void __launch_bounds__(256) k_descent_warp(const NodeDev* __restrict_
   const NodeDev nd = nodes[node];
   const int m = nd.m, b = nd.b, nf = nd.nf;
   const int32_t* vid = maps + nd.map_off;
-  const T* F = warp_F<T>(A, nd, s);
+  const T* Fg = warp_F<T>(A, nd, s);
+  const T* F = Fg;
+  if (stage) {
+    T* Fs = wv + ((nf + 3) & ~3);
+    for (int idx = lane; idx < nf * m; idx += 32) Fs[idx] = Fg[idx];
+    F = Fs;
+  }
+  const T* Y = node_Y<T>(A, nd, s);
   double* us = u + (int64_t)s * u_stride;
   for (int i = lane; i < b; i += 32) wv[m + i] = (T)us[vid[m + i]];
   __syncwarp();
@@ -246,7 +280,7 @@ __global__ void __launch_bounds__(256) k_descent_warp(const NodeDev* __restrict_
     for (int r = c + 1 + lane; r < nf - 1; r += 32) acc += col[r] * wv[r];
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(kFull, acc, o);
-    const T uc = (col[nf - 1] - acc) / col[c];
+    const T uc = (Y[c] - acc) / col[c];
     if (lane == 0) wv[c] = uc;
     __syncwarp();
   }
@@ -255,18 +289,20 @@ __global__ void __launch_bounds__(256) k_descent_warp(const NodeDev* __restrict_
 
 template <typename T>
 cudaError_t launch_descent_warp(const NodeDev* nodes, const int32_t* maps, const int32_t* list, int nlist, int batch,
-                                const Arenas& A, double* u, int64_t u_stride, int max_nf, cudaStream_t st) {
+                                const Arenas& A, double* u, int64_t u_stride, int max_nf, int max_m,
+                                cudaStream_t st) {
   if (nlist == 0) return cudaSuccess;
-  const int ws = (max_nf + 1) & ~1;
-  const int wpb = sweep_warps(ws * sizeof(T));
+  int stage = 0;
+  const int ws = sweep_stride<T>(max_nf, max_m, &stage);
+  const int wpb = sweep_warps((size_t)ws * sizeof(T));
   k_descent_warp<T><<<dim3(nlist, (batch + wpb - 1) / wpb), 32 * wpb, (size_t)wpb * ws * sizeof(T), st>>>(
-      nodes, maps, list, batch, ws, A, u, u_stride);
+      nodes, maps, list, batch, ws, stage, A, u, u_stride);
   return cudaGetLastError();
 }
 template cudaError_t launch_descent_warp<double>(const NodeDev*, const int32_t*, const int32_t*, int, int,
-                                                 const Arenas&, double*, int64_t, int, cudaStream_t);
+                                                 const Arenas&, double*, int64_t, int, int, cudaStream_t);
 template cudaError_t launch_descent_warp<float>(const NodeDev*, const int32_t*, const int32_t*, int, int,
-                                                const Arenas&, double*, int64_t, int, cudaStream_t);
+                                                const Arenas&, double*, int64_t, int, int, cudaStream_t);
 
 }  // namespace hdd
 

@@ -33,12 +33,15 @@ template <typename T> cudaError_t launch_front_warp(const StepArgs& a, cudaStrea
 // sweeps with one warp per (node, sample)
 template <typename T>
 cudaError_t launch_forward_warp(const NodeDev* nodes, const int32_t* maps, const int32_t* list, int nlist, int batch,
-                                const Arenas& A, const Rhs& rhs, int max_nf, cudaStream_t st);
+                                const Arenas& A, const Rhs& rhs, int max_nf, int max_m, cudaStream_t st);
 template <typename T>
 cudaError_t launch_descent_warp(const NodeDev* nodes, const int32_t* maps, const int32_t* list, int nlist, int batch,
-                                const Arenas& A, double* u, int64_t u_stride, int max_nf, cudaStream_t st);
+                                const Arenas& A, double* u, int64_t u_stride, int max_nf, int max_m,
+                                cudaStream_t st);
 // fronts that fit in shared memory: build + partial Cholesky + store, one CTA each
 template <typename T> cudaError_t launch_front_small(const StepArgs& a, cudaStream_t st);
+// SYRK of large FP32 fronts on the tensor cores (tcgen05, 3xTF32)
+cudaError_t launch_syrk_tc(const StepArgs& a, cudaStream_t st);
 // large fronts: fill in global memory, then POTRF of gamma, TRSM of the rest, SYRK into S
 template <typename T> cudaError_t launch_front_large(const StepArgs& a, cudaStream_t st);
 

@@ -172,11 +172,28 @@ std::string build_plan(const hdd_plan_desc& d, Plan& p) {
 
   // factor store offsets (all nodes keep their factors)
   p.f64_stride = p.f32_stride = 0;
+  p.y64_stride = p.y32_stride = 0;
   for (Node& nd : p.nodes) {
+    int64_t& ys = nd.fp64 ? p.y64_stride : p.y32_stride;
+    nd.y_off = ys;
+    ys += nd.m;
     int64_t sz = (int64_t)nd.nf * nd.m;
     int64_t& st = nd.fp64 ? p.f64_stride : p.f32_stride;
     nd.f_off = st;
     st += (sz + 31) / 32 * 32;
+  }
+
+  // tensor-core staging (large FP32 fronts): lives within one height step
+  p.tc_stride = 0;
+  for (int hgt = 0; hgt <= p.height; ++hgt) {
+    int64_t off = 0;
+    for (int k : p.steps[hgt].large32) {
+      Node& nd = p.nodes[k];
+      const int64_t tiles = (nd.b + kTcTile - 1) / kTcTile, chunks = (nd.m + kTcChunk - 1) / kTcChunk;
+      nd.tc_off = off;
+      off += tiles * chunks * 2 * kTcBlockBytes;
+    }
+    p.tc_stride = std::max(p.tc_stride, off);
   }
 
   // Schur arena: a node's S lives from its own step to its parent's step.
@@ -316,6 +333,8 @@ std::string build_plan(const hdd_plan_desc& d, Plan& p) {
     d.map_off = (int32_t)nd.map_off;
     d.up_off = (int32_t)nd.up_off;
     d.fp64 = nd.fp64;
+    d.y_off = (int32_t)nd.y_off;
+    d.tc_off = nd.tc_off;
     d.f_off = nd.f_off; d.s_off = nd.s_off;
   }
 
@@ -348,6 +367,9 @@ Layout layout(const Plan& p, int batch) {
   }
   L.f64 = take(B * (size_t)p.f64_stride * 8);
   L.f32 = take(B * (size_t)p.f32_stride * 4);
+  L.tc = take(B * (size_t)p.tc_stride);
+  L.y64 = take(B * (size_t)p.y64_stride * 8);
+  L.y32 = take(B * (size_t)p.y32_stride * 4);
   L.s64 = take(B * (size_t)p.s64_stride * 8);
   L.s32 = take(B * (size_t)p.s32_stride * 4);
   L.uobs = take(B * p.n_obs * 8);

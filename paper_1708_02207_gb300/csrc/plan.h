@@ -12,7 +12,7 @@
 
 namespace hdd {
 
-// Device-side node descriptor (72 bytes).  A node's front has nf = m + b + 1
+// Device-side node descriptor (80 bytes).  A node's front has nf = m + b + 1
 // rows: m eliminated vertices (gamma, or a leaf's interior), b boundary unknowns,
 // and one bordered right-hand-side row.  Per sample the front is stored as
 //   F: nf x m column-major (ld nf)      -> L_gg (rows < m), L_Bg, y_g^T (last row)
@@ -25,11 +25,12 @@ struct NodeDev {
   int32_t map_off;          // ints into the map table: vid[nf-1], then pos0[nf], pos1[nf]
   int32_t up_off;           // ints into the map table: father-front row of each Schur row [b+1]
   int32_t fp64;             // 1 if this node's factors are FP64 (mixed plans: top levels)
-  int32_t pad_;
+  int32_t y_off;            // elements into a sample's y arena of the node's type: y_g [m]
   int64_t f_off;            // elements into a sample's factor store of the node's type
   int64_t s_off;            // elements into a sample's Schur arena of the node's type
+  int64_t tc_off;           // bytes into a sample's tensor-core staging arena, or -1
 };
-static_assert(sizeof(NodeDev) == 72, "NodeDev layout");
+static_assert(sizeof(NodeDev) == 80, "NodeDev layout");
 
 struct Node {
   int x0, x1, y0, y1;
@@ -43,7 +44,7 @@ struct Node {
   bool visited = false;
   bool fp64 = true;
   int m = 0, b = 0, nf = 0;
-  int64_t f_off = 0, s_off = 0;
+  int64_t f_off = 0, s_off = 0, y_off = 0, tc_off = -1;
   int64_t map_off = 0;
   int64_t up_off = 0;
   bool leaf() const { return child[0] < 0; }
@@ -81,6 +82,8 @@ struct Plan {
 
   // per-sample sizes (elements)
   int64_t f64_stride = 0, f32_stride = 0;   // factor stores
+  int64_t y64_stride = 0, y32_stride = 0;   // y_g arenas (one entry per eliminated vertex)
+  int64_t tc_stride = 0;                    // bytes: split TF32 tiles of one height step
   int64_t s64_stride = 0, s32_stride = 0;   // Schur arenas (lifetime-packed)
   double flops_up = 0.0, flops_down = 0.0;
 
@@ -102,6 +105,10 @@ struct Plan {
 // Fronts of at most kTinyMax rows run one per warp in registers; up to the
 // kSmallMax limits one per CTA in shared memory; larger ones in global memory.
 constexpr int kTinyMax = 32;
+// Tensor-core SYRK staging: 128-row tiles x 16-column chunks, hi and lo parts of
+// 8 KiB each (TF32 values in the 8-row x 16-byte core-matrix layout).
+constexpr int kTcTile = 128, kTcChunk = 16;
+constexpr int64_t kTcBlockBytes = (int64_t)kTcTile * kTcChunk * 4;
 constexpr int kSmallMax64 = 160;   // 160^2 * 8 B = 200 KiB
 constexpr int kSmallMax32 = 224;   // 224^2 * 4 B = 196 KiB
 
@@ -112,7 +119,7 @@ std::string build_plan(const hdd_plan_desc& d, Plan& p);
 struct Layout {
   size_t status = 0, kappa = 0, kappa32 = 0;
   size_t u = 0, r = 0, du = 0;        // FP64 vertex vectors [batch x N^2]
-  size_t f64 = 0, f32 = 0, s64 = 0, s32 = 0;
+  size_t f64 = 0, f32 = 0, s64 = 0, s32 = 0, y64 = 0, y32 = 0, tc = 0;
   size_t uobs = 0, ll = 0, z = 0, y = 0, conv = 0;
   size_t total = 0;
 };
