@@ -81,6 +81,23 @@ __device__ __forceinline__ void tri_index(int idx, int& ti, int& tj) {
 // Panel width of the blocked factorisation of shared-memory fronts.
 constexpr int kSmallPanel = 8;
 
+// Four consecutive values through 16-byte shared-memory accesses.
+__device__ __forceinline__ void load4(const float* p, float (&v)[4]) {
+  const float4 t = *reinterpret_cast<const float4*>(p);
+  v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
+}
+__device__ __forceinline__ void load4(const double* p, double (&v)[4]) {
+  const double2 a = *reinterpret_cast<const double2*>(p), b = *reinterpret_cast<const double2*>(p + 2);
+  v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+}
+__device__ __forceinline__ void store4(float* p, const float (&v)[4]) {
+  *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+}
+__device__ __forceinline__ void store4(double* p, const double (&v)[4]) {
+  *reinterpret_cast<double2*>(p) = make_double2(v[0], v[1]);
+  *reinterpret_cast<double2*>(p + 2) = make_double2(v[2], v[3]);
+}
+
 // Leading dimension of a shared-memory front: a multiple of 4, congruent to 4
 // modulo 8, so that column-varying accesses spread over 8 banks.
 __host__ __device__ __forceinline__ int front_ld(int nf) {
@@ -154,24 +171,34 @@ __global__ void __launch_bounds__(512) k_front_small(StepArgs a) {
         for (int l = k0; l < kend; ++l) {
           const T* col = K + l * ld;
           T x[4], y[4];
-#pragma unroll
-          for (int q = 0; q < 4; ++q) {
-            x[q] = col[i0 + q];
-            y[q] = col[j0 + q];
-          }
+          load4(col + i0, x);   // 16-byte aligned: ld and i0 are multiples of 4
+          load4(col + j0, y);
 #pragma unroll
           for (int q = 0; q < 4; ++q)
 #pragma unroll
             for (int w = 0; w < 4; ++w) acc[q][w] += x[q] * y[w];
         }
+        const bool interior = j0 >= kend && i0 >= j0 + 4 && i0 + 3 < nf;
+        if (interior) {
 #pragma unroll
-        for (int w = 0; w < 4; ++w) {
-          const int j = j0 + w;
-          if (j < kend || j >= nf) continue;
+          for (int w = 0; w < 4; ++w) {
+            T* cw = K + (j0 + w) * ld + i0;
+            T v[4];
+            load4(cw, v);
 #pragma unroll
-          for (int q = 0; q < 4; ++q) {
-            const int i = i0 + q;
-            if (i < nf && i >= j) K[j * ld + i] -= acc[q][w];
+            for (int q = 0; q < 4; ++q) v[q] -= acc[q][w];
+            store4(cw, v);
+          }
+        } else {
+#pragma unroll
+          for (int w = 0; w < 4; ++w) {
+            const int j = j0 + w;
+            if (j < kend || j >= nf) continue;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+              const int i = i0 + q;
+              if (i < nf && i >= j) K[j * ld + i] -= acc[q][w];
+            }
           }
         }
       }
@@ -302,16 +329,21 @@ __global__ void __launch_bounds__(256) k_potrf(StepArgs a) {
 #pragma unroll
             for (int w = 0; w < 4; ++w) acc[q][w] += x[q] * y[w];
         }
+        T av[4][4];   // loads first (in flight together), then the stores
 #pragma unroll
-        for (int w = 0; w < 4; ++w) {
-          const int j = j0 + w;
-          if (j >= rows) break;
+        for (int w = 0; w < 4; ++w)
 #pragma unroll
           for (int q = 0; q < 4; ++q) {
-            const int i = i0 + q;
-            if (i < rows && i >= j) A[(int64_t)(k0 + j) * nf + k0 + i] -= acc[q][w];
+            const int j = j0 + w, i = i0 + q;
+            av[q][w] = (j < rows && i < rows && i >= j) ? A[(int64_t)(k0 + j) * nf + k0 + i] : (T)0;
           }
-        }
+#pragma unroll
+        for (int w = 0; w < 4; ++w)
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            const int j = j0 + w, i = i0 + q;
+            if (j < rows && i < rows && i >= j) A[(int64_t)(k0 + j) * nf + k0 + i] = av[q][w] - acc[q][w];
+          }
       }
     }
   }
@@ -509,13 +541,23 @@ __global__ void k_syrk(StepArgs a) {
     }
     __syncthreads();
   }
+  T sv[4][4];   // loads first (in flight together), then the stores
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
     const int i = TI * kSyrkTile + ty + 16 * q;
 #pragma unroll
     for (int w = 0; w < 4; ++w) {
       const int j = TJ * kSyrkTile + tx + 16 * w;
-      if (i < nb && j < nb && i >= j) S[(int64_t)j * nb + i] -= acc[q][w];
+      sv[q][w] = (i < nb && j < nb && i >= j) ? S[(int64_t)j * nb + i] : (T)0;
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int i = TI * kSyrkTile + ty + 16 * q;
+#pragma unroll
+    for (int w = 0; w < 4; ++w) {
+      const int j = TJ * kSyrkTile + tx + 16 * w;
+      if (i < nb && j < nb && i >= j) S[(int64_t)j * nb + i] = sv[q][w] - acc[q][w];
     }
   }
 }

@@ -6,11 +6,11 @@
 // (Eq. SchurC1: A11 - A12 A22^-1 A21 = K_BB - L_Bg L_Bg^T).  One CTA of 128
 // threads computes one 128 x 128 lower tile pair of one (node, sample):
 //   * the TRSM that produced X also wrote it split into TF32 hi and lo parts,
-//     in 128-row x 16-column tiles in the K-major, no-swizzle core-matrix layout
+//     in 128-row x 8-column tiles in the K-major, no-swizzle core-matrix layout
 //     (8-row x 16-byte core matrices) that the MMA reads from shared memory;
 //   * one thread runs the pipeline: cp.async.bulk copies (completion counted in
 //     bytes on an mbarrier) fill kStages shared-memory stages, and for each
-//     16-column chunk it issues tcgen05.mma kind::tf32 (M = N = 128, K = 8)
+//     8-column chunk it issues tcgen05.mma kind::tf32 (M = N = 128, K = 8)
 //     three times per step, hi*hi + hi*lo + lo*hi ("3xTF32", about FP32
 //     accuracy), with the accumulator in tensor memory (128 lanes x 128 columns);
 //     tcgen05.commit frees a stage for the next copy;
@@ -25,9 +25,9 @@ namespace {
 
 constexpr int kTile = kTcTile;        // M = N of the MMA and of the output tile
 constexpr int kChunk = kTcChunk;      // contraction columns staged per buffer
-constexpr int kTileBytes = (int)kTcBlockBytes;          // one operand part (8 KiB)
-constexpr int kStageBytes = 4 * kTileBytes;             // A hi/lo, B hi/lo (32 KiB)
-constexpr int kStages = 2;                              // pipeline depth: 64 KiB, 3 CTAs per SM
+constexpr int kTileBytes = (int)kTcBlockBytes;          // one operand part (4 KiB)
+constexpr int kStageBytes = 4 * kTileBytes;             // A hi/lo, B hi/lo (16 KiB)
+constexpr int kStages = 4;                              // pipeline depth: 64 KiB, 3 CTAs per SM
 constexpr uint32_t kWaitLimit = 1u << 24;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -147,13 +147,18 @@ __global__ void __launch_bounds__(128, 3) k_syrk_tc(StepArgs a) {
       }
       asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
           smem_u32(&empty[b])));
-      if (c + kStages < nchunks) {   // refill this stage once its MMAs are done
-        if (!mbar_wait(smem_u32(&empty[b]), ph_empty[b])) { ok = false; break; }
-        ph_empty[b] ^= 1u;
-        load(c + kStages);
+      // refill the stage of the previous chunk (its MMAs were queued one step
+      // earlier), so that the MMAs of this chunk stay queued meanwhile
+      const int cp = c - 1;
+      if (cp >= 0 && cp + kStages < nchunks) {
+        const int bp = cp % kStages;
+        if (!mbar_wait(smem_u32(&empty[bp]), ph_empty[bp])) { ok = false; break; }
+        ph_empty[bp] ^= 1u;
+        load(cp + kStages);
       }
     }
-    // the MMAs of the last chunks: their commits have not been waited for yet
+    // chunks whose commits have not been waited for: the last kStages, and the
+    // last chunk when it had no refill step
     if (ok)
       for (int c = max(0, nchunks - kStages); c < nchunks; ++c) {
         const int b = c % kStages;
@@ -184,12 +189,17 @@ __global__ void __launch_bounds__(128, 3) k_syrk_tc(StepArgs a) {
             "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
           : "r"(taddr));
       asm volatile("tcgen05.wait::ld.sync.aligned;");
-      if (i < nbt) {
+      // all 32 loads of S first (independent, in flight together), then the stores
+      float sv[32];
 #pragma unroll
-        for (int q = 0; q < 32; ++q) {
-          const int j = TJ * kTile + c0 + q;
-          if (j < nbt && i >= j) S[(int64_t)j * nb + i] -= __uint_as_float(r[q]);
-        }
+      for (int q = 0; q < 32; ++q) {
+        const int j = TJ * kTile + c0 + q;
+        sv[q] = (i < nbt && j < nbt && i >= j) ? S[(int64_t)j * nb + i] : 0.0f;
+      }
+#pragma unroll
+      for (int q = 0; q < 32; ++q) {
+        const int j = TJ * kTile + c0 + q;
+        if (i < nbt && j < nbt && i >= j) S[(int64_t)j * nb + i] = sv[q] - __uint_as_float(r[q]);
       }
     }
   }

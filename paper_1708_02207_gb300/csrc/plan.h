@@ -105,9 +105,9 @@ struct Plan {
 // Fronts of at most kTinyMax rows run one per warp in registers; up to the
 // kSmallMax limits one per CTA in shared memory; larger ones in global memory.
 constexpr int kTinyMax = 32;
-// Tensor-core SYRK staging: 128-row tiles x 16-column chunks, hi and lo parts of
-// 8 KiB each (TF32 values in the 8-row x 16-byte core-matrix layout).
-constexpr int kTcTile = 128, kTcChunk = 16;
+// Tensor-core SYRK staging: 128-row tiles x 8-column chunks, hi and lo parts of
+// 4 KiB each (TF32 values in the 8-row x 16-byte core-matrix layout).
+constexpr int kTcTile = 128, kTcChunk = 8;
 constexpr int64_t kTcBlockBytes = (int64_t)kTcTile * kTcChunk * 4;
 constexpr int kSmallMax64 = 160;   // 160^2 * 8 B = 200 KiB
 constexpr int kSmallMax32 = 224;   // 224^2 * 4 B = 196 KiB
