@@ -40,6 +40,17 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 
 
+def _measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return json.load(fh)
+    except (OSError, ValueError):
+        return {}
+
+
+MEASURED = _measured_peaks()
+
+
 def _env_int(name, default):
     try:
         return int(os.environ.get(name, default))
@@ -213,6 +224,7 @@ def run_hdd(args, cfg):
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
+    plan.profile_begin()   # per-kernel CUDA events on the launching stream, inside the timed region
     with ClockSampler(local) as clk:
         with torch.cuda.stream(stream):
             t_start.record(stream)
@@ -220,6 +232,7 @@ def run_hdd(args, cfg):
                 step(evs[k])
             t_end.record(stream)
         stream.synchronize()
+    kstats = plan.profile_end()
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
@@ -258,19 +271,39 @@ def run_hdd(args, cfg):
     h2d = B * plan.n_z * 8 + plan.n_obs * 8
     d2h = B * 8 + B * plan.n_obs * 8 + B * 4
 
-    # roofline of the dominant stage (the upsweep: every Schur elimination)
-    up_flops = info["flops_upsweep"] * B
-    achieved = up_flops / (stage_ms["upsweep"] / 1e3) / 1e12
+    # per-kernel-family times and algorithmic flops over the timed region
+    kernels = {}
+    for name, st_ in kstats.items():
+        ms = st_["ms"] / args.steps
+        kernels[name] = {"ms_per_step": ms, "launches_per_step": st_["launches"] / args.steps,
+                         "share": st_["ms"] / max(1e-9, sum(v["ms"] for v in kstats.values())),
+                         "tflops": (st_["flops"] / args.steps) / (ms / 1e3) / 1e12 if st_["flops"] > 0 and ms > 0 else None}
+    # roofline of the dominant kernel (largest share of device time with arithmetic work)
+    compute = {k: v for k, v in kernels.items() if v["tflops"] is not None}
+    dom = max(compute, key=lambda k: compute[k]["ms_per_step"]) if compute else None
     if precision == hdd.HDD_FP64:
-        roof = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
-                "kernel": "hdd_upsweep (front_small, front_fill, potrf, trsm, syrk launches), FP64 FMA",
-                "peak_source": "derived: 2 FP64 FMA/clk/SM x 152 SMs x 2070 MHz (1.25 TFLOP/s nominal)"}
+        peak, peak_src = FP64_PEAK_TFLOPS, "derived: 2 FP64 FMA/clk/SM x 152 SMs x 2070 MHz (1.25 TFLOP/s nominal)"
     else:
-        roof = {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": achieved / FP32_PEAK_TFLOPS, "traffic": None,
-                "kernel": "hdd_upsweep (front_small, front_fill, potrf, trsm, syrk launches), FP32 FMA",
-                "peak_source": "derived: 128 FP32 FMA/clk/SM x 152 SMs x 2070 MHz"}
+        peak, peak_src = FP32_PEAK_TFLOPS, "derived: 128 FP32 FMA/clk/SM x 152 SMs x 2070 MHz"
+    roof = None
+    if dom:
+        ach = compute[dom]["tflops"]
+        roof = {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+                "traffic": None, "kernel": dom, "peak_source": peak_src,
+                "flops_per_launch_note": "Cholesky m^3/3 + TRSM (b+1)m^2/2 + SYRK (b+1)(b+2)m/2 multiply-adds x2 per front"}
+    tc = kernels.get("syrk_tc")
+    if tc and tc["tflops"]:
+        # 3xTF32: three tensor-core products per FP32 multiply-add; TF32 peak = measured BF16
+        # burst x the nominal TF32/BF16 ratio (1.1 / 2.25)
+        tf32_peak = MEASURED.get("bf16_tflops", 1899.9) * 1.1 / 2.25
+        ach_tc = 3.0 * tc["tflops"]
+        kernels["syrk_tc"]["roofline"] = {"bound": "tensor", "achieved": ach_tc, "peak": tf32_peak,
+                                          "unit": "TFLOP/s (TF32 tensor ops, 3 per FP32 FMA)",
+                                          "frac": ach_tc / tf32_peak,
+                                          "peak_source": "of measured: MEASURED_PEAKS bf16_tflops x 1.1/2.25"}
+    up_flops = info["flops_upsweep"] * B
+    upsweep_roof = {"achieved": up_flops / (stage_ms["upsweep"] / 1e3) / 1e12, "unit": "TFLOP/s",
+                    "note": "whole hdd_upsweep call"}
 
     # the plain FP64 path on the same inputs (the speedup of the mixed path is over it)
     fp64 = None
@@ -326,6 +359,8 @@ def run_hdd(args, cfg):
         "latency_ms": {"p50": pct(0.5), "p99": pct(0.99), "note": "per step (one batch of samples)"},
         "fp64_path": fp64,
         "roofline": roof,
+        "upsweep": upsweep_roof,
+        "kernels": kernels,
         "e2e": {"value": e2e_value, "unit": "evals/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": info["launches_evaluate"] * args.steps,
         "clocks": clk.summary(),

@@ -191,6 +191,23 @@ hdd_status hdd_evaluate_static(hdd_plan_t plan, int32_t batch, const double* Z, 
                                int32_t y_per_sample, double* loglik, double* u_obs, int32_t* sample_status,
                                void* stream);
 
+/* Per-kernel timing, for benchmarks.  Between hdd_profile_begin and
+ * hdd_profile_end every kernel the library launches for this plan is bracketed
+ * by a pair of CUDA events on its stream (a few microseconds of overhead per
+ * launch).  hdd_profile_end waits for those events and returns, per kernel
+ * family, the launches, the summed event time and the summed algorithmic flops
+ * (2 per multiply-add: Cholesky m^3/3, TRSM (b+1) m^2/2, SYRK b(b+1)m/2 and
+ * (b+1)m for the bordered row, per node and sample).  Not thread-safe: profile
+ * a plan from one thread.  stats: host array of max_stats entries. */
+typedef struct {
+  char name[24];
+  int32_t launches;
+  double ms;
+  double flops;
+} hdd_kernel_stat_t;
+hdd_status hdd_profile_begin(hdd_plan_t plan);
+hdd_status hdd_profile_end(hdd_plan_t plan, hdd_kernel_stat_t* stats, int32_t max_stats, int32_t* n_stats);
+
 /* Plan queries (work on host-only plans too). */
 hdd_status hdd_plan_info(hdd_plan_t plan, hdd_plan_info_t* info);
 hdd_status hdd_node_info(hdd_plan_t plan, int32_t node, hdd_node_info_t* info);

@@ -116,8 +116,25 @@ hdd_status check_call(hdd_plan_t plan, int32_t batch, void* ws) {
   return HDD_OK;
 }
 
+hdd::Profiler* profiler(hdd_plan_t plan) {
+  hdd::Profiler* pr = static_cast<hdd::Profiler*>(plan->prof);
+  return (pr && pr->on) ? pr : nullptr;
+}
+
+struct ProfScope {
+  hdd::Profiler* pr;
+  cudaStream_t st;
+  ProfScope(hdd::Profiler* p, int fam, double fl, cudaStream_t s) : pr(p), st(s) {
+    if (pr) pr->begin(fam, fl, st);
+  }
+  ~ProfScope() {
+    if (pr) pr->end(st);
+  }
+};
+
 // One pass of "Leaves to Root" over all heights with the given right-hand side.
-cudaError_t run_upsweep(const hdd::Plan& p, int batch, void* ws, const hdd::Rhs& rhs, cudaStream_t st) {
+cudaError_t run_upsweep(const hdd::Plan& p, int batch, void* ws, const hdd::Rhs& rhs, cudaStream_t st,
+                        hdd::Profiler* prof) {
   const hdd::Layout L = hdd::layout(p, batch);
   char* w = static_cast<char*>(ws);
   hdd::StepArgs a{};
@@ -131,6 +148,7 @@ cudaError_t run_upsweep(const hdd::Plan& p, int batch, void* ws, const hdd::Rhs&
   a.rhs = rhs;
   a.arenas = arenas(p, L, ws);
   a.status = reinterpret_cast<int32_t*>(w + L.status);
+  a.prof = prof;
   for (int h = 0; h <= p.height; ++h) {
     for (int kind = 0; kind < 6; ++kind) {
       const hdd::ListInfo& li = p.lists[p.step_lists[h][kind]];
@@ -140,6 +158,10 @@ cudaError_t run_upsweep(const hdd::Plan& p, int batch, void* ws, const hdd::Rhs&
       a.max_nf = li.max_nf;
       a.max_m = li.max_m;
       a.max_b = li.max_b;
+      a.fl_chol = li.fl_chol * batch;
+      a.fl_trsm = li.fl_trsm * batch;
+      a.fl_syrk = li.fl_syrk * batch;
+      a.fl_rhs = li.fl_rhs * batch;
       cudaError_t e;
       switch (kind) {
         case 0: e = hdd::launch_front_warp<double>(a, st); break;
@@ -157,7 +179,7 @@ cudaError_t run_upsweep(const hdd::Plan& p, int batch, void* ws, const hdd::Rhs&
 
 // "Root to Leaves" over the given per-depth lists, writing u (FP64).
 cudaError_t run_descent(const hdd::Plan& p, int batch, void* ws, const std::vector<int>& per_depth, double* u,
-                        cudaStream_t st) {
+                        cudaStream_t st, hdd::Profiler* prof) {
   const hdd::Layout L = hdd::layout(p, batch);
   const hdd::Arenas A = arenas(p, L, ws);
   const int64_t NN = (int64_t)p.N * p.N;
@@ -169,6 +191,7 @@ cudaError_t run_descent(const hdd::Plan& p, int batch, void* ws, const std::vect
     // nodes with long interfaces: one CTA per (node, sample), blocked back substitution;
     // otherwise one warp per (node, sample)
     const bool cta = li.max_m >= kSweepCtaMinM;
+    ProfScope ps(prof, hdd::kProfDescent, 0.0, st);
     cudaError_t e;
     if (cta)
       e = fp64 ? hdd::launch_descent<double>(p.d_nodes, p.d_maps, p.d_lists + li.off, li.n, batch, A, u, NN,
@@ -186,7 +209,8 @@ cudaError_t run_descent(const hdd::Plan& p, int batch, void* ws, const std::vect
 }
 
 // Right-hand-side sweep (leaves to root) through the stored factors.
-cudaError_t run_forward(const hdd::Plan& p, int batch, void* ws, const hdd::Rhs& rhs, cudaStream_t st) {
+cudaError_t run_forward(const hdd::Plan& p, int batch, void* ws, const hdd::Rhs& rhs, cudaStream_t st,
+                        hdd::Profiler* prof) {
   const hdd::Layout L = hdd::layout(p, batch);
   const hdd::Arenas A = arenas(p, L, ws);
   for (int h = 0; h <= p.height; ++h)
@@ -194,6 +218,7 @@ cudaError_t run_forward(const hdd::Plan& p, int batch, void* ws, const hdd::Rhs&
       const hdd::ListInfo& li = p.lists[p.fwd_lists[h][k]];
       if (li.n == 0) continue;
       const bool cta = li.max_m >= kSweepCtaMinM;
+      ProfScope ps(prof, hdd::kProfForward, 0.0, st);
       cudaError_t e;
       if (cta)
         e = k == 0 ? hdd::launch_forward<double>(p.d_nodes, p.d_maps, p.d_lists + li.off, li.n, batch, A, rhs,
@@ -213,7 +238,8 @@ cudaError_t run_forward(const hdd::Plan& p, int batch, void* ws, const hdd::Rhs&
 // Mixed precision point solve: full descent, then ir_max_iter refinement steps
 // (FP64 residual, sweep through the FP32/FP64 factors, update); the last step's
 // descent is pruned to the observation paths and checked against ir_tol.
-cudaError_t run_refined_solve(const hdd::Plan& p, int batch, void* ws, double* u_obs, cudaStream_t st) {
+cudaError_t run_refined_solve(const hdd::Plan& p, int batch, void* ws, double* u_obs, cudaStream_t st,
+                              hdd::Profiler* prof) {
   const hdd::Layout L = hdd::layout(p, batch);
   char* w = static_cast<char*>(ws);
   double* u = reinterpret_cast<double*>(w + L.u);
@@ -225,18 +251,24 @@ cudaError_t run_refined_solve(const hdd::Plan& p, int batch, void* ws, double* u
   const int64_t NN = (int64_t)p.N * p.N;
   const double load = p.h * p.h * p.f;
   const int K = p.ir_max_iter;
-  cudaError_t e = run_descent(p, batch, ws, K > 0 ? p.down_all_lists : p.down_vis_lists, u, st);
+  cudaError_t e = run_descent(p, batch, ws, K > 0 ? p.down_all_lists : p.down_vis_lists, u, st, prof);
   for (int it = 1; it <= K && e == cudaSuccess; ++it) {
     const bool last = it == K;
-    e = hdd::launch_residual(kappa, p.n_t, u, NN, p.N, load, r, batch, st);
-    if (e == cudaSuccess) e = run_forward(p, batch, ws, hdd::Rhs{r, NN, 0.0}, st);
-    if (e == cudaSuccess) e = run_descent(p, batch, ws, last ? p.down_vis_lists : p.down_all_lists, du, st);
+    {
+      ProfScope ps(prof, hdd::kProfResidual, 0.0, st);
+      e = hdd::launch_residual(kappa, p.n_t, u, NN, p.N, load, r, batch, st);
+    }
+    if (e == cudaSuccess) e = run_forward(p, batch, ws, hdd::Rhs{r, NN, 0.0}, st, prof);
+    if (e == cudaSuccess) e = run_descent(p, batch, ws, last ? p.down_vis_lists : p.down_all_lists, du, st, prof);
+    ProfScope ps(prof, hdd::kProfMisc, 0.0, st);
     if (e == cudaSuccess && !last) e = hdd::launch_delta_obs(du, NN, p.d_obs, p.n_obs, dprev, batch, st);
     if (e == cudaSuccess && !last) e = hdd::launch_update(u, du, NN, p.N, batch, st);
   }
-  if (e == cudaSuccess)
+  if (e == cudaSuccess) {
+    ProfScope ps(prof, hdd::kProfMisc, 0.0, st);
     e = hdd::launch_final_obs(u, K > 0 ? du : nullptr, NN, p.d_obs, p.n_obs, K > 0 ? p.ir_tol : -1.0, dprev, u_obs,
                               status, batch, st);
+  }
   return e;
 }
 
@@ -314,6 +346,12 @@ hdd_status hdd_plan_destroy(hdd_plan_t plan) {
   if (plan->p.device >= 0) {
     DeviceScope ds(plan->p.device);
     free_device(plan->p);
+    if (plan->prof) {
+      hdd::Profiler* pr = static_cast<hdd::Profiler*>(plan->prof);
+      for (cudaEvent_t e : pr->ev) cudaEventDestroy(e);
+      delete pr;
+      plan->prof = nullptr;
+    }
   }
   delete plan;
   return HDD_OK;
@@ -338,9 +376,11 @@ hdd_status hdd_assemble(hdd_plan_t plan, const double* Z, int32_t batch, void* w
   char* w = static_cast<char*>(workspace);
   cudaError_t e = cudaMemsetAsync(w + L.status, 0, (size_t)batch * 4, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(w + L.conv, 0, (size_t)batch * 8, st);
-  if (e == cudaSuccess)
+  if (e == cudaSuccess) {
+    ProfScope ps(profiler(plan), hdd::kProfKappa, 2.0 * p.n_t * p.n_z * batch, st);
     e = hdd::launch_kappa(p.d_phi, Z, p.n_t, p.n_z, batch, reinterpret_cast<double*>(w + L.kappa),
                           L.kappa32 ? reinterpret_cast<float*>(w + L.kappa32) : nullptr, p.n_t, st);
+  }
   return e == cudaSuccess ? HDD_OK : fail_cuda(e, "hdd_assemble");
 }
 
@@ -351,7 +391,7 @@ hdd_status hdd_upsweep(hdd_plan_t plan, int32_t batch, void* workspace, void* st
   DeviceScope ds(p.device);
   if (ds.err != cudaSuccess) return fail_cuda(ds.err, "cudaSetDevice");
   hdd::Rhs rhs{nullptr, 0, p.h * p.h * p.f};
-  cudaError_t e = run_upsweep(p, batch, workspace, rhs, static_cast<cudaStream_t>(stream));
+  cudaError_t e = run_upsweep(p, batch, workspace, rhs, static_cast<cudaStream_t>(stream), profiler(plan));
   return e == cudaSuccess ? HDD_OK : fail_cuda(e, "hdd_upsweep");
 }
 
@@ -369,9 +409,10 @@ hdd_status hdd_point_solve(hdd_plan_t plan, int32_t batch, void* workspace, doub
   const int64_t NN = (int64_t)p.N * p.N;
   cudaError_t e;
   if (p.precision == HDD_MIXED_FP32) {
-    e = run_refined_solve(p, batch, workspace, u_obs, st);
+    e = run_refined_solve(p, batch, workspace, u_obs, st, profiler(plan));
   } else {
-    e = run_descent(p, batch, workspace, p.down_vis_lists, u, st);
+    e = run_descent(p, batch, workspace, p.down_vis_lists, u, st, profiler(plan));
+    ProfScope ps(profiler(plan), hdd::kProfMisc, 0.0, st);
     if (e == cudaSuccess) e = hdd::launch_gather_obs(u, NN, p.d_obs, p.n_obs, batch, u_obs, st);
   }
   return e == cudaSuccess ? HDD_OK : fail_cuda(e, "hdd_point_solve");
@@ -389,7 +430,11 @@ hdd_status hdd_loglik(hdd_plan_t plan, int32_t batch, void* workspace, const dou
   const hdd::Layout L = hdd::layout(p, batch);
   char* w = static_cast<char*>(workspace);
   const int32_t* status = reinterpret_cast<const int32_t*>(w + L.status);
-  cudaError_t e = hdd::launch_loglik(u_obs, p.n_obs, batch, y, y_per_sample ? 1 : 0, p.sigma, status, loglik, st);
+  cudaError_t e;
+  {
+    ProfScope ps(profiler(plan), hdd::kProfMisc, 0.0, st);
+    e = hdd::launch_loglik(u_obs, p.n_obs, batch, y, y_per_sample ? 1 : 0, p.sigma, status, loglik, st);
+  }
   if (e == cudaSuccess && sample_status)
     e = cudaMemcpyAsync(sample_status, status, (size_t)batch * 4, cudaMemcpyDeviceToDevice, st);
   return e == cudaSuccess ? HDD_OK : fail_cuda(e, "hdd_loglik");
@@ -426,6 +471,56 @@ hdd_status hdd_evaluate_host(hdd_plan_t plan, int32_t batch, void* workspace, co
     e = cudaMemcpyAsync(sample_status, w + L.status, (size_t)batch * 4, cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   return e == cudaSuccess ? HDD_OK : fail_cuda(e, "hdd_evaluate_host");
+}
+
+hdd_status hdd_profile_begin(hdd_plan_t plan) {
+  if (!plan) return fail_inval("plan is NULL");
+  if (plan->p.device < 0) {
+    g_err = "host-only plan";
+    return HDD_ESTATE;
+  }
+  if (!plan->prof) plan->prof = new (std::nothrow) hdd::Profiler;
+  if (!plan->prof) return HDD_ENOMEM;
+  hdd::Profiler* pr = static_cast<hdd::Profiler*>(plan->prof);
+  pr->used = 0;
+  pr->on = true;
+  return HDD_OK;
+}
+
+hdd_status hdd_profile_end(hdd_plan_t plan, hdd_kernel_stat_t* stats, int32_t max_stats, int32_t* n_stats) {
+  if (!plan || !plan->prof) return fail_inval("profiling was not started");
+  hdd::Profiler* pr = static_cast<hdd::Profiler*>(plan->prof);
+  pr->on = false;
+  static const char* names[hdd::kProfCount] = {"kappa", "front_warp", "front_small", "front_fill", "potrf", "trsm",
+                                                "syrk_simt", "syrk_tc", "syrk_rhs", "forward", "descent",
+                                                "residual", "misc"};
+  int launches[hdd::kProfCount] = {};
+  double ms[hdd::kProfCount] = {}, fl[hdd::kProfCount] = {};
+  DeviceScope ds(plan->p.device);
+  for (size_t k = 0; k < pr->used; ++k) {
+    float t = 0.0f;
+    cudaError_t e = cudaEventSynchronize(pr->ev[2 * k + 1]);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&t, pr->ev[2 * k], pr->ev[2 * k + 1]);
+    if (e != cudaSuccess) return fail_cuda(e, "hdd_profile_end");
+    launches[pr->fam[k]] += 1;
+    ms[pr->fam[k]] += t;
+    fl[pr->fam[k]] += pr->flops[k];
+  }
+  pr->used = 0;
+  int n = 0;
+  for (int f = 0; f < hdd::kProfCount; ++f) {
+    if (!launches[f]) continue;
+    if (stats && n < max_stats) {
+      std::strncpy(stats[n].name, names[f], sizeof(stats[n].name) - 1);
+      stats[n].name[sizeof(stats[n].name) - 1] = 0;
+      stats[n].launches = launches[f];
+      stats[n].ms = ms[f];
+      stats[n].flops = fl[f];
+    }
+    ++n;
+  }
+  if (n_stats) *n_stats = n;
+  return HDD_OK;
 }
 
 hdd_status hdd_plan_info(hdd_plan_t plan, hdd_plan_info_t* info) {

@@ -223,7 +223,9 @@ cudaError_t launch_front_small(const StepArgs& a, cudaStream_t st) {
   if (a.nlist == 0) return cudaSuccess;
   const size_t smem = (size_t)a.max_nf * front_ld(a.max_nf) * sizeof(T) + 4 * 4 * sizeof(T);
   dim3 grid(a.nlist, a.batch);
+  if (a.prof) a.prof->begin(kProfFrontSmall, a.fl_chol + a.fl_trsm + a.fl_syrk + a.fl_rhs, st);
   k_front_small<T><<<grid, small_threads(a.max_nf), smem, st>>>(a);
+  if (a.prof) a.prof->end(st);
   return cudaGetLastError();
 }
 
@@ -589,31 +591,44 @@ cudaError_t launch_front_large(const StepArgs& a, cudaStream_t st) {
   if (a.nlist == 0) return cudaSuccess;
   {
     dim3 grid((a.max_nf + 7) / 8, a.nlist, a.batch);
+    if (a.prof) a.prof->begin(kProfFill, 0.0, st);
     k_front_fill<T><<<grid, 256, 0, st>>>(a);
+    if (a.prof) a.prof->end(st);
   }
   const size_t rows_smem = (size_t)min(a.max_m, SmemCap<T>::rows);
   {
     const size_t smem = (rows_smem * kPanel + kPanel) * sizeof(T);
+    if (a.prof) a.prof->begin(kProfPotrf, a.fl_chol, st);
     k_potrf<T><<<dim3(a.nlist, a.batch), 256, smem, st>>>(a);
+    if (a.prof) a.prof->end(st);
   }
   {
     constexpr int R = TrsmShape<T>::rows;
     const size_t xrows = (size_t)min(a.max_m, TrsmShape<T>::cap);
     const size_t smem = (xrows * R + 32 * 33 + 3 + 32 * 64) * sizeof(T) + 16;
     dim3 grid((a.max_b + 1 + R - 1) / R, a.nlist, a.batch);
+    if (a.prof) a.prof->begin(kProfTrsm, a.fl_trsm, st);
     k_trsm<T><<<grid, 256, smem, st>>>(a);
+    if (a.prof) a.prof->end(st);
   }
   if (std::is_same<T, float>::value) {
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    if ((e = launch_syrk_tc(a, st)) != cudaSuccess) return e;   // tensor cores, 3xTF32, boundary rows
+    if (a.prof) a.prof->begin(kProfSyrkTc, a.fl_syrk, st);
+    e = launch_syrk_tc(a, st);   // tensor cores, 3xTF32, boundary rows
+    if (a.prof) a.prof->end(st);
+    if (e != cudaSuccess) return e;
+    if (a.prof) a.prof->begin(kProfSyrkRhs, a.fl_rhs, st);
     k_syrk_rhs<<<dim3(a.nlist, a.batch), 256, (size_t)a.max_m * sizeof(float), st>>>(a);
+    if (a.prof) a.prof->end(st);
     return cudaGetLastError();
   }
   {
     const int nt = (a.max_b + 1 + kSyrkTile - 1) / kSyrkTile;
     dim3 grid(nt * (nt + 1) / 2, a.nlist, a.batch);
+    if (a.prof) a.prof->begin(kProfSyrk, a.fl_syrk + a.fl_rhs, st);
     k_syrk<T><<<grid, 256, 0, st>>>(a);
+    if (a.prof) a.prof->end(st);
   }
   return cudaGetLastError();
 }

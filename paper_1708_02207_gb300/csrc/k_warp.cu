@@ -137,7 +137,9 @@ __global__ void __launch_bounds__(256) k_front_warp(StepArgs a) {
 template <typename T>
 cudaError_t launch_front_warp(const StepArgs& a, cudaStream_t st) {
   if (a.nlist == 0) return cudaSuccess;
+  if (a.prof) a.prof->begin(kProfFrontWarp, a.fl_chol + a.fl_trsm + a.fl_syrk + a.fl_rhs, st);
   k_front_warp<T><<<dim3(a.nlist, (a.batch + 7) / 8), 256, 0, st>>>(a);
+  if (a.prof) a.prof->end(st);
   return cudaGetLastError();
 }
 template cudaError_t launch_front_warp<double>(const StepArgs&, cudaStream_t);

@@ -4,9 +4,45 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <vector>
+
 #include "common.cuh"
 
 namespace hdd {
+
+// Optional per-kernel timing (host side): CUDA event pairs recorded on the
+// launching stream around each kernel, tagged with a kernel family and the
+// algorithmic flops of the launch.  Owned by a plan; not thread-safe.
+enum ProfFamily {
+  kProfKappa, kProfFrontWarp, kProfFrontSmall, kProfFill, kProfPotrf, kProfTrsm, kProfSyrk, kProfSyrkTc,
+  kProfSyrkRhs, kProfForward, kProfDescent, kProfResidual, kProfMisc, kProfCount
+};
+struct Profiler {
+  bool on = false;
+  std::vector<cudaEvent_t> ev;       // 2 per record
+  std::vector<int> fam;
+  std::vector<double> flops;
+  size_t used = 0;
+  void begin(int family, double fl, cudaStream_t st) {
+    if (!on) return;
+    if (2 * used + 2 > ev.size()) {
+      for (int k = 0; k < 64; ++k) {
+        cudaEvent_t e;
+        if (cudaEventCreate(&e) != cudaSuccess) return;
+        ev.push_back(e);
+      }
+    }
+    if (fam.size() <= used) { fam.resize(used + 1); flops.resize(used + 1); }
+    fam[used] = family;
+    flops[used] = fl;
+    cudaEventRecord(ev[2 * used], st);
+  }
+  void end(cudaStream_t st) {
+    if (!on || 2 * used + 2 > ev.size()) return;
+    cudaEventRecord(ev[2 * used + 1], st);
+    ++used;
+  }
+};
 
 struct StepArgs {
   const NodeDev* nodes;
@@ -22,6 +58,8 @@ struct StepArgs {
   Arenas arenas;
   int32_t* status;
   int max_nf, max_m, max_b;
+  Profiler* prof;            // nullptr unless profiling
+  double fl_chol, fl_trsm, fl_syrk, fl_rhs;   // algorithmic flops of this launch (whole batch)
 };
 
 // assembly: kappa = exp(Phi Z) (Sec. 3.1; kappa = e^q)

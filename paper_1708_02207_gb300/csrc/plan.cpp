@@ -292,9 +292,15 @@ std::string build_plan(const hdd_plan_desc& d, Plan& p) {
     li.n = (int)v.size();
     for (int k : v) {
       p.list_data.push_back(k);
-      li.max_nf = std::max(li.max_nf, p.nodes[k].nf);
-      li.max_m = std::max(li.max_m, p.nodes[k].m);
-      li.max_b = std::max(li.max_b, p.nodes[k].b);
+      const Node& nd = p.nodes[k];
+      li.max_nf = std::max(li.max_nf, nd.nf);
+      li.max_m = std::max(li.max_m, nd.m);
+      li.max_b = std::max(li.max_b, nd.b);
+      const double m = nd.m, b = nd.b;
+      li.fl_chol += 2.0 * m * m * m / 3.0;
+      li.fl_trsm += 2.0 * (b + 1.0) * m * m / 2.0;
+      li.fl_syrk += 2.0 * b * (b + 1.0) / 2.0 * m;
+      li.fl_rhs += 2.0 * (b + 1.0) * m;
     }
     p.lists.push_back(li);
     return (int)p.lists.size() - 1;

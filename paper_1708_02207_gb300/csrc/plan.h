@@ -55,6 +55,7 @@ struct ListInfo {
   int64_t off = 0;   // into the concatenated list table
   int n = 0;
   int max_nf = 0, max_m = 0, max_b = 0;
+  double fl_chol = 0, fl_trsm = 0, fl_syrk = 0, fl_rhs = 0;   // algorithmic flops per sample
 };
 
 // One upsweep step: all nodes of one height, split by front size and precision.
@@ -130,4 +131,5 @@ Layout layout(const Plan& p, int batch);
 // The opaque plan handle of the C ABI.
 struct hdd_plan_s {
   hdd::Plan p;
+  void* prof = nullptr;   // per-kernel timing state (api.cu), or nullptr
 };

@@ -22,6 +22,7 @@ EXPORTED = [
     "hdd_plan", "hdd_plan_destroy", "hdd_workspace_size", "hdd_assemble", "hdd_upsweep",
     "hdd_point_solve", "hdd_loglik", "hdd_evaluate_host", "hdd_plan_info", "hdd_node_info",
     "hdd_node_indices", "hdd_status_string", "hdd_last_error", "hdd_evaluate_static",
+    "hdd_profile_begin", "hdd_profile_end",
 ]
 STATIC_WORKSPACE_BYTES = 32 << 20
 
@@ -44,6 +45,10 @@ class PlanInfo(C.Structure):
         ("factor_bytes", C.c_double), ("schur_bytes", C.c_double),
         ("launches_upsweep", C.c_int32), ("launches_evaluate", C.c_int32),
     ]
+
+
+class KernelStat(C.Structure):
+    _fields_ = [("name", C.c_char * 24), ("launches", C.c_int32), ("ms", C.c_double), ("flops", C.c_double)]
 
 
 class NodeInfo(C.Structure):
@@ -73,6 +78,8 @@ def load_library() -> C.CDLL:
     lib.hdd_loglik.argtypes = [vp, i32, vp, vp, vp, i32, vp, vp, vp]
     lib.hdd_evaluate_host.argtypes = [vp, i32, vp, pd, pd, i32, pd, pd, pi32, vp]
     lib.hdd_evaluate_static.argtypes = [vp, i32, vp, vp, i32, vp, vp, vp, vp]
+    lib.hdd_profile_begin.argtypes = [vp]
+    lib.hdd_profile_end.argtypes = [vp, C.POINTER(KernelStat), i32, C.POINTER(i32)]
     lib.hdd_plan_info.argtypes = [vp, C.POINTER(PlanInfo)]
     lib.hdd_node_info.argtypes = [vp, i32, C.POINTER(NodeInfo)]
     lib.hdd_node_indices.argtypes = [vp, i32, pi32, pi32]
@@ -160,6 +167,18 @@ class Plan:
             self.close()
         except Exception:
             pass
+
+    # ---- per-kernel timing ---------------------------------------------
+    def profile_begin(self):
+        _check(self.lib.hdd_profile_begin(self._h), "hdd_profile_begin")
+
+    def profile_end(self) -> dict:
+        """{family: {"launches", "ms", "flops"}} of the kernels launched since profile_begin."""
+        arr = (KernelStat * 32)()
+        n = C.c_int32()
+        _check(self.lib.hdd_profile_end(self._h, arr, 32, C.byref(n)), "hdd_profile_end")
+        return {arr[k].name.decode(): {"launches": arr[k].launches, "ms": arr[k].ms, "flops": arr[k].flops}
+                for k in range(min(n.value, 32))}
 
     # ---- queries -------------------------------------------------------
     def info(self) -> dict:
