@@ -120,8 +120,9 @@ hdd_status hdd_plan_destroy(hdd_plan_t plan);
 hdd_status hdd_workspace_size(hdd_plan_t plan, int32_t batch, size_t* bytes);
 
 /* Assembly (Sec. 3.1, Eq. coefA, Eq. coefc; kappa = e^q): for each sample s and
- * triangle t, q = sum_k Phi[t,k] Z[s,k] and kappa = exp(q) in FP64, written to
- * the workspace; the per-triangle stiffness kappa_t |t| grad b_i . grad b_j is
+ * triangle t, q = sum_k Phi[t,k] Z[s,k] and kappa = exp(q), written to the
+ * workspace -- in FP64 for FP64 plans, in double-float arithmetic (FP32 pairs,
+ * ~1e-14 relative) for mixed plans, which also keep an FP32 copy; the per-triangle stiffness kappa_t |t| grad b_i . grad b_j is
  * formed from it by hdd_upsweep.  Z: device, [batch x n_z] row-major FP64.
  * workspace: device, >= hdd_workspace_size(plan, batch) bytes, 256-byte aligned. */
 hdd_status hdd_assemble(hdd_plan_t plan, const double* Z, int32_t batch,
@@ -190,6 +191,11 @@ hdd_status hdd_evaluate_host(hdd_plan_t plan, int32_t batch, void* workspace,
 hdd_status hdd_evaluate_static(hdd_plan_t plan, int32_t batch, const double* Z, const double* y,
                                int32_t y_per_sample, double* loglik, double* u_obs, int32_t* sample_status,
                                void* stream);
+
+/* Copy of the coefficient field of the last hdd_assemble on this workspace:
+ * kappa: device [batch x n_t] FP64 (triangle order as above).  For inspection
+ * and tests. */
+hdd_status hdd_kappa(hdd_plan_t plan, int32_t batch, void* workspace, double* kappa, void* stream);
 
 /* Per-kernel timing, for benchmarks.  Between hdd_profile_begin and
  * hdd_profile_end every kernel the library launches for this plan is bracketed

@@ -69,6 +69,9 @@ cudaError_t configure_device(int dev) {
 
 void free_device(hdd::Plan& p) {
   cudaFree(p.d_phi);
+  cudaFree(p.d_phi_hi);
+  cudaFree(p.d_phi_lo);
+  p.d_phi_hi = nullptr; p.d_phi_lo = nullptr;
   cudaFree(p.d_nodes);
   cudaFree(p.d_maps);
   cudaFree(p.d_lists);
@@ -326,6 +329,16 @@ hdd_status hdd_plan(const hdd_plan_desc* desc, hdd_plan_t* out) {
     }
     cudaError_t e = configure_device(p.device);
     if (e == cudaSuccess) e = upload(&p.d_phi, desc->kl_basis, (size_t)p.n_t * p.n_z);
+    if (e == cudaSuccess && p.precision == HDD_MIXED_FP32) {
+      const size_t n = (size_t)p.n_t * p.n_z;
+      std::vector<float> hi(n), lo(n);
+      for (size_t i = 0; i < n; ++i) {
+        hi[i] = (float)desc->kl_basis[i];
+        lo[i] = (float)(desc->kl_basis[i] - (double)hi[i]);
+      }
+      e = upload(&p.d_phi_hi, hi.data(), n);
+      if (e == cudaSuccess) e = upload(&p.d_phi_lo, lo.data(), n);
+    }
     if (e == cudaSuccess) e = upload(&p.d_nodes, p.dev_nodes.data(), p.dev_nodes.size());
     if (e == cudaSuccess) e = upload(&p.d_maps, p.maps.data(), p.maps.size());
     if (e == cudaSuccess) e = upload(&p.d_lists, p.list_data.data(), p.list_data.size());
@@ -378,8 +391,12 @@ hdd_status hdd_assemble(hdd_plan_t plan, const double* Z, int32_t batch, void* w
   if (e == cudaSuccess) e = cudaMemsetAsync(w + L.conv, 0, (size_t)batch * 8, st);
   if (e == cudaSuccess) {
     ProfScope ps(profiler(plan), hdd::kProfKappa, 2.0 * p.n_t * p.n_z * batch, st);
-    e = hdd::launch_kappa(p.d_phi, Z, p.n_t, p.n_z, batch, reinterpret_cast<double*>(w + L.kappa),
-                          L.kappa32 ? reinterpret_cast<float*>(w + L.kappa32) : nullptr, p.n_t, st);
+    if (p.precision == HDD_MIXED_FP32)
+      e = hdd::launch_kappa_df(p.d_phi_hi, p.d_phi_lo, Z, p.n_t, p.n_z, batch, reinterpret_cast<double*>(w + L.kappa),
+                               reinterpret_cast<float*>(w + L.kappa32), p.n_t, st);
+    else
+      e = hdd::launch_kappa(p.d_phi, Z, p.n_t, p.n_z, batch, reinterpret_cast<double*>(w + L.kappa), nullptr, p.n_t,
+                            st);
   }
   return e == cudaSuccess ? HDD_OK : fail_cuda(e, "hdd_assemble");
 }
@@ -471,6 +488,19 @@ hdd_status hdd_evaluate_host(hdd_plan_t plan, int32_t batch, void* workspace, co
     e = cudaMemcpyAsync(sample_status, w + L.status, (size_t)batch * 4, cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   return e == cudaSuccess ? HDD_OK : fail_cuda(e, "hdd_evaluate_host");
+}
+
+hdd_status hdd_kappa(hdd_plan_t plan, int32_t batch, void* workspace, double* kappa, void* stream) {
+  hdd_status s = check_call(plan, batch, workspace);
+  if (s != HDD_OK) return s;
+  if (!kappa) return fail_inval("kappa is NULL");
+  const hdd::Plan& p = plan->p;
+  DeviceScope ds(p.device);
+  if (ds.err != cudaSuccess) return fail_cuda(ds.err, "cudaSetDevice");
+  const hdd::Layout L = hdd::layout(p, batch);
+  cudaError_t e = cudaMemcpyAsync(kappa, static_cast<char*>(workspace) + L.kappa, (size_t)batch * p.n_t * 8,
+                                  cudaMemcpyDeviceToDevice, static_cast<cudaStream_t>(stream));
+  return e == cudaSuccess ? HDD_OK : fail_cuda(e, "hdd_kappa");
 }
 
 hdd_status hdd_profile_begin(hdd_plan_t plan) {

@@ -47,6 +47,120 @@ __global__ void k_kappa(const double* __restrict__ phi, const double* __restrict
   }
 }
 
+// ---------------------------------------------------------------------------
+// Assembly for mixed-precision plans without the FP64 pipe: q = sum_k Phi Z and
+// kappa = exp(q) in double-float arithmetic (pairs of FP32 values, hi + lo, ~48
+// significant bits), with the error-free transformations TwoSum (Knuth) and
+// TwoProduct via FMA (Dekker's product).  exp uses the additive range reduction
+// q = k ln2 + r (ln2 as a hi/lo pair, the product k ln2 formed exactly) and the
+// Taylor series of e^r to degree 12 (|r| <= ln2/2, remainder < 2e-16) in
+// Horner form; e^q = 2^k e^r.  Outputs the FP64 kappa (residual) and its FP32
+// copy (factorisation).
+namespace {
+struct dflt { float hi, lo; };
+__device__ __forceinline__ dflt qsum(float a, float b) { const float s = a + b; return {s, b - (s - a)}; }
+__device__ __forceinline__ dflt tsum(float a, float b) {
+  const float s = a + b, bb = s - a;
+  return {s, (a - (s - bb)) + (b - bb)};
+}
+__device__ __forceinline__ dflt df_add(dflt a, dflt b) {
+  dflt s = tsum(a.hi, b.hi);
+  s.lo += a.lo + b.lo;
+  return qsum(s.hi, s.lo);
+}
+__device__ __forceinline__ dflt df_mul(dflt a, dflt b) {
+  const float p = a.hi * b.hi;
+  float e = fmaf(a.hi, b.hi, -p);
+  e = fmaf(a.hi, b.lo, fmaf(a.lo, b.hi, e));
+  return qsum(p, e);
+}
+// 1/n! as hi + lo pairs (the FP32 value nearest to 1/n!, then the nearest to the rest)
+__constant__ float kInvFact[13][2] = {
+    {1.0f, 0.0f}, {1.0f, 0.0f}, {0.5f, 0.0f},
+    {0.1666666716337204f, -4.967053879312289e-09f}, {0.0416666679084301f, -1.2417634698280722e-09f},
+    {0.008333333767950535f, -4.34617203337595e-10f}, {0.0013888889225199819f, -3.3631094437103215e-11f},
+    {0.00019841270113829523f, -2.725596874933456e-12f}, {2.4801587642286904e-05f, -3.40699609366682e-13f},
+    {2.7557318844628753e-06f, 3.793571224297229e-14f}, {2.755731998149713e-07f, -7.575112209051195e-15f},
+    {2.5052107943679403e-08f, 4.4176230446483665e-16f}, {2.0876755879584152e-09f, 1.1082839147459852e-16f}};
+// ln 2 as hi + lo
+constexpr float kLn2Hi = 0.6931471824645996f, kLn2Lo = -1.9046542121259336e-09f;
+
+__device__ __forceinline__ dflt df_exp(dflt q, int* k_out) {
+  const float kf = rintf(q.hi * 1.4426950408889634f);
+  dflt kl = {kf * kLn2Hi, 0.0f};
+  kl.lo = fmaf(kf, kLn2Hi, -kl.hi);          // k ln2_hi exactly, as hi + lo
+  kl.lo = fmaf(kf, kLn2Lo, kl.lo);
+  const dflt r = df_add(q, dflt{-kl.hi, -kl.lo});
+  dflt p = {kInvFact[12][0], kInvFact[12][1]};
+#pragma unroll
+  for (int n = 11; n >= 0; --n) p = df_add(df_mul(p, r), dflt{kInvFact[n][0], kInvFact[n][1]});
+  *k_out = (int)kf;
+  return p;
+}
+}  // namespace
+
+__global__ void k_kappa_df(const float* __restrict__ phi_hi, const float* __restrict__ phi_lo,
+                           const double* __restrict__ Z, int n_t, int n_z, int batch, double* __restrict__ kappa,
+                           float* __restrict__ kappa32, int64_t kap_stride) {
+  __shared__ float ph[kKapK][kKapT + 1], pl[kKapK][kKapT + 1];
+  __shared__ float zh[kKapS][kKapK], zl[kKapS][kKapK];
+  const int t0 = blockIdx.x * kKapT, s0 = blockIdx.y * kKapS;
+  const int t = t0 + threadIdx.x;
+  float ah[kKapS], al[kKapS];
+#pragma unroll
+  for (int q = 0; q < kKapS; ++q) ah[q] = al[q] = 0.0f;
+  for (int k0 = 0; k0 < n_z; k0 += kKapK) {
+    const int kc = min(kKapK, n_z - k0);
+    __syncthreads();
+    for (int e = threadIdx.x; e < kKapT * kc; e += blockDim.x) {
+      const int tt = e / kc, kk = e - tt * kc;
+      const bool in = t0 + tt < n_t;
+      ph[kk][tt] = in ? phi_hi[(int64_t)(t0 + tt) * n_z + k0 + kk] : 0.0f;
+      pl[kk][tt] = in ? phi_lo[(int64_t)(t0 + tt) * n_z + k0 + kk] : 0.0f;
+    }
+    for (int e = threadIdx.x; e < kKapS * kc; e += blockDim.x) {
+      const int ss = e / kc, kk = e - ss * kc;
+      const double z = (s0 + ss < batch) ? Z[(int64_t)(s0 + ss) * n_z + k0 + kk] : 0.0;
+      const float h = (float)z;
+      zh[ss][kk] = h;
+      zl[ss][kk] = (float)(z - (double)h);
+    }
+    __syncthreads();
+    for (int kk = 0; kk < kc; ++kk) {
+      const float a = ph[kk][threadIdx.x], b = pl[kk][threadIdx.x];
+#pragma unroll
+      for (int q = 0; q < kKapS; ++q) {
+        const float zq = zh[q][kk];
+        const float p = a * zq;
+        float e = fmaf(a, zq, -p);
+        e = fmaf(a, zl[q][kk], fmaf(b, zq, e));
+        const dflt s = tsum(ah[q], p);     // (ah, al) += (p, e)
+        ah[q] = s.hi;
+        al[q] += s.lo + e;
+      }
+    }
+  }
+  if (t < n_t) {
+#pragma unroll
+    for (int q = 0; q < kKapS; ++q) {
+      if (s0 + q >= batch) continue;
+      int k;
+      const dflt ex = df_exp(qsum(ah[q], al[q]), &k);
+      const double scale = k > 1023 ? (double)INFINITY
+                                    : (k < -1022 ? 0.0 : __longlong_as_double((long long)(1023 + k) << 52));   // 2^k
+      kappa[(int64_t)(s0 + q) * kap_stride + t] = ((double)ex.hi + (double)ex.lo) * scale;
+      kappa32[(int64_t)(s0 + q) * kap_stride + t] = ldexpf(ex.hi, k);
+    }
+  }
+}
+
+cudaError_t launch_kappa_df(const float* phi_hi, const float* phi_lo, const double* Z, int n_t, int n_z, int batch,
+                            double* kappa, float* kappa32, int64_t kap_stride, cudaStream_t st) {
+  dim3 grid((n_t + kKapT - 1) / kKapT, (batch + kKapS - 1) / kKapS);
+  k_kappa_df<<<grid, kKapT, 0, st>>>(phi_hi, phi_lo, Z, n_t, n_z, batch, kappa, kappa32, kap_stride);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_kappa(const double* phi, const double* Z, int n_t, int n_z, int batch, double* kappa,
                          float* kappa32, int64_t kap_stride, cudaStream_t st) {
   dim3 grid((n_t + kKapT - 1) / kKapT, (batch + kKapS - 1) / kKapS);

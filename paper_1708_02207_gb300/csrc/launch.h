@@ -65,6 +65,9 @@ struct StepArgs {
 // assembly: kappa = exp(Phi Z) (Sec. 3.1; kappa = e^q)
 cudaError_t launch_kappa(const double* phi, const double* Z, int n_t, int n_z, int batch, double* kappa,
                          float* kappa32, int64_t kap_stride, cudaStream_t st);
+// the same in double-float arithmetic (mixed plans; Phi pre-split into FP32 hi + lo)
+cudaError_t launch_kappa_df(const float* phi_hi, const float* phi_lo, const double* Z, int n_t, int n_z, int batch,
+                            double* kappa, float* kappa32, int64_t kap_stride, cudaStream_t st);
 
 // fronts of at most 32 rows: one warp each, in registers
 template <typename T> cudaError_t launch_front_warp(const StepArgs& a, cudaStream_t st);

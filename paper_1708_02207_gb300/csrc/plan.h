@@ -97,6 +97,8 @@ struct Plan {
 
   // device copies
   double* d_phi = nullptr;
+  float* d_phi_hi = nullptr;   // mixed plans: Phi as FP32 hi + lo pairs
+  float* d_phi_lo = nullptr;
   NodeDev* d_nodes = nullptr;
   int32_t* d_maps = nullptr;
   int32_t* d_lists = nullptr;

@@ -22,7 +22,7 @@ EXPORTED = [
     "hdd_plan", "hdd_plan_destroy", "hdd_workspace_size", "hdd_assemble", "hdd_upsweep",
     "hdd_point_solve", "hdd_loglik", "hdd_evaluate_host", "hdd_plan_info", "hdd_node_info",
     "hdd_node_indices", "hdd_status_string", "hdd_last_error", "hdd_evaluate_static",
-    "hdd_profile_begin", "hdd_profile_end",
+    "hdd_profile_begin", "hdd_profile_end", "hdd_kappa",
 ]
 STATIC_WORKSPACE_BYTES = 32 << 20
 
@@ -78,6 +78,7 @@ def load_library() -> C.CDLL:
     lib.hdd_loglik.argtypes = [vp, i32, vp, vp, vp, i32, vp, vp, vp]
     lib.hdd_evaluate_host.argtypes = [vp, i32, vp, pd, pd, i32, pd, pd, pi32, vp]
     lib.hdd_evaluate_static.argtypes = [vp, i32, vp, vp, i32, vp, vp, vp, vp]
+    lib.hdd_kappa.argtypes = [vp, i32, vp, vp, vp]
     lib.hdd_profile_begin.argtypes = [vp]
     lib.hdd_profile_end.argtypes = [vp, C.POINTER(KernelStat), i32, C.POINTER(i32)]
     lib.hdd_plan_info.argtypes = [vp, C.POINTER(PlanInfo)]
@@ -212,6 +213,10 @@ class Plan:
     def assemble(self, Z, ws, stream=None):
         batch = Z.shape[0]
         _check(self.lib.hdd_assemble(self._h, _ptr(Z), batch, _ptr(ws), _stream_ptr(stream)), "hdd_assemble")
+
+    def kappa(self, batch: int, ws, out, stream=None):
+        """Copy the coefficient field of the last assembly into out (device [batch, n_t] FP64)."""
+        _check(self.lib.hdd_kappa(self._h, batch, _ptr(ws), _ptr(out), _stream_ptr(stream)), "hdd_kappa")
 
     def upsweep(self, batch: int, ws, stream=None):
         _check(self.lib.hdd_upsweep(self._h, batch, _ptr(ws), _stream_ptr(stream)), "hdd_upsweep")

@@ -90,3 +90,38 @@ def test_grid513_full_batch_mixed_sampled(hdd):
     u_ref, ll_ref = oracle_eval(cfg.N, prob.phi, prob.Z[samples], prob.obs, prob.y, cfg.sigma)
     assert rel_err_field(u[samples], u_ref).max() <= TOL
     assert rel_err_scalar(ll[samples], ll_ref).max() <= TOL
+
+
+def test_double_float_assembly_matches_fp64_exp(hdd):
+    # mixed plans form kappa = exp(Phi Z) in double-float arithmetic; compare with
+    # the FP64 plan's kappa (CUDA's FP64 exp) entry by entry, and check overflow
+    N = 65
+    phi, Z = small_problem(N, n_z=20, corr_len=0.2, variance=2.0, batch=3, seed=21)
+    Z = Z.copy()
+    Z[2] *= 900.0 / np.abs(phi @ Z[2]).max()        # |q| up to 900: kappa overflows / underflows
+    obs = w.obs_vertices(N, 4)
+    Zd = torch.from_numpy(Z).cuda()
+    ks = []
+    for prec in (hdd.HDD_FP64, hdd.HDD_MIXED_FP32):
+        plan = hdd.Plan(N, 4, phi, obs, 0.1, precision=prec)
+        ws = plan.workspace(3)
+        plan.assemble(Zd, ws)
+        k = torch.empty(3, 2 * (N - 1) ** 2, dtype=torch.float64, device="cuda")
+        plan.kappa(3, ws, k)
+        ks.append(k.cpu().numpy())
+    k64, kdf = ks
+    # double-float arithmetic carries ~48 bits (unit 2^-48 = 3.6e-15).  The error of
+    # q is bounded by ~2 n_z 2^-48 sum_k |Phi_tk Z_k|, which is also the relative error
+    # it causes in exp(q); the Horner evaluation of exp adds ~13 units.
+    u = 2.0 ** -48
+    for s in range(3):
+        q = phi @ Z[s]
+        fin = np.abs(q) < 700.0
+        bound = 2 * phi.shape[1] * u * (np.abs(phi) @ np.abs(Z[s])) + 16 * u
+        rel = np.abs(kdf[s][fin] - k64[s][fin]) / k64[s][fin]
+        assert (rel <= bound[fin]).all()
+        if s < 2:
+            assert rel.max() <= 1e-12 and np.median(rel) <= 2e-14
+    q2 = phi @ Z[2]
+    assert np.isinf(kdf[2][q2 > 710.0]).all() and np.isinf(k64[2][q2 > 710.0]).all()
+    assert (kdf[2][q2 < -750.0] == 0.0).all()
