@@ -78,6 +78,8 @@ typedef struct {
                                  after the last step as d_K min(1, d_K / d_{K-1}) / max_k |u_k|
                                  with d = max_k |du_k| over the observations */
   int32_t fp64_top_levels;    /* mixed only: tree depths 0..fp64_top_levels-1 are factorised in FP64 */
+  int32_t fuse_height;        /* 0: off; else the largest height (<= 6) of bottom subtrees eliminated
+                                 by one CTA each with their Schur complements kept on chip */
   int32_t device;             /* CUDA device ordinal, or -1 for a host-only plan that supports
                                  the hdd_plan_info / hdd_node_info queries and nothing else */
 } hdd_plan_desc;

@@ -17,6 +17,7 @@ cudaError_t configure_solve_kernels();
 cudaError_t configure_refine_kernels();
 cudaError_t configure_warp_kernels();
 cudaError_t configure_tc_kernels();
+cudaError_t configure_fused_kernels();
 }  // namespace hdd
 
 namespace {
@@ -63,6 +64,7 @@ cudaError_t configure_device(int dev) {
   if (e == cudaSuccess) e = hdd::configure_refine_kernels();
   if (e == cudaSuccess) e = hdd::configure_warp_kernels();
   if (e == cudaSuccess) e = hdd::configure_tc_kernels();
+  if (e == cudaSuccess) e = hdd::configure_fused_kernels();
   if (e == cudaSuccess) g_configured[dev] = true;
   return e;
 }
@@ -76,6 +78,13 @@ void free_device(hdd::Plan& p) {
   cudaFree(p.d_maps);
   cudaFree(p.d_lists);
   cudaFree(p.d_obs);
+  for (auto& fu : p.fusion) {
+    cudaFree(fu.d_roots);
+    cudaFree(fu.d_nodes);
+    fu.d_roots = fu.d_nodes = nullptr;
+  }
+  cudaFree(p.d_fuse_soff);
+  p.d_fuse_soff = nullptr;
   p.d_phi = nullptr; p.d_nodes = nullptr; p.d_maps = nullptr; p.d_lists = nullptr; p.d_obs = nullptr;
 }
 
@@ -152,6 +161,28 @@ cudaError_t run_upsweep(const hdd::Plan& p, int batch, void* ws, const hdd::Rhs&
   a.arenas = arenas(p, L, ws);
   a.status = reinterpret_cast<int32_t*>(w + L.status);
   a.prof = prof;
+  // fused bottom subtrees first (their roots' Schur blocks feed the regular steps)
+  for (int prec = 0; prec < 2; ++prec) {
+    const hdd::Plan::Fusion& fu = p.fusion[prec];
+    if (fu.height == 0) continue;
+    hdd::FuseArgs fa;
+    fa.a = a;
+    fa.roots = fu.d_roots;
+    fa.fused = fu.d_nodes;
+    fa.fuse_soff = p.d_fuse_soff;
+    fa.sbuf_elems = fu.sbuf_elems;
+    fa.front_elems = fu.front_elems;
+    const int nroots = (int)fu.roots.size() / 12;
+    double fl = 0.0;
+    for (int q : fu.nodes) {
+      const double m = p.nodes[q].m, b = p.nodes[q].b;
+      fl += 2.0 * (m * m * m / 3.0 + (b + 1.0) * m * m / 2.0 + (b + 1.0) * (b + 2.0) / 2.0 * m);
+    }
+    ProfScope ps(prof, hdd::kProfFused, fl * batch, st);
+    cudaError_t e = prec == 0 ? hdd::launch_subtree<double>(fa, nroots, fu.smem_bytes, st)
+                              : hdd::launch_subtree<float>(fa, nroots, fu.smem_bytes, st);
+    if (e != cudaSuccess) return e;
+  }
   for (int h = 0; h <= p.height; ++h) {
     for (int kind = 0; kind < 6; ++kind) {
       const hdd::ListInfo& li = p.lists[p.step_lists[h][kind]];
@@ -343,6 +374,12 @@ hdd_status hdd_plan(const hdd_plan_desc* desc, hdd_plan_t* out) {
     if (e == cudaSuccess) e = upload(&p.d_maps, p.maps.data(), p.maps.size());
     if (e == cudaSuccess) e = upload(&p.d_lists, p.list_data.data(), p.list_data.size());
     if (e == cudaSuccess) e = upload(&p.d_obs, p.obs.data(), p.obs.size());
+    if (e == cudaSuccess) e = upload(&p.d_fuse_soff, p.fuse_soff.data(), p.fuse_soff.size());
+    for (auto& fu : p.fusion)
+      if (e == cudaSuccess && fu.height > 0) {
+        e = upload(&fu.d_roots, fu.roots.data(), fu.roots.size());
+        if (e == cudaSuccess) e = upload(&fu.d_nodes, fu.nodes.data(), fu.nodes.size());
+      }
     if (e != cudaSuccess) {
       free_device(p);
       delete h;
@@ -523,7 +560,7 @@ hdd_status hdd_profile_end(hdd_plan_t plan, hdd_kernel_stat_t* stats, int32_t ma
   pr->on = false;
   static const char* names[hdd::kProfCount] = {"kappa", "front_warp", "front_small", "front_fill", "potrf", "trsm",
                                                 "syrk_simt", "syrk_tc", "syrk_rhs", "forward", "descent",
-                                                "residual", "misc"};
+                                                "residual", "misc", "subtree"};
   int launches[hdd::kProfCount] = {};
   double ms[hdd::kProfCount] = {}, fl[hdd::kProfCount] = {};
   DeviceScope ds(plan->p.device);
@@ -572,6 +609,7 @@ hdd_status hdd_plan_info(hdd_plan_t plan, hdd_plan_info_t* info) {
       const hdd::ListInfo& li = p.lists[p.step_lists[h][kind]];
       if (li.n) up += kind == 2 ? 4 : (kind == 5 ? 5 : 1);
     }
+  for (const auto& fu : p.fusion) up += fu.height > 0;
   int down_all = 0, fwd = 0;
   for (int d = 0; d <= p.depth; ++d) {
     down += p.lists[p.down_vis_lists[d]].n > 0;

@@ -15,7 +15,7 @@ namespace hdd {
 // algorithmic flops of the launch.  Owned by a plan; not thread-safe.
 enum ProfFamily {
   kProfKappa, kProfFrontWarp, kProfFrontSmall, kProfFill, kProfPotrf, kProfTrsm, kProfSyrk, kProfSyrkTc,
-  kProfSyrkRhs, kProfForward, kProfDescent, kProfResidual, kProfMisc, kProfCount
+  kProfSyrkRhs, kProfForward, kProfDescent, kProfResidual, kProfMisc, kProfFused, kProfCount
 };
 struct Profiler {
   bool on = false;
@@ -61,6 +61,17 @@ struct StepArgs {
   Profiler* prof;            // nullptr unless profiling
   double fl_chol, fl_trsm, fl_syrk, fl_rhs;   // algorithmic flops of this launch (whole batch)
 };
+
+// Fused bottom subtrees of the upsweep (one CTA per subtree and sample)
+struct FuseArgs {
+  StepArgs a;
+  const int32_t* roots;       // [nroots x 12] subtree descriptors
+  const int32_t* fused;       // node lists, bottom-up
+  const int32_t* fuse_soff;   // per node: offset of its Schur square in the level buffer
+  int sbuf_elems;             // elements of one level buffer
+  int front_elems;            // elements of the front workspace shared by the warp groups
+};
+template <typename T> cudaError_t launch_subtree(const FuseArgs& f, int nroots, size_t smem_bytes, cudaStream_t st);
 
 // assembly: kappa = exp(Phi Z) (Sec. 3.1; kappa = e^q)
 cudaError_t launch_kappa(const double* phi, const double* Z, int n_t, int n_z, int batch, double* kappa,

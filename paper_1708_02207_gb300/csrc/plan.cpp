@@ -94,11 +94,13 @@ std::string build_plan(const hdd_plan_desc& d, Plan& p) {
   if (d.precision != HDD_FP64 && d.precision != HDD_MIXED_FP32) return "unknown precision";
   if (d.ir_max_iter < 0 || d.ir_max_iter > 64) return "ir_max_iter must be in 0..64";
   if (d.fp64_top_levels < 0 || d.fp64_top_levels > 64) return "fp64_top_levels must be in 0..64";
+  if (d.fuse_height < 0 || d.fuse_height > kFuseMaxHeight) return "fuse_height must be in 0..6";
   p.N = d.N; p.leaf = d.leaf; p.n_z = d.n_z; p.n_obs = d.n_obs;
   p.n_t = 2 * (d.N - 1) * (d.N - 1);
   p.f = d.f; p.sigma = d.sigma; p.h = 1.0 / (d.N - 1);
   p.precision = d.precision; p.ir_max_iter = d.ir_max_iter; p.ir_tol = d.ir_tol;
   p.fp64_top_levels = d.fp64_top_levels;
+  p.fuse_height = d.fuse_height;
   p.device = d.device;
   p.obs.assign(d.obs_vertex, d.obs_vertex + d.n_obs);
   for (int v : p.obs) {
@@ -133,6 +135,78 @@ std::string build_plan(const hdd_plan_desc& d, Plan& p) {
   // precision per node: mixed plans factorise the top fp64_top_levels depths in FP64
   for (Node& nd : p.nodes) nd.fp64 = (p.precision == HDD_FP64) || nd.depth < p.fp64_top_levels;
 
+  // fused bottom subtrees: complete subtrees of one precision whose whole
+  // elimination fits the shared memory of one CTA (two level buffers of Schur
+  // squares + the fronts of the warp groups); the largest such height wins
+  p.fuse_soff.assign(nn, 0);
+  for (int prec = 0; prec < 2; ++prec) {
+    const bool want64 = prec == 0;
+    const size_t esz = want64 ? 8 : 4;
+    Plan::Fusion best;
+    for (int H = p.fuse_height; H >= 1 && best.height == 0; --H) {
+      Plan::Fusion fu;
+      fu.height = H;
+      bool any = false, fits = true;
+      for (int k = 0; k < nn && fits; ++k) {
+        const Node& r = p.nodes[k];
+        if (r.height != H || r.fp64 != want64) continue;
+        // complete subtree: every node at height h > 0 has two sons at height h - 1
+        std::vector<std::vector<int>> lev(H + 1);
+        lev[H].push_back(k);
+        bool complete = true;
+        for (int hh = H; hh > 0 && complete; --hh)
+          for (int q : lev[hh]) {
+            const Node& nd = p.nodes[q];
+            if (nd.leaf()) { complete = false; break; }
+            for (int cidx = 0; cidx < 2; ++cidx) {
+              const Node& ch = p.nodes[nd.child[cidx]];
+              if (ch.height != hh - 1 || ch.fp64 != want64) complete = false;
+              lev[hh - 1].push_back(nd.child[cidx]);
+            }
+          }
+        if (!complete) continue;
+        for (int q : lev[0])
+          if (!p.nodes[q].leaf()) complete = false;
+        if (!complete) continue;
+        any = true;
+        int32_t desc[12] = {0};
+        desc[0] = (int32_t)fu.nodes.size();
+        desc[1] = H + 1;
+        for (int hh = 0; hh <= H; ++hh) {
+          desc[2 + hh] = (int32_t)fu.nodes.size() - desc[0];
+          int off = 0, maxk = 0;
+          for (int q : lev[hh]) {
+            fu.nodes.push_back(q);
+            const Node& nd = p.nodes[q];
+            if (hh < H) {
+              p.fuse_soff[q] = off;
+              off += ((nd.b + 1) * (nd.b + 1) + 3) & ~3;
+            }
+            int ld = (nd.nf + 3) & ~3;
+            if ((ld & 7) == 0) ld += 4;
+            maxk = std::max(maxk, ((nd.nf * ld) + 3) & ~3);
+          }
+          fu.sbuf_elems = std::max(fu.sbuf_elems, off);
+          const int nh = (int)lev[hh].size();
+          int wpf = std::max(1, 16 / nh);
+          while (wpf & (wpf - 1)) wpf &= wpf - 1;
+          const int ngroups = 16 / wpf;
+          int maxnf = 0;
+          for (int q : lev[hh]) maxnf = std::max(maxnf, p.nodes[q].nf);
+          if (!(wpf == 1 && maxnf <= kTinyMax)) fu.front_elems = std::max(fu.front_elems, ngroups * maxk);
+        }
+        desc[2 + H + 1] = (int32_t)fu.nodes.size() - desc[0];
+        fu.roots.insert(fu.roots.end(), desc, desc + 12);
+        fu.smem_bytes = (2 * (size_t)fu.sbuf_elems + (size_t)fu.front_elems) * esz + 64;
+        if (fu.smem_bytes > 200 * 1024) fits = false;
+      }
+      if (any && fits) best = fu;
+    }
+    if (best.height > 0)
+      for (int q : best.nodes) p.nodes[q].fused = true;
+    p.fusion[prec] = best;
+  }
+
   // stats, schedule
   p.n_leaves = 0; p.depth = 0; p.n_visited = 0; p.max_front = 0;
   for (const Node& nd : p.nodes) {
@@ -149,6 +223,8 @@ std::string build_plan(const hdd_plan_desc& d, Plan& p) {
   p.max_nf_large = p.max_m_large = p.max_b_large = 0;
   for (int k = 0; k < nn; ++k) {
     Node& nd = p.nodes[k];
+    if (nd.fused) goto descent_lists;
+    {
     Step& st = p.steps[nd.height];
     if (nd.fp64) {
       if (nd.nf <= kTinyMax) st.tiny64.push_back(k);
@@ -165,6 +241,8 @@ std::string build_plan(const hdd_plan_desc& d, Plan& p) {
       p.max_m_large = std::max(p.max_m_large, nd.m);
       p.max_b_large = std::max(p.max_b_large, nd.b);
     }
+    }
+  descent_lists:
     if (nd.m == 0) continue;   // a front with nothing to eliminate has no descent work
     p.down_all[nd.depth].push_back(k);
     if (nd.visited) p.down_visited[nd.depth].push_back(k);
@@ -311,15 +389,12 @@ std::string build_plan(const hdd_plan_desc& d, Plan& p) {
     p.step_lists[hgt] = {add_list(st.tiny64), add_list(st.small64), add_list(st.large64),
                          add_list(st.tiny32), add_list(st.small32), add_list(st.large32)};
   }
+  // right-hand-side sweep: every node (fused or not), by height and precision
   p.fwd_lists.assign(p.height + 1, {0, 0});
-  for (int hgt = 0; hgt <= p.height; ++hgt) {
-    const Step& st = p.steps[hgt];
-    std::vector<int> l64(st.tiny64), l32(st.tiny32);
-    l64.insert(l64.end(), st.small64.begin(), st.small64.end());
-    l64.insert(l64.end(), st.large64.begin(), st.large64.end());
-    l32.insert(l32.end(), st.small32.begin(), st.small32.end());
-    l32.insert(l32.end(), st.large32.begin(), st.large32.end());
-    p.fwd_lists[hgt] = {add_list(l64), add_list(l32)};
+  {
+    std::vector<std::vector<int>> l64(p.height + 1), l32(p.height + 1);
+    for (int k = 0; k < nn; ++k) (p.nodes[k].fp64 ? l64 : l32)[p.nodes[k].height].push_back(k);
+    for (int hgt = 0; hgt <= p.height; ++hgt) p.fwd_lists[hgt] = {add_list(l64[hgt]), add_list(l32[hgt])};
   }
   p.down_vis_lists.assign(p.depth + 1, 0);
   p.down_all_lists.assign(p.depth + 1, 0);

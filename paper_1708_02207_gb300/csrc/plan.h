@@ -43,6 +43,7 @@ struct Node {
   std::vector<int> bnd;    // boundary unknowns, ascending id
   bool visited = false;
   bool fp64 = true;
+  bool fused = false;      // eliminated inside a fused subtree
   int m = 0, b = 0, nf = 0;
   int64_t f_off = 0, s_off = 0, y_off = 0, tc_off = -1;
   int64_t map_off = 0;
@@ -66,7 +67,7 @@ struct Step {
 struct Plan {
   // problem
   int N = 0, leaf = 0, n_z = 0, n_obs = 0, n_t = 0, device = -1;
-  int precision = HDD_FP64, ir_max_iter = 0, fp64_top_levels = 0;
+  int precision = HDD_FP64, ir_max_iter = 0, fp64_top_levels = 0, fuse_height = 0;
   double f = 1.0, sigma = 1.0, h = 0.0, ir_tol = 1e-10;
   std::vector<int32_t> obs;
 
@@ -88,6 +89,19 @@ struct Plan {
   int64_t s64_stride = 0, s32_stride = 0;   // Schur arenas (lifetime-packed)
   double flops_up = 0.0, flops_down = 0.0;
 
+  // fused bottom subtrees, per precision (0: FP64, 1: FP32)
+  struct Fusion {
+    int height = 0;                 // subtree height (0: no fusion)
+    std::vector<int32_t> roots;     // 12 ints per subtree
+    std::vector<int32_t> nodes;     // node lists
+    int sbuf_elems = 0, front_elems = 0;
+    size_t smem_bytes = 0;
+    int32_t* d_roots = nullptr;
+    int32_t* d_nodes = nullptr;
+  } fusion[2];
+  std::vector<int32_t> fuse_soff;   // per node
+  int32_t* d_fuse_soff = nullptr;
+
   // node lists concatenated (host copy of d_lists) and their descriptors
   std::vector<int32_t> list_data;
   std::vector<ListInfo> lists;
@@ -108,6 +122,8 @@ struct Plan {
 // Fronts of at most kTinyMax rows run one per warp in registers; up to the
 // kSmallMax limits one per CTA in shared memory; larger ones in global memory.
 constexpr int kTinyMax = 32;
+// Largest height of a fused bottom subtree allowed by the kernel.
+constexpr int kFuseMaxHeight = 6;
 // Tensor-core SYRK staging: 128-row tiles x 8-column chunks, hi and lo parts of
 // 4 KiB each (TF32 values in the 8-row x 16-byte core-matrix layout).
 constexpr int kTcTile = 128, kTcChunk = 8;

@@ -33,7 +33,8 @@ class PlanDesc(C.Structure):
         ("kl_basis", C.POINTER(C.c_double)), ("f", C.c_double),
         ("n_obs", C.c_int32), ("obs_vertex", C.POINTER(C.c_int32)),
         ("sigma", C.c_double), ("precision", C.c_int32), ("ir_max_iter", C.c_int32),
-        ("ir_tol", C.c_double), ("fp64_top_levels", C.c_int32), ("device", C.c_int32),
+        ("ir_tol", C.c_double), ("fp64_top_levels", C.c_int32), ("fuse_height", C.c_int32),
+        ("device", C.c_int32),
     ]
 
 
@@ -129,7 +130,7 @@ class Plan:
 
     def __init__(self, N: int, leaf: int, phi: np.ndarray | None, obs: np.ndarray, sigma: float,
                  f: float = 1.0, precision: int = HDD_FP64, ir_max_iter: int = 2, ir_tol: float = 1e-8,
-                 fp64_top_levels: int = 0, device: int = 0):
+                 fp64_top_levels: int = 0, fuse_height: int = 0, device: int = 0):
         self.lib = load_library()
         self.N, self.leaf, self.sigma, self.f = N, leaf, float(sigma), float(f)
         self.obs = np.ascontiguousarray(obs, dtype=np.int32)
@@ -151,6 +152,7 @@ class Plan:
         desc.sigma = self.sigma
         desc.precision, desc.ir_max_iter, desc.ir_tol = precision, ir_max_iter, ir_tol
         desc.fp64_top_levels = fp64_top_levels
+        desc.fuse_height = fuse_height
         desc.device = device
         self.precision = precision
         h = C.c_void_p()

@@ -54,6 +54,17 @@ def test_full_field_mixed(hdd, N, leaf, top):
     assert rel_err_field(u, ref).max() <= TOL
 
 
+@pytest.mark.parametrize("fuse", [4, 5])
+def test_fused_subtrees_mixed(hdd, fuse):
+    N = 129
+    phi, Z = small_problem(N, n_z=20, corr_len=0.2, variance=2.0, batch=2, seed=77)
+    obs = interior(N)
+    _, u, st = gpu_eval(hdd, N, 4, phi, obs, Z, np.zeros(obs.size), 0.1, ir_max_iter=2, fuse_height=fuse)
+    ref = oracle_full(N, phi, Z)[:, obs]
+    assert (st == 0).all()
+    assert rel_err_field(u, ref).max() <= TOL
+
+
 def test_refinement_contracts(hdd):
     # each refinement step multiplies the error by the contraction factor of the
     # FP32 factorisation; no refinement leaves an FP32-sized error

@@ -61,6 +61,17 @@ def test_full_field_every_vertex(hdd, N, leaf):
     assert rel_err_field(u, ref).max() <= TOL
 
 
+@pytest.mark.parametrize("N,leaf,fuse", [(65, 4, 4), (129, 4, 5), (129, 8, 2)])
+def test_fused_subtrees_full_field(hdd, N, leaf, fuse):
+    # bottom subtrees eliminated by one CTA each (Schur complements on chip)
+    phi, Z = small_problem(N, batch=2, seed=N + fuse)
+    obs = interior(N)
+    _, u, st = gpu_eval(hdd, N, leaf, phi, obs, Z, np.zeros(obs.size), 0.1, fuse_height=fuse)
+    ref = oracle_full(N, phi, Z)[:, obs]
+    assert (st == 0).all()
+    assert rel_err_field(u, ref).max() <= TOL
+
+
 def test_leaf_size_invariance(hdd):
     # the Schur complement onto a separator does not depend on the elimination order
     N = 65
