@@ -113,6 +113,8 @@ hdd::Arenas arenas(const hdd::Plan& p, const hdd::Layout& L, void* ws) {
   A.y32_stride = p.y32_stride;
   A.tc = reinterpret_cast<unsigned char*>(w + L.tc);
   A.tc_stride = p.tc_stride;
+  A.inv = reinterpret_cast<unsigned char*>(w + L.inv);
+  A.inv_stride = p.inv_stride;
   return A;
 }
 

@@ -79,6 +79,7 @@ struct Arenas {
   double* y64; int64_t y64_stride;
   float* y32; int64_t y32_stride;
   unsigned char* tc; int64_t tc_stride;   // split TF32 tiles for the tensor-core SYRK
+  unsigned char* inv; int64_t inv_stride; // inverted diagonal blocks of L_gg (POTRF -> TRSM)
 };
 
 // y_g of a node (the bordered row of its front): written by the upsweep and by

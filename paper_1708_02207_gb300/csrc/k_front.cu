@@ -48,19 +48,33 @@ __device__ __forceinline__ T front_entry(int r, int c, int s, int node, const No
 // column j updates rows j..nf-1 (contiguous, conflict-free) with l_j.
 template <typename T>
 __device__ __forceinline__ void scatter_son(T* K, int ld, const NodeDev& ch, const int32_t* maps, const Arenas& A,
-                                            int s) {
+                                            int s, int* ups) {
   const int ldc = ch.b + 1;
   const int32_t* up = maps + ch.up_off;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarp = blockDim.x >> 5;
+  for (int i = threadIdx.x; i < ldc; i += blockDim.x) ups[i] = up[i];
+  __syncthreads();
   const int64_t base = (int64_t)s * (ch.fp64 ? A.s64_stride : A.s32_stride) + ch.s_off;
-  for (int cc = warp; cc < ldc; cc += nwarp) {
-    const int pc = up[cc];
-    for (int aa = cc + lane; aa < ldc; aa += 32) {
-      const int64_t idx = base + (int64_t)cc * ldc + aa;
-      const T val = ch.fp64 ? (T)A.s64[idx] : (T)A.s32[idx];
-      const int pr = up[aa];
-      const int r = max(pr, pc), c = min(pr, pc);
-      K[c * ld + r] += val;
+  const int total = ldc * ldc;
+  // four entries per thread and pass: all loads first (in flight together), then the adds
+  for (int i0 = threadIdx.x; i0 < total; i0 += 4 * blockDim.x) {
+    T v[4];
+    int rr[4], cc[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int idx = i0 + q * blockDim.x;
+      const int c = idx / ldc, r = idx - c * ldc;
+      rr[q] = r;
+      cc[q] = c;
+      const bool use = idx < total && r >= c;
+      v[q] = use ? (ch.fp64 ? (T)A.s64[base + idx] : (T)A.s32[base + idx]) : (T)0;
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int idx = i0 + q * blockDim.x;
+      if (idx < total && rr[q] >= cc[q]) {
+        const int pr = ups[rr[q]], pc = ups[cc[q]];
+        K[min(pr, pc) * ld + max(pr, pc)] += v[q];
+      }
     }
   }
 }
@@ -123,11 +137,12 @@ __global__ void __launch_bounds__(512) k_front_small(StepArgs a) {
       for (int r = lane; r < nf; r += 32)
         K[c * ld + r] = (r >= c) ? leaf_entry<T>(r, c, s, nd, map, kap, a.N, a.rhs) : (T)0;
   } else {
+    int* ups = reinterpret_cast<int*>(K + (size_t)nf * ld + 16);
     for (int idx = threadIdx.x; idx < nf * ld; idx += blockDim.x) K[idx] = (T)0;
     __syncthreads();
-    scatter_son<T>(K, ld, a.nodes[nd.child0], a.maps, a.arenas, s);
+    scatter_son<T>(K, ld, a.nodes[nd.child0], a.maps, a.arenas, s, ups);
     __syncthreads();
-    scatter_son<T>(K, ld, a.nodes[nd.child1], a.maps, a.arenas, s);
+    scatter_son<T>(K, ld, a.nodes[nd.child1], a.maps, a.arenas, s, ups);
     __syncthreads();
     for (int c = threadIdx.x; c < m; c += blockDim.x) K[c * ld + nf - 1] += (T)a.rhs(s, map[c]);
   }
@@ -221,7 +236,7 @@ static int small_threads(int nf) { return nf <= 64 ? 128 : (nf <= 128 ? 256 : 51
 template <typename T>
 cudaError_t launch_front_small(const StepArgs& a, cudaStream_t st) {
   if (a.nlist == 0) return cudaSuccess;
-  const size_t smem = (size_t)a.max_nf * front_ld(a.max_nf) * sizeof(T) + 4 * 4 * sizeof(T);
+  const size_t smem = ((size_t)a.max_nf * front_ld(a.max_nf) + 16) * sizeof(T) + (size_t)(a.max_nf + 4) * sizeof(int);
   dim3 grid(a.nlist, a.batch);
   if (a.prof) a.prof->begin(kProfFrontSmall, a.fl_chol + a.fl_trsm + a.fl_syrk + a.fl_rhs, st);
   k_front_small<T><<<grid, small_threads(a.max_nf), smem, st>>>(a);
@@ -266,7 +281,8 @@ __global__ void __launch_bounds__(256) k_potrf(StepArgs a) {
   T* A = node_F<T>(a.arenas, nd, s);
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* piv = reinterpret_cast<T*>(smem_raw);                 // [kPanel]
-  T* Ps = piv + kPanel;                                     // panel, ld = rows
+  T* W = piv + kPanel;                                      // [32][33] inverse of a diagonal block
+  T* Ps = W + 32 * 33;                                      // panel, ld = rows
   const bool in_smem = m <= SmemCap<T>::rows;
   for (int k0 = 0; k0 < m; k0 += kPanel) {
     const int kb = min(kPanel, m - k0), rows = m - k0;
@@ -300,6 +316,25 @@ __global__ void __launch_bounds__(256) k_potrf(StepArgs a) {
       }
     }
     __syncthreads();
+    // inverse of the diagonal block L_kk (lower), one column per lane of warp 0,
+    // by forward substitution on the unit vectors; TRSM applies it as a product
+    if (threadIdx.x < 32) {
+      T* Wc = W + threadIdx.x * 33;          // column c of inv(L_kk), rows c..kb-1
+      const int c = threadIdx.x;
+      if (c < kb) {
+        for (int r = 0; r < kb; ++r) {
+          if (r < c) { Wc[r] = (T)0; continue; }
+          T acc = (r == c) ? (T)1 : (T)0;
+          for (int l = c; l < r; ++l) acc -= P[(int64_t)l * ld + r] * Wc[l];
+          Wc[r] = acc / P[(int64_t)r * ld + r];
+        }
+        T* G = reinterpret_cast<T*>(a.arenas.inv + (int64_t)s * a.arenas.inv_stride + nd.inv_off) + (k0 / 32) * 1024;
+        for (int r = 0; r < 32; ++r) G[c * 32 + r] = (r < kb) ? Wc[r] : (T)0;
+      } else {
+        T* G = reinterpret_cast<T*>(a.arenas.inv + (int64_t)s * a.arenas.inv_stride + nd.inv_off) + (k0 / 32) * 1024;
+        for (int r = 0; r < 32; ++r) G[c * 32 + r] = (r == c) ? (T)1 : (T)0;
+      }
+    }
     if (in_smem)
       for (int idx = threadIdx.x; idx < kb * rows; idx += blockDim.x) {
         const int l = idx / rows, i = idx - l * rows;
@@ -435,18 +470,34 @@ __global__ void __launch_bounds__(256) k_trsm(StepArgs a) {
   for (int j0 = 0; j0 < m; j0 += 32) {
     const int jb = min(32, m - j0);
     __syncthreads();
-    for (int idx = threadIdx.x; idx < jb * jb; idx += blockDim.x) {
-      const int l = idx / jb, q = idx - l * jb;
-      L[l * 33 + q] = (q >= l) ? A[(int64_t)(j0 + l) * nf + j0 + q] : (T)0;
+    // inv(L_jj), written by POTRF: column c at G[c * 32 .. c * 32 + 31]; L[l * 33 + c] = inv[c][l]
+    {
+      const T* G = reinterpret_cast<const T*>(a.arenas.inv + (int64_t)s * a.arenas.inv_stride + nd.inv_off) +
+                   (j0 / 32) * 1024;
+      for (int idx = threadIdx.x; idx < 1024; idx += blockDim.x) L[(idx >> 5) * 33 + (idx & 31)] = G[idx];
     }
     __syncthreads();
-    if (threadIdx.x < nr) {
-      const int r = threadIdx.x;
-      for (int cc = 0; cc < jb; ++cc) {
-        T x = X[(j0 + cc) * ldx + r];
-        for (int l = 0; l < cc; ++l) x -= X[(j0 + l) * ldx + r] * L[l * 33 + cc];
-        X[(j0 + cc) * ldx + r] = x / L[cc * 33 + cc];
+    // X_blk <- X_blk inv(L_jj)^T: x_c = sum_{l <= c} x_l inv[c][l]; each thread one row and a
+    // group of columns, results kept in registers until all threads have read X_blk
+    {
+      constexpr int CPB = 32 * R / 256;        // columns per thread
+      const int r = threadIdx.x % R, cbase = (threadIdx.x / R) * CPB;
+      T acc[CPB];
+#pragma unroll
+      for (int q = 0; q < CPB; ++q) acc[q] = (T)0;
+      for (int l = 0; l < jb; ++l) {
+        const T x = X[(j0 + l) * ldx + r];
+#pragma unroll
+        for (int q = 0; q < CPB; ++q) {
+          const int c = cbase + q;
+          if (l <= c) acc[q] += x * L[l * 33 + c];
+        }
       }
+      __syncthreads();
+      if (r < nr)
+#pragma unroll
+        for (int q = 0; q < CPB; ++q)
+          if (cbase + q < jb) X[(j0 + cbase + q) * ldx + r] = acc[q];
     }
     for (int c0 = j0 + jb; c0 < m; c0 += 64) {
       const int nc = min(64, m - c0);
@@ -597,7 +648,7 @@ cudaError_t launch_front_large(const StepArgs& a, cudaStream_t st) {
   }
   const size_t rows_smem = (size_t)min(a.max_m, SmemCap<T>::rows);
   {
-    const size_t smem = (rows_smem * kPanel + kPanel) * sizeof(T);
+    const size_t smem = (rows_smem * kPanel + kPanel + 32 * 33) * sizeof(T);
     if (a.prof) a.prof->begin(kProfPotrf, a.fl_chol, st);
     k_potrf<T><<<dim3(a.nlist, a.batch), 256, smem, st>>>(a);
     if (a.prof) a.prof->end(st);

@@ -274,6 +274,20 @@ std::string build_plan(const hdd_plan_desc& d, Plan& p) {
     p.tc_stride = std::max(p.tc_stride, off);
   }
 
+  // inverted 32 x 32 diagonal blocks of L_gg of the large fronts (POTRF writes
+  // them, TRSM applies them): live within one height step
+  p.inv_stride = 0;
+  for (int hgt = 0; hgt <= p.height; ++hgt) {
+    int64_t off = 0;
+    for (int prec = 0; prec < 2; ++prec)
+      for (int k : (prec ? p.steps[hgt].large32 : p.steps[hgt].large64)) {
+        Node& nd = p.nodes[k];
+        nd.inv_off = off;
+        off += (int64_t)((nd.m + 31) / 32) * 32 * 32 * (nd.fp64 ? 8 : 4);
+      }
+    p.inv_stride = std::max(p.inv_stride, off);
+  }
+
   // Schur arena: a node's S lives from its own step to its parent's step.
   // Group by the parent's height; first-fit packing of the groups' intervals.
   for (int prec = 0; prec < 2; ++prec) {
@@ -416,6 +430,7 @@ std::string build_plan(const hdd_plan_desc& d, Plan& p) {
     d.fp64 = nd.fp64;
     d.y_off = (int32_t)nd.y_off;
     d.tc_off = nd.tc_off;
+    d.inv_off = nd.inv_off;
     d.f_off = nd.f_off; d.s_off = nd.s_off;
   }
 
@@ -449,6 +464,7 @@ Layout layout(const Plan& p, int batch) {
   L.f64 = take(B * (size_t)p.f64_stride * 8);
   L.f32 = take(B * (size_t)p.f32_stride * 4);
   L.tc = take(B * (size_t)p.tc_stride);
+  L.inv = take(B * (size_t)p.inv_stride);
   L.y64 = take(B * (size_t)p.y64_stride * 8);
   L.y32 = take(B * (size_t)p.y32_stride * 4);
   L.s64 = take(B * (size_t)p.s64_stride * 8);

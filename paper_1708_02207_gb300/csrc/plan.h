@@ -12,7 +12,7 @@
 
 namespace hdd {
 
-// Device-side node descriptor (80 bytes).  A node's front has nf = m + b + 1
+// Device-side node descriptor (88 bytes).  A node's front has nf = m + b + 1
 // rows: m eliminated vertices (gamma, or a leaf's interior), b boundary unknowns,
 // and one bordered right-hand-side row.  Per sample the front is stored as
 //   F: nf x m column-major (ld nf)      -> L_gg (rows < m), L_Bg, y_g^T (last row)
@@ -29,8 +29,9 @@ struct NodeDev {
   int64_t f_off;            // elements into a sample's factor store of the node's type
   int64_t s_off;            // elements into a sample's Schur arena of the node's type
   int64_t tc_off;           // bytes into a sample's tensor-core staging arena, or -1
+  int64_t inv_off;          // bytes into a sample's arena of inverted 32 x 32 diagonal blocks of L_gg, or -1
 };
-static_assert(sizeof(NodeDev) == 80, "NodeDev layout");
+static_assert(sizeof(NodeDev) == 88, "NodeDev layout");
 
 struct Node {
   int x0, x1, y0, y1;
@@ -45,7 +46,7 @@ struct Node {
   bool fp64 = true;
   bool fused = false;      // eliminated inside a fused subtree
   int m = 0, b = 0, nf = 0;
-  int64_t f_off = 0, s_off = 0, y_off = 0, tc_off = -1;
+  int64_t f_off = 0, s_off = 0, y_off = 0, tc_off = -1, inv_off = -1;
   int64_t map_off = 0;
   int64_t up_off = 0;
   bool leaf() const { return child[0] < 0; }
@@ -86,6 +87,7 @@ struct Plan {
   int64_t f64_stride = 0, f32_stride = 0;   // factor stores
   int64_t y64_stride = 0, y32_stride = 0;   // y_g arenas (one entry per eliminated vertex)
   int64_t tc_stride = 0;                    // bytes: split TF32 tiles of one height step
+  int64_t inv_stride = 0;                   // bytes: inverted diagonal blocks of one height step
   int64_t s64_stride = 0, s32_stride = 0;   // Schur arenas (lifetime-packed)
   double flops_up = 0.0, flops_down = 0.0;
 
@@ -138,7 +140,7 @@ std::string build_plan(const hdd_plan_desc& d, Plan& p);
 struct Layout {
   size_t status = 0, kappa = 0, kappa32 = 0;
   size_t u = 0, r = 0, du = 0;        // FP64 vertex vectors [batch x N^2]
-  size_t f64 = 0, f32 = 0, s64 = 0, s32 = 0, y64 = 0, y32 = 0, tc = 0;
+  size_t f64 = 0, f32 = 0, s64 = 0, s32 = 0, y64 = 0, y32 = 0, tc = 0, inv = 0;
   size_t uobs = 0, ll = 0, z = 0, y = 0, conv = 0;
   size_t total = 0;
 };
