@@ -229,7 +229,10 @@ cudaError_t run_descent(const hdd::Plan& p, int batch, void* ws, const std::vect
     const bool cta = li.max_m >= kSweepCtaMinM;
     ProfScope ps(prof, hdd::kProfDescent, 0.0, st);
     cudaError_t e;
-    if (cta)
+    if (li.max_nf <= hdd::kTinyMax)
+      e = fp64 ? hdd::launch_descent_tiny<double>(p.d_nodes, p.d_maps, p.d_lists + li.off, li.n, batch, A, u, NN, st)
+               : hdd::launch_descent_tiny<float>(p.d_nodes, p.d_maps, p.d_lists + li.off, li.n, batch, A, u, NN, st);
+    else if (cta)
       e = fp64 ? hdd::launch_descent<double>(p.d_nodes, p.d_maps, p.d_lists + li.off, li.n, batch, A, u, NN,
                                              li.max_b, li.max_m, st)
                : hdd::launch_descent<float>(p.d_nodes, p.d_maps, p.d_lists + li.off, li.n, batch, A, u, NN,
@@ -256,7 +259,10 @@ cudaError_t run_forward(const hdd::Plan& p, int batch, void* ws, const hdd::Rhs&
       const bool cta = li.max_m >= kSweepCtaMinM;
       ProfScope ps(prof, hdd::kProfForward, 0.0, st);
       cudaError_t e;
-      if (cta)
+      if (li.max_nf <= hdd::kTinyMax)
+        e = k == 0 ? hdd::launch_forward_tiny<double>(p.d_nodes, p.d_maps, p.d_lists + li.off, li.n, batch, A, rhs, st)
+                   : hdd::launch_forward_tiny<float>(p.d_nodes, p.d_maps, p.d_lists + li.off, li.n, batch, A, rhs, st);
+      else if (cta)
         e = k == 0 ? hdd::launch_forward<double>(p.d_nodes, p.d_maps, p.d_lists + li.off, li.n, batch, A, rhs,
                                                  li.max_nf, st)
                    : hdd::launch_forward<float>(p.d_nodes, p.d_maps, p.d_lists + li.off, li.n, batch, A, rhs,

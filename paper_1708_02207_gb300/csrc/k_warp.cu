@@ -306,6 +306,107 @@ template cudaError_t launch_descent_warp<double>(const NodeDev*, const int32_t*,
 template cudaError_t launch_descent_warp<float>(const NodeDev*, const int32_t*, const int32_t*, int, int,
                                                 const Arenas&, double*, int64_t, int, int, cudaStream_t);
 
+
+// ---------------------------------------------------------------------------
+// Sweeps over fronts of at most 32 rows with the node's factor rows in registers
+// (lane r holds row r of F, m <= 31 columns), one warp per (node, sample):
+// forward substitution and the descent's dot products by shuffles, without
+// shared memory.
+template <typename T>
+__global__ void __launch_bounds__(256) k_forward_tiny(const NodeDev* __restrict__ nodes,
+                                                      const int32_t* __restrict__ maps,
+                                                      const int32_t* __restrict__ list, int batch, Arenas A,
+                                                      Rhs rhs) {
+  const int node = list[blockIdx.x];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int s = blockIdx.y * 8 + warp;
+  if (s >= batch) return;
+  const NodeDev nd = nodes[node];
+  const int m = nd.m, b = nd.b, nf = nd.nf;
+  const int32_t* vid = maps + nd.map_off;
+  const T* F = warp_F<T>(A, nd, s);
+  T row[32];
+#pragma unroll
+  for (int c = 0; c < 32; ++c) row[c] = (c < m && lane < nf - 1) ? F[c * nf + lane] : (T)0;
+  T z = (T)0;
+  if (lane < nf - 1) {
+    if (lane < m) z = (T)rhs(s, vid[lane]);
+    if (!nd.leaf) {
+      const int32_t* pos0 = vid + (nf - 1);
+      const int32_t* pos1 = pos0 + nf;
+      const int q0 = pos0[lane], q1 = pos1[lane];
+      if (q0 >= 0) z += son_cond<T>(A, nodes[nd.child0], s, q0);
+      if (q1 >= 0) z += son_cond<T>(A, nodes[nd.child1], s, q1);
+    }
+  }
+#pragma unroll
+  for (int c = 0; c < 32; ++c) {
+    if (c >= m) break;    // warp-uniform
+    const T d = __shfl_sync(kFull, row[c], c);
+    const T yc = __shfl_sync(kFull, z, c) / d;
+    if (lane == c) z = yc;
+    if (lane > c) z -= row[c] * yc;
+  }
+  if (lane < m) node_Y<T>(A, nd, s)[lane] = z;
+  if (lane >= m && lane < nf - 1) warp_S<T>(A, nd, s)[lane - m] = z;
+  (void)b;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_descent_tiny(const NodeDev* __restrict__ nodes,
+                                                      const int32_t* __restrict__ maps,
+                                                      const int32_t* __restrict__ list, int batch, Arenas A,
+                                                      double* __restrict__ u, int64_t u_stride) {
+  const int node = list[blockIdx.x];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int s = blockIdx.y * 8 + warp;
+  if (s >= batch) return;
+  const NodeDev nd = nodes[node];
+  const int m = nd.m, nf = nd.nf;
+  const int32_t* vid = maps + nd.map_off;
+  const T* F = warp_F<T>(A, nd, s);
+  double* us = u + (int64_t)s * u_stride;
+  T row[32];
+#pragma unroll
+  for (int c = 0; c < 32; ++c) row[c] = (c < m && lane < nf - 1) ? F[c * nf + lane] : (T)0;
+  T wv = (lane >= m && lane < nf - 1) ? (T)us[vid[lane]] : (T)0;   // u_B; u_g filled below
+  const T yl = (lane < m) ? node_Y<T>(A, nd, s)[lane] : (T)0;
+#pragma unroll
+  for (int c = 31; c >= 0; --c) {
+    if (c >= m) continue;    // warp-uniform
+    T t = (lane > c) ? row[c] * wv : (T)0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(kFull, t, o);
+    const T d = __shfl_sync(kFull, row[c], c);
+    const T uc = (__shfl_sync(kFull, yl, c) - t) / d;
+    if (lane == c) wv = uc;
+  }
+  if (lane < m) us[vid[lane]] = (double)wv;
+}
+
+template <typename T>
+cudaError_t launch_forward_tiny(const NodeDev* nodes, const int32_t* maps, const int32_t* list, int nlist, int batch,
+                                const Arenas& A, const Rhs& rhs, cudaStream_t st) {
+  if (nlist == 0) return cudaSuccess;
+  k_forward_tiny<T><<<dim3(nlist, (batch + 7) / 8), 256, 0, st>>>(nodes, maps, list, batch, A, rhs);
+  return cudaGetLastError();
+}
+template <typename T>
+cudaError_t launch_descent_tiny(const NodeDev* nodes, const int32_t* maps, const int32_t* list, int nlist, int batch,
+                                const Arenas& A, double* u, int64_t u_stride, cudaStream_t st) {
+  if (nlist == 0) return cudaSuccess;
+  k_descent_tiny<T><<<dim3(nlist, (batch + 7) / 8), 256, 0, st>>>(nodes, maps, list, batch, A, u, u_stride);
+  return cudaGetLastError();
+}
+template cudaError_t launch_forward_tiny<double>(const NodeDev*, const int32_t*, const int32_t*, int, int,
+                                                 const Arenas&, const Rhs&, cudaStream_t);
+template cudaError_t launch_forward_tiny<float>(const NodeDev*, const int32_t*, const int32_t*, int, int,
+                                                const Arenas&, const Rhs&, cudaStream_t);
+template cudaError_t launch_descent_tiny<double>(const NodeDev*, const int32_t*, const int32_t*, int, int,
+                                                 const Arenas&, double*, int64_t, cudaStream_t);
+template cudaError_t launch_descent_tiny<float>(const NodeDev*, const int32_t*, const int32_t*, int, int,
+                                                const Arenas&, double*, int64_t, cudaStream_t);
+
 }  // namespace hdd
 
 namespace hdd {

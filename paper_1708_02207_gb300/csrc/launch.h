@@ -90,6 +90,13 @@ template <typename T>
 cudaError_t launch_descent_warp(const NodeDev* nodes, const int32_t* maps, const int32_t* list, int nlist, int batch,
                                 const Arenas& A, double* u, int64_t u_stride, int max_nf, int max_m,
                                 cudaStream_t st);
+// sweeps over fronts of at most 32 rows, factor rows in registers
+template <typename T>
+cudaError_t launch_forward_tiny(const NodeDev* nodes, const int32_t* maps, const int32_t* list, int nlist, int batch,
+                                const Arenas& A, const Rhs& rhs, cudaStream_t st);
+template <typename T>
+cudaError_t launch_descent_tiny(const NodeDev* nodes, const int32_t* maps, const int32_t* list, int nlist, int batch,
+                                const Arenas& A, double* u, int64_t u_stride, cudaStream_t st);
 // fronts that fit in shared memory: build + partial Cholesky + store, one CTA each
 template <typename T> cudaError_t launch_front_small(const StepArgs& a, cudaStream_t st);
 // SYRK of large FP32 fronts on the tensor cores (tcgen05, 3xTF32)

@@ -131,7 +131,7 @@ constexpr int kFuseMaxHeight = 6;
 constexpr int kTcTile = 128, kTcChunk = 8;
 constexpr int64_t kTcBlockBytes = (int64_t)kTcTile * kTcChunk * 4;
 constexpr int kSmallMax64 = 160;   // 160^2 * 8 B = 200 KiB
-constexpr int kSmallMax32 = 224;   // 224^2 * 4 B = 196 KiB
+constexpr int kSmallMax32 = 128;   // 128 * 132 * 4 B = 66 KiB (larger FP32 fronts: tensor-core path)
 
 // Build the host plan; returns an empty string on success, else an error text.
 std::string build_plan(const hdd_plan_desc& d, Plan& p);
