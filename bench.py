@@ -127,6 +127,19 @@ def cpu_baseline(cfg, prob, n_samples, processes):
     return n_samples / dt, dt
 
 
+def aggregate(total_ms: float, batch: int, steps: int, dist=None, device="cpu"):
+    """Replica timing: the slowest rank's time and the whole-job rate (all ranks'
+    samples / that time).  The samples of different ranks are independent, so the
+    only collective is this reduction of the elapsed time."""
+    world = dist.get_world_size() if dist is not None else 1
+    if dist is not None:
+        import torch
+        t = torch.tensor([float(total_ms)], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    return total_ms, world * batch * steps / (total_ms / 1e3)
+
+
 def host_cores():
     try:
         return len(os.sched_getaffinity(0))
@@ -236,18 +249,13 @@ def run_hdd(args, cfg):
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
-    total_ms = t_start.elapsed_time(t_end)
-    if dist:
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms, value = aggregate(t_start.elapsed_time(t_end), B, args.steps, dist, dev)
     stage_ms = {s: statistics.mean(e[i].elapsed_time(e[i + 1]) for e in evs) for i, s in enumerate(stages)}
     step_ms = sorted(e[0].elapsed_time(e[4]) for e in evs)
 
     def pct(q):
         return step_ms[min(len(step_ms) - 1, int(round(q * (len(step_ms) - 1))))]
 
-    value = world * B * args.steps / (total_ms / 1e3)
 
     # end to end through the C ABI with host buffers (pinned), copies inside
     Zh = torch.from_numpy(prob.Z).pin_memory()
