@@ -286,24 +286,69 @@ def run_hdd(args, cfg):
         kernels[name] = {"ms_per_step": ms, "launches_per_step": st_["launches"] / args.steps,
                          "share": st_["ms"] / max(1e-9, sum(v["ms"] for v in kstats.values())),
                          "tflops": (st_["flops"] / args.steps) / (ms / 1e3) / 1e12 if st_["flops"] > 0 and ms > 0 else None}
-    # roofline of the dominant kernel (largest share of device time with arithmetic work)
-    compute = {k: v for k, v in kernels.items() if v["tflops"] is not None}
-    dom = max(compute, key=lambda k: compute[k]["ms_per_step"]) if compute else None
+    # Rooflines per kernel family and stage: t_roof = max(flops / compute peak, algorithmic
+    # bytes / HBM bandwidth) and frac = t_roof / measured time.  Algorithmic bytes come from the
+    # plan (each input read once, each output written once); flops from the profiler.
+    hbm = MEASURED.get("hbm_gbs", 6756.5)
+    tf32_peak = MEASURED.get("bf16_tflops", 1899.9) * 1.1 / 2.25
     if precision == hdd.HDD_FP64:
-        peak, peak_src = FP64_PEAK_TFLOPS, "derived: 2 FP64 FMA/clk/SM x 152 SMs x 2070 MHz (1.25 TFLOP/s nominal)"
+        simt_peak, simt_src = FP64_PEAK_TFLOPS, "derived: 2 FP64 FMA/clk/SM x 152 SMs x 2070 MHz"
     else:
-        peak, peak_src = FP32_PEAK_TFLOPS, "derived: 128 FP32 FMA/clk/SM x 152 SMs x 2070 MHz"
+        simt_peak, simt_src = FP32_PEAK_TFLOPS, "derived: 128 FP32 FMA/clk/SM x 152 SMs x 2070 MHz"
+    K = args.ir_iters if precision != hdd.HDD_FP64 else 0
+    n_desc_all, n_desc_vis, n_fwd, n_res = (K, 1, K, K) if K > 0 else (0, 1, 0, 0)
+    stage_bytes = {   # per step
+        "kappa": info["bytes_assemble"] * B + info["bytes_kl_basis"],
+        "front_warp": info["bytes_upsweep_tiny"] * B,
+        "front_small": info["bytes_upsweep_small"] * B,
+        "large_fronts": info["bytes_upsweep_large"] * B,
+        "subtree": info["bytes_upsweep_fused"] * B,
+        "forward": n_fwd * info["bytes_forward"] * B,
+        "descent": (n_desc_all * info["bytes_descent_all"] + n_desc_vis * info["bytes_descent_visited"]) * B,
+        "residual": n_res * info["bytes_residual"] * B,
+    }
+    groups = {"large_fronts": ("front_fill", "potrf", "trsm", "syrk_simt", "syrk_tc", "syrk_rhs")}
+
+    def fam_roof(name, members):
+        ms = sum(kernels[m]["ms_per_step"] for m in members if m in kernels)
+        if ms <= 0:
+            return None
+        t_alu = 0.0
+        for m in members:
+            fl = kstats.get(m, {}).get("flops", 0.0) / args.steps
+            pk = tf32_peak / 3.0 if m == "syrk_tc" else simt_peak   # 3xTF32: 3 tensor products per FMA
+            t_alu += fl / (pk * 1e12) * 1e3
+        by = stage_bytes.get(name, 0.0)
+        t_hbm = by / (hbm * 1e9) * 1e3
+        bound = "hbm" if t_hbm >= t_alu else "alu"
+        return {"ms_per_step": ms, "bytes_per_step": by, "gbs": by / (ms / 1e3) / 1e9,
+                "t_roof_ms": max(t_hbm, t_alu), "bound": bound, "frac": max(t_hbm, t_alu) / ms}
+
+    stages_roof = {}
+    for name in ("kappa", "front_warp", "front_small", "large_fronts", "subtree", "forward", "descent", "residual"):
+        r = fam_roof(name, groups.get(name, (name,)))
+        if r:
+            stages_roof[name] = r
+    # the dominant family (largest device time) carries the headline roofline
     roof = None
-    if dom:
-        ach = compute[dom]["tflops"]
-        roof = {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
-                "traffic": None, "kernel": dom, "peak_source": peak_src,
-                "flops_per_launch_note": "Cholesky m^3/3 + TRSM (b+1)m^2/2 + SYRK (b+1)(b+2)m/2 multiply-adds x2 per front"}
+    if stages_roof:
+        dom = max((k for k in stages_roof if k in kernels), key=lambda k: stages_roof[k]["ms_per_step"])
+        r = stages_roof[dom]
+        if r["bound"] == "hbm":
+            roof = {"bound": "hbm", "achieved": r["gbs"], "peak": hbm, "unit": "GB/s", "frac": r["gbs"] / hbm,
+                    "traffic": None, "kernel": dom,
+                    "peak_source": "of measured: MEASURED_PEAKS hbm_gbs (copy bandwidth)",
+                    "algorithmic_bytes_per_step": r["bytes_per_step"],
+                    "bytes_note": "per front and sample: sons' lower Schur triangles (leaves: kappa) read once; "
+                                  "factor columns, y_g and the lower Schur triangle written once"}
+        else:
+            ach = kernels[dom]["tflops"]
+            roof = {"bound": "alu", "achieved": ach, "peak": simt_peak, "unit": "TFLOP/s", "frac": ach / simt_peak,
+                    "traffic": None, "kernel": dom, "peak_source": simt_src}
     tc = kernels.get("syrk_tc")
     if tc and tc["tflops"]:
         # 3xTF32: three tensor-core products per FP32 multiply-add; TF32 peak = measured BF16
         # burst x the nominal TF32/BF16 ratio (1.1 / 2.25)
-        tf32_peak = MEASURED.get("bf16_tflops", 1899.9) * 1.1 / 2.25
         ach_tc = 3.0 * tc["tflops"]
         kernels["syrk_tc"]["roofline"] = {"bound": "tensor", "achieved": ach_tc, "peak": tf32_peak,
                                           "unit": "TFLOP/s (TF32 tensor ops, 3 per FP32 FMA)",
@@ -368,6 +413,7 @@ def run_hdd(args, cfg):
         "fp64_path": fp64,
         "roofline": roof,
         "upsweep": upsweep_roof,
+        "stages": stages_roof,
         "kernels": kernels,
         "e2e": {"value": e2e_value, "unit": "evals/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": info["launches_evaluate"] * args.steps,

@@ -97,6 +97,23 @@ typedef struct {
   double schur_bytes;         /* per sample, peak bytes of live Schur complements */
   int32_t launches_upsweep;   /* kernel launches of one hdd_upsweep */
   int32_t launches_evaluate;  /* kernel launches of assemble + upsweep + point solve + loglik */
+  /* Algorithmic bytes per sample, each input read once and each output written
+   * once: the roofline denominators of the stages.  Upsweep fronts read their
+   * sons' lower Schur triangles (leaves: their triangles' kappa) and write the
+   * factor columns, y_g and their own lower Schur triangle; they are split by
+   * the kernel class that runs them: fronts of up to 32 rows (one warp each),
+   * up to 128 rows in FP32 / 160 in FP64 (one CTA each in shared memory),
+   * larger ones (global-memory path), fused subtrees. */
+  double bytes_upsweep_tiny;
+  double bytes_upsweep_small;
+  double bytes_upsweep_large;
+  double bytes_upsweep_fused;
+  double bytes_forward;          /* one right-hand-side sweep over every node */
+  double bytes_descent_all;      /* one descent over every node */
+  double bytes_descent_visited;  /* one pruned descent (Sec. 5.3) */
+  double bytes_residual;         /* one FP64 residual r = b - A u */
+  double bytes_assemble;         /* kappa written (FP64, plus the FP32 copy of mixed plans) and Z read */
+  double bytes_kl_basis;         /* the KL basis, read once per hdd_assemble call */
 } hdd_plan_info_t;
 
 typedef struct {

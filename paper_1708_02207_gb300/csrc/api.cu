@@ -2,6 +2,7 @@
 // schedule of the HDD likelihood path.  No exceptions cross this boundary.
 #include <cuda_runtime.h>
 
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 #include <new>
@@ -18,6 +19,7 @@ cudaError_t configure_refine_kernels();
 cudaError_t configure_warp_kernels();
 cudaError_t configure_tc_kernels();
 cudaError_t configure_fused_kernels();
+cudaError_t configure_group_kernels();
 }  // namespace hdd
 
 namespace {
@@ -65,6 +67,7 @@ cudaError_t configure_device(int dev) {
   if (e == cudaSuccess) e = hdd::configure_warp_kernels();
   if (e == cudaSuccess) e = hdd::configure_tc_kernels();
   if (e == cudaSuccess) e = hdd::configure_fused_kernels();
+  if (e == cudaSuccess) e = hdd::configure_group_kernels();
   if (e == cudaSuccess) g_configured[dev] = true;
   return e;
 }
@@ -146,6 +149,16 @@ struct ProfScope {
   }
 };
 
+// Previous front kernels for fronts of up to kSmallMax rows (register rows per
+// warp / one CTA per front), selected with HDD_LEGACY_FRONTS=1 for comparison.
+bool legacy_fronts() {
+  static const bool on = [] {
+    const char* v = getenv("HDD_LEGACY_FRONTS");
+    return v && v[0] == '1';
+  }();
+  return on;
+}
+
 // One pass of "Leaves to Root" over all heights with the given right-hand side.
 cudaError_t run_upsweep(const hdd::Plan& p, int batch, void* ws, const hdd::Rhs& rhs, cudaStream_t st,
                         hdd::Profiler* prof) {
@@ -194,17 +207,22 @@ cudaError_t run_upsweep(const hdd::Plan& p, int batch, void* ws, const hdd::Rhs&
       a.max_nf = li.max_nf;
       a.max_m = li.max_m;
       a.max_b = li.max_b;
+      a.max_rect = li.max_rect;
       a.fl_chol = li.fl_chol * batch;
       a.fl_trsm = li.fl_trsm * batch;
       a.fl_syrk = li.fl_syrk * batch;
       a.fl_rhs = li.fl_rhs * batch;
       cudaError_t e;
       switch (kind) {
-        case 0: e = hdd::launch_front_warp<double>(a, st); break;
-        case 1: e = hdd::launch_front_small<double>(a, st); break;
+        case 0: e = legacy_fronts() ? hdd::launch_front_warp<double>(a, st)
+                                    : hdd::launch_front_group<double>(a, hdd::kProfFrontWarp, st); break;
+        case 1: e = legacy_fronts() ? hdd::launch_front_small<double>(a, st)
+                                    : hdd::launch_front_group<double>(a, hdd::kProfFrontSmall, st); break;
         case 2: e = hdd::launch_front_large<double>(a, st); break;
-        case 3: e = hdd::launch_front_warp<float>(a, st); break;
-        case 4: e = hdd::launch_front_small<float>(a, st); break;
+        case 3: e = legacy_fronts() ? hdd::launch_front_warp<float>(a, st)
+                                    : hdd::launch_front_group<float>(a, hdd::kProfFrontWarp, st); break;
+        case 4: e = legacy_fronts() ? hdd::launch_front_small<float>(a, st)
+                                    : hdd::launch_front_group<float>(a, hdd::kProfFrontSmall, st); break;
         default: e = hdd::launch_front_large<float>(a, st); break;
       }
       if (e != cudaSuccess) return e;
@@ -611,6 +629,16 @@ hdd_status hdd_plan_info(hdd_plan_t plan, hdd_plan_info_t* info) {
   info->flops_point_solve = p.flops_down;
   info->factor_bytes = (double)p.f64_stride * 8 + (double)p.f32_stride * 4;
   info->schur_bytes = (double)p.s64_stride * 8 + (double)p.s32_stride * 4;
+  info->bytes_upsweep_tiny = p.by_tiny;
+  info->bytes_upsweep_small = p.by_small;
+  info->bytes_upsweep_large = p.by_large;
+  info->bytes_upsweep_fused = p.by_fused;
+  info->bytes_forward = p.by_fwd;
+  info->bytes_descent_all = p.by_desc_all;
+  info->bytes_descent_visited = p.by_desc_vis;
+  info->bytes_residual = p.by_residual;
+  info->bytes_assemble = p.by_assemble;
+  info->bytes_kl_basis = p.by_kl_basis;
   int up = 0, down = 0;
   for (int h = 0; h <= p.height; ++h)
     for (int kind = 0; kind < 6; ++kind) {

@@ -58,6 +58,7 @@ struct StepArgs {
   Arenas arenas;
   int32_t* status;
   int max_nf, max_m, max_b;
+  int max_rect;             // leaves: vertices of the largest closed rectangle
   Profiler* prof;            // nullptr unless profiling
   double fl_chol, fl_trsm, fl_syrk, fl_rhs;   // algorithmic flops of this launch (whole batch)
 };
@@ -97,6 +98,8 @@ cudaError_t launch_forward_tiny(const NodeDev* nodes, const int32_t* maps, const
 template <typename T>
 cudaError_t launch_descent_tiny(const NodeDev* nodes, const int32_t* maps, const int32_t* list, int nlist, int batch,
                                 const Arenas& A, double* u, int64_t u_stride, cudaStream_t st);
+// fronts of up to kSmallMax rows: W warps per front, several samples of a node per CTA
+template <typename T> cudaError_t launch_front_group(const StepArgs& a, int family, cudaStream_t st);
 // fronts that fit in shared memory: build + partial Cholesky + store, one CTA each
 template <typename T> cudaError_t launch_front_small(const StepArgs& a, cudaStream_t st);
 // SYRK of large FP32 fronts on the tensor cores (tcgen05, 3xTF32)

@@ -388,6 +388,7 @@ std::string build_plan(const hdd_plan_desc& d, Plan& p) {
       li.max_nf = std::max(li.max_nf, nd.nf);
       li.max_m = std::max(li.max_m, nd.m);
       li.max_b = std::max(li.max_b, nd.b);
+      if (nd.leaf()) li.max_rect = std::max(li.max_rect, (nd.x1 - nd.x0 + 1) * (nd.y1 - nd.y0 + 1));
       const double m = nd.m, b = nd.b;
       li.fl_chol += 2.0 * m * m * m / 3.0;
       li.fl_trsm += 2.0 * (b + 1.0) * m * m / 2.0;
@@ -442,6 +443,37 @@ std::string build_plan(const hdd_plan_desc& d, Plan& p) {
     p.flops_up += 2.0 * (m * m * m / 3.0 + nb * m * m / 2.0 + nb * (nb + 1.0) / 2.0 * m);
     if (nd.visited) p.flops_down += 2.0 * (nd.b * m + m * m / 2.0);
   }
+  // algorithmic bytes per sample (see plan.h)
+  p.by_tiny = p.by_small = p.by_large = p.by_fused = p.by_fwd = p.by_desc_all = p.by_desc_vis = 0.0;
+  auto esz = [](const Node& nd) { return nd.fp64 ? 8.0 : 4.0; };
+  auto tri = [](double n) { return n * (n + 1.0) / 2.0; };
+  for (const Node& nd : p.nodes) {
+    const double E = esz(nd), m = nd.m, b = nd.b, nf = nd.nf;
+    double in = 0.0, sons_cond = 0.0;
+    if (nd.leaf()) {
+      in = 2.0 * (nd.x1 - nd.x0) * (nd.y1 - nd.y0) * E;   // kappa of the leaf's triangles
+    } else {
+      for (int c = 0; c < 2; ++c) {
+        const Node& ch = p.nodes[nd.child[c]];
+        in += tri(ch.b + 1.0) * esz(ch);
+        sons_cond += ch.b * esz(ch);
+      }
+    }
+    const double front = in + (nf * m + m + tri(b + 1.0)) * E;
+    if (nd.fused) p.by_fused += front;
+    else if (nd.nf <= kTinyMax) p.by_tiny += front;
+    else if (nd.nf <= (nd.fp64 ? kSmallMax64 : kSmallMax32)) p.by_small += front;
+    else p.by_large += front;
+    const double fwd = (nf - 1.0) * m * E + m * 8.0 + sons_cond + (m + b) * E;
+    const double down = (nf - 1.0) * m * E + m * E + b * 8.0 + m * 8.0;
+    p.by_fwd += fwd;
+    p.by_desc_all += down;
+    if (nd.visited) p.by_desc_vis += down;
+  }
+  const double NN = (double)p.N * p.N;
+  p.by_residual = 2.0 * p.n_t * 8.0 + 2.0 * NN * 8.0;   // kappa and u in, r out
+  p.by_assemble = p.n_z * 8.0 + p.n_t * (p.precision == HDD_MIXED_FP32 ? 12.0 : 8.0);
+  p.by_kl_basis = (double)p.n_t * p.n_z * 8.0;
   return "";
 }
 

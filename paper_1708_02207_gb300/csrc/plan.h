@@ -57,6 +57,7 @@ struct ListInfo {
   int64_t off = 0;   // into the concatenated list table
   int n = 0;
   int max_nf = 0, max_m = 0, max_b = 0;
+  int max_rect = 0;   // leaves: vertices of the largest closed rectangle
   double fl_chol = 0, fl_trsm = 0, fl_syrk = 0, fl_rhs = 0;   // algorithmic flops per sample
 };
 
@@ -90,6 +91,14 @@ struct Plan {
   int64_t inv_stride = 0;                   // bytes: inverted diagonal blocks of one height step
   int64_t s64_stride = 0, s32_stride = 0;   // Schur arenas (lifetime-packed)
   double flops_up = 0.0, flops_down = 0.0;
+  // algorithmic bytes per sample: each input read once and each output written
+  // once (fronts: sons' lower Schur triangles or the leaf's kappa in; F, y_g and
+  // the lower Schur triangle out)
+  double by_tiny = 0.0, by_small = 0.0, by_large = 0.0, by_fused = 0.0;   // upsweep fronts by kernel class
+  double by_fwd = 0.0;                                     // one right-hand-side sweep
+  double by_desc_all = 0.0, by_desc_vis = 0.0;             // full and pruned descents
+  double by_residual = 0.0, by_assemble = 0.0;             // FP64 residual; kappa written
+  double by_kl_basis = 0.0;                                // Phi, read once per batch
 
   // fused bottom subtrees, per precision (0: FP64, 1: FP32)
   struct Fusion {

@@ -45,6 +45,11 @@ class PlanInfo(C.Structure):
         ("flops_upsweep", C.c_double), ("flops_point_solve", C.c_double),
         ("factor_bytes", C.c_double), ("schur_bytes", C.c_double),
         ("launches_upsweep", C.c_int32), ("launches_evaluate", C.c_int32),
+        ("bytes_upsweep_tiny", C.c_double), ("bytes_upsweep_small", C.c_double),
+        ("bytes_upsweep_large", C.c_double),
+        ("bytes_upsweep_fused", C.c_double), ("bytes_forward", C.c_double),
+        ("bytes_descent_all", C.c_double), ("bytes_descent_visited", C.c_double),
+        ("bytes_residual", C.c_double), ("bytes_assemble", C.c_double), ("bytes_kl_basis", C.c_double),
     ]
 
 

@@ -97,3 +97,41 @@ def test_flop_count_matches_front_sizes(hdd):
         m, nb = len(nd.gamma), len(nd.bnd) + 1
         ref += 2 * (m ** 3 / 3 + nb * m * m / 2 + nb * (nb + 1) / 2 * m)
     assert np.isclose(plan.info()["flops_upsweep"], ref)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("N,leaf", [(33, 8), (129, 4), (65, 2)])
+def test_algorithmic_bytes_match_front_sizes(hdd, precision, N, leaf):
+    """The per-stage byte counts that the roofline reports follow from the front sizes of the
+    oracle's tree: fronts read their sons' lower Schur triangles (leaves: their triangles'
+    kappa) and write F (nf x m), y_g and their lower Schur triangle; the sweeps read F once."""
+    prec = hdd.HDD_FP64 if precision == "fp64" else hdd.HDD_MIXED_FP32
+    obs = w.obs_vertices(N, 3)
+    plan = hdd.Plan(N, leaf, None, obs, 0.01, precision=prec, device=-1)
+    info = plan.info()
+    E = 8.0 if precision == "fp64" else 4.0
+    small_max = 160 if precision == "fp64" else 128
+    nodes = hd.build_tree(N, leaf)
+    tri = lambda n: n * (n + 1) / 2
+    cls = {"tiny": 0.0, "small": 0.0, "large": 0.0}
+    fwd = desc = 0.0
+    for nd in nodes:
+        m, b = len(nd.gamma), len(nd.bnd)
+        nf = m + b + 1
+        if nd.children:
+            sons = [nodes[c] for c in nd.children]
+            inp = sum(tri(len(c.bnd) + 1) * E for c in sons)
+            cond = sum(len(c.bnd) * E for c in sons)
+        else:
+            inp, cond = 2 * (nd.x1 - nd.x0) * (nd.y1 - nd.y0) * E, 0.0
+        front = inp + (nf * m + m + tri(b + 1)) * E
+        cls["tiny" if nf <= 32 else ("small" if nf <= small_max else "large")] += front
+        fwd += (nf - 1) * m * E + m * 8 + cond + (m + b) * E
+        desc += (nf - 1) * m * E + m * E + b * 8 + m * 8
+    assert np.isclose(info["bytes_upsweep_tiny"], cls["tiny"])
+    assert np.isclose(info["bytes_upsweep_small"], cls["small"])
+    assert np.isclose(info["bytes_upsweep_large"], cls["large"])
+    assert info["bytes_upsweep_fused"] == 0.0
+    assert np.isclose(info["bytes_forward"], fwd)
+    assert np.isclose(info["bytes_descent_all"], desc)
+    assert 0 < info["bytes_descent_visited"] < info["bytes_descent_all"]
