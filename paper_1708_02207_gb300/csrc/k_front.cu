@@ -245,25 +245,80 @@ cudaError_t launch_front_small(const StepArgs& a, cudaStream_t st) {
 }
 
 // ---------------------------------------------------------------------------
-// Large fronts (global memory).  Fill: one warp per front column.
+// Large fronts (global memory).  Fill: one warp per front column, columns
+// 0..ncols-1 (all nf columns, or only the m gamma columns when the Schur
+// update gathers the sons' entries itself).  Father entries are gathered from
+// the sons' lower Schur triangles through the position maps (son row of each
+// front row, -1 if absent), with the column's positions hoisted and four rows
+// per lane loaded before any store.
+template <typename T, typename TS>
+__device__ __forceinline__ void fill_father_column(T* F, T* S, int c, int lane, const NodeDev& nd, const int32_t* map,
+                                                   const TS* S0, int ld0, const TS* S1, int ld1, T load_c) {
+  const int nf = nd.nf, m = nd.m, nb = nd.b + 1;
+  const int32_t* pos0 = map + (nf - 1);
+  const int32_t* pos1 = pos0 + nf;
+  const int q0 = pos0[c], q1 = pos1[c];
+  if (c < m)
+    for (int r = lane; r < c; r += 32) F[(int64_t)c * nf + r] = (T)0;
+  for (int r0 = c + lane; r0 < nf; r0 += 128) {
+    T v[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int r = r0 + 32 * q;
+      v[q] = (T)0;
+      if (r < nf) {
+        const int a0 = pos0[r], a1 = pos1[r];
+        if (a0 >= 0 && q0 >= 0) v[q] += (T)S0[min(a0, q0) * ld0 + max(a0, q0)];
+        if (a1 >= 0 && q1 >= 0) v[q] += (T)S1[min(a1, q1) * ld1 + max(a1, q1)];
+        if (r == nf - 1) v[q] += load_c;
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int r = r0 + 32 * q;
+      if (r >= nf) break;
+      if (c < m) F[(int64_t)c * nf + r] = v[q];
+      else if (r >= m) S[(int64_t)(c - m) * nb + (r - m)] = v[q];
+    }
+  }
+}
+
 template <typename T>
-__global__ void k_front_fill(StepArgs a) {
+__global__ void __launch_bounds__(256) k_front_fill(StepArgs a, int gamma_only) {
   const int node = a.list[blockIdx.y];
   const int s = blockIdx.z;
   const NodeDev nd = a.nodes[node];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int c = blockIdx.x * (blockDim.x >> 5) + warp;
   const int nf = nd.nf, m = nd.m, nb = nd.b + 1;
-  if (c >= nf) return;
+  if (c >= ((gamma_only && !nd.leaf) ? m : nf)) return;   // leaves fill their whole front
   const int32_t* map = a.maps + nd.map_off;
-  const T* kap = kappa_of<T>(a.kappa, a.kappa32) + (int64_t)s * a.kap_stride;
   T* F = node_F<T>(a.arenas, nd, s);
   T* S = node_S<T>(a.arenas, nd, s);
-  for (int r = lane; r < nf; r += 32) {
-    const T v = (r >= c) ? front_entry<T>(r, c, s, node, nd, a.nodes, map, kap, a.N, a.rhs, a.arenas) : (T)0;
-    if (c < m) F[(int64_t)c * nf + r] = v;
-    else if (r >= m) S[(int64_t)(c - m) * nb + (r - m)] = v;
+  if (nd.leaf) {
+    const T* kap = kappa_of<T>(a.kappa, a.kappa32) + (int64_t)s * a.kap_stride;
+    for (int r = lane; r < nf; r += 32) {
+      const T v = (r >= c) ? leaf_entry<T>(r, c, s, nd, map, kap, a.N, a.rhs) : (T)0;
+      if (c < m) F[(int64_t)c * nf + r] = v;
+      else if (r >= m) S[(int64_t)(c - m) * nb + (r - m)] = v;
+    }
+    return;
   }
+  const NodeDev c0 = a.nodes[nd.child0], c1 = a.nodes[nd.child1];
+  const T load_c = (c < m) ? (T)a.rhs(s, map[c]) : (T)0;
+  const Arenas& A = a.arenas;
+  if (!c0.fp64 && !c1.fp64)
+    fill_father_column<T, float>(F, S, c, lane, nd, map, A.s32 + (int64_t)s * A.s32_stride + c0.s_off, c0.b + 1,
+                                 A.s32 + (int64_t)s * A.s32_stride + c1.s_off, c1.b + 1, load_c);
+  else if (c0.fp64 && c1.fp64)
+    fill_father_column<T, double>(F, S, c, lane, nd, map, A.s64 + (int64_t)s * A.s64_stride + c0.s_off, c0.b + 1,
+                                  A.s64 + (int64_t)s * A.s64_stride + c1.s_off, c1.b + 1, load_c);
+  else
+    for (int r = lane; r < nf; r += 32) {
+      const T v = (r >= c) ? father_entry<T>(r, c, s, nd, map, c0, c1, A, a.rhs) : (T)0;
+      if (c < m) F[(int64_t)c * nf + r] = v;
+      else if (r >= m) S[(int64_t)(c - m) * nb + (r - m)] = v;
+    }
 }
 
 // Rows of a panel (POTRF) or of a row block (TRSM) kept in shared memory; larger
@@ -616,8 +671,10 @@ __global__ void k_syrk(StepArgs a) {
 }
 
 // The bordered right-hand-side row of S for fronts whose SYRK runs on the tensor
-// cores: S[b, j] -= sum_k y_k X[j, k] for j = 0..b (y = the last row of X), one
-// CTA per (node, sample), threads over j (coalesced down the columns of F).
+// cores: S[b, j] = (sons' entries at (rhs, m + j)) - sum_k y_k X[j, k] for
+// j = 0..b (y = the last row of X), one CTA per (node, sample), threads over j
+// (coalesced down the columns of F).  The sons' entries are gathered here: the
+// fill of these fronts writes only the gamma columns.
 __global__ void k_syrk_rhs(StepArgs a) {
   const int node = a.list[blockIdx.x];
   const int s = blockIdx.y;
@@ -626,6 +683,8 @@ __global__ void k_syrk_rhs(StepArgs a) {
   if (m == 0) return;
   const float* X = a.arenas.f32 + (int64_t)s * a.arenas.f32_stride + nd.f_off + m;
   float* S = a.arenas.s32 + (int64_t)s * a.arenas.s32_stride + nd.s_off;
+  const int32_t* map = a.maps + nd.map_off;
+  const NodeDev c0 = nd.leaf ? nd : a.nodes[nd.child0], c1 = nd.leaf ? nd : a.nodes[nd.child1];
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float* y = reinterpret_cast<float*>(smem_raw);
   for (int k = threadIdx.x; k < m; k += blockDim.x) y[k] = X[(int64_t)k * nf + b];
@@ -633,7 +692,9 @@ __global__ void k_syrk_rhs(StepArgs a) {
   for (int j = threadIdx.x; j <= b; j += blockDim.x) {
     float acc = 0.0f;
     for (int k = 0; k < m; ++k) acc += y[k] * X[(int64_t)k * nf + j];
-    S[(int64_t)j * nb + b] -= acc;
+    const float g = nd.leaf ? S[(int64_t)j * nb + b]
+                            : father_entry<float>(nf - 1, m + j, s, nd, map, c0, c1, a.arenas, a.rhs);
+    S[(int64_t)j * nb + b] = g - acc;
   }
 }
 
@@ -641,9 +702,12 @@ template <typename T>
 cudaError_t launch_front_large(const StepArgs& a, cudaStream_t st) {
   if (a.nlist == 0) return cudaSuccess;
   {
+    // FP32 fronts: the tensor-core Schur update gathers the sons' boundary block
+    // itself, so only the gamma columns are filled
+    const bool gamma_only = std::is_same<T, float>::value;
     dim3 grid((a.max_nf + 7) / 8, a.nlist, a.batch);
     if (a.prof) a.prof->begin(kProfFill, 0.0, st);
-    k_front_fill<T><<<grid, 256, 0, st>>>(a);
+    k_front_fill<T><<<grid, 256, 0, st>>>(a, gamma_only ? 1 : 0);
     if (a.prof) a.prof->end(st);
   }
   const size_t rows_smem = (size_t)min(a.max_m, SmemCap<T>::rows);

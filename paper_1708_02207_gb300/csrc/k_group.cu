@@ -127,9 +127,12 @@ __global__ void __launch_bounds__(256) k_front_group(StepArgs a, int W, int ld, 
     const int cells = tw * (nd.y1 - nd.y0 + 1);
     for (int i = threadIdx.x; i < cells; i += blockDim.x) sh[i] = -1;
     __syncthreads();
+    int* loc = sh + cells;   // per front row: local (column, row) of its vertex, 16 bits each
     for (int r = threadIdx.x; r < nf - 1; r += blockDim.x) {
       const int v = map[r];
-      sh[(v / N - nd.y0) * tw + (v % N - nd.x0)] = r;
+      const int li = v % N - nd.x0, lj = v / N - nd.y0;
+      sh[lj * tw + li] = r;
+      loc[r] = (lj << 16) | li;
     }
   } else {
     c0 = a.nodes[nd.child0];
@@ -151,18 +154,19 @@ __global__ void __launch_bounds__(256) k_front_group(StepArgs a, int W, int ld, 
   g.sync();
   if (nd.leaf) {
     const T* kap = kappa_of<T>(a.kappa, a.kappa32) + (int64_t)s * a.kap_stride;
+    const int* loc = sh + tw * (nd.y1 - nd.y0 + 1);
     for (int r = g.t; r < nf - 1; r += g.size) {
-      const int v = map[r], vi = v % N, vj = v / N;
+      const int li = loc[r] & 0xffff, lj = loc[r] >> 16;
+      const int vi = nd.x0 + li, vj = nd.y0 + lj;
       const T wl = w_horizontal(kap, N, nd, vi - 1, vj), wr = w_horizontal(kap, N, nd, vi, vj);
       const T wd = w_vertical(kap, N, nd, vi, vj - 1), wu = w_vertical(kap, N, nd, vi, vj);
       K[r * ld + r] = wl + wr + wd + wu;
       // couplings to neighbours of a smaller front row: entry (r, c), r > c
-      const int li = vi - nd.x0, lj = vj - nd.y0;
       if (li > 0) { const int c = sh[lj * tw + li - 1]; if (c >= 0 && c < r) K[c * ld + r] = -wl; }
       if (vi < nd.x1) { const int c = sh[lj * tw + li + 1]; if (c >= 0 && c < r) K[c * ld + r] = -wr; }
       if (lj > 0) { const int c = sh[(lj - 1) * tw + li]; if (c >= 0 && c < r) K[c * ld + r] = -wd; }
       if (vj < nd.y1) { const int c = sh[(lj + 1) * tw + li]; if (c >= 0 && c < r) K[c * ld + r] = -wu; }
-      if (r < m) K[r * ld + nf - 1] = (T)a.rhs(s, v);   // load of an interior vertex (Eq. coefc)
+      if (r < m) K[r * ld + nf - 1] = (T)a.rhs(s, vj * N + vi);   // load of an interior vertex (Eq. coefc)
     }
   } else {
     add_son<T>(K, ld, c0, sh, a.arenas, s, g);
@@ -179,6 +183,7 @@ __global__ void __launch_bounds__(256) k_front_group(StepArgs a, int W, int ld, 
     for (int r = k + g.t; r < nf; r += g.size) {
       T acc = K[k * ld + r];
       if (r == nf - 1 && !nd.leaf) acc += (T)a.rhs(s, map[k]);   // father: load of its gamma vertex
+#pragma unroll 4
       for (int l = 0; l < k; ++l) acc -= K[l * ld + r] * rowk[l * ld];
       K[k * ld + r] = acc;
     }
@@ -219,6 +224,7 @@ __global__ void __launch_bounds__(256) k_front_group(StepArgs a, int W, int ld, 
 #pragma unroll
       for (int q = 0; q < 4; ++q) acc[q][w] = v[q];
     }
+#pragma unroll 2
     for (int l = 0; l < m; ++l) {
       T x[4], y[4];
       ld4(K + l * ld + i0, x);
@@ -264,7 +270,7 @@ cudaError_t launch_front_group(const StepArgs& a, int family, cudaStream_t st) {
   const int G = warps / W;
   const int ld = group_ld(a.max_nf);
   const int fr_elems = (((a.max_nf + 3) & ~3) * ld + a.max_m + 3) & ~3;
-  const int ints = max(a.max_rect, 2 * a.max_nf + 2);
+  const int ints = max(a.max_rect + a.max_nf, 2 * a.max_nf + 2);
   const size_t smem = (size_t)G * fr_elems * sizeof(T) + (size_t)ints * sizeof(int);
   if (smem > 227 * 1024) return cudaErrorInvalidConfiguration;
   dim3 grid(a.nlist, (a.batch + G - 1) / G);
@@ -281,6 +287,14 @@ cudaError_t configure_group_kernels() {
   cudaError_t e;
   if ((e = cudaFuncSetAttribute(k_front_group<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
   if ((e = cudaFuncSetAttribute(k_front_group<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
+  // the whole unified L1 / shared-memory array as shared memory: the residency of
+  // these CTAs is bounded by their fronts, not by L1
+  if ((e = cudaFuncSetAttribute(k_front_group<double>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                cudaSharedmemCarveoutMaxShared)))
+    return e;
+  if ((e = cudaFuncSetAttribute(k_front_group<float>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                cudaSharedmemCarveoutMaxShared)))
+    return e;
   return cudaSuccess;
 }
 

@@ -84,6 +84,7 @@ __global__ void __launch_bounds__(128, 3) k_syrk_tc(StepArgs a) {
   __shared__ __align__(8) uint64_t full[kStages], empty[kStages];
   __shared__ uint32_t tmem_slot;
   __shared__ int timed_out;
+  __shared__ int cpos[2][kTile];   // sons' rows of this tile's columns (fathers)
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   if (warp == 0) {
@@ -98,6 +99,14 @@ __global__ void __launch_bounds__(128, 3) k_syrk_tc(StepArgs a) {
     }
     asm volatile("fence.mbarrier_init.release.cluster;");
     timed_out = 0;
+  }
+  const bool gather = !nd.leaf;
+  const int32_t* pos0 = a.maps + nd.map_off + (nd.nf - 1);
+  const int32_t* pos1 = pos0 + nd.nf;
+  if (gather) {
+    const int j = TJ * kTile + tid;
+    cpos[0][tid] = j < nbt ? pos0[m + j] : -1;
+    cpos[1][tid] = j < nbt ? pos1[m + j] : -1;
   }
   asm volatile("tcgen05.fence::before_thread_sync;");
   __syncthreads();
@@ -175,6 +184,27 @@ __global__ void __launch_bounds__(128, 3) k_syrk_tc(StepArgs a) {
   } else {
     float* S = a.arenas.s32 + (int64_t)s * a.arenas.s32_stride + nd.s_off;
     const int i = TI * kTile + warp * 32 + lane;   // accumulator lane = tile row
+    // fathers: the boundary block of the front is the sum of the sons' Schur
+    // entries (Eq. block_equation4), gathered here (rows of one column are
+    // consecutive in the son as in the father: both order boundary vertices
+    // by id); leaves: their boundary block was filled into S
+    NodeDev ch0{}, ch1{};
+    const float *S0 = nullptr, *S1 = nullptr;
+    int p0 = -1, p1 = -1;
+    bool mixed_sons = false;
+    if (gather) {
+      ch0 = a.nodes[nd.child0];
+      ch1 = a.nodes[nd.child1];
+      mixed_sons = ch0.fp64 || ch1.fp64;
+      S0 = a.arenas.s32 + (int64_t)s * a.arenas.s32_stride + ch0.s_off;
+      S1 = a.arenas.s32 + (int64_t)s * a.arenas.s32_stride + ch1.s_off;
+      if (i < nbt) {
+        p0 = pos0[m + i];
+        p1 = pos1[m + i];
+      }
+    }
+    const int ld0 = ch0.b + 1, ld1 = ch1.b + 1;
+    const int32_t* map = a.maps + nd.map_off;
 #pragma unroll 1
     for (int c0 = 0; c0 < kTile; c0 += 32) {
       if (TI == TJ && c0 > warp * 32 + 31) break;   // strictly above the diagonal of this warp's rows
@@ -189,12 +219,33 @@ __global__ void __launch_bounds__(128, 3) k_syrk_tc(StepArgs a) {
             "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
           : "r"(taddr));
       asm volatile("tcgen05.wait::ld.sync.aligned;");
-      // all 32 loads of S first (independent, in flight together), then the stores
+      // all 32 loads first (independent, in flight together), then the stores
       float sv[32];
+      if (!gather) {
 #pragma unroll
-      for (int q = 0; q < 32; ++q) {
-        const int j = TJ * kTile + c0 + q;
-        sv[q] = (i < nbt && j < nbt && i >= j) ? S[(int64_t)j * nb + i] : 0.0f;
+        for (int q = 0; q < 32; ++q) {
+          const int j = TJ * kTile + c0 + q;
+          sv[q] = (i < nbt && j < nbt && i >= j) ? S[(int64_t)j * nb + i] : 0.0f;
+        }
+      } else if (!mixed_sons) {
+#pragma unroll
+        for (int q = 0; q < 32; ++q) {
+          const int j = TJ * kTile + c0 + q;
+          const int q0 = cpos[0][c0 + q], q1 = cpos[1][c0 + q];
+          const bool v = i < nbt && j < nbt && i >= j;
+          float x = 0.0f;
+          if (v && p0 >= 0 && q0 >= 0) x = S0[min(p0, q0) * ld0 + max(p0, q0)];
+          if (v && p1 >= 0 && q1 >= 0) x += S1[min(p1, q1) * ld1 + max(p1, q1)];
+          sv[q] = x;
+        }
+      } else {
+#pragma unroll
+        for (int q = 0; q < 32; ++q) {
+          const int j = TJ * kTile + c0 + q;
+          sv[q] = (i < nbt && j < nbt && i >= j)
+                      ? father_entry<float>(m + i, m + j, s, nd, map, ch0, ch1, a.arenas, a.rhs)
+                      : 0.0f;
+        }
       }
 #pragma unroll
       for (int q = 0; q < 32; ++q) {
