@@ -490,6 +490,74 @@ __device__ __forceinline__ void write_tc_tiles(const float* X, int64_t ldx, cons
 // the diagonal triangle is solved one thread per row, then the remaining columns
 // are updated in 64-column chunks of L staged in shared memory, with register
 // micro-tiles (4 rows x kTrsmCols columns per thread).
+// POTRF of gamma blocks of at most 32 columns: one warp per (node, sample),
+// lane r holding row r of K_gg in registers.  Right-looking Cholesky with the
+// pivot column broadcast by shuffles, then the inverse of L (lane c solves
+// L w = e_c by forward substitution, rows of L broadcast by shuffles), stored
+// as the single 32 x 32 block that the TRSM applies as a product.
+template <typename T>
+__global__ void __launch_bounds__(256) k_potrf_warp(StepArgs a) {
+  constexpr unsigned kAll = 0xffffffffu;
+  const int node = a.list[blockIdx.x];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int s = blockIdx.y * 8 + warp;
+  if (s >= a.batch) return;
+  const NodeDev nd = a.nodes[node];
+  const int nf = nd.nf, m = nd.m;
+  T* A = node_F<T>(a.arenas, nd, s);
+  T row[32];
+#pragma unroll
+  for (int c = 0; c < 32; ++c) row[c] = (c < m && lane < m && c <= lane) ? A[(int64_t)c * nf + lane] : (T)0;
+  bool bad = false;
+#pragma unroll
+  for (int k = 0; k < 32; ++k) {
+    if (k < m) {
+      T pk = __shfl_sync(kAll, row[k], k);
+      if (!(pk > (T)0) || !isfinite(pk)) {
+        bad = true;
+        pk = (T)1;
+      }
+      const T d = sqrt(pk), inv = (T)1 / d;
+      T lk = (lane == k) ? d : row[k] * inv;
+      if (lane < k) lk = (T)0;
+#pragma unroll
+      for (int j = k + 1; j < 32; ++j) {
+        const T lj = __shfl_sync(kAll, lk, j);
+        if (lane > k) row[j] -= lk * lj;
+      }
+      row[k] = lk;
+    }
+  }
+  if (bad && lane == 0) flag_status(a.status, s, -HDD_ENOTSPD, node);
+#pragma unroll
+  for (int c = 0; c < 32; ++c)
+    if (c < m && lane < m && c <= lane) A[(int64_t)c * nf + lane] = row[c];
+  // inverse: lane c solves L w = e_c (identity columns beyond m), rows of L read
+  // from shared memory (one row per step, the same address for all lanes)
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* Ls = reinterpret_cast<T*>(smem_raw) + warp * (32 * 33 + 32);
+  T* dinv = Ls + 32 * 33;
+#pragma unroll
+  for (int c = 0; c < 32; ++c) Ls[lane * 33 + c] = row[c];
+  T diag = (T)1;
+#pragma unroll
+  for (int c = 0; c < 32; ++c)
+    if (c == lane && c < m) diag = row[c];
+  dinv[lane] = (T)1 / diag;
+  __syncwarp();
+  T w[32];
+#pragma unroll
+  for (int r = 0; r < 32; ++r) {
+    T acc = (lane == r) ? (T)1 : (T)0;
+#pragma unroll
+    for (int l = 0; l < r; ++l) acc -= Ls[r * 33 + l] * w[l];
+    w[r] = acc * dinv[r];
+  }
+  T* G = reinterpret_cast<T*>(a.arenas.inv + (int64_t)s * a.arenas.inv_stride + nd.inv_off);
+#pragma unroll
+  for (int r = 0; r < 32; ++r) G[lane * 32 + r] = (lane < m) ? ((r < m) ? w[r] : (T)0) : ((r == lane) ? (T)1 : (T)0);
+}
+
 template <typename T> struct TrsmShape;
 template <> struct TrsmShape<float> { static constexpr int rows = 64, cap = 760; };
 template <> struct TrsmShape<double> { static constexpr int rows = 32, cap = 760; };
@@ -714,7 +782,10 @@ cudaError_t launch_front_large(const StepArgs& a, cudaStream_t st) {
   {
     const size_t smem = (rows_smem * kPanel + kPanel + 32 * 33) * sizeof(T);
     if (a.prof) a.prof->begin(kProfPotrf, a.fl_chol, st);
-    k_potrf<T><<<dim3(a.nlist, a.batch), 256, smem, st>>>(a);
+    if (a.max_m <= 32)
+      k_potrf_warp<T><<<dim3(a.nlist, (a.batch + 7) / 8), 256, 8 * (32 * 33 + 32) * sizeof(T), st>>>(a);
+    else
+      k_potrf<T><<<dim3(a.nlist, a.batch), 256, smem, st>>>(a);
     if (a.prof) a.prof->end(st);
   }
   {
@@ -760,6 +831,7 @@ cudaError_t configure_front_kernels() {
   if ((e = cudaFuncSetAttribute(k_front_small<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
   if ((e = cudaFuncSetAttribute(k_potrf<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
   if ((e = cudaFuncSetAttribute(k_potrf<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
+  if ((e = cudaFuncSetAttribute(k_potrf_warp<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
   if ((e = cudaFuncSetAttribute(k_trsm<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
   if ((e = cudaFuncSetAttribute(k_trsm<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
   return cudaSuccess;

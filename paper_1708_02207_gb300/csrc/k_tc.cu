@@ -113,6 +113,63 @@ __global__ void __launch_bounds__(128, 3) k_syrk_tc(StepArgs a) {
   asm volatile("tcgen05.fence::after_thread_sync;");
   const uint32_t tmem = tmem_slot;
 
+  // Epilogue operands.  The values subtracted from are loaded chunk by chunk
+  // (32 columns), the first chunk before the MMAs so that its loads overlap
+  // them, each later one while the previous chunk is stored.
+  float* S = a.arenas.s32 + (int64_t)s * a.arenas.s32_stride + nd.s_off;
+  const int i = TI * kTile + warp * 32 + lane;   // accumulator lane = tile row
+  // fathers: the boundary block of the front is the sum of the sons' Schur
+  // entries (Eq. block_equation4), gathered here (rows of one column are
+  // consecutive in the son as in the father: both order boundary vertices
+  // by id); leaves: their boundary block was filled into S
+  NodeDev ch0{}, ch1{};
+  const float *S0 = nullptr, *S1 = nullptr;
+  int p0 = -1, p1 = -1;
+  bool mixed_sons = false;
+  if (gather) {
+    ch0 = a.nodes[nd.child0];
+    ch1 = a.nodes[nd.child1];
+    mixed_sons = ch0.fp64 || ch1.fp64;
+    S0 = a.arenas.s32 + (int64_t)s * a.arenas.s32_stride + ch0.s_off;
+    S1 = a.arenas.s32 + (int64_t)s * a.arenas.s32_stride + ch1.s_off;
+    if (i < nbt) {
+      p0 = pos0[m + i];
+      p1 = pos1[m + i];
+    }
+  }
+  const int ld0 = ch0.b + 1, ld1 = ch1.b + 1;
+  const int32_t* map = a.maps + nd.map_off;
+  auto load_chunk = [&](int c0, float (&sv)[32]) {
+    if (!gather) {
+#pragma unroll
+      for (int q = 0; q < 32; ++q) {
+        const int j = TJ * kTile + c0 + q;
+        sv[q] = (i < nbt && j < nbt && i >= j) ? S[(int64_t)j * nb + i] : 0.0f;
+      }
+    } else if (!mixed_sons) {
+#pragma unroll
+      for (int q = 0; q < 32; ++q) {
+        const int j = TJ * kTile + c0 + q;
+        const int q0 = cpos[0][c0 + q], q1 = cpos[1][c0 + q];
+        const bool v = i < nbt && j < nbt && i >= j;
+        float x = 0.0f;
+        if (v && p0 >= 0 && q0 >= 0) x = S0[min(p0, q0) * ld0 + max(p0, q0)];
+        if (v && p1 >= 0 && q1 >= 0) x += S1[min(p1, q1) * ld1 + max(p1, q1)];
+        sv[q] = x;
+      }
+    } else {
+#pragma unroll
+      for (int q = 0; q < 32; ++q) {
+        const int j = TJ * kTile + c0 + q;
+        sv[q] = (i < nbt && j < nbt && i >= j)
+                    ? father_entry<float>(m + i, m + j, s, nd, map, ch0, ch1, a.arenas, a.rhs)
+                    : 0.0f;
+      }
+    }
+  };
+  float sv[32];
+  load_chunk(0, sv);
+
   if (tid == 0) {
     // one thread runs the pipeline: bulk copies of the split tiles (TI: A, TJ: B)
     // into kStages shared-memory stages, tensor-core MMAs out of them
@@ -182,29 +239,6 @@ __global__ void __launch_bounds__(128, 3) k_syrk_tc(StepArgs a) {
   if (timed_out) {
     if (tid == 0) flag_status(a.status, s, -HDD_ETIMEOUT, node);
   } else {
-    float* S = a.arenas.s32 + (int64_t)s * a.arenas.s32_stride + nd.s_off;
-    const int i = TI * kTile + warp * 32 + lane;   // accumulator lane = tile row
-    // fathers: the boundary block of the front is the sum of the sons' Schur
-    // entries (Eq. block_equation4), gathered here (rows of one column are
-    // consecutive in the son as in the father: both order boundary vertices
-    // by id); leaves: their boundary block was filled into S
-    NodeDev ch0{}, ch1{};
-    const float *S0 = nullptr, *S1 = nullptr;
-    int p0 = -1, p1 = -1;
-    bool mixed_sons = false;
-    if (gather) {
-      ch0 = a.nodes[nd.child0];
-      ch1 = a.nodes[nd.child1];
-      mixed_sons = ch0.fp64 || ch1.fp64;
-      S0 = a.arenas.s32 + (int64_t)s * a.arenas.s32_stride + ch0.s_off;
-      S1 = a.arenas.s32 + (int64_t)s * a.arenas.s32_stride + ch1.s_off;
-      if (i < nbt) {
-        p0 = pos0[m + i];
-        p1 = pos1[m + i];
-      }
-    }
-    const int ld0 = ch0.b + 1, ld1 = ch1.b + 1;
-    const int32_t* map = a.maps + nd.map_off;
 #pragma unroll 1
     for (int c0 = 0; c0 < kTile; c0 += 32) {
       if (TI == TJ && c0 > warp * 32 + 31) break;   // strictly above the diagonal of this warp's rows
@@ -219,38 +253,17 @@ __global__ void __launch_bounds__(128, 3) k_syrk_tc(StepArgs a) {
             "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
           : "r"(taddr));
       asm volatile("tcgen05.wait::ld.sync.aligned;");
-      // all 32 loads first (independent, in flight together), then the stores
-      float sv[32];
-      if (!gather) {
-#pragma unroll
-        for (int q = 0; q < 32; ++q) {
-          const int j = TJ * kTile + c0 + q;
-          sv[q] = (i < nbt && j < nbt && i >= j) ? S[(int64_t)j * nb + i] : 0.0f;
-        }
-      } else if (!mixed_sons) {
-#pragma unroll
-        for (int q = 0; q < 32; ++q) {
-          const int j = TJ * kTile + c0 + q;
-          const int q0 = cpos[0][c0 + q], q1 = cpos[1][c0 + q];
-          const bool v = i < nbt && j < nbt && i >= j;
-          float x = 0.0f;
-          if (v && p0 >= 0 && q0 >= 0) x = S0[min(p0, q0) * ld0 + max(p0, q0)];
-          if (v && p1 >= 0 && q1 >= 0) x += S1[min(p1, q1) * ld1 + max(p1, q1)];
-          sv[q] = x;
-        }
-      } else {
-#pragma unroll
-        for (int q = 0; q < 32; ++q) {
-          const int j = TJ * kTile + c0 + q;
-          sv[q] = (i < nbt && j < nbt && i >= j)
-                      ? father_entry<float>(m + i, m + j, s, nd, map, ch0, ch1, a.arenas, a.rhs)
-                      : 0.0f;
-        }
-      }
+      const bool more = c0 + 32 < kTile && !(TI == TJ && c0 + 32 > warp * 32 + 31);
+      float nx[32];
+      if (more) load_chunk(c0 + 32, nx);
 #pragma unroll
       for (int q = 0; q < 32; ++q) {
         const int j = TJ * kTile + c0 + q;
         if (i < nbt && j < nbt && i >= j) S[(int64_t)j * nb + i] = sv[q] - __uint_as_float(r[q]);
+      }
+      if (more) {
+#pragma unroll
+        for (int q = 0; q < 32; ++q) sv[q] = nx[q];
       }
     }
   }
