@@ -58,11 +58,15 @@ __device__ __forceinline__ void tile_of(int t, int nt, int& ti, int& tj) {
   ti = nt - 1 - c;
 }
 
+// Barrier of one group.  A CTA holds at most two groups of more than one warp,
+// which use the named barriers 1 and 2 (constant ids: the SM's barrier budget
+// per CTA is what the kernel names, and it bounds the CTAs per SM).
 struct Group {
-  int id, size, t;   // named barrier id, threads, thread index in the group
+  int id, size, t;   // named barrier id (1 or 2), threads, thread index in the group
   __device__ __forceinline__ void sync() const {
     if (size == 32) __syncwarp();
-    else asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(size) : "memory");
+    else if (id == 1) asm volatile("bar.sync 1, %0;" ::"r"(size) : "memory");
+    else asm volatile("bar.sync 2, %0;" ::"r"(size) : "memory");
   }
 };
 
