@@ -151,6 +151,19 @@ struct ProfScope {
 
 // Previous front kernels for fronts of up to kSmallMax rows (register rows per
 // warp / one CTA per front), selected with HDD_LEGACY_FRONTS=1 for comparison.
+int env_int(const char* name, int dflt) {
+  const char* v = getenv(name);
+  return v && *v ? atoi(v) : dflt;
+}
+int sweep_cta_min_m() {
+  static const int v = env_int("HDD_SWEEP_CTA_MIN_M", kSweepCtaMinM);
+  return v;
+}
+int bb_gather() {
+  static const int v = env_int("HDD_BB_GATHER", 1);
+  return v;
+}
+
 bool legacy_fronts() {
   static const bool on = [] {
     const char* v = getenv("HDD_LEGACY_FRONTS");
@@ -208,6 +221,7 @@ cudaError_t run_upsweep(const hdd::Plan& p, int batch, void* ws, const hdd::Rhs&
       a.max_m = li.max_m;
       a.max_b = li.max_b;
       a.max_rect = li.max_rect;
+      a.bb_gather = bb_gather();
       a.fl_chol = li.fl_chol * batch;
       a.fl_trsm = li.fl_trsm * batch;
       a.fl_syrk = li.fl_syrk * batch;
@@ -244,7 +258,7 @@ cudaError_t run_descent(const hdd::Plan& p, int batch, void* ws, const std::vect
     const bool fp64 = p.nodes[p.list_data[li.off]].fp64;
     // nodes with long interfaces: one CTA per (node, sample), blocked back substitution;
     // otherwise one warp per (node, sample)
-    const bool cta = li.max_m >= kSweepCtaMinM;
+    const bool cta = li.max_m >= sweep_cta_min_m();
     ProfScope ps(prof, hdd::kProfDescent, 0.0, st);
     cudaError_t e;
     if (li.max_nf <= hdd::kTinyMax)
@@ -274,7 +288,7 @@ cudaError_t run_forward(const hdd::Plan& p, int batch, void* ws, const hdd::Rhs&
     for (int k = 0; k < 2; ++k) {
       const hdd::ListInfo& li = p.lists[p.fwd_lists[h][k]];
       if (li.n == 0) continue;
-      const bool cta = li.max_m >= kSweepCtaMinM;
+      const bool cta = li.max_m >= sweep_cta_min_m();
       ProfScope ps(prof, hdd::kProfForward, 0.0, st);
       cudaError_t e;
       if (li.max_nf <= hdd::kTinyMax)

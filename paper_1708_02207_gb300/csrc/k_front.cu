@@ -760,7 +760,7 @@ __global__ void k_syrk_rhs(StepArgs a) {
   for (int j = threadIdx.x; j <= b; j += blockDim.x) {
     float acc = 0.0f;
     for (int k = 0; k < m; ++k) acc += y[k] * X[(int64_t)k * nf + j];
-    const float g = nd.leaf ? S[(int64_t)j * nb + b]
+    const float g = (nd.leaf || !a.bb_gather) ? S[(int64_t)j * nb + b]
                             : father_entry<float>(nf - 1, m + j, s, nd, map, c0, c1, a.arenas, a.rhs);
     S[(int64_t)j * nb + b] = g - acc;
   }
@@ -772,7 +772,7 @@ cudaError_t launch_front_large(const StepArgs& a, cudaStream_t st) {
   {
     // FP32 fronts: the tensor-core Schur update gathers the sons' boundary block
     // itself, so only the gamma columns are filled
-    const bool gamma_only = std::is_same<T, float>::value;
+    const bool gamma_only = std::is_same<T, float>::value && a.bb_gather;
     dim3 grid((a.max_nf + 7) / 8, a.nlist, a.batch);
     if (a.prof) a.prof->begin(kProfFill, 0.0, st);
     k_front_fill<T><<<grid, 256, 0, st>>>(a, gamma_only ? 1 : 0);

@@ -61,16 +61,22 @@ __global__ void k_forward(const NodeDev* __restrict__ nodes, const int32_t* __re
       z[r] = v;
     }
   }
+  T* Ld = z + ((nf + 3) & ~3);   // [32][33] diagonal block of L_gg, staged per block
   for (int cb = 0; cb < m; cb += 32) {
     const int jb = min(32, m - cb);
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < 32 * jb; idx += blockDim.x) {
+      const int c = idx >> 5, l = idx & 31;
+      Ld[c * 33 + l] = (l < jb) ? F[(int64_t)(cb + c) * nf + cb + l] : (T)0;
+    }
     __syncthreads();
     if (warp == 0) {
       T x = (lane < jb) ? z[cb + lane] : (T)0;
       for (int c = 0; c < jb; ++c) {
         T yc = __shfl_sync(0xffffffffu, x, c);
-        yc = yc / F[(int64_t)(cb + c) * nf + cb + c];
+        yc = yc / Ld[c * 33 + c];
         if (lane == c) x = yc;
-        if (lane > c && lane < jb) x -= F[(int64_t)(cb + c) * nf + cb + lane] * yc;
+        if (lane > c && lane < jb) x -= Ld[c * 33 + lane] * yc;
       }
       if (lane < jb) z[cb + lane] = x;
     }
@@ -94,7 +100,8 @@ template <typename T>
 cudaError_t launch_forward(const NodeDev* nodes, const int32_t* maps, const int32_t* list, int nlist, int batch,
                            const Arenas& A, const Rhs& rhs, int max_nf, cudaStream_t st) {
   if (nlist == 0) return cudaSuccess;
-  k_forward<T><<<dim3(nlist, batch), 256, (size_t)max_nf * sizeof(T), st>>>(nodes, maps, list, A, rhs);
+  const size_t smem = ((size_t)((max_nf + 3) & ~3) + 32 * 33) * sizeof(T);
+  k_forward<T><<<dim3(nlist, batch), 256, smem, st>>>(nodes, maps, list, A, rhs);
   return cudaGetLastError();
 }
 template cudaError_t launch_forward<double>(const NodeDev*, const int32_t*, const int32_t*, int, int, const Arenas&,

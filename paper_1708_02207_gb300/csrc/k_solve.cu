@@ -215,16 +215,22 @@ __global__ void k_descent(const NodeDev* __restrict__ nodes, const int32_t* __re
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
     if (lane == 0) t[c] = Y[c] - acc;
   }
+  T* Ld = t + ((m + 3) & ~3);   // [32][33] diagonal block of L_gg, staged per block
   for (int cb = ((m - 1) / 32) * 32; cb >= 0; cb -= 32) {
     const int jb = min(32, m - cb);
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < 32 * jb; idx += blockDim.x) {
+      const int c = idx >> 5, l = idx & 31;
+      Ld[c * 33 + l] = (l < jb) ? F[(int64_t)(cb + c) * nf + cb + l] : (T)0;
+    }
     __syncthreads();
     if (warp == 0) {
       T x = (lane < jb) ? t[cb + lane] : (T)0;
       for (int r = jb - 1; r >= 0; --r) {
         T ur = __shfl_sync(0xffffffffu, x, r);
-        ur = ur / F[(int64_t)(cb + r) * nf + cb + r];
+        ur = ur / Ld[r * 33 + r];
         if (lane == r) x = ur;
-        if (lane < r) x -= F[(int64_t)(cb + lane) * nf + cb + r] * ur;
+        if (lane < r) x -= Ld[lane * 33 + r] * ur;
       }
       if (lane < jb) t[cb + lane] = x;    // now u_g
     }
@@ -245,7 +251,7 @@ template <typename T>
 cudaError_t launch_descent(const NodeDev* nodes, const int32_t* maps, const int32_t* list, int nlist, int batch,
                            const Arenas& A, double* u, int64_t u_stride, int max_b, int max_m, cudaStream_t st) {
   if (nlist == 0) return cudaSuccess;
-  const size_t smem = (size_t)(max_b + max_m) * sizeof(T);
+  const size_t smem = ((size_t)max_b + ((max_m + 3) & ~3) + 32 * 33) * sizeof(T);
   k_descent<T><<<dim3(nlist, batch), 256, smem, st>>>(nodes, maps, list, A, u, u_stride);
   return cudaGetLastError();
 }
