@@ -28,7 +28,7 @@ thread_local std::string g_err;
 
 // Sweeps over nodes whose interface has at least this many vertices use one CTA
 // per (node, sample) with blocked substitution; smaller nodes one warp each.
-constexpr int kSweepCtaMinM = 32;
+constexpr int kSweepCtaMinM = 16;
 
 hdd_status fail_cuda(cudaError_t e, const char* where) {
   g_err = std::string(where) + ": " + cudaGetErrorString(e);

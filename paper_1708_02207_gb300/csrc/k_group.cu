@@ -71,34 +71,33 @@ struct Group {
 };
 
 // Adds a son's lower Schur triangle ((b+1) x (b+1), column-major) into the front
-// through its up map ups (son row -> front row).  Four entries per thread and
-// pass, loads first; the column of an entry comes from a float reciprocal
-// (exact here: indices stay far below 2^22 and the quotient's distance to the
-// next integer is at least 0.5 / ldc).
+// through its up map ups (son row -> front row).  The lower entries are walked
+// in packed column order: a thread starts at its rank and advances by the group
+// size, carrying its (row, column) along (no division); four entries per pass,
+// loads first.
 template <typename T>
 __device__ __forceinline__ void add_son(T* K, int ld, const NodeDev& ch, const int* ups, const Arenas& A, int s,
                                         const Group& g) {
   const int ldc = ch.b + 1;
-  const int total = ldc * ldc;
-  const float inv = 1.0f / (float)ldc;
+  const int total = ldc * (ldc + 1) / 2;
   const int64_t base = (int64_t)s * (ch.fp64 ? A.s64_stride : A.s32_stride) + ch.s_off;
+  int c = 0, off = g.t;   // entry = (c + off, c)
+  while (c < ldc && off >= ldc - c) { off -= ldc - c; ++c; }
   for (int i0 = g.t; i0 < total; i0 += 4 * g.size) {
     T v[4];
     int rr[4], cc[4];
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-      const int idx = i0 + q * g.size;
-      const int c = (int)(((float)idx + 0.5f) * inv);
-      const int r = idx - c * ldc;
-      rr[q] = r;
+      const bool use = i0 + q * g.size < total;
+      rr[q] = c + off;
       cc[q] = c;
-      const bool use = idx < total && r >= c;
-      v[q] = use ? (ch.fp64 ? (T)A.s64[base + idx] : (T)A.s32[base + idx]) : (T)0;
+      v[q] = use ? (ch.fp64 ? (T)A.s64[base + c * ldc + c + off] : (T)A.s32[base + c * ldc + c + off]) : (T)0;
+      off += g.size;
+      while (c < ldc && off >= ldc - c) { off -= ldc - c; ++c; }
     }
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-      const int idx = i0 + q * g.size;
-      if (idx < total && rr[q] >= cc[q]) {
+      if (i0 + q * g.size < total) {
         const int pr = ups[rr[q]], pc = ups[cc[q]];
         K[min(pr, pc) * ld + max(pr, pc)] += v[q];
       }
