@@ -299,6 +299,7 @@ def run_hdd(args, cfg):
     n_desc_all, n_desc_vis, n_fwd, n_res = (K, 1, K, K) if K > 0 else (0, 1, 0, 0)
     stage_bytes = {   # per step
         "kappa": info["bytes_assemble"] * B + info["bytes_kl_basis"],
+        "leaf_front": info["bytes_upsweep_leaf"] * B,
         "front_warp": info["bytes_upsweep_tiny"] * B,
         "front_small": info["bytes_upsweep_small"] * B,
         "large_fronts": info["bytes_upsweep_large"] * B,
@@ -325,7 +326,8 @@ def run_hdd(args, cfg):
                 "t_roof_ms": max(t_hbm, t_alu), "bound": bound, "frac": max(t_hbm, t_alu) / ms}
 
     stages_roof = {}
-    for name in ("kappa", "front_warp", "front_small", "large_fronts", "subtree", "forward", "descent", "residual"):
+    for name in ("kappa", "leaf_front", "front_warp", "front_small", "large_fronts", "subtree", "forward", "descent",
+                 "residual"):
         r = fam_roof(name, groups.get(name, (name,)))
         if r:
             stages_roof[name] = r

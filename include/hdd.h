@@ -114,6 +114,9 @@ typedef struct {
   double bytes_residual;         /* one FP64 residual r = b - A u */
   double bytes_assemble;         /* kappa written (FP64, plus the FP32 copy of mixed plans) and Z read */
   double bytes_kl_basis;         /* the KL basis, read once per hdd_assemble call */
+  double bytes_upsweep_leaf;     /* condensed leaves (at most 16 interior vertices): kappa in; K_gg^-1,
+                                    the boundary couplings, y_g and the lower Schur triangle out */
+  int32_t n_condensed_leaves;    /* leaves stored as K_gg^-1 and boundary couplings instead of factors */
 } hdd_plan_info_t;
 
 typedef struct {

@@ -2,6 +2,7 @@
 // schedule of the HDD likelihood path.  No exceptions cross this boundary.
 #include <cuda_runtime.h>
 
+#include <array>
 #include <cstdlib>
 #include <cstring>
 #include <mutex>
@@ -20,6 +21,7 @@ cudaError_t configure_warp_kernels();
 cudaError_t configure_tc_kernels();
 cudaError_t configure_fused_kernels();
 cudaError_t configure_group_kernels();
+cudaError_t configure_leaf_kernels();
 }  // namespace hdd
 
 namespace {
@@ -68,6 +70,7 @@ cudaError_t configure_device(int dev) {
   if (e == cudaSuccess) e = hdd::configure_tc_kernels();
   if (e == cudaSuccess) e = hdd::configure_fused_kernels();
   if (e == cudaSuccess) e = hdd::configure_group_kernels();
+  if (e == cudaSuccess) e = hdd::configure_leaf_kernels();
   if (e == cudaSuccess) g_configured[dev] = true;
   return e;
 }
@@ -212,7 +215,7 @@ cudaError_t run_upsweep(const hdd::Plan& p, int batch, void* ws, const hdd::Rhs&
     if (e != cudaSuccess) return e;
   }
   for (int h = 0; h <= p.height; ++h) {
-    for (int kind = 0; kind < 6; ++kind) {
+    for (int kind = 0; kind < 8; ++kind) {
       const hdd::ListInfo& li = p.lists[p.step_lists[h][kind]];
       if (li.n == 0) continue;
       a.list = p.d_lists + li.off;
@@ -237,7 +240,9 @@ cudaError_t run_upsweep(const hdd::Plan& p, int batch, void* ws, const hdd::Rhs&
                                     : hdd::launch_front_group<float>(a, hdd::kProfFrontWarp, st); break;
         case 4: e = legacy_fronts() ? hdd::launch_front_small<float>(a, st)
                                     : hdd::launch_front_group<float>(a, hdd::kProfFrontSmall, st); break;
-        default: e = hdd::launch_front_large<float>(a, st); break;
+        case 5: e = hdd::launch_front_large<float>(a, st); break;
+        case 6: e = hdd::launch_leaf_front<double>(a, st); break;
+        default: e = hdd::launch_leaf_front<float>(a, st); break;
       }
       if (e != cudaSuccess) return e;
     }
@@ -246,13 +251,23 @@ cudaError_t run_upsweep(const hdd::Plan& p, int batch, void* ws, const hdd::Rhs&
 }
 
 // "Root to Leaves" over the given per-depth lists, writing u (FP64).
-cudaError_t run_descent(const hdd::Plan& p, int batch, void* ws, const std::vector<int>& per_depth, double* u,
-                        cudaStream_t st, hdd::Profiler* prof) {
+cudaError_t run_descent(const hdd::Plan& p, int batch, void* ws, const std::vector<std::array<int, 3>>& per_depth,
+                        double* u, cudaStream_t st, hdd::Profiler* prof) {
   const hdd::Layout L = hdd::layout(p, batch);
   const hdd::Arenas A = arenas(p, L, ws);
   const int64_t NN = (int64_t)p.N * p.N;
   for (int d = 0; d <= p.depth; ++d) {
-    const hdd::ListInfo& li = p.lists[per_depth[d]];
+    for (int kind = 1; kind < 3; ++kind) {   // condensed leaves of this depth
+      const hdd::ListInfo& ll = p.lists[per_depth[d][kind]];
+      if (ll.n == 0) continue;
+      ProfScope ps(prof, hdd::kProfDescent, 0.0, st);
+      cudaError_t e = kind == 1 ? hdd::launch_leaf_descent<double>(p.d_nodes, p.d_maps, p.d_lists + ll.off, ll.n,
+                                                                   batch, A, u, NN, st)
+                                : hdd::launch_leaf_descent<float>(p.d_nodes, p.d_maps, p.d_lists + ll.off, ll.n,
+                                                                  batch, A, u, NN, st);
+      if (e != cudaSuccess) return e;
+    }
+    const hdd::ListInfo& li = p.lists[per_depth[d][0]];
     if (li.n == 0) continue;
     // the lists hold one precision per depth in the plans built here
     const bool fp64 = p.nodes[p.list_data[li.off]].fp64;
@@ -285,9 +300,18 @@ cudaError_t run_forward(const hdd::Plan& p, int batch, void* ws, const hdd::Rhs&
   const hdd::Layout L = hdd::layout(p, batch);
   const hdd::Arenas A = arenas(p, L, ws);
   for (int h = 0; h <= p.height; ++h)
-    for (int k = 0; k < 2; ++k) {
+    for (int k = 0; k < 4; ++k) {
       const hdd::ListInfo& li = p.lists[p.fwd_lists[h][k]];
       if (li.n == 0) continue;
+      if (k >= 2) {   // condensed leaves
+        ProfScope ps(prof, hdd::kProfForward, 0.0, st);
+        cudaError_t e = k == 2 ? hdd::launch_leaf_forward<double>(p.d_nodes, p.d_maps, p.d_lists + li.off, li.n,
+                                                                  batch, A, rhs, st)
+                               : hdd::launch_leaf_forward<float>(p.d_nodes, p.d_maps, p.d_lists + li.off, li.n,
+                                                                 batch, A, rhs, st);
+        if (e != cudaSuccess) return e;
+        continue;
+      }
       const bool cta = li.max_m >= sweep_cta_min_m();
       ProfScope ps(prof, hdd::kProfForward, 0.0, st);
       cudaError_t e;
@@ -600,7 +624,7 @@ hdd_status hdd_profile_end(hdd_plan_t plan, hdd_kernel_stat_t* stats, int32_t ma
   pr->on = false;
   static const char* names[hdd::kProfCount] = {"kappa", "front_warp", "front_small", "front_fill", "potrf", "trsm",
                                                 "syrk_simt", "syrk_tc", "syrk_rhs", "forward", "descent",
-                                                "residual", "misc", "subtree"};
+                                                "residual", "misc", "subtree", "leaf_front"};
   int launches[hdd::kProfCount] = {};
   double ms[hdd::kProfCount] = {}, fl[hdd::kProfCount] = {};
   DeviceScope ds(plan->p.device);
@@ -653,19 +677,24 @@ hdd_status hdd_plan_info(hdd_plan_t plan, hdd_plan_info_t* info) {
   info->bytes_residual = p.by_residual;
   info->bytes_assemble = p.by_assemble;
   info->bytes_kl_basis = p.by_kl_basis;
+  info->bytes_upsweep_leaf = p.by_leaf;
+  info->n_condensed_leaves = 0;
+  for (const hdd::Node& nd : p.nodes) info->n_condensed_leaves += nd.linv;
   int up = 0, down = 0;
   for (int h = 0; h <= p.height; ++h)
-    for (int kind = 0; kind < 6; ++kind) {
+    for (int kind = 0; kind < 8; ++kind) {
       const hdd::ListInfo& li = p.lists[p.step_lists[h][kind]];
       if (li.n) up += kind == 2 ? 4 : (kind == 5 ? 5 : 1);
     }
   for (const auto& fu : p.fusion) up += fu.height > 0;
   int down_all = 0, fwd = 0;
-  for (int d = 0; d <= p.depth; ++d) {
-    down += p.lists[p.down_vis_lists[d]].n > 0;
-    down_all += p.lists[p.down_all_lists[d]].n > 0;
-  }
-  for (int h = 0; h <= p.height; ++h) fwd += (p.lists[p.fwd_lists[h][0]].n > 0) + (p.lists[p.fwd_lists[h][1]].n > 0);
+  for (int d = 0; d <= p.depth; ++d)
+    for (int kind = 0; kind < 3; ++kind) {
+      down += p.lists[p.down_vis_lists[d][kind]].n > 0;
+      down_all += p.lists[p.down_all_lists[d][kind]].n > 0;
+    }
+  for (int h = 0; h <= p.height; ++h)
+    for (int k = 0; k < 4; ++k) fwd += p.lists[p.fwd_lists[h][k]].n > 0;
   int solve = down + 1;
   if (p.precision == HDD_MIXED_FP32) {
     const int K = p.ir_max_iter;

@@ -15,7 +15,7 @@ namespace hdd {
 // algorithmic flops of the launch.  Owned by a plan; not thread-safe.
 enum ProfFamily {
   kProfKappa, kProfFrontWarp, kProfFrontSmall, kProfFill, kProfPotrf, kProfTrsm, kProfSyrk, kProfSyrkTc,
-  kProfSyrkRhs, kProfForward, kProfDescent, kProfResidual, kProfMisc, kProfFused, kProfCount
+  kProfSyrkRhs, kProfForward, kProfDescent, kProfResidual, kProfMisc, kProfFused, kProfLeaf, kProfCount
 };
 struct Profiler {
   bool on = false;
@@ -103,6 +103,14 @@ cudaError_t launch_descent_tiny(const NodeDev* nodes, const int32_t* maps, const
 template <typename T> cudaError_t launch_front_group(const StepArgs& a, int family, cudaStream_t st);
 // fronts that fit in shared memory: build + partial Cholesky + store, one CTA each
 template <typename T> cudaError_t launch_front_small(const StepArgs& a, cudaStream_t st);
+// condensed leaves (K_gg^-1 and boundary couplings): upsweep, right-hand-side sweep, descent
+template <typename T> cudaError_t launch_leaf_front(const StepArgs& a, cudaStream_t st);
+template <typename T>
+cudaError_t launch_leaf_forward(const NodeDev* nodes, const int32_t* maps, const int32_t* list, int nlist, int batch,
+                                const Arenas& A, const Rhs& rhs, cudaStream_t st);
+template <typename T>
+cudaError_t launch_leaf_descent(const NodeDev* nodes, const int32_t* maps, const int32_t* list, int nlist, int batch,
+                                const Arenas& A, double* u, int64_t u_stride, cudaStream_t st);
 // SYRK of large FP32 fronts on the tensor cores (tcgen05, 3xTF32)
 cudaError_t launch_syrk_tc(const StepArgs& a, cudaStream_t st);
 // large fronts: fill in global memory, then POTRF of gamma, TRSM of the rest, SYRK into S

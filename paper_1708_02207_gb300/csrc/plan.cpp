@@ -223,7 +223,15 @@ std::string build_plan(const hdd_plan_desc& d, Plan& p) {
   p.max_nf_large = p.max_m_large = p.max_b_large = 0;
   for (int k = 0; k < nn; ++k) {
     Node& nd = p.nodes[k];
+    nd.linv = nd.leaf() && !nd.fused && nd.m >= 1 && nd.m <= kLeafInvMax && nd.b <= kLeafInvMaxB;
+  }
+  for (int k = 0; k < nn; ++k) {
+    Node& nd = p.nodes[k];
     if (nd.fused) goto descent_lists;
+    if (nd.linv) {
+      (nd.fp64 ? p.steps[nd.height].linv64 : p.steps[nd.height].linv32).push_back(k);
+      goto descent_lists;
+    }
     {
     Step& st = p.steps[nd.height];
     if (nd.fp64) {
@@ -255,7 +263,7 @@ std::string build_plan(const hdd_plan_desc& d, Plan& p) {
     int64_t& ys = nd.fp64 ? p.y64_stride : p.y32_stride;
     nd.y_off = ys;
     ys += nd.m;
-    int64_t sz = (int64_t)nd.nf * nd.m;
+    int64_t sz = nd.linv ? (int64_t)nd.m * (nd.m + 1) / 2 + nd.b : (int64_t)nd.nf * nd.m;
     int64_t& st = nd.fp64 ? p.f64_stride : p.f32_stride;
     nd.f_off = st;
     st += (sz + 31) / 32 * 32;
@@ -339,6 +347,22 @@ std::string build_plan(const hdd_plan_desc& d, Plan& p) {
     std::vector<int> rows(nd.gamma);
     rows.insert(rows.end(), nd.bnd.begin(), nd.bnd.end());
     p.maps.insert(p.maps.end(), rows.begin(), rows.end());
+    if (nd.linv) {
+      // the interior row coupled to each boundary row (-1: a corner, no interior neighbour)
+      std::map<int, int> grow;
+      for (int r = 0; r < nd.m; ++r) grow[nd.gamma[r]] = r;
+      for (int v : nd.bnd) {
+        const int vi = v % p.N, vj = v / p.N;
+        int c = -1, hits = 0;
+        const int nbr[4][2] = {{vi - 1, vj}, {vi + 1, vj}, {vi, vj - 1}, {vi, vj + 1}};
+        for (const auto& q : nbr) {
+          auto it = grow.find(q[1] * p.N + q[0]);
+          if (it != grow.end()) { c = it->second; ++hits; }
+        }
+        if (hits > 1) return "internal: boundary vertex with two interior neighbours in a leaf";
+        p.maps.push_back(c);
+      }
+    }
     if (!nd.leaf()) {
       for (int c = 0; c < 2; ++c) {
         const Node& ch = p.nodes[nd.child[c]];
@@ -398,24 +422,37 @@ std::string build_plan(const hdd_plan_desc& d, Plan& p) {
     p.lists.push_back(li);
     return (int)p.lists.size() - 1;
   };
-  p.step_lists.assign(p.height + 1, {0, 0, 0, 0, 0, 0});
+  p.step_lists.assign(p.height + 1, {0, 0, 0, 0, 0, 0, 0, 0});
   for (int hgt = 0; hgt <= p.height; ++hgt) {
     const Step& st = p.steps[hgt];
     p.step_lists[hgt] = {add_list(st.tiny64), add_list(st.small64), add_list(st.large64),
-                         add_list(st.tiny32), add_list(st.small32), add_list(st.large32)};
+                         add_list(st.tiny32), add_list(st.small32), add_list(st.large32),
+                         add_list(st.linv64), add_list(st.linv32)};
   }
-  // right-hand-side sweep: every node (fused or not), by height and precision
-  p.fwd_lists.assign(p.height + 1, {0, 0});
+  // right-hand-side sweep: every node (fused or not), by height, precision and format
+  p.fwd_lists.assign(p.height + 1, {0, 0, 0, 0});
   {
-    std::vector<std::vector<int>> l64(p.height + 1), l32(p.height + 1);
-    for (int k = 0; k < nn; ++k) (p.nodes[k].fp64 ? l64 : l32)[p.nodes[k].height].push_back(k);
-    for (int hgt = 0; hgt <= p.height; ++hgt) p.fwd_lists[hgt] = {add_list(l64[hgt]), add_list(l32[hgt])};
+    std::vector<std::vector<int>> l[4];
+    for (auto& v : l) v.assign(p.height + 1, {});
+    for (int k = 0; k < nn; ++k) {
+      const Node& nd = p.nodes[k];
+      l[(nd.linv ? 2 : 0) + (nd.fp64 ? 0 : 1)][nd.height].push_back(k);
+    }
+    for (int hgt = 0; hgt <= p.height; ++hgt)
+      p.fwd_lists[hgt] = {add_list(l[0][hgt]), add_list(l[1][hgt]), add_list(l[2][hgt]), add_list(l[3][hgt])};
   }
-  p.down_vis_lists.assign(p.depth + 1, 0);
-  p.down_all_lists.assign(p.depth + 1, 0);
+  p.down_vis_lists.assign(p.depth + 1, {0, 0, 0});
+  p.down_all_lists.assign(p.depth + 1, {0, 0, 0});
   for (int d = 0; d <= p.depth; ++d) {
-    p.down_vis_lists[d] = add_list(p.down_visited[d]);
-    p.down_all_lists[d] = add_list(p.down_all[d]);
+    std::vector<int> vis[3], all[3];
+    for (int k : p.down_all[d]) {
+      const Node& nd = p.nodes[k];
+      const int kind = nd.linv ? (nd.fp64 ? 1 : 2) : 0;
+      all[kind].push_back(k);
+      if (nd.visited) vis[kind].push_back(k);
+    }
+    p.down_vis_lists[d] = {add_list(vis[0]), add_list(vis[1]), add_list(vis[2])};
+    p.down_all_lists[d] = {add_list(all[0]), add_list(all[1]), add_list(all[2])};
   }
 
   // device descriptors
@@ -423,7 +460,7 @@ std::string build_plan(const hdd_plan_desc& d, Plan& p) {
   for (int k = 0; k < nn; ++k) {
     const Node& nd = p.nodes[k];
     NodeDev& d = p.dev_nodes[k];
-    d.m = nd.m; d.b = nd.b; d.nf = nd.nf; d.leaf = nd.leaf();
+    d.m = nd.m; d.b = nd.b; d.nf = nd.nf; d.leaf = nd.linv ? 2 : (nd.leaf() ? 1 : 0);
     d.child0 = nd.child[0]; d.child1 = nd.child[1];
     d.x0 = nd.x0; d.y0 = nd.y0; d.x1 = nd.x1; d.y1 = nd.y1;
     d.map_off = (int32_t)nd.map_off;
@@ -444,7 +481,8 @@ std::string build_plan(const hdd_plan_desc& d, Plan& p) {
     if (nd.visited) p.flops_down += 2.0 * (nd.b * m + m * m / 2.0);
   }
   // algorithmic bytes per sample (see plan.h)
-  p.by_tiny = p.by_small = p.by_large = p.by_fused = p.by_fwd = p.by_desc_all = p.by_desc_vis = 0.0;
+  p.by_tiny = p.by_small = p.by_large = p.by_fused = p.by_leaf = 0.0;
+  p.by_fwd = p.by_desc_all = p.by_desc_vis = 0.0;
   auto esz = [](const Node& nd) { return nd.fp64 ? 8.0 : 4.0; };
   auto tri = [](double n) { return n * (n + 1.0) / 2.0; };
   for (const Node& nd : p.nodes) {
@@ -458,6 +496,15 @@ std::string build_plan(const hdd_plan_desc& d, Plan& p) {
         in += tri(ch.b + 1.0) * esz(ch);
         sons_cond += ch.b * esz(ch);
       }
+    }
+    if (nd.linv) {   // condensed leaf: G (packed) and the couplings instead of F
+      const double g = tri(m) + b;
+      p.by_leaf += in + (g + m + tri(b + 1.0)) * E;
+      p.by_fwd += g * E + m * 8.0 + (m + b) * E;
+      const double down = (g + m) * E + b * 8.0 + m * 8.0;
+      p.by_desc_all += down;
+      if (nd.visited) p.by_desc_vis += down;
+      continue;
     }
     const double front = in + (nf * m + m + tri(b + 1.0)) * E;
     if (nd.fused) p.by_fused += front;

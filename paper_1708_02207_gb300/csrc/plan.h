@@ -16,6 +16,8 @@ namespace hdd {
 // rows: m eliminated vertices (gamma, or a leaf's interior), b boundary unknowns,
 // and one bordered right-hand-side row.  Per sample the front is stored as
 //   F: nf x m column-major (ld nf)      -> L_gg (rows < m), L_Bg, y_g^T (last row)
+//      (condensed leaves, leaf == 2: G = K_gg^-1 packed lower [m(m+1)/2], then the
+//      boundary coupling weights [b]; y_g holds G b_g)
 //   S: (b+1) x (b+1) column-major (ld b+1), lower triangle -> Schur complement and
 //      condensed right-hand side (last row)
 struct NodeDev {
@@ -45,6 +47,7 @@ struct Node {
   bool visited = false;
   bool fp64 = true;
   bool fused = false;      // eliminated inside a fused subtree
+  bool linv = false;       // condensed leaf: stores K_gg^-1 and its boundary couplings instead of F
   int m = 0, b = 0, nf = 0;
   int64_t f_off = 0, s_off = 0, y_off = 0, tc_off = -1, inv_off = -1;
   int64_t map_off = 0;
@@ -63,7 +66,7 @@ struct ListInfo {
 
 // One upsweep step: all nodes of one height, split by front size and precision.
 struct Step {
-  std::vector<int> tiny64, small64, large64, tiny32, small32, large32;
+  std::vector<int> tiny64, small64, large64, tiny32, small32, large32, linv64, linv32;
 };
 
 struct Plan {
@@ -77,7 +80,7 @@ struct Plan {
   std::vector<Node> nodes;
   std::vector<int32_t> owner;          // vertex id -> node that eliminates it (-1: Dirichlet)
   std::vector<Step> steps;             // by height, leaves first
-  std::vector<std::vector<int>> down_visited, down_all;   // by depth, root first
+  std::vector<std::vector<int>> down_visited, down_all;   // by depth, root first (condensed leaves excluded)
   std::vector<int32_t> maps;           // concatenated per-node maps
   std::vector<NodeDev> dev_nodes;
   int max_front = 0, max_front_small64 = 0, max_front_small32 = 0;
@@ -95,6 +98,7 @@ struct Plan {
   // once (fronts: sons' lower Schur triangles or the leaf's kappa in; F, y_g and
   // the lower Schur triangle out)
   double by_tiny = 0.0, by_small = 0.0, by_large = 0.0, by_fused = 0.0;   // upsweep fronts by kernel class
+  double by_leaf = 0.0;                                    // condensed leaves
   double by_fwd = 0.0;                                     // one right-hand-side sweep
   double by_desc_all = 0.0, by_desc_vis = 0.0;             // full and pruned descents
   double by_residual = 0.0, by_assemble = 0.0;             // FP64 residual; kappa written
@@ -116,9 +120,12 @@ struct Plan {
   // node lists concatenated (host copy of d_lists) and their descriptors
   std::vector<int32_t> list_data;
   std::vector<ListInfo> lists;
-  std::vector<std::array<int, 6>> step_lists;   // [height][tiny64, small64, large64, tiny32, small32, large32]
-  std::vector<int> down_vis_lists, down_all_lists;   // [depth]
-  std::vector<std::array<int, 2>> fwd_lists;         // [height][fp64, fp32]: right-hand-side sweep
+  // [height][tiny64, small64, large64, tiny32, small32, large32, linv64, linv32]
+  std::vector<std::array<int, 8>> step_lists;
+  // [depth][fp64 and fp32 fronts, condensed leaves (fp64), condensed leaves (fp32)]
+  std::vector<std::array<int, 3>> down_vis_lists, down_all_lists;
+  // [height][fp64, fp32, condensed fp64, condensed fp32]: right-hand-side sweep
+  std::vector<std::array<int, 4>> fwd_lists;
 
   // device copies
   double* d_phi = nullptr;
@@ -141,6 +148,12 @@ constexpr int kTcTile = 128, kTcChunk = 8;
 constexpr int64_t kTcBlockBytes = (int64_t)kTcTile * kTcChunk * 4;
 constexpr int kSmallMax64 = 160;   // 160^2 * 8 B = 200 KiB
 constexpr int kSmallMax32 = 128;   // 128 * 132 * 4 B = 66 KiB (larger FP32 fronts: tensor-core path)
+// Condensed leaves: leaves with 1..kLeafInvMax interior vertices and at most
+// kLeafInvMaxB boundary unknowns store, per sample, G = K_gg^-1 (packed lower,
+// column-major) followed by the coupling weight of each boundary row (on this
+// mesh every boundary vertex of a rectangle has at most one interior neighbour).
+constexpr int kLeafInvMax = 16;
+constexpr int kLeafInvMaxB = 63;
 
 // Build the host plan; returns an empty string on success, else an error text.
 std::string build_plan(const hdd_plan_desc& d, Plan& p);

@@ -50,6 +50,7 @@ class PlanInfo(C.Structure):
         ("bytes_upsweep_fused", C.c_double), ("bytes_forward", C.c_double),
         ("bytes_descent_all", C.c_double), ("bytes_descent_visited", C.c_double),
         ("bytes_residual", C.c_double), ("bytes_assemble", C.c_double), ("bytes_kl_basis", C.c_double),
+        ("bytes_upsweep_leaf", C.c_double), ("n_condensed_leaves", C.c_int32),
     ]
 
 

@@ -113,11 +113,21 @@ def test_algorithmic_bytes_match_front_sizes(hdd, precision, N, leaf):
     small_max = 160 if precision == "fp64" else 128
     nodes = hd.build_tree(N, leaf)
     tri = lambda n: n * (n + 1) / 2
-    cls = {"tiny": 0.0, "small": 0.0, "large": 0.0}
+    cls = {"tiny": 0.0, "small": 0.0, "large": 0.0, "leaf": 0.0}
     fwd = desc = 0.0
+    n_condensed = 0
     for nd in nodes:
         m, b = len(nd.gamma), len(nd.bnd)
         nf = m + b + 1
+        if not nd.children and 1 <= m <= 16 and b <= 63:
+            # condensed leaf: K_gg^-1 (packed) and one coupling weight per boundary row
+            g = tri(m) + b
+            inp = 2 * (nd.x1 - nd.x0) * (nd.y1 - nd.y0) * E
+            cls["leaf"] += inp + (g + m + tri(b + 1)) * E
+            fwd += g * E + m * 8 + (m + b) * E
+            desc += (g + m) * E + b * 8 + m * 8
+            n_condensed += 1
+            continue
         if nd.children:
             sons = [nodes[c] for c in nd.children]
             inp = sum(tri(len(c.bnd) + 1) * E for c in sons)
@@ -131,7 +141,19 @@ def test_algorithmic_bytes_match_front_sizes(hdd, precision, N, leaf):
     assert np.isclose(info["bytes_upsweep_tiny"], cls["tiny"])
     assert np.isclose(info["bytes_upsweep_small"], cls["small"])
     assert np.isclose(info["bytes_upsweep_large"], cls["large"])
+    assert np.isclose(info["bytes_upsweep_leaf"], cls["leaf"])
+    assert info["n_condensed_leaves"] == n_condensed
     assert info["bytes_upsweep_fused"] == 0.0
     assert np.isclose(info["bytes_forward"], fwd)
     assert np.isclose(info["bytes_descent_all"], desc)
     assert 0 < info["bytes_descent_visited"] < info["bytes_descent_all"]
+
+
+def test_condensed_leaves_follow_the_leaf_size(hdd):
+    """Leaves with at most 16 interior vertices are condensed; larger leaves and
+    leaves inside fused subtrees keep their partial Cholesky factors."""
+    obs = w.obs_vertices(65, 3)
+    assert hdd.Plan(65, 4, None, obs, 0.01, device=-1).info()["n_condensed_leaves"] == 256
+    assert hdd.Plan(65, 8, None, obs, 0.01, device=-1).info()["n_condensed_leaves"] == 0
+    fused = hdd.Plan(65, 4, None, obs, 0.01, precision=hdd.HDD_MIXED_FP32, fuse_height=2, device=-1)
+    assert fused.info()["n_condensed_leaves"] == 0
