@@ -9,7 +9,7 @@
 //   u_g       = G b_g - sum_i w_i u_B,i G[:, c_i]           (descent, "Root to Leaves")
 // which is the same elimination in exact arithmetic.  Per sample the factor
 // store holds G (packed lower, column-major) followed by w [b]; y_g holds
-// G b_g.  One warp per (leaf, sample), eight samples of one leaf per CTA.
+// G b_g.
 #include "launch.h"
 
 namespace hdd {
@@ -37,56 +37,66 @@ template <> __device__ __forceinline__ float* leaf_S<float>(const Arenas& A, con
   return A.s32 + (int64_t)s * A.s32_stride + nd.s_off;
 }
 
-// per-warp shared buffers of the leaf front (elements of T)
-constexpr int kWarpElems = 3 * kLeafInvMax * kLd + (kLeafInvMaxB + 1) + kLeafInvMax;
+// per-sample shared buffers of the leaf front (elements of T, then ints)
+constexpr int kSampElems = kLeafInvMax * kLd + 4 * (kLeafInvMaxB + 1) + kLeafInvMax;
+constexpr int kSampInts = 2 * (kLeafInvMaxB + 1);
+constexpr int kLeafSamples = 16;   // samples per CTA: two per warp, one per half-warp
 
 }  // namespace
 
-// Upsweep at condensed leaves: stiffness of the leaf's own triangles (only the
-// stencil nonzeros), Cholesky of K_gg in registers (lane r holds row r), W =
-// L^-1 by forward substitution (lane c solves L w = e_c), G = W^T W, then G,
-// w, y_g = G b_g and the leaf's lower Schur triangle with its condensed load.
+// Upsweep at condensed leaves, one half-warp per (leaf, sample): lane r builds
+// row r of K_gg (stencil nonzeros of the leaf's own triangles), Gauss-Jordan
+// elimination of [K_gg | I] in registers (no pivoting: K_gg is SPD, the pivots
+// are those of its Cholesky factorisation) leaves G = K_gg^-1 in the right
+// half; then y_g = G b_g and the leaf's lower Schur triangle with its
+// condensed load, the boundary block of K read from a sparse row list (a
+// boundary vertex has at most two boundary neighbours).
 template <typename T>
 __global__ void __launch_bounds__(256) k_leaf_front(StepArgs a) {
   const int node = a.list[blockIdx.x];
   const NodeDev nd = a.nodes[node];
   const int m = nd.m, b = nd.b, nf = nd.nf, nb = b + 1, N = a.N;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int s = blockIdx.y * 8 + warp;
+  const int hw = threadIdx.x >> 4, r = threadIdx.x & 15;   // half-warp = sample, lane r = row
+  const int s = blockIdx.y * kLeafSamples + hw;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* Kg = reinterpret_cast<T*>(smem_raw) + warp * kWarpElems;   // K_gg, then L (row-major, ld kLd)
-  T* Wm = Kg + kLeafInvMax * kLd;                                // W = L^-1 (row-major)
-  T* Gs = Wm + kLeafInvMax * kLd;                                // G (full, row-major)
-  T* wv = Gs + kLeafInvMax * kLd;                                // w [b]
-  T* vs = wv + kLeafInvMaxB + 1;                                 // G b_g [m]
-  int* tbl = reinterpret_cast<int*>(reinterpret_cast<T*>(smem_raw) + 8 * kWarpElems);
+  T* Gs = reinterpret_cast<T*>(smem_raw) + hw * kSampElems;   // K_gg rows, then G (ld kLd)
+  T* wv = Gs + kLeafInvMax * kLd;                               // couplings w [b]
+  T* dB = wv + kLeafInvMaxB + 1;                                // K_BB diagonal [b]
+  T* nw0 = dB + kLeafInvMaxB + 1;                               // K_BB entries to lower boundary rows
+  T* nw1 = nw0 + kLeafInvMaxB + 1;
+  T* vs = nw1 + kLeafInvMaxB + 1;                               // y_g = G b_g [m]
+  int* ints = reinterpret_cast<int*>(reinterpret_cast<T*>(smem_raw) + kLeafSamples * kSampElems);
+  int* nj0 = ints + hw * kSampInts;                             // their rows (-1: none)
+  int* nj1 = nj0 + kLeafInvMaxB + 1;
+  int* tbl = ints + kLeafSamples * kSampInts;
   const int32_t* vid = a.maps + nd.map_off;
   const int32_t* cpl = vid + (nf - 1);
   const int tw = nd.x1 - nd.x0 + 1, cells = tw * (nd.y1 - nd.y0 + 1);
   int* loc = tbl + cells;   // local (column, row) of each front row's vertex
   for (int i = threadIdx.x; i < cells; i += blockDim.x) tbl[i] = -1;
   __syncthreads();
-  for (int r = threadIdx.x; r < nf - 1; r += blockDim.x) {
-    const int v = vid[r];
+  for (int q = threadIdx.x; q < nf - 1; q += blockDim.x) {
+    const int v = vid[q];
     const int li = v % N - nd.x0, lj = v / N - nd.y0;
-    tbl[lj * tw + li] = r;
-    loc[r] = (lj << 16) | li;
+    tbl[lj * tw + li] = q;
+    loc[q] = (lj << 16) | li;
   }
   __syncthreads();
-  if (s >= a.batch) return;
-  const T* kap = kappa_of<T>(a.kappa, a.kappa32) + (int64_t)s * a.kap_stride;
+  const bool active = s < a.batch;   // both half-warps stay for the shuffles
+  const int ss = active ? s : 0;
+  const T* kap = kappa_of<T>(a.kappa, a.kappa32) + (int64_t)ss * a.kap_stride;
 
   // 1. interior rows of the stiffness and the boundary couplings
-  for (int i = lane; i < kLeafInvMax * kLd; i += 32) Kg[i] = (T)0;
-  for (int i = lane; i < b; i += 32) wv[i] = (T)0;
+  for (int i = r; i < kLeafInvMax * kLd; i += 16) Gs[i] = (T)0;
+  for (int i = r; i < b; i += 16) wv[i] = (T)0;
   __syncwarp();
-  T bg = (T)0;   // load of interior vertex `lane` (Eq. coefc)
-  if (lane < m) {
-    const int li = loc[lane] & 0xffff, lj = loc[lane] >> 16;
+  T bg = (T)0;   // load of interior vertex r (Eq. coefc)
+  if (r < m) {
+    const int li = loc[r] & 0xffff, lj = loc[r] >> 16;
     const int vi = nd.x0 + li, vj = nd.y0 + lj;
     const T wl = w_horizontal(kap, N, nd, vi - 1, vj), wr = w_horizontal(kap, N, nd, vi, vj);
     const T wd = w_vertical(kap, N, nd, vi, vj - 1), wu = w_vertical(kap, N, nd, vi, vj);
-    Kg[lane * kLd + lane] = wl + wr + wd + wu;
+    Gs[r * kLd + r] = wl + wr + wd + wu;
     const int nbr[4] = {li > 0 ? tbl[lj * tw + li - 1] : -1, vi < nd.x1 ? tbl[lj * tw + li + 1] : -1,
                         lj > 0 ? tbl[(lj - 1) * tw + li] : -1, vj < nd.y1 ? tbl[(lj + 1) * tw + li] : -1};
     const T wgt[4] = {wl, wr, wd, wu};
@@ -94,108 +104,104 @@ __global__ void __launch_bounds__(256) k_leaf_front(StepArgs a) {
     for (int q = 0; q < 4; ++q) {
       const int c = nbr[q];
       if (c < 0) continue;
-      if (c < m) Kg[lane * kLd + c] = -wgt[q];
+      if (c < m) Gs[r * kLd + c] = -wgt[q];
       else wv[c - m] = -wgt[q];   // the boundary row's only interior neighbour is this vertex
     }
-    bg = (T)a.rhs(s, vj * N + vi);
+    bg = (T)a.rhs(ss, vj * N + vi);
+  }
+  // boundary block of K, sparse: diagonal, and the entries to boundary rows below
+  for (int i = r; i < b; i += 16) {
+    const int li = loc[m + i] & 0xffff, lj = loc[m + i] >> 16;
+    const int vi = nd.x0 + li, vj = nd.y0 + lj;
+    const T wl = w_horizontal(kap, N, nd, vi - 1, vj), wr = w_horizontal(kap, N, nd, vi, vj);
+    const T wd = w_vertical(kap, N, nd, vi, vj - 1), wu = w_vertical(kap, N, nd, vi, vj);
+    dB[i] = wl + wr + wd + wu;
+    const int nbr[4] = {li > 0 ? tbl[lj * tw + li - 1] : -1, vi < nd.x1 ? tbl[lj * tw + li + 1] : -1,
+                        lj > 0 ? tbl[(lj - 1) * tw + li] : -1, vj < nd.y1 ? tbl[(lj + 1) * tw + li] : -1};
+    const T wgt[4] = {wl, wr, wd, wu};
+    int j0 = -1, j1 = -1;
+    T w0 = (T)0, w1 = (T)0;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int c = nbr[q] - m;   // boundary row of the neighbour
+      if (nbr[q] < m || c >= i) continue;
+      if (j0 < 0) { j0 = c; w0 = -wgt[q]; }
+      else { j1 = c; w1 = -wgt[q]; }
+    }
+    nj0[i] = j0; nw0[i] = w0;
+    nj1[i] = j1; nw1[i] = w1;
   }
   __syncwarp();
 
-  // 2. Cholesky K_gg = L L^T, lane r holding row r; pivot column by shuffles
-  T row[kLeafInvMax];
+  // 2. Gauss-Jordan on [K_gg | I]: lane r holds row r; after pivot k, column k
+  // of the left half is e_k and only columns > k of it are still needed, while
+  // the right half is nonzero only in columns <= k
+  T x[kLeafInvMax], g[kLeafInvMax];
 #pragma unroll
-  for (int c = 0; c < kLeafInvMax; ++c) row[c] = (lane < m && c < m) ? Kg[lane * kLd + c] : (T)0;
+  for (int c = 0; c < kLeafInvMax; ++c) {
+    x[c] = (r < m && c < m) ? Gs[r * kLd + c] : (T)0;
+    g[c] = (T)0;
+  }
   bool bad = false;
 #pragma unroll
   for (int k = 0; k < kLeafInvMax; ++k) {
-    if (k < m) {
-      T pkk = __shfl_sync(kAllLanes, row[k], k);
-      if (!(pkk > (T)0) || !isfinite(pkk)) {   // not SPD: record, continue with a unit pivot
+    if (k < m) {   // uniform
+      T p = __shfl_sync(kAllLanes, x[k], k, 16);
+      if (!(p > (T)0) || !isfinite(p)) {   // not SPD: record, continue with a unit pivot
         bad = true;
-        pkk = (T)1;
+        p = (T)1;
       }
-      const T d = sqrt(pkk), inv = (T)1 / d;
-      T lk = (lane == k) ? d : row[k] * inv;
-      if (lane < k) lk = (T)0;
+      const T inv = (T)1 / p;
+      const T f = x[k];
+      const bool piv = r == k;
+      if (piv) g[k] = (T)1;
 #pragma unroll
-      for (int j = k + 1; j < kLeafInvMax; ++j) {
-        const T lj = __shfl_sync(kAllLanes, lk, j);
-        if (lane > k) row[j] -= lk * lj;
+      for (int c = k + 1; c < kLeafInvMax; ++c) {
+        const T pc = __shfl_sync(kAllLanes, x[c], k, 16) * inv;
+        x[c] = piv ? pc : x[c] - f * pc;
       }
-      row[k] = lk;
+#pragma unroll
+      for (int c = 0; c <= k; ++c) {
+        const T pc = __shfl_sync(kAllLanes, g[c], k, 16) * inv;
+        g[c] = piv ? pc : g[c] - f * pc;
+      }
     }
   }
-  if (bad && lane == 0) flag_status(a.status, s, -HDD_ENOTSPD, node);
-  if (lane < kLeafInvMax)
-#pragma unroll
-    for (int c = 0; c < kLeafInvMax; ++c) Kg[lane * kLd + c] = row[c];
-  __syncwarp();
+  if (bad && r == 0 && active) flag_status(a.status, s, -HDD_ENOTSPD, node);
 
-  // 3. W = L^-1: lane c solves L w = e_c (rows of L read by all lanes at once)
-  T w[kLeafInvMax];
-#pragma unroll
-  for (int r = 0; r < kLeafInvMax; ++r) {
-    T acc = (lane == r) ? (T)1 : (T)0;
-#pragma unroll
-    for (int l = 0; l < r; ++l) acc -= Kg[r * kLd + l] * w[l];
-    w[r] = (r < m) ? acc / Kg[r * kLd + r] : (T)0;
-  }
-  if (lane < kLeafInvMax)
-#pragma unroll
-    for (int r = 0; r < kLeafInvMax; ++r) Wm[r * kLd + lane] = w[r];
+  // 3. G, y_g = G b_g, couplings
+  T* F = active ? leaf_F<T>(a.arenas, nd, s) : nullptr;
   __syncwarp();
-
-  // 4. G = W^T W (lane i: row i; W is lower, so w[k] = W[k, i] vanishes for k < i)
-  T* F = leaf_F<T>(a.arenas, nd, s);
-  if (lane < m) {
-#pragma unroll
-    for (int j = 0; j < kLeafInvMax; ++j) {
-      if (j >= m) break;
-      T g = (T)0;
-#pragma unroll
-      for (int k = 0; k < kLeafInvMax; ++k)
-        if (k < m) g += w[k] * Wm[k * kLd + j];
-      Gs[lane * kLd + j] = g;
-      if (j <= lane) F[pk(lane, j, m)] = g;
-    }
-  }
-  __syncwarp();
-
-  // 5. y_g = G b_g
   T vI = (T)0;
 #pragma unroll
-  for (int j = 0; j < kLeafInvMax; ++j) {
-    const T bj = __shfl_sync(kAllLanes, bg, j);
-    if (lane < m && j < m) vI += Gs[lane * kLd + j] * bj;
+  for (int c = 0; c < kLeafInvMax; ++c) {
+    const T bc = __shfl_sync(kAllLanes, bg, c, 16);
+    if (r < m && c < m) {
+      Gs[r * kLd + c] = g[c];
+      vI += g[c] * bc;
+      if (active && c <= r) F[pk(r, c, m)] = g[c];
+    }
   }
-  if (lane < m) {
-    node_Y<T>(a.arenas, nd, s)[lane] = vI;
-    vs[lane] = vI;
+  if (r < m) {
+    vs[r] = vI;
+    if (active) node_Y<T>(a.arenas, nd, s)[r] = vI;
   }
   const int g_elems = m * (m + 1) / 2;
-  for (int i = lane; i < b; i += 32) F[g_elems + i] = wv[i];
+  if (active)
+    for (int i = r; i < b; i += 16) F[g_elems + i] = wv[i];
   __syncwarp();
+  if (!active) return;
 
-  // 6. lower Schur triangle ((b+1) x (b+1), column-major), walked in packed order
+  // 4. lower Schur triangle ((b+1) x (b+1), column-major), walked in packed order
   T* S = leaf_S<T>(a.arenas, nd, s);
   const int total = nb * (nb + 1) / 2;
-  int c = 0, off = lane;   // entry (c + off, c)
+  int c = 0, off = r;   // entry (c + off, c)
   while (c < nb && off >= nb - c) { off -= nb - c; ++c; }
-  for (int t = lane; t < total; t += 32) {
+  for (int t = r; t < total; t += 16) {
     const int i = c + off, j = c;   // i >= j
     T val = (T)0;
     if (i < b) {
-      const int ri = loc[m + i], rj = loc[m + j];
-      const int lii = ri & 0xffff, lji = ri >> 16, lij = rj & 0xffff, ljj = rj >> 16;
-      const int vi = nd.x0 + lii, vj = nd.y0 + lji;
-      if (i == j) {
-        val = w_horizontal(kap, N, nd, vi - 1, vj) + w_horizontal(kap, N, nd, vi, vj) +
-              w_vertical(kap, N, nd, vi, vj - 1) + w_vertical(kap, N, nd, vi, vj);
-      } else if (lji == ljj && (lii - lij == 1 || lij - lii == 1)) {
-        val = -w_horizontal(kap, N, nd, nd.x0 + min(lii, lij), vj);
-      } else if (lii == lij && (lji - ljj == 1 || ljj - lji == 1)) {
-        val = -w_vertical(kap, N, nd, vi, nd.y0 + min(lji, ljj));
-      }
+      val = (i == j) ? dB[i] : ((nj0[i] == j) ? nw0[i] : ((nj1[i] == j) ? nw1[i] : (T)0));
       const int ci = cpl[i], cj = cpl[j];
       if (ci >= 0 && cj >= 0) val -= wv[i] * wv[j] * Gs[ci * kLd + cj];
     } else if (j < b) {   // condensed load (bordered row)
@@ -203,7 +209,7 @@ __global__ void __launch_bounds__(256) k_leaf_front(StepArgs a) {
       if (cj >= 0) val = -wv[j] * vs[cj];
     }
     S[j * nb + i] = val;
-    off += 32;
+    off += 16;
     while (c < nb && off >= nb - c) { off -= nb - c; ++c; }
   }
 }
@@ -279,9 +285,10 @@ __global__ void __launch_bounds__(256) k_leaf_descent(const NodeDev* __restrict_
 template <typename T>
 cudaError_t launch_leaf_front(const StepArgs& a, cudaStream_t st) {
   if (a.nlist == 0) return cudaSuccess;
-  const size_t smem = (size_t)8 * kWarpElems * sizeof(T) + (size_t)(a.max_rect + a.max_nf) * sizeof(int);
+  const size_t smem = (size_t)kLeafSamples * (kSampElems * sizeof(T) + kSampInts * sizeof(int)) +
+                      (size_t)(a.max_rect + a.max_nf) * sizeof(int);
   if (a.prof) a.prof->begin(kProfLeaf, a.fl_chol + a.fl_trsm + a.fl_syrk + a.fl_rhs, st);
-  k_leaf_front<T><<<dim3(a.nlist, (a.batch + 7) / 8), 256, smem, st>>>(a);
+  k_leaf_front<T><<<dim3(a.nlist, (a.batch + kLeafSamples - 1) / kLeafSamples), 256, smem, st>>>(a);
   if (a.prof) a.prof->end(st);
   return cudaGetLastError();
 }
