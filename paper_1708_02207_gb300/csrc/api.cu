@@ -624,7 +624,7 @@ hdd_status hdd_profile_end(hdd_plan_t plan, hdd_kernel_stat_t* stats, int32_t ma
   pr->on = false;
   static const char* names[hdd::kProfCount] = {"kappa", "front_warp", "front_small", "front_fill", "potrf", "trsm",
                                                 "syrk_simt", "syrk_tc", "syrk_rhs", "forward", "descent",
-                                                "residual", "misc", "subtree", "leaf_front"};
+                                                "residual", "misc", "subtree", "leaf_front", "chol_trsm"};
   int launches[hdd::kProfCount] = {};
   double ms[hdd::kProfCount] = {}, fl[hdd::kProfCount] = {};
   DeviceScope ds(plan->p.device);

@@ -558,6 +558,133 @@ __global__ void __launch_bounds__(256) k_potrf_warp(StepArgs a) {
   for (int r = 0; r < 32; ++r) G[lane * 32 + r] = (lane < m) ? ((r < m) ? w[r] : (T)0) : ((r == lane) ? (T)1 : (T)0);
 }
 
+// POTRF and TRSM of large fronts whose gamma block has at most 32 columns, one
+// CTA per (node, sample): warp 0 factors K_gg in registers (as k_potrf_warp)
+// and forms W = L^-1 in shared memory; every thread then takes boundary rows
+// (their gamma columns prefetched into registers meanwhile) and computes
+// L_Bg = K_Bg W^T row by row (x_c = sum_{l <= c} a_l W[c, l]), writing the
+// factor rows, y_g (bordered row) and, for FP32 fronts, the split TF32 tiles
+// of the tensor-core Schur update.
+template <typename T>
+__global__ void __launch_bounds__(256, 2) k_chol_trsm32(StepArgs a) {
+  constexpr unsigned kAll = 0xffffffffu;
+  const int node = a.list[blockIdx.x];
+  const int s = blockIdx.y;
+  const NodeDev nd = a.nodes[node];
+  const int nf = nd.nf, m = nd.m, b = nd.b;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  T* A = node_F<T>(a.arenas, nd, s);
+  constexpr int kW = 36;   // row stride of W: 16-byte aligned groups of four columns
+  __shared__ __align__(16) T Wt[32 * kW];
+  __shared__ T Ls[32 * 33], dinv[32];
+  const int r_first = m + (int)threadIdx.x;
+  if (warp == 0) {
+    T row[32];
+#pragma unroll
+    for (int c = 0; c < 32; ++c) row[c] = (c < m && lane < m && c <= lane) ? A[(int64_t)c * nf + lane] : (T)0;
+    bool bad = false;
+#pragma unroll
+    for (int k = 0; k < 32; ++k) {
+      if (k < m) {
+        T pk = __shfl_sync(kAll, row[k], k);
+        if (!(pk > (T)0) || !isfinite(pk)) {
+          bad = true;
+          pk = (T)1;
+        }
+        const T d = sqrt(pk), inv = (T)1 / d;
+        T lk = (lane == k) ? d : row[k] * inv;
+        if (lane < k) lk = (T)0;
+#pragma unroll
+        for (int j = k + 1; j < 32; ++j) {
+          const T lj = __shfl_sync(kAll, lk, j);
+          if (lane > k) row[j] -= lk * lj;
+        }
+        row[k] = lk;
+      }
+    }
+    if (bad && lane == 0) flag_status(a.status, s, -HDD_ENOTSPD, node);
+#pragma unroll
+    for (int c = 0; c < 32; ++c) {
+      if (c < m && lane < m && c <= lane) A[(int64_t)c * nf + lane] = row[c];
+      Ls[lane * 33 + c] = row[c];
+    }
+    T diag = (T)1;
+#pragma unroll
+    for (int c = 0; c < 32; ++c)
+      if (c == lane && c < m) diag = row[c];
+    dinv[lane] = (T)1 / diag;
+    __syncwarp();
+    // lane c solves L w = e_c; W[r, c] stored at Wt[r * 33 + c]
+    T w[32];
+#pragma unroll
+    for (int r = 0; r < 32; ++r) {
+      T acc = (lane == r) ? (T)1 : (T)0;
+#pragma unroll
+      for (int l = 0; l < r; ++l) acc -= Ls[r * 33 + l] * w[l];
+      w[r] = (r < m) ? acc * dinv[r] : (T)0;
+      Wt[r * kW + lane] = (lane < m) ? w[r] : (T)0;
+    }
+  }
+  __syncthreads();
+  const bool tc = std::is_same<T, float>::value && nd.tc_off >= 0 && b > 0;
+  const int nchunks = (m + kTcChunk - 1) / kTcChunk;
+  unsigned char* tcb = tc ? a.arenas.tc + (int64_t)s * a.arenas.tc_stride + nd.tc_off : nullptr;
+  const int tc_rows = ((b + kTcTile - 1) / kTcTile) * kTcTile;   // boundary rows, zero-filled to the tile end
+  for (int r = r_first; r < m + max(tc ? tc_rows : 0, nf - m); r += blockDim.x) {
+    const bool real = r < nf;
+    T y[32];   // the row's gamma entries, overwritten by its factor row (last column first)
+#pragma unroll
+    for (int c = 0; c < 32; ++c) y[c] = (c < m && real) ? A[(int64_t)c * nf + r] : (T)0;
+#pragma unroll
+    for (int c = 31; c >= 0; --c) {
+      T acc = (T)0;
+#pragma unroll
+      for (int l4 = 0; l4 <= c; l4 += 4) {   // W is lower: entries l > c of row c are zero
+        T wv[4];
+        load4(Wt + c * kW + l4, wv);
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+          if (l4 + q <= c) acc += y[l4 + q] * wv[q];
+      }
+      y[c] = (c < m) ? acc : (T)0;
+    }
+    if (real) {
+#pragma unroll
+      for (int c = 0; c < 32; ++c)
+        if (c < m) A[(int64_t)c * nf + r] = y[c];
+      if (r == nf - 1) {
+        T* Y = node_Y<T>(a.arenas, nd, s);
+#pragma unroll
+        for (int c = 0; c < 32; ++c)
+          if (c < m) Y[c] = y[c];
+      }
+    }
+    const int br = r - m;   // boundary row (tile row space); the bordered row is not a tile row
+    if (tc && br < tc_rows) {   // rows b.. (the bordered row included) are zero tile rows
+      const int Tt = br / kTcTile, tr = br % kTcTile;
+      const bool zero = br >= b;
+#pragma unroll
+      for (int c8 = 0; c8 < 4; ++c8) {
+        if (c8 >= nchunks) break;
+#pragma unroll
+        for (int kq = 0; kq < 2; ++kq) {
+          float v[4];
+#pragma unroll
+          for (int q = 0; q < 4; ++q) v[q] = zero ? 0.0f : (float)y[c8 * 8 + 4 * kq + q];
+          float4 hi, lo;
+          hi.x = tf32_rna(v[0]); hi.y = tf32_rna(v[1]); hi.z = tf32_rna(v[2]); hi.w = tf32_rna(v[3]);
+          lo.x = tf32_rna(v[0] - hi.x); lo.y = tf32_rna(v[1] - hi.y);
+          lo.z = tf32_rna(v[2] - hi.z); lo.w = tf32_rna(v[3] - hi.w);
+          const int64_t blk = ((int64_t)Tt * nchunks + c8) * 2 * kTcBlockBytes;
+          const int off = (tr >> 3) * (kTcChunk / 4) * 128 + kq * 128 + (tr & 7) * 16;
+          *reinterpret_cast<float4*>(tcb + blk + off) = hi;
+          *reinterpret_cast<float4*>(tcb + blk + kTcBlockBytes + off) = lo;
+        }
+      }
+    }
+  }
+}
+
 template <typename T> struct TrsmShape;
 template <> struct TrsmShape<float> { static constexpr int rows = 64, cap = 760; };
 template <> struct TrsmShape<double> { static constexpr int rows = 32, cap = 760; };
@@ -779,16 +906,17 @@ cudaError_t launch_front_large(const StepArgs& a, cudaStream_t st) {
     if (a.prof) a.prof->end(st);
   }
   const size_t rows_smem = (size_t)min(a.max_m, SmemCap<T>::rows);
-  {
+  if (a.max_m <= 32) {   // POTRF and TRSM in one kernel
+    if (a.prof) a.prof->begin(kProfCholTrsm, a.fl_chol + a.fl_trsm, st);
+    k_chol_trsm32<T><<<dim3(a.nlist, a.batch), 256, 0, st>>>(a);
+    if (a.prof) a.prof->end(st);
+  } else {
     const size_t smem = (rows_smem * kPanel + kPanel + 32 * 33) * sizeof(T);
     if (a.prof) a.prof->begin(kProfPotrf, a.fl_chol, st);
-    if (a.max_m <= 32)
-      k_potrf_warp<T><<<dim3(a.nlist, (a.batch + 7) / 8), 256, 8 * (32 * 33 + 32) * sizeof(T), st>>>(a);
-    else
-      k_potrf<T><<<dim3(a.nlist, a.batch), 256, smem, st>>>(a);
+    k_potrf<T><<<dim3(a.nlist, a.batch), 256, smem, st>>>(a);
     if (a.prof) a.prof->end(st);
   }
-  {
+  if (a.max_m > 32) {
     constexpr int R = TrsmShape<T>::rows;
     const size_t xrows = (size_t)min(a.max_m, TrsmShape<T>::cap);
     const size_t smem = (xrows * R + 32 * 33 + 3 + 32 * 64) * sizeof(T) + 16;

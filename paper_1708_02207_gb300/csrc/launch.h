@@ -15,7 +15,7 @@ namespace hdd {
 // algorithmic flops of the launch.  Owned by a plan; not thread-safe.
 enum ProfFamily {
   kProfKappa, kProfFrontWarp, kProfFrontSmall, kProfFill, kProfPotrf, kProfTrsm, kProfSyrk, kProfSyrkTc,
-  kProfSyrkRhs, kProfForward, kProfDescent, kProfResidual, kProfMisc, kProfFused, kProfLeaf, kProfCount
+  kProfSyrkRhs, kProfForward, kProfDescent, kProfResidual, kProfMisc, kProfFused, kProfLeaf, kProfCholTrsm, kProfCount
 };
 struct Profiler {
   bool on = false;
