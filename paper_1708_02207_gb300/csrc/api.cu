@@ -166,6 +166,12 @@ int bb_gather() {
   static const int v = env_int("HDD_BB_GATHER", 1);
   return v;
 }
+// Large fronts (heights above the leaves) whose gamma block has at most this
+// many columns run on the grouped front kernel with the sons' entries gathered.
+int gather_max_m() {
+  static const int v = env_int("HDD_GATHER_MAX_M", 64);
+  return v;
+}
 
 bool legacy_fronts() {
   static const bool on = [] {
@@ -235,12 +241,22 @@ cudaError_t run_upsweep(const hdd::Plan& p, int batch, void* ws, const hdd::Rhs&
                                     : hdd::launch_front_group<double>(a, hdd::kProfFrontWarp, st); break;
         case 1: e = legacy_fronts() ? hdd::launch_front_small<double>(a, st)
                                     : hdd::launch_front_group<double>(a, hdd::kProfFrontSmall, st); break;
-        case 2: e = hdd::launch_front_large<double>(a, st); break;
+        case 2:
+          e = (h > 0 && li.max_m <= gather_max_m() &&
+               hdd::front_group_smem(li.max_nf, li.max_m, li.max_rect, true, 8) <= 227 * 1024)
+                  ? hdd::launch_front_group<double>(a, hdd::kProfFrontGather, st, true)
+                  : hdd::launch_front_large<double>(a, st);
+          break;
         case 3: e = legacy_fronts() ? hdd::launch_front_warp<float>(a, st)
                                     : hdd::launch_front_group<float>(a, hdd::kProfFrontWarp, st); break;
         case 4: e = legacy_fronts() ? hdd::launch_front_small<float>(a, st)
                                     : hdd::launch_front_group<float>(a, hdd::kProfFrontSmall, st); break;
-        case 5: e = hdd::launch_front_large<float>(a, st); break;
+        case 5:
+          e = (h > 0 && li.max_m <= gather_max_m() &&
+               hdd::front_group_smem(li.max_nf, li.max_m, li.max_rect, true, 4) <= 227 * 1024)
+                  ? hdd::launch_front_group<float>(a, hdd::kProfFrontGather, st, true)
+                  : hdd::launch_front_large<float>(a, st);
+          break;
         case 6: e = hdd::launch_leaf_front<double>(a, st); break;
         default: e = hdd::launch_leaf_front<float>(a, st); break;
       }
@@ -624,7 +640,8 @@ hdd_status hdd_profile_end(hdd_plan_t plan, hdd_kernel_stat_t* stats, int32_t ma
   pr->on = false;
   static const char* names[hdd::kProfCount] = {"kappa", "front_warp", "front_small", "front_fill", "potrf", "trsm",
                                                 "syrk_simt", "syrk_tc", "syrk_rhs", "forward", "descent",
-                                                "residual", "misc", "subtree", "leaf_front", "chol_trsm"};
+                                                "residual", "misc", "subtree", "leaf_front", "chol_trsm",
+                                                "front_gather"};
   int launches[hdd::kProfCount] = {};
   double ms[hdd::kProfCount] = {}, fl[hdd::kProfCount] = {};
   DeviceScope ds(plan->p.device);

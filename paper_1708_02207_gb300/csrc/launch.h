@@ -15,7 +15,7 @@ namespace hdd {
 // algorithmic flops of the launch.  Owned by a plan; not thread-safe.
 enum ProfFamily {
   kProfKappa, kProfFrontWarp, kProfFrontSmall, kProfFill, kProfPotrf, kProfTrsm, kProfSyrk, kProfSyrkTc,
-  kProfSyrkRhs, kProfForward, kProfDescent, kProfResidual, kProfMisc, kProfFused, kProfLeaf, kProfCholTrsm, kProfCount
+  kProfSyrkRhs, kProfForward, kProfDescent, kProfResidual, kProfMisc, kProfFused, kProfLeaf, kProfCholTrsm, kProfFrontGather, kProfCount
 };
 struct Profiler {
   bool on = false;
@@ -100,7 +100,10 @@ template <typename T>
 cudaError_t launch_descent_tiny(const NodeDev* nodes, const int32_t* maps, const int32_t* list, int nlist, int batch,
                                 const Arenas& A, double* u, int64_t u_stride, cudaStream_t st);
 // fronts of up to kSmallMax rows: W warps per front, several samples of a node per CTA
-template <typename T> cudaError_t launch_front_group(const StepArgs& a, int family, cudaStream_t st);
+template <typename T>
+cudaError_t launch_front_group(const StepArgs& a, int family, cudaStream_t st, bool gather = false);
+// shared memory of one CTA of the grouped front kernel (0 < result; > 227 KiB: does not fit)
+size_t front_group_smem(int max_nf, int max_m, int max_rect, bool gather, size_t elem);
 // fronts that fit in shared memory: build + partial Cholesky + store, one CTA each
 template <typename T> cudaError_t launch_front_small(const StepArgs& a, cudaStream_t st);
 // condensed leaves (K_gg^-1 and boundary couplings): upsweep, right-hand-side sweep, descent
