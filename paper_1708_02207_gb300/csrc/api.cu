@@ -166,6 +166,10 @@ int bb_gather() {
   static const int v = env_int("HDD_BB_GATHER", 1);
   return v;
 }
+int fp32_syrk_simt() {
+  static const int v = env_int("HDD_FP32_SYRK_SIMT", 0);
+  return v;
+}
 // Large fronts (heights above the leaves) whose gamma block has at most this
 // many columns run on the grouped front kernel with the sons' entries gathered.
 int gather_max_m() {
@@ -231,6 +235,7 @@ cudaError_t run_upsweep(const hdd::Plan& p, int batch, void* ws, const hdd::Rhs&
       a.max_b = li.max_b;
       a.max_rect = li.max_rect;
       a.bb_gather = bb_gather();
+      a.syrk_simt = fp32_syrk_simt();
       a.fl_chol = li.fl_chol * batch;
       a.fl_trsm = li.fl_trsm * batch;
       a.fl_syrk = li.fl_syrk * batch;

@@ -899,7 +899,7 @@ cudaError_t launch_front_large(const StepArgs& a, cudaStream_t st) {
   {
     // FP32 fronts: the tensor-core Schur update gathers the sons' boundary block
     // itself, so only the gamma columns are filled
-    const bool gamma_only = std::is_same<T, float>::value && a.bb_gather;
+    const bool gamma_only = std::is_same<T, float>::value && a.bb_gather && !a.syrk_simt;
     dim3 grid((a.max_nf + 7) / 8, a.nlist, a.batch);
     if (a.prof) a.prof->begin(kProfFill, 0.0, st);
     k_front_fill<T><<<grid, 256, 0, st>>>(a, gamma_only ? 1 : 0);
@@ -925,7 +925,7 @@ cudaError_t launch_front_large(const StepArgs& a, cudaStream_t st) {
     k_trsm<T><<<grid, 256, smem, st>>>(a);
     if (a.prof) a.prof->end(st);
   }
-  if (std::is_same<T, float>::value) {
+  if (std::is_same<T, float>::value && !a.syrk_simt) {
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     if (a.prof) a.prof->begin(kProfSyrkTc, a.fl_syrk, st);

@@ -174,6 +174,7 @@ __global__ void __launch_bounds__(256) k_front_group(StepArgs a, int W, int ld, 
     // 1'. gamma columns of the front from the sons, four rows per thread and pass
     for (int c = 0; c < m; ++c) {
       const int q0 = pos0[c], q1 = pos1[c];
+      for (int r = g.t; r < c; r += g.size) K[c * ld + r] = (T)0;   // above the diagonal
       for (int r0 = c + g.t; r0 < nf; r0 += 4 * g.size) {
         T v[4];
 #pragma unroll
@@ -234,9 +235,12 @@ __global__ void __launch_bounds__(256) k_front_group(StepArgs a, int W, int ld, 
     for (int r = k + g.t; r < nf; r += g.size) {
       T acc = K[k * ld + r];
       if (r == nf - 1 && !nd.leaf) acc += (T)a.rhs(s, map[k]);   // father: load of its gamma vertex
+      // the products are summed first and subtracted once: the entry is usually much
+      // larger than what is left of it, and one rounding at its magnitude is enough
+      T dot = (T)0;
 #pragma unroll 4
-      for (int l = 0; l < k; ++l) acc -= K[l * ld + r] * rowk[l * ld];
-      K[k * ld + r] = acc;
+      for (int l = 0; l < k; ++l) dot += K[l * ld + r] * rowk[l * ld];
+      K[k * ld + r] = acc - dot;
     }
     g.sync();
     T p = K[k * ld + k];
@@ -267,8 +271,8 @@ __global__ void __launch_bounds__(256) k_front_group(StepArgs a, int W, int ld, 
     int ti, tj;
     tile_of(t, nt, ti, tj);
     const int i0 = t0 + 4 * ti, j0 = t0 + 4 * tj;
-    T acc[4][4];
-    if (gather) {   // boundary-block entries from the sons (Eq. block_equation4)
+    T kb[4][4];   // boundary-block entries of the front
+    if (gather) {   // from the sons (Eq. block_equation4)
       int x0[4], x1[4];
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
@@ -287,7 +291,7 @@ __global__ void __launch_bounds__(256) k_front_group(StepArgs a, int W, int ld, 
             if (x0[q] >= 0 && q0 >= 0) v += son_at<T>(c0, a.arenas, sb32, sb64, x0[q], q0);
             if (x1[q] >= 0 && q1 >= 0) v += son_at<T>(c1, a.arenas, sb32, sb64, x1[q], q1);
           }
-          acc[q][w] = v;
+          kb[q][w] = v;
         }
       }
     } else {
@@ -296,9 +300,14 @@ __global__ void __launch_bounds__(256) k_front_group(StepArgs a, int W, int ld, 
         T v[4];
         ld4(K + (j0 + w) * ld + i0, v);
 #pragma unroll
-        for (int q = 0; q < 4; ++q) acc[q][w] = v[q];
+        for (int q = 0; q < 4; ++q) kb[q][w] = v[q];
       }
     }
+    T acc[4][4];   // L_Bg L_Bg^T, summed before it is subtracted
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+#pragma unroll
+      for (int w = 0; w < 4; ++w) acc[q][w] = (T)0;
 #pragma unroll 2
     for (int l = 0; l < m; ++l) {
       T x[4], y[4];
@@ -307,7 +316,7 @@ __global__ void __launch_bounds__(256) k_front_group(StepArgs a, int W, int ld, 
 #pragma unroll
       for (int q = 0; q < 4; ++q)
 #pragma unroll
-        for (int w = 0; w < 4; ++w) acc[q][w] -= x[q] * y[w];
+        for (int w = 0; w < 4; ++w) acc[q][w] += x[q] * y[w];
     }
 #pragma unroll
     for (int w = 0; w < 4; ++w) {
@@ -316,7 +325,7 @@ __global__ void __launch_bounds__(256) k_front_group(StepArgs a, int W, int ld, 
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
         const int r = i0 + q;
-        if (r >= c && r < nf) S[(c - m) * nb + (r - m)] = acc[q][w];
+        if (r >= c && r < nf) S[(c - m) * nb + (r - m)] = kb[q][w] - acc[q][w];
       }
     }
   }

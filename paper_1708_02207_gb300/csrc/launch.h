@@ -60,6 +60,7 @@ struct StepArgs {
   int max_nf, max_m, max_b;
   int max_rect;             // leaves: vertices of the largest closed rectangle
   int bb_gather;            // large FP32 fronts: the Schur update gathers the sons' boundary block
+  int syrk_simt;            // large FP32 fronts: SIMT Schur update instead of the tensor cores
   Profiler* prof;            // nullptr unless profiling
   double fl_chol, fl_trsm, fl_syrk, fl_rhs;   // algorithmic flops of this launch (whole batch)
 };
