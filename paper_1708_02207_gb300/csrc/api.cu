@@ -176,10 +176,7 @@ int gather_max_m() {
   static const int v = env_int("HDD_GATHER_MAX_M", 0);
   return v;
 }
-int gather_small() {
-  static const int v = env_int("HDD_GATHER_SMALL", 0);
-  return v;
-}
+
 
 bool legacy_fronts() {
   static const bool on = [] {
@@ -249,9 +246,7 @@ cudaError_t run_upsweep(const hdd::Plan& p, int batch, void* ws, const hdd::Rhs&
         case 0: e = legacy_fronts() ? hdd::launch_front_warp<double>(a, st)
                                     : hdd::launch_front_group<double>(a, hdd::kProfFrontWarp, st); break;
         case 1: e = legacy_fronts() ? hdd::launch_front_small<double>(a, st)
-                                    : hdd::launch_front_group<double>(a, hdd::kProfFrontSmall, st,
-                                                                      h > 0 && li.max_m >= gather_small() &&
-                                                                          gather_small() > 0); break;
+                                    : hdd::launch_front_group<double>(a, hdd::kProfFrontSmall, st); break;
         case 2:
           e = (h > 0 && li.max_m <= gather_max_m() &&
                hdd::front_group_smem(li.max_nf, li.max_m, li.max_rect, true, 8) <= 227 * 1024)
@@ -261,9 +256,7 @@ cudaError_t run_upsweep(const hdd::Plan& p, int batch, void* ws, const hdd::Rhs&
         case 3: e = legacy_fronts() ? hdd::launch_front_warp<float>(a, st)
                                     : hdd::launch_front_group<float>(a, hdd::kProfFrontWarp, st); break;
         case 4: e = legacy_fronts() ? hdd::launch_front_small<float>(a, st)
-                                    : hdd::launch_front_group<float>(a, hdd::kProfFrontSmall, st,
-                                                                     h > 0 && li.max_m >= gather_small() &&
-                                                                         gather_small() > 0); break;
+                                    : hdd::launch_front_group<float>(a, hdd::kProfFrontSmall, st); break;
         case 5:
           e = (h > 0 && li.max_m <= gather_max_m() &&
                hdd::front_group_smem(li.max_nf, li.max_m, li.max_rect, true, 4) <= 227 * 1024)

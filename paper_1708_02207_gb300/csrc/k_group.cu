@@ -16,6 +16,8 @@
 //      L_Bg; y_g^T] to the factor store.
 // Barriers are per group (a warp barrier when W = 1), so the groups of a CTA
 // never wait for one another.
+#include <cstdlib>
+
 #include "launch.h"
 
 namespace hdd {
@@ -271,39 +273,7 @@ __global__ void __launch_bounds__(256) k_front_group(StepArgs a, int W, int ld, 
     int ti, tj;
     tile_of(t, nt, ti, tj);
     const int i0 = t0 + 4 * ti, j0 = t0 + 4 * tj;
-    T kb[4][4];   // boundary-block entries of the front
-    if (gather) {   // from the sons (Eq. block_equation4)
-      int x0[4], x1[4];
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const int r = i0 + q;
-        x0[q] = r < nf ? pos0[r] : -1;
-        x1[q] = r < nf ? pos1[r] : -1;
-      }
-#pragma unroll
-      for (int w = 0; w < 4; ++w) {
-        const int c = j0 + w;
-        const int q0 = (c < nf && c >= m) ? pos0[c] : -1, q1 = (c < nf && c >= m) ? pos1[c] : -1;
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          T v = (T)0;
-          if (i0 + q >= c) {
-            if (x0[q] >= 0 && q0 >= 0) v += son_at<T>(c0, a.arenas, sb32, sb64, x0[q], q0);
-            if (x1[q] >= 0 && q1 >= 0) v += son_at<T>(c1, a.arenas, sb32, sb64, x1[q], q1);
-          }
-          kb[q][w] = v;
-        }
-      }
-    } else {
-#pragma unroll
-      for (int w = 0; w < 4; ++w) {
-        T v[4];
-        ld4(K + (j0 + w) * ld + i0, v);
-#pragma unroll
-        for (int q = 0; q < 4; ++q) kb[q][w] = v[q];
-      }
-    }
-    T acc[4][4];   // L_Bg L_Bg^T, summed before it is subtracted
+    T acc[4][4];   // L_Bg L_Bg^T, summed before it is subtracted from the front's entries
 #pragma unroll
     for (int q = 0; q < 4; ++q)
 #pragma unroll
@@ -318,14 +288,38 @@ __global__ void __launch_bounds__(256) k_front_group(StepArgs a, int W, int ld, 
 #pragma unroll
         for (int w = 0; w < 4; ++w) acc[q][w] += x[q] * y[w];
     }
+    // the front's boundary-block entries: from shared memory, or (gather mode)
+    // from the sons (Eq. block_equation4)
+    int x0[4], x1[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int r = i0 + q;
+      x0[q] = (gather && r < nf) ? pos0[r] : -1;
+      x1[q] = (gather && r < nf) ? pos1[r] : -1;
+    }
 #pragma unroll
     for (int w = 0; w < 4; ++w) {
       const int c = j0 + w;
       if (c < m || c >= nf) continue;
+      T kv[4];
+      if (gather) {
+        const int q0 = pos0[c], q1 = pos1[c];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          T v = (T)0;
+          if (i0 + q >= c) {
+            if (x0[q] >= 0 && q0 >= 0) v += son_at<T>(c0, a.arenas, sb32, sb64, x0[q], q0);
+            if (x1[q] >= 0 && q1 >= 0) v += son_at<T>(c1, a.arenas, sb32, sb64, x1[q], q1);
+          }
+          kv[q] = v;
+        }
+      } else {
+        ld4(K + c * ld + i0, kv);
+      }
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
         const int r = i0 + q;
-        if (r >= c && r < nf) S[(c - m) * nb + (r - m)] = kb[q][w] - acc[q][w];
+        if (r >= c && r < nf) S[(c - m) * nb + (r - m)] = kv[q] - acc[q][w];
       }
     }
   }
@@ -333,9 +327,14 @@ __global__ void __launch_bounds__(256) k_front_group(StepArgs a, int W, int ld, 
 
 // Warps per front: enough that a group's rows and tiles keep its lanes busy,
 // few enough that several fronts share a CTA.
+static int env_or(const char* name, int dflt) {
+  const char* v = getenv(name);
+  return v && *v ? atoi(v) : dflt;
+}
 static int group_warps(int max_nf, bool fp64) {
-  if (max_nf <= 48) return 1;
-  if (max_nf <= 96) return 2;
+  static const int w1 = env_or("HDD_GW1", 48), w2 = env_or("HDD_GW2", 96);
+  if (max_nf <= w1) return 1;
+  if (max_nf <= w2) return 2;
   if (!fp64 || max_nf <= 128) return 4;
   return 8;
 }
