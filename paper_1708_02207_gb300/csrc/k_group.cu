@@ -332,7 +332,7 @@ static int env_or(const char* name, int dflt) {
   return v && *v ? atoi(v) : dflt;
 }
 static int group_warps(int max_nf, bool fp64) {
-  static const int w1 = env_or("HDD_GW1", 48), w2 = env_or("HDD_GW2", 96);
+  static const int w1 = env_or("HDD_GW1", 48), w2 = env_or("HDD_GW2", 64);
   if (max_nf <= w1) return 1;
   if (max_nf <= w2) return 2;
   if (!fp64 || max_nf <= 128) return 4;

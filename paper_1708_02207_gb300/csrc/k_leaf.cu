@@ -216,69 +216,73 @@ __global__ void __launch_bounds__(256) k_leaf_front(StepArgs a) {
 
 // Right-hand-side sweep at condensed leaves: y_g = G r_g, z_B,i = -w_i y_g[c_i]
 // (written to the start of the leaf's Schur block, where the father reads it).
+// One half-warp per (leaf, sample), lane r = interior row r.
 template <typename T>
 __global__ void __launch_bounds__(256) k_leaf_forward(const NodeDev* __restrict__ nodes,
                                                       const int32_t* __restrict__ maps,
                                                       const int32_t* __restrict__ list, int batch, Arenas A,
                                                       Rhs rhs) {
   const int node = list[blockIdx.x];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int s = blockIdx.y * 8 + warp;
-  if (s >= batch) return;
+  const int hw = threadIdx.x >> 4, r = threadIdx.x & 15;
+  const int s = blockIdx.y * kLeafSamples + hw;
+  const bool active = s < batch;   // both half-warps stay for the shuffles
+  const int ss = active ? s : 0;
   const NodeDev nd = nodes[node];
   const int m = nd.m, b = nd.b, nf = nd.nf;
   const int32_t* vid = maps + nd.map_off;
   const int32_t* cpl = vid + (nf - 1);
-  const T* F = leaf_F<T>(A, nd, s);
-  const T z = (lane < m) ? (T)rhs(s, vid[lane]) : (T)0;
+  const T* F = leaf_F<T>(A, nd, ss);
+  const T z = (r < m) ? (T)rhs(ss, vid[r]) : (T)0;
   T v = (T)0;
 #pragma unroll
   for (int j = 0; j < kLeafInvMax; ++j) {
-    const T zj = __shfl_sync(kAllLanes, z, j);
-    if (lane < m && j < m) v += F[lane >= j ? pk(lane, j, m) : pk(j, lane, m)] * zj;
+    const T zj = __shfl_sync(kAllLanes, z, j, 16);
+    if (r < m && j < m) v += F[r >= j ? pk(r, j, m) : pk(j, r, m)] * zj;
   }
-  if (lane < m) node_Y<T>(A, nd, s)[lane] = v;
-  T* S = leaf_S<T>(A, nd, s);
+  if (active && r < m) node_Y<T>(A, nd, s)[r] = v;
+  T* S = leaf_S<T>(A, nd, ss);
   const int g_elems = m * (m + 1) / 2;
-  for (int i0 = 0; i0 < b; i0 += 32) {
-    const int i = i0 + lane;
+  for (int i0 = 0; i0 < b; i0 += 16) {
+    const int i = i0 + r;
     const int ci = (i < b) ? cpl[i] : -1;
-    const T vc = __shfl_sync(kAllLanes, v, ci >= 0 ? ci : 0);
-    if (i < b) S[i] = (ci >= 0) ? -F[g_elems + i] * vc : (T)0;
+    const T vc = __shfl_sync(kAllLanes, v, ci >= 0 ? ci : 0, 16);
+    if (active && i < b) S[i] = (ci >= 0) ? -F[g_elems + i] * vc : (T)0;
   }
 }
 
-// Descent at condensed leaves: u_g = y_g - sum_i (w_i u_B,i) G[:, c_i].
+// Descent at condensed leaves: u_g = y_g - sum_i (w_i u_B,i) G[:, c_i].  One
+// half-warp per (leaf, sample).
 template <typename T>
 __global__ void __launch_bounds__(256) k_leaf_descent(const NodeDev* __restrict__ nodes,
                                                       const int32_t* __restrict__ maps,
                                                       const int32_t* __restrict__ list, int batch, Arenas A,
                                                       double* __restrict__ u, int64_t u_stride) {
   const int node = list[blockIdx.x];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int s = blockIdx.y * 8 + warp;
-  __shared__ T tw[8][kLeafInvMaxB + 1];
-  __shared__ int cw[8][kLeafInvMaxB + 1];
-  if (s >= batch) return;
+  const int hw = threadIdx.x >> 4, r = threadIdx.x & 15;
+  const int s = blockIdx.y * kLeafSamples + hw;
+  const bool active = s < batch;
+  const int ss = active ? s : 0;
+  __shared__ T tw[kLeafSamples][kLeafInvMaxB + 1];
+  __shared__ int cw[kLeafSamples][kLeafInvMaxB + 1];
   const NodeDev nd = nodes[node];
   const int m = nd.m, b = nd.b, nf = nd.nf;
   const int32_t* vid = maps + nd.map_off;
   const int32_t* cpl = vid + (nf - 1);
-  const T* F = leaf_F<T>(A, nd, s);
-  double* us = u + (int64_t)s * u_stride;
+  const T* F = leaf_F<T>(A, nd, ss);
+  double* us = u + (int64_t)ss * u_stride;
   const int g_elems = m * (m + 1) / 2;
-  for (int i = lane; i < b; i += 32) {
-    cw[warp][i] = cpl[i];
-    tw[warp][i] = F[g_elems + i] * (T)us[vid[m + i]];
+  for (int i = r; i < b; i += 16) {
+    cw[hw][i] = cpl[i];
+    tw[hw][i] = F[g_elems + i] * (T)us[vid[m + i]];
   }
   __syncwarp();
-  if (lane < m) {
-    T acc = node_Y<T>(A, nd, s)[lane];
+  if (r < m) {
+    T acc = node_Y<T>(A, nd, ss)[r];
     for (int i = 0; i < b; ++i) {
-      const int ci = cw[warp][i];
-      if (ci >= 0) acc -= tw[warp][i] * F[lane >= ci ? pk(lane, ci, m) : pk(ci, lane, m)];
+      const int ci = cw[hw][i];
+      if (ci >= 0) acc -= tw[hw][i] * F[r >= ci ? pk(r, ci, m) : pk(ci, r, m)];
     }
-    us[vid[lane]] = (double)acc;
+    if (active) us[vid[r]] = (double)acc;
   }
 }
 
@@ -296,14 +300,16 @@ template <typename T>
 cudaError_t launch_leaf_forward(const NodeDev* nodes, const int32_t* maps, const int32_t* list, int nlist, int batch,
                                 const Arenas& A, const Rhs& rhs, cudaStream_t st) {
   if (nlist == 0) return cudaSuccess;
-  k_leaf_forward<T><<<dim3(nlist, (batch + 7) / 8), 256, 0, st>>>(nodes, maps, list, batch, A, rhs);
+  k_leaf_forward<T><<<dim3(nlist, (batch + kLeafSamples - 1) / kLeafSamples), 256, 0, st>>>(nodes, maps, list, batch,
+                                                                                            A, rhs);
   return cudaGetLastError();
 }
 template <typename T>
 cudaError_t launch_leaf_descent(const NodeDev* nodes, const int32_t* maps, const int32_t* list, int nlist, int batch,
                                 const Arenas& A, double* u, int64_t u_stride, cudaStream_t st) {
   if (nlist == 0) return cudaSuccess;
-  k_leaf_descent<T><<<dim3(nlist, (batch + 7) / 8), 256, 0, st>>>(nodes, maps, list, batch, A, u, u_stride);
+  k_leaf_descent<T><<<dim3(nlist, (batch + kLeafSamples - 1) / kLeafSamples), 256, 0, st>>>(nodes, maps, list, batch,
+                                                                                            A, u, u_stride);
   return cudaGetLastError();
 }
 template cudaError_t launch_leaf_front<double>(const StepArgs&, cudaStream_t);
