@@ -558,104 +558,180 @@ __global__ void __launch_bounds__(256) k_potrf_warp(StepArgs a) {
   for (int r = 0; r < 32; ++r) G[lane * 32 + r] = (lane < m) ? ((r < m) ? w[r] : (T)0) : ((r == lane) ? (T)1 : (T)0);
 }
 
-// POTRF and TRSM of large fronts whose gamma block has at most 32 columns, one
-// CTA per (node, sample): warp 0 factors K_gg in registers (as k_potrf_warp)
-// and forms W = L^-1 in shared memory; every thread then takes boundary rows
-// (their gamma columns prefetched into registers meanwhile) and computes
-// L_Bg = K_Bg W^T row by row (x_c = sum_{l <= c} a_l W[c, l]), writing the
-// factor rows, y_g (bordered row) and, for FP32 fronts, the split TF32 tiles
-// of the tensor-core Schur update.
+// POTRF and TRSM of large fronts whose gamma block has at most 32 * NB columns
+// (NB = 1, 2), one CTA per (node, sample).  Diagonal 32 x 32 blocks are factored
+// by warp 0 in registers (pivot column by shuffles) and inverted in shared
+// memory (lane c solves L w = e_c); for NB = 2 the block below the first
+// diagonal block is L21 = A21 W11^T and the second diagonal block is factored
+// after A22 - L21 L21^T.  Every thread then takes boundary rows, their gamma
+// entries in registers, and applies the blocked substitution
+//   x_0 = a_0 W11^T,  x_1 = (a_1 - x_0 L21^T) W22^T
+// (the same arithmetic as k_potrf + k_trsm), writing the factor rows, y_g
+// (bordered row) and, for FP32 fronts, the split TF32 tiles of the
+// tensor-core Schur update.
+constexpr int kWs = 36;   // row stride of shared 32 x 32 blocks read four columns at a time
+
+// Cholesky of the 32 x 32 block held as rows (lane r: row r, entries c <= r; size
+// mb), its inverse into W (W[r][c] at W[r * kWs + c]); L itself into Ls.
 template <typename T>
-__global__ void __launch_bounds__(256, 2) k_chol_trsm32(StepArgs a) {
+__device__ __forceinline__ void warp_chol_inverse(T (&row)[32], int mb, T* Ls, T* W, T* dinv, bool& bad) {
   constexpr unsigned kAll = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int k = 0; k < 32; ++k) {
+    if (k < mb) {
+      T pk = __shfl_sync(kAll, row[k], k);
+      if (!(pk > (T)0) || !isfinite(pk)) {
+        bad = true;
+        pk = (T)1;
+      }
+      const T d = sqrt(pk), inv = (T)1 / d;
+      T lk = (lane == k) ? d : row[k] * inv;
+      if (lane < k) lk = (T)0;
+#pragma unroll
+      for (int j = k + 1; j < 32; ++j) {
+        const T lj = __shfl_sync(kAll, lk, j);
+        if (lane > k) row[j] -= lk * lj;
+      }
+      row[k] = lk;
+    }
+  }
+#pragma unroll
+  for (int c = 0; c < 32; ++c) Ls[lane * kWs + c] = row[c];
+  T diag = (T)1;
+#pragma unroll
+  for (int c = 0; c < 32; ++c)
+    if (c == lane && c < mb) diag = row[c];
+  dinv[lane] = (T)1 / diag;
+  __syncwarp();
+  T w[32];
+#pragma unroll
+  for (int r = 0; r < 32; ++r) {
+    T acc = (lane == r) ? (T)1 : (T)0;
+#pragma unroll
+    for (int l = 0; l < r; ++l) acc -= Ls[r * kWs + l] * w[l];
+    w[r] = (r < mb) ? acc * dinv[r] : (T)0;
+    W[r * kWs + lane] = (lane < mb) ? w[r] : (T)0;
+  }
+}
+
+// x <- x W^T in place for the 32 entries x[o .. o+31] (W lower, last column first)
+template <typename T, int O, int NX>
+__device__ __forceinline__ void apply_inverse(T (&x)[NX], const T* W) {
+#pragma unroll
+  for (int c = 31; c >= 0; --c) {
+    T acc = (T)0;
+#pragma unroll
+    for (int l4 = 0; l4 <= c; l4 += 4) {
+      T wv[4];
+      load4(W + c * kWs + l4, wv);
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+        if (l4 + q <= c) acc += x[O + l4 + q] * wv[q];
+    }
+    x[O + c] = acc;
+  }
+}
+
+template <typename T, int NB>
+__global__ void __launch_bounds__(256, 2) k_chol_trsm(StepArgs a) {
   const int node = a.list[blockIdx.x];
   const int s = blockIdx.y;
   const NodeDev nd = a.nodes[node];
   const int nf = nd.nf, m = nd.m, b = nd.b;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   T* A = node_F<T>(a.arenas, nd, s);
-  constexpr int kW = 36;   // row stride of W: 16-byte aligned groups of four columns
-  __shared__ __align__(16) T Wt[32 * kW];
-  __shared__ T Ls[32 * 33], dinv[32];
-  const int r_first = m + (int)threadIdx.x;
+  __shared__ __align__(16) T Wt[NB][32 * kWs];
+  __shared__ __align__(16) T Ls[32 * kWs];
+  __shared__ __align__(16) T L21[NB > 1 ? 32 * kWs : 1];
+  __shared__ T dinv[32];
+  const int mb0 = min(32, m), mb1 = m - mb0;
+  bool bad = false;
   if (warp == 0) {
     T row[32];
 #pragma unroll
-    for (int c = 0; c < 32; ++c) row[c] = (c < m && lane < m && c <= lane) ? A[(int64_t)c * nf + lane] : (T)0;
-    bool bad = false;
-#pragma unroll
-    for (int k = 0; k < 32; ++k) {
-      if (k < m) {
-        T pk = __shfl_sync(kAll, row[k], k);
-        if (!(pk > (T)0) || !isfinite(pk)) {
-          bad = true;
-          pk = (T)1;
-        }
-        const T d = sqrt(pk), inv = (T)1 / d;
-        T lk = (lane == k) ? d : row[k] * inv;
-        if (lane < k) lk = (T)0;
-#pragma unroll
-        for (int j = k + 1; j < 32; ++j) {
-          const T lj = __shfl_sync(kAll, lk, j);
-          if (lane > k) row[j] -= lk * lj;
-        }
-        row[k] = lk;
-      }
-    }
-    if (bad && lane == 0) flag_status(a.status, s, -HDD_ENOTSPD, node);
-#pragma unroll
-    for (int c = 0; c < 32; ++c) {
-      if (c < m && lane < m && c <= lane) A[(int64_t)c * nf + lane] = row[c];
-      Ls[lane * 33 + c] = row[c];
-    }
-    T diag = (T)1;
+    for (int c = 0; c < 32; ++c) row[c] = (c < mb0 && lane < mb0 && c <= lane) ? A[(int64_t)c * nf + lane] : (T)0;
+    warp_chol_inverse<T>(row, mb0, Ls, Wt[0], dinv, bad);
 #pragma unroll
     for (int c = 0; c < 32; ++c)
-      if (c == lane && c < m) diag = row[c];
-    dinv[lane] = (T)1 / diag;
-    __syncwarp();
-    // lane c solves L w = e_c; W[r, c] stored at Wt[r * 33 + c]
-    T w[32];
-#pragma unroll
-    for (int r = 0; r < 32; ++r) {
-      T acc = (lane == r) ? (T)1 : (T)0;
-#pragma unroll
-      for (int l = 0; l < r; ++l) acc -= Ls[r * 33 + l] * w[l];
-      w[r] = (r < m) ? acc * dinv[r] : (T)0;
-      Wt[r * kW + lane] = (lane < m) ? w[r] : (T)0;
-    }
+      if (c < mb0 && lane < mb0 && c <= lane) A[(int64_t)c * nf + lane] = row[c];
   }
   __syncthreads();
+  if (NB > 1) {
+    // L21 = A21 W11^T (rows 32..m-1), by warp 1
+    if (warp == 1) {
+      T x[32];
+#pragma unroll
+      for (int c = 0; c < 32; ++c) x[c] = (lane < mb1) ? A[(int64_t)c * nf + 32 + lane] : (T)0;
+      apply_inverse<T, 0, 32>(x, Wt[0]);
+#pragma unroll
+      for (int c = 0; c < 32; ++c) {
+        L21[lane * kWs + c] = (lane < mb1) ? x[c] : (T)0;
+        if (lane < mb1) A[(int64_t)c * nf + 32 + lane] = x[c];
+      }
+    }
+    __syncthreads();
+    // second diagonal block: A22 - L21 L21^T, factored by warp 0
+    if (warp == 0) {
+      T row[32];
+#pragma unroll
+      for (int c = 0; c < 32; ++c) {
+        T v = (T)0;
+        if (c < mb1 && lane < mb1 && c <= lane) {
+          T dot = (T)0;
+#pragma unroll
+          for (int l4 = 0; l4 < 32; l4 += 4) {
+            T p[4], q[4];
+            load4(L21 + lane * kWs + l4, p);
+            load4(L21 + c * kWs + l4, q);
+#pragma unroll
+            for (int t = 0; t < 4; ++t) dot += p[t] * q[t];
+          }
+          v = A[(int64_t)(32 + c) * nf + 32 + lane] - dot;
+        }
+        row[c] = v;
+      }
+      warp_chol_inverse<T>(row, mb1, Ls, Wt[NB - 1], dinv, bad);
+#pragma unroll
+      for (int c = 0; c < 32; ++c)
+        if (c < mb1 && lane < mb1 && c <= lane) A[(int64_t)(32 + c) * nf + 32 + lane] = row[c];
+    }
+    __syncthreads();
+  }
+  if (bad && lane == 0) flag_status(a.status, s, -HDD_ENOTSPD, node);
   const bool tc = std::is_same<T, float>::value && nd.tc_off >= 0 && b > 0;
   const int nchunks = (m + kTcChunk - 1) / kTcChunk;
   unsigned char* tcb = tc ? a.arenas.tc + (int64_t)s * a.arenas.tc_stride + nd.tc_off : nullptr;
   const int tc_rows = ((b + kTcTile - 1) / kTcTile) * kTcTile;   // boundary rows, zero-filled to the tile end
-  for (int r = r_first; r < m + max(tc ? tc_rows : 0, nf - m); r += blockDim.x) {
+  for (int r = m + (int)threadIdx.x; r < m + max(tc ? tc_rows : 0, nf - m); r += blockDim.x) {
     const bool real = r < nf;
-    T y[32];   // the row's gamma entries, overwritten by its factor row (last column first)
+    T y[32 * NB];   // the row's gamma entries, overwritten by its factor row
 #pragma unroll
-    for (int c = 0; c < 32; ++c) y[c] = (c < m && real) ? A[(int64_t)c * nf + r] : (T)0;
+    for (int c = 0; c < 32 * NB; ++c) y[c] = (c < m && real) ? A[(int64_t)c * nf + r] : (T)0;
+    apply_inverse<T, 0, 32 * NB>(y, Wt[0]);
+    if (NB > 1) {
 #pragma unroll
-    for (int c = 31; c >= 0; --c) {
-      T acc = (T)0;
+      for (int j = 0; j < 32; ++j) {   // a_1 - x_0 L21^T
+        T dot = (T)0;
 #pragma unroll
-      for (int l4 = 0; l4 <= c; l4 += 4) {   // W is lower: entries l > c of row c are zero
-        T wv[4];
-        load4(Wt + c * kW + l4, wv);
+        for (int l4 = 0; l4 < 32; l4 += 4) {
+          T q[4];
+          load4(L21 + j * kWs + l4, q);
 #pragma unroll
-        for (int q = 0; q < 4; ++q)
-          if (l4 + q <= c) acc += y[l4 + q] * wv[q];
+          for (int t = 0; t < 4; ++t) dot += y[l4 + t] * q[t];
+        }
+        y[(NB - 1) * 32 + j] -= dot;
       }
-      y[c] = (c < m) ? acc : (T)0;
+      apply_inverse<T, (NB - 1) * 32, 32 * NB>(y, Wt[NB - 1]);
     }
     if (real) {
 #pragma unroll
-      for (int c = 0; c < 32; ++c)
+      for (int c = 0; c < 32 * NB; ++c)
         if (c < m) A[(int64_t)c * nf + r] = y[c];
       if (r == nf - 1) {
         T* Y = node_Y<T>(a.arenas, nd, s);
 #pragma unroll
-        for (int c = 0; c < 32; ++c)
+        for (int c = 0; c < 32 * NB; ++c)
           if (c < m) Y[c] = y[c];
       }
     }
@@ -664,13 +740,13 @@ __global__ void __launch_bounds__(256, 2) k_chol_trsm32(StepArgs a) {
       const int Tt = br / kTcTile, tr = br % kTcTile;
       const bool zero = br >= b;
 #pragma unroll
-      for (int c8 = 0; c8 < 4; ++c8) {
+      for (int c8 = 0; c8 < 4 * NB; ++c8) {
         if (c8 >= nchunks) break;
 #pragma unroll
         for (int kq = 0; kq < 2; ++kq) {
           float v[4];
 #pragma unroll
-          for (int q = 0; q < 4; ++q) v[q] = zero ? 0.0f : (float)y[c8 * 8 + 4 * kq + q];
+          for (int q = 0; q < 4; ++q) v[q] = (zero || c8 * 8 + 4 * kq + q >= m) ? 0.0f : (float)y[c8 * 8 + 4 * kq + q];
           float4 hi, lo;
           hi.x = tf32_rna(v[0]); hi.y = tf32_rna(v[1]); hi.z = tf32_rna(v[2]); hi.w = tf32_rna(v[3]);
           lo.x = tf32_rna(v[0] - hi.x); lo.y = tf32_rna(v[1] - hi.y);
@@ -906,9 +982,13 @@ cudaError_t launch_front_large(const StepArgs& a, cudaStream_t st) {
     if (a.prof) a.prof->end(st);
   }
   const size_t rows_smem = (size_t)min(a.max_m, SmemCap<T>::rows);
-  if (a.max_m <= 32) {   // POTRF and TRSM in one kernel
+  const bool fused_pt = a.max_m <= 32 || (sizeof(T) == 4 && a.max_m <= 64);
+  if (fused_pt) {   // POTRF and TRSM in one kernel (two 32-column blocks in FP32 only: registers)
     if (a.prof) a.prof->begin(kProfCholTrsm, a.fl_chol + a.fl_trsm, st);
-    k_chol_trsm32<T><<<dim3(a.nlist, a.batch), 256, 0, st>>>(a);
+    if (a.max_m <= 32)
+      k_chol_trsm<T, 1><<<dim3(a.nlist, a.batch), 256, 0, st>>>(a);
+    else
+      k_chol_trsm<T, 2><<<dim3(a.nlist, a.batch), 256, 0, st>>>(a);
     if (a.prof) a.prof->end(st);
   } else {
     const size_t smem = (rows_smem * kPanel + kPanel + 32 * 33) * sizeof(T);
@@ -916,7 +996,7 @@ cudaError_t launch_front_large(const StepArgs& a, cudaStream_t st) {
     k_potrf<T><<<dim3(a.nlist, a.batch), 256, smem, st>>>(a);
     if (a.prof) a.prof->end(st);
   }
-  if (a.max_m > 32) {
+  if (!fused_pt) {
     constexpr int R = TrsmShape<T>::rows;
     const size_t xrows = (size_t)min(a.max_m, TrsmShape<T>::cap);
     const size_t smem = (xrows * R + 32 * 33 + 3 + 32 * 64) * sizeof(T) + 16;
