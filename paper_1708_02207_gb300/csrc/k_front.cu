@@ -634,45 +634,51 @@ __device__ __forceinline__ void apply_inverse(T (&x)[NX], const T* W) {
 }
 
 template <typename T, int NB>
-__global__ void __launch_bounds__(256, 2) k_chol_trsm(StepArgs a) {
+struct CholTrsmSmem {   // per warp (sample)
+  T W[NB][32 * kWs];
+  T Ls[32 * kWs];
+  T L21[NB > 1 ? 32 * kWs : 4];
+  T dinv[32];
+};
+constexpr int kCholTrsmWarps = 4;   // samples of one node per CTA, one warp each
+
+template <typename T, int NB>
+__global__ void __launch_bounds__(32 * kCholTrsmWarps, 3) k_chol_trsm(StepArgs a) {
   const int node = a.list[blockIdx.x];
-  const int s = blockIdx.y;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int s = blockIdx.y * kCholTrsmWarps + warp;
+  if (s >= a.batch) return;
   const NodeDev nd = a.nodes[node];
   const int nf = nd.nf, m = nd.m, b = nd.b;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   T* A = node_F<T>(a.arenas, nd, s);
-  __shared__ __align__(16) T Wt[NB][32 * kWs];
-  __shared__ __align__(16) T Ls[32 * kWs];
-  __shared__ __align__(16) T L21[NB > 1 ? 32 * kWs : 1];
-  __shared__ T dinv[32];
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  CholTrsmSmem<T, NB>& sm = reinterpret_cast<CholTrsmSmem<T, NB>*>(smem_raw)[warp];
   const int mb0 = min(32, m), mb1 = m - mb0;
   bool bad = false;
-  if (warp == 0) {
+  {
     T row[32];
 #pragma unroll
     for (int c = 0; c < 32; ++c) row[c] = (c < mb0 && lane < mb0 && c <= lane) ? A[(int64_t)c * nf + lane] : (T)0;
-    warp_chol_inverse<T>(row, mb0, Ls, Wt[0], dinv, bad);
+    warp_chol_inverse<T>(row, mb0, sm.Ls, sm.W[0], sm.dinv, bad);
 #pragma unroll
     for (int c = 0; c < 32; ++c)
       if (c < mb0 && lane < mb0 && c <= lane) A[(int64_t)c * nf + lane] = row[c];
   }
-  __syncthreads();
+  __syncwarp();
   if (NB > 1) {
-    // L21 = A21 W11^T (rows 32..m-1), by warp 1
-    if (warp == 1) {
+    {   // L21 = A21 W11^T (rows 32..m-1, lane = row)
       T x[32];
 #pragma unroll
       for (int c = 0; c < 32; ++c) x[c] = (lane < mb1) ? A[(int64_t)c * nf + 32 + lane] : (T)0;
-      apply_inverse<T, 0, 32>(x, Wt[0]);
+      apply_inverse<T, 0, 32>(x, sm.W[0]);
 #pragma unroll
       for (int c = 0; c < 32; ++c) {
-        L21[lane * kWs + c] = (lane < mb1) ? x[c] : (T)0;
+        sm.L21[lane * kWs + c] = (lane < mb1) ? x[c] : (T)0;
         if (lane < mb1) A[(int64_t)c * nf + 32 + lane] = x[c];
       }
     }
-    __syncthreads();
-    // second diagonal block: A22 - L21 L21^T, factored by warp 0
-    if (warp == 0) {
+    __syncwarp();
+    {   // second diagonal block: A22 - L21 L21^T
       T row[32];
 #pragma unroll
       for (int c = 0; c < 32; ++c) {
@@ -682,8 +688,8 @@ __global__ void __launch_bounds__(256, 2) k_chol_trsm(StepArgs a) {
 #pragma unroll
           for (int l4 = 0; l4 < 32; l4 += 4) {
             T p[4], q[4];
-            load4(L21 + lane * kWs + l4, p);
-            load4(L21 + c * kWs + l4, q);
+            load4(sm.L21 + lane * kWs + l4, p);
+            load4(sm.L21 + c * kWs + l4, q);
 #pragma unroll
             for (int t = 0; t < 4; ++t) dot += p[t] * q[t];
           }
@@ -691,24 +697,25 @@ __global__ void __launch_bounds__(256, 2) k_chol_trsm(StepArgs a) {
         }
         row[c] = v;
       }
-      warp_chol_inverse<T>(row, mb1, Ls, Wt[NB - 1], dinv, bad);
+      __syncwarp();
+      warp_chol_inverse<T>(row, mb1, sm.Ls, sm.W[NB - 1], sm.dinv, bad);
 #pragma unroll
       for (int c = 0; c < 32; ++c)
         if (c < mb1 && lane < mb1 && c <= lane) A[(int64_t)(32 + c) * nf + 32 + lane] = row[c];
     }
-    __syncthreads();
+    __syncwarp();
   }
   if (bad && lane == 0) flag_status(a.status, s, -HDD_ENOTSPD, node);
   const bool tc = std::is_same<T, float>::value && nd.tc_off >= 0 && b > 0;
   const int nchunks = (m + kTcChunk - 1) / kTcChunk;
   unsigned char* tcb = tc ? a.arenas.tc + (int64_t)s * a.arenas.tc_stride + nd.tc_off : nullptr;
   const int tc_rows = ((b + kTcTile - 1) / kTcTile) * kTcTile;   // boundary rows, zero-filled to the tile end
-  for (int r = m + (int)threadIdx.x; r < m + max(tc ? tc_rows : 0, nf - m); r += blockDim.x) {
+  for (int r = m + lane; r < m + max(tc ? tc_rows : 0, nf - m); r += 32) {
     const bool real = r < nf;
     T y[32 * NB];   // the row's gamma entries, overwritten by its factor row
 #pragma unroll
     for (int c = 0; c < 32 * NB; ++c) y[c] = (c < m && real) ? A[(int64_t)c * nf + r] : (T)0;
-    apply_inverse<T, 0, 32 * NB>(y, Wt[0]);
+    apply_inverse<T, 0, 32 * NB>(y, sm.W[0]);
     if (NB > 1) {
 #pragma unroll
       for (int j = 0; j < 32; ++j) {   // a_1 - x_0 L21^T
@@ -716,13 +723,13 @@ __global__ void __launch_bounds__(256, 2) k_chol_trsm(StepArgs a) {
 #pragma unroll
         for (int l4 = 0; l4 < 32; l4 += 4) {
           T q[4];
-          load4(L21 + j * kWs + l4, q);
+          load4(sm.L21 + j * kWs + l4, q);
 #pragma unroll
           for (int t = 0; t < 4; ++t) dot += y[l4 + t] * q[t];
         }
         y[(NB - 1) * 32 + j] -= dot;
       }
-      apply_inverse<T, (NB - 1) * 32, 32 * NB>(y, Wt[NB - 1]);
+      apply_inverse<T, (NB - 1) * 32, 32 * NB>(y, sm.W[NB - 1]);
     }
     if (real) {
 #pragma unroll
@@ -985,10 +992,11 @@ cudaError_t launch_front_large(const StepArgs& a, cudaStream_t st) {
   const bool fused_pt = a.max_m <= 32 || (sizeof(T) == 4 && a.max_m <= 64);
   if (fused_pt) {   // POTRF and TRSM in one kernel (two 32-column blocks in FP32 only: registers)
     if (a.prof) a.prof->begin(kProfCholTrsm, a.fl_chol + a.fl_trsm, st);
+    const dim3 grid(a.nlist, (a.batch + kCholTrsmWarps - 1) / kCholTrsmWarps);
     if (a.max_m <= 32)
-      k_chol_trsm<T, 1><<<dim3(a.nlist, a.batch), 256, 0, st>>>(a);
+      k_chol_trsm<T, 1><<<grid, 32 * kCholTrsmWarps, kCholTrsmWarps * sizeof(CholTrsmSmem<T, 1>), st>>>(a);
     else
-      k_chol_trsm<T, 2><<<dim3(a.nlist, a.batch), 256, 0, st>>>(a);
+      k_chol_trsm<T, 2><<<grid, 32 * kCholTrsmWarps, kCholTrsmWarps * sizeof(CholTrsmSmem<T, 2>), st>>>(a);
     if (a.prof) a.prof->end(st);
   } else {
     const size_t smem = (rows_smem * kPanel + kPanel + 32 * 33) * sizeof(T);
@@ -1040,6 +1048,9 @@ cudaError_t configure_front_kernels() {
   if ((e = cudaFuncSetAttribute(k_potrf<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
   if ((e = cudaFuncSetAttribute(k_potrf<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
   if ((e = cudaFuncSetAttribute(k_potrf_warp<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
+  if ((e = cudaFuncSetAttribute(k_chol_trsm<float, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
+  if ((e = cudaFuncSetAttribute(k_chol_trsm<float, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
+  if ((e = cudaFuncSetAttribute(k_chol_trsm<double, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
   if ((e = cudaFuncSetAttribute(k_trsm<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
   if ((e = cudaFuncSetAttribute(k_trsm<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
   return cudaSuccess;
