@@ -308,8 +308,7 @@ def run_hdd(args, cfg):
         "descent": (n_desc_all * info["bytes_descent_all"] + n_desc_vis * info["bytes_descent_visited"]) * B,
         "residual": n_res * info["bytes_residual"] * B,
     }
-    groups = {"large_fronts": ("front_gather", "front_fill", "potrf", "chol_trsm", "trsm", "syrk_simt", "syrk_tc",
-                               "syrk_rhs")}
+    groups = {"large_fronts": ("front_fill", "potrf", "chol_trsm", "trsm", "syrk_simt", "syrk_tc", "syrk_rhs")}
 
     def fam_roof(name, members):
         ms = sum(kernels[m]["ms_per_step"] for m in members if m in kernels)

@@ -154,38 +154,6 @@ struct ProfScope {
 
 // Previous front kernels for fronts of up to kSmallMax rows (register rows per
 // warp / one CTA per front), selected with HDD_LEGACY_FRONTS=1 for comparison.
-int env_int(const char* name, int dflt) {
-  const char* v = getenv(name);
-  return v && *v ? atoi(v) : dflt;
-}
-int sweep_cta_min_m() {
-  static const int v = env_int("HDD_SWEEP_CTA_MIN_M", kSweepCtaMinM);
-  return v;
-}
-int bb_gather() {
-  static const int v = env_int("HDD_BB_GATHER", 1);
-  return v;
-}
-int fp32_syrk_simt() {
-  static const int v = env_int("HDD_FP32_SYRK_SIMT", 0);
-  return v;
-}
-// Large fronts (heights above the leaves) whose gamma block has at most this
-// many columns run on the grouped front kernel with the sons' entries gathered.
-int gather_max_m() {
-  static const int v = env_int("HDD_GATHER_MAX_M", 0);
-  return v;
-}
-
-
-bool legacy_fronts() {
-  static const bool on = [] {
-    const char* v = getenv("HDD_LEGACY_FRONTS");
-    return v && v[0] == '1';
-  }();
-  return on;
-}
-
 // One pass of "Leaves to Root" over all heights with the given right-hand side.
 cudaError_t run_upsweep(const hdd::Plan& p, int batch, void* ws, const hdd::Rhs& rhs, cudaStream_t st,
                         hdd::Profiler* prof) {
@@ -235,34 +203,18 @@ cudaError_t run_upsweep(const hdd::Plan& p, int batch, void* ws, const hdd::Rhs&
       a.max_m = li.max_m;
       a.max_b = li.max_b;
       a.max_rect = li.max_rect;
-      a.bb_gather = bb_gather();
-      a.syrk_simt = fp32_syrk_simt();
       a.fl_chol = li.fl_chol * batch;
       a.fl_trsm = li.fl_trsm * batch;
       a.fl_syrk = li.fl_syrk * batch;
       a.fl_rhs = li.fl_rhs * batch;
       cudaError_t e;
       switch (kind) {
-        case 0: e = legacy_fronts() ? hdd::launch_front_warp<double>(a, st)
-                                    : hdd::launch_front_group<double>(a, hdd::kProfFrontWarp, st); break;
-        case 1: e = legacy_fronts() ? hdd::launch_front_small<double>(a, st)
-                                    : hdd::launch_front_group<double>(a, hdd::kProfFrontSmall, st); break;
-        case 2:
-          e = (h > 0 && li.max_m <= gather_max_m() &&
-               hdd::front_group_smem(li.max_nf, li.max_m, li.max_rect, true, 8) <= 227 * 1024)
-                  ? hdd::launch_front_group<double>(a, hdd::kProfFrontGather, st, true)
-                  : hdd::launch_front_large<double>(a, st);
-          break;
-        case 3: e = legacy_fronts() ? hdd::launch_front_warp<float>(a, st)
-                                    : hdd::launch_front_group<float>(a, hdd::kProfFrontWarp, st); break;
-        case 4: e = legacy_fronts() ? hdd::launch_front_small<float>(a, st)
-                                    : hdd::launch_front_group<float>(a, hdd::kProfFrontSmall, st); break;
-        case 5:
-          e = (h > 0 && li.max_m <= gather_max_m() &&
-               hdd::front_group_smem(li.max_nf, li.max_m, li.max_rect, true, 4) <= 227 * 1024)
-                  ? hdd::launch_front_group<float>(a, hdd::kProfFrontGather, st, true)
-                  : hdd::launch_front_large<float>(a, st);
-          break;
+        case 0: e = hdd::launch_front_group<double>(a, hdd::kProfFrontWarp, st); break;
+        case 1: e = hdd::launch_front_group<double>(a, hdd::kProfFrontSmall, st); break;
+        case 2: e = hdd::launch_front_large<double>(a, st); break;
+        case 3: e = hdd::launch_front_group<float>(a, hdd::kProfFrontWarp, st); break;
+        case 4: e = hdd::launch_front_group<float>(a, hdd::kProfFrontSmall, st); break;
+        case 5: e = hdd::launch_front_large<float>(a, st); break;
         case 6: e = hdd::launch_leaf_front<double>(a, st); break;
         default: e = hdd::launch_leaf_front<float>(a, st); break;
       }
@@ -295,7 +247,7 @@ cudaError_t run_descent(const hdd::Plan& p, int batch, void* ws, const std::vect
     const bool fp64 = p.nodes[p.list_data[li.off]].fp64;
     // nodes with long interfaces: one CTA per (node, sample), blocked back substitution;
     // otherwise one warp per (node, sample)
-    const bool cta = li.max_m >= sweep_cta_min_m();
+    const bool cta = li.max_m >= kSweepCtaMinM;
     ProfScope ps(prof, hdd::kProfDescent, 0.0, st);
     cudaError_t e;
     if (li.max_nf <= hdd::kTinyMax)
@@ -334,7 +286,7 @@ cudaError_t run_forward(const hdd::Plan& p, int batch, void* ws, const hdd::Rhs&
         if (e != cudaSuccess) return e;
         continue;
       }
-      const bool cta = li.max_m >= sweep_cta_min_m();
+      const bool cta = li.max_m >= kSweepCtaMinM;
       ProfScope ps(prof, hdd::kProfForward, 0.0, st);
       cudaError_t e;
       if (li.max_nf <= hdd::kTinyMax)
@@ -646,8 +598,7 @@ hdd_status hdd_profile_end(hdd_plan_t plan, hdd_kernel_stat_t* stats, int32_t ma
   pr->on = false;
   static const char* names[hdd::kProfCount] = {"kappa", "front_warp", "front_small", "front_fill", "potrf", "trsm",
                                                 "syrk_simt", "syrk_tc", "syrk_rhs", "forward", "descent",
-                                                "residual", "misc", "subtree", "leaf_front", "chol_trsm",
-                                                "front_gather"};
+                                                "residual", "misc", "subtree", "leaf_front", "chol_trsm"};
   int launches[hdd::kProfCount] = {};
   double ms[hdd::kProfCount] = {}, fl[hdd::kProfCount] = {};
   DeviceScope ds(plan->p.device);

@@ -1,4 +1,4 @@
-// Front kernels of the upsweep ("Leaves to Root", Sec. 3.4).
+// Large-front kernels of the upsweep ("Leaves to Root", Sec. 3.4).
 //
 // A front of node omega is the matrix of the local system over
 // [gamma (m rows), boundary unknowns (b rows), right-hand side (1 row)]:
@@ -31,57 +31,7 @@ template <> __device__ __forceinline__ float* node_S<float>(const Arenas& A, con
   return A.s32 + (int64_t)s * A.s32_stride + nd.s_off;
 }
 
-template <typename T>
-__device__ __forceinline__ T front_entry(int r, int c, int s, int node, const NodeDev& nd, const NodeDev* nodes,
-                                         const int32_t* map, const T* kap, int N, const Rhs& rhs,
-                                         const Arenas& A) {
-  if (nd.leaf) return leaf_entry<T>(r, c, s, nd, map, kap, N, rhs);
-  return father_entry<T>(r, c, s, nd, map, nodes[nd.child0], nodes[nd.child1], A, rhs);
-}
-
-// ---------------------------------------------------------------------------
-// Fronts of 33..kSmallMax rows: the whole front lives in shared memory
-// (column-major, ld nf), one CTA per (node, sample).  Fathers are assembled by
-// scattering each son's lower Schur triangle (read column by column, coalesced)
-// through the son's up map; sons one after the other, then the gamma loads.
-// Partial Cholesky: per column k, scale column k, then one warp per trailing
-// column j updates rows j..nf-1 (contiguous, conflict-free) with l_j.
-template <typename T>
-__device__ __forceinline__ void scatter_son(T* K, int ld, const NodeDev& ch, const int32_t* maps, const Arenas& A,
-                                            int s, int* ups) {
-  const int ldc = ch.b + 1;
-  const int32_t* up = maps + ch.up_off;
-  for (int i = threadIdx.x; i < ldc; i += blockDim.x) ups[i] = up[i];
-  __syncthreads();
-  const int64_t base = (int64_t)s * (ch.fp64 ? A.s64_stride : A.s32_stride) + ch.s_off;
-  const int total = ldc * ldc;
-  // four entries per thread and pass: all loads first (in flight together), then the adds
-  for (int i0 = threadIdx.x; i0 < total; i0 += 4 * blockDim.x) {
-    T v[4];
-    int rr[4], cc[4];
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const int idx = i0 + q * blockDim.x;
-      const int c = idx / ldc, r = idx - c * ldc;
-      rr[q] = r;
-      cc[q] = c;
-      const bool use = idx < total && r >= c;
-      v[q] = use ? (ch.fp64 ? (T)A.s64[base + idx] : (T)A.s32[base + idx]) : (T)0;
-    }
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const int idx = i0 + q * blockDim.x;
-      if (idx < total && rr[q] >= cc[q]) {
-        const int pr = ups[rr[q]], pc = ups[cc[q]];
-        K[min(pr, pc) * ld + max(pr, pc)] += v[q];
-      }
-    }
-  }
-}
-
-// POTRF of K_gg (m x m, in F with ld nf): one CTA per (node, sample), blocked
-// right-looking with 32-column panels staged in shared memory; the trailing
-// update uses 4 x 4 register tiles over the lower triangle.
+// Panel width of the blocked POTRF of large fronts.
 constexpr int kPanel = 32;
 
 __device__ __forceinline__ void tri_index(int idx, int& ti, int& tj) {
@@ -92,9 +42,6 @@ __device__ __forceinline__ void tri_index(int idx, int& ti, int& tj) {
   tj = idx - t * (t + 1) / 2;
 }
 
-// Panel width of the blocked factorisation of shared-memory fronts.
-constexpr int kSmallPanel = 8;
-
 // Four consecutive values through 16-byte shared-memory accesses.
 __device__ __forceinline__ void load4(const float* p, float (&v)[4]) {
   const float4 t = *reinterpret_cast<const float4*>(p);
@@ -103,145 +50,6 @@ __device__ __forceinline__ void load4(const float* p, float (&v)[4]) {
 __device__ __forceinline__ void load4(const double* p, double (&v)[4]) {
   const double2 a = *reinterpret_cast<const double2*>(p), b = *reinterpret_cast<const double2*>(p + 2);
   v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
-}
-__device__ __forceinline__ void store4(float* p, const float (&v)[4]) {
-  *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
-}
-__device__ __forceinline__ void store4(double* p, const double (&v)[4]) {
-  *reinterpret_cast<double2*>(p) = make_double2(v[0], v[1]);
-  *reinterpret_cast<double2*>(p + 2) = make_double2(v[2], v[3]);
-}
-
-// Leading dimension of a shared-memory front: a multiple of 4, congruent to 4
-// modulo 8, so that column-varying accesses spread over 8 banks.
-__host__ __device__ __forceinline__ int front_ld(int nf) {
-  int ld = (nf + 3) & ~3;
-  if ((ld & 7) == 0) ld += 4;
-  return ld;
-}
-
-template <typename T>
-__global__ void __launch_bounds__(512) k_front_small(StepArgs a) {
-  const int node = a.list[blockIdx.x];
-  const int s = blockIdx.y;
-  const NodeDev nd = a.nodes[node];
-  const int nf = nd.nf, m = nd.m, ld = front_ld(nf);
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* K = reinterpret_cast<T*>(smem_raw);
-  const int32_t* map = a.maps + nd.map_off;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarp = blockDim.x >> 5;
-
-  if (nd.leaf) {
-    const T* kap = kappa_of<T>(a.kappa, a.kappa32) + (int64_t)s * a.kap_stride;
-    for (int c = warp; c < nf; c += nwarp)
-      for (int r = lane; r < nf; r += 32)
-        K[c * ld + r] = (r >= c) ? leaf_entry<T>(r, c, s, nd, map, kap, a.N, a.rhs) : (T)0;
-  } else {
-    int* ups = reinterpret_cast<int*>(K + (size_t)nf * ld + 16);
-    for (int idx = threadIdx.x; idx < nf * ld; idx += blockDim.x) K[idx] = (T)0;
-    __syncthreads();
-    scatter_son<T>(K, ld, a.nodes[nd.child0], a.maps, a.arenas, s, ups);
-    __syncthreads();
-    scatter_son<T>(K, ld, a.nodes[nd.child1], a.maps, a.arenas, s, ups);
-    __syncthreads();
-    for (int c = threadIdx.x; c < m; c += blockDim.x) K[c * ld + nf - 1] += (T)a.rhs(s, map[c]);
-  }
-  // Blocked right-looking partial Cholesky: factor a panel of kSmallPanel columns
-  // (rank-1 steps restricted to the panel), then one rank-kb update of the
-  // trailing lower triangle with 4 x 4 register tiles; one warp walks a column
-  // of tiles, its lanes down the rows (conflict-free, no index division).
-  for (int k0 = 0; k0 < m; k0 += kSmallPanel) {
-    const int kb = min(kSmallPanel, m - k0), kend = k0 + kb;
-    for (int k = k0; k < kend; ++k) {
-      __syncthreads();
-      T p = K[k * ld + k];
-      if (!(p > (T)0) || !isfinite(p)) {   // not SPD: record, continue with a unit pivot
-        if (threadIdx.x == 0) flag_status(a.status, s, -HDD_ENOTSPD, node);
-        p = (T)1;
-      }
-      const T d = sqrt(p), inv = (T)1 / d;
-      T* colk = K + k * ld;
-      for (int i = k + 1 + threadIdx.x; i < nf; i += blockDim.x) colk[i] *= inv;
-      __syncthreads();
-      if (threadIdx.x == 0) colk[k] = d;
-      for (int j = k + 1 + warp; j < kend; j += nwarp) {
-        const T lj = colk[j];
-        T* colj = K + j * ld;
-        for (int i = j + lane; i < nf; i += 32) colj[i] -= colk[i] * lj;
-      }
-    }
-    __syncthreads();
-    if (kend >= nf) continue;
-    const int t0 = kend & ~3;                    // tiles aligned to multiples of 4
-    const int nt = (nf - t0 + 3) >> 2;
-    for (int tj = warp; tj < nt; tj += nwarp) {
-      const int j0 = t0 + 4 * tj;
-      for (int ti = tj + lane; ti < nt; ti += 32) {
-        const int i0 = t0 + 4 * ti;
-        T acc[4][4];
-#pragma unroll
-        for (int q = 0; q < 4; ++q)
-#pragma unroll
-          for (int w = 0; w < 4; ++w) acc[q][w] = (T)0;
-        for (int l = k0; l < kend; ++l) {
-          const T* col = K + l * ld;
-          T x[4], y[4];
-          load4(col + i0, x);   // 16-byte aligned: ld and i0 are multiples of 4
-          load4(col + j0, y);
-#pragma unroll
-          for (int q = 0; q < 4; ++q)
-#pragma unroll
-            for (int w = 0; w < 4; ++w) acc[q][w] += x[q] * y[w];
-        }
-        const bool interior = j0 >= kend && i0 >= j0 + 4 && i0 + 3 < nf;
-        if (interior) {
-#pragma unroll
-          for (int w = 0; w < 4; ++w) {
-            T* cw = K + (j0 + w) * ld + i0;
-            T v[4];
-            load4(cw, v);
-#pragma unroll
-            for (int q = 0; q < 4; ++q) v[q] -= acc[q][w];
-            store4(cw, v);
-          }
-        } else {
-#pragma unroll
-          for (int w = 0; w < 4; ++w) {
-            const int j = j0 + w;
-            if (j < kend || j >= nf) continue;
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-              const int i = i0 + q;
-              if (i < nf && i >= j) K[j * ld + i] -= acc[q][w];
-            }
-          }
-        }
-      }
-    }
-  }
-  __syncthreads();
-  T* F = node_F<T>(a.arenas, nd, s);
-  for (int c = warp; c < m; c += nwarp)
-    for (int r = lane; r < nf; r += 32) F[c * nf + r] = K[c * ld + r];
-  T* Y = node_Y<T>(a.arenas, nd, s);
-  for (int c = threadIdx.x; c < m; c += blockDim.x) Y[c] = K[c * ld + nf - 1];
-  const int nb = nd.b + 1;
-  T* S = node_S<T>(a.arenas, nd, s);
-  for (int c = warp; c < nb; c += nwarp)
-    for (int r = c + lane; r < nb; r += 32) S[c * nb + r] = K[(m + c) * ld + m + r];
-}
-
-static int small_threads(int nf) { return nf <= 64 ? 128 : (nf <= 128 ? 256 : 512); }
-
-template <typename T>
-cudaError_t launch_front_small(const StepArgs& a, cudaStream_t st) {
-  if (a.nlist == 0) return cudaSuccess;
-  const size_t smem = ((size_t)a.max_nf * front_ld(a.max_nf) + 16) * sizeof(T) + (size_t)(a.max_nf + 4) * sizeof(int);
-  dim3 grid(a.nlist, a.batch);
-  if (a.prof) a.prof->begin(kProfFrontSmall, a.fl_chol + a.fl_trsm + a.fl_syrk + a.fl_rhs, st);
-  k_front_small<T><<<grid, small_threads(a.max_nf), smem, st>>>(a);
-  if (a.prof) a.prof->end(st);
-  return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------------------
@@ -327,6 +135,9 @@ template <typename T> struct SmemCap;
 template <> struct SmemCap<double> { static constexpr int rows = 800; };
 template <> struct SmemCap<float> { static constexpr int rows = 1600; };
 
+// POTRF of K_gg (m x m, in F with ld nf): one CTA per (node, sample), blocked
+// right-looking with 32-column panels staged in shared memory; the trailing
+// update uses 4 x 4 register tiles over the lower triangle.
 template <typename T>
 __global__ void __launch_bounds__(256) k_potrf(StepArgs a) {
   const int node = a.list[blockIdx.x];
@@ -490,74 +301,6 @@ __device__ __forceinline__ void write_tc_tiles(const float* X, int64_t ldx, cons
 // the diagonal triangle is solved one thread per row, then the remaining columns
 // are updated in 64-column chunks of L staged in shared memory, with register
 // micro-tiles (4 rows x kTrsmCols columns per thread).
-// POTRF of gamma blocks of at most 32 columns: one warp per (node, sample),
-// lane r holding row r of K_gg in registers.  Right-looking Cholesky with the
-// pivot column broadcast by shuffles, then the inverse of L (lane c solves
-// L w = e_c by forward substitution, rows of L broadcast by shuffles), stored
-// as the single 32 x 32 block that the TRSM applies as a product.
-template <typename T>
-__global__ void __launch_bounds__(256) k_potrf_warp(StepArgs a) {
-  constexpr unsigned kAll = 0xffffffffu;
-  const int node = a.list[blockIdx.x];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int s = blockIdx.y * 8 + warp;
-  if (s >= a.batch) return;
-  const NodeDev nd = a.nodes[node];
-  const int nf = nd.nf, m = nd.m;
-  T* A = node_F<T>(a.arenas, nd, s);
-  T row[32];
-#pragma unroll
-  for (int c = 0; c < 32; ++c) row[c] = (c < m && lane < m && c <= lane) ? A[(int64_t)c * nf + lane] : (T)0;
-  bool bad = false;
-#pragma unroll
-  for (int k = 0; k < 32; ++k) {
-    if (k < m) {
-      T pk = __shfl_sync(kAll, row[k], k);
-      if (!(pk > (T)0) || !isfinite(pk)) {
-        bad = true;
-        pk = (T)1;
-      }
-      const T d = sqrt(pk), inv = (T)1 / d;
-      T lk = (lane == k) ? d : row[k] * inv;
-      if (lane < k) lk = (T)0;
-#pragma unroll
-      for (int j = k + 1; j < 32; ++j) {
-        const T lj = __shfl_sync(kAll, lk, j);
-        if (lane > k) row[j] -= lk * lj;
-      }
-      row[k] = lk;
-    }
-  }
-  if (bad && lane == 0) flag_status(a.status, s, -HDD_ENOTSPD, node);
-#pragma unroll
-  for (int c = 0; c < 32; ++c)
-    if (c < m && lane < m && c <= lane) A[(int64_t)c * nf + lane] = row[c];
-  // inverse: lane c solves L w = e_c (identity columns beyond m), rows of L read
-  // from shared memory (one row per step, the same address for all lanes)
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* Ls = reinterpret_cast<T*>(smem_raw) + warp * (32 * 33 + 32);
-  T* dinv = Ls + 32 * 33;
-#pragma unroll
-  for (int c = 0; c < 32; ++c) Ls[lane * 33 + c] = row[c];
-  T diag = (T)1;
-#pragma unroll
-  for (int c = 0; c < 32; ++c)
-    if (c == lane && c < m) diag = row[c];
-  dinv[lane] = (T)1 / diag;
-  __syncwarp();
-  T w[32];
-#pragma unroll
-  for (int r = 0; r < 32; ++r) {
-    T acc = (lane == r) ? (T)1 : (T)0;
-#pragma unroll
-    for (int l = 0; l < r; ++l) acc -= Ls[r * 33 + l] * w[l];
-    w[r] = acc * dinv[r];
-  }
-  T* G = reinterpret_cast<T*>(a.arenas.inv + (int64_t)s * a.arenas.inv_stride + nd.inv_off);
-#pragma unroll
-  for (int r = 0; r < 32; ++r) G[lane * 32 + r] = (lane < m) ? ((r < m) ? w[r] : (T)0) : ((r == lane) ? (T)1 : (T)0);
-}
-
 // POTRF and TRSM of large fronts whose gamma block has at most 32 * NB columns
 // (NB = 1, 2), one CTA per (node, sample).  Diagonal 32 x 32 blocks are factored
 // by warp 0 in registers (pivot column by shuffles) and inverted in shared
@@ -970,7 +713,7 @@ __global__ void k_syrk_rhs(StepArgs a) {
   for (int j = threadIdx.x; j <= b; j += blockDim.x) {
     float acc = 0.0f;
     for (int k = 0; k < m; ++k) acc += y[k] * X[(int64_t)k * nf + j];
-    const float g = (nd.leaf || !a.bb_gather) ? S[(int64_t)j * nb + b]
+    const float g = nd.leaf ? S[(int64_t)j * nb + b]
                             : father_entry<float>(nf - 1, m + j, s, nd, map, c0, c1, a.arenas, a.rhs);
     S[(int64_t)j * nb + b] = g - acc;
   }
@@ -982,7 +725,7 @@ cudaError_t launch_front_large(const StepArgs& a, cudaStream_t st) {
   {
     // FP32 fronts: the tensor-core Schur update gathers the sons' boundary block
     // itself, so only the gamma columns are filled
-    const bool gamma_only = std::is_same<T, float>::value && a.bb_gather && !a.syrk_simt;
+    const bool gamma_only = std::is_same<T, float>::value;
     dim3 grid((a.max_nf + 7) / 8, a.nlist, a.batch);
     if (a.prof) a.prof->begin(kProfFill, 0.0, st);
     k_front_fill<T><<<grid, 256, 0, st>>>(a, gamma_only ? 1 : 0);
@@ -1013,7 +756,7 @@ cudaError_t launch_front_large(const StepArgs& a, cudaStream_t st) {
     k_trsm<T><<<grid, 256, smem, st>>>(a);
     if (a.prof) a.prof->end(st);
   }
-  if (std::is_same<T, float>::value && !a.syrk_simt) {
+  if (std::is_same<T, float>::value) {
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     if (a.prof) a.prof->begin(kProfSyrkTc, a.fl_syrk, st);
@@ -1035,19 +778,14 @@ cudaError_t launch_front_large(const StepArgs& a, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-template cudaError_t launch_front_small<double>(const StepArgs&, cudaStream_t);
-template cudaError_t launch_front_small<float>(const StepArgs&, cudaStream_t);
 template cudaError_t launch_front_large<double>(const StepArgs&, cudaStream_t);
 template cudaError_t launch_front_large<float>(const StepArgs&, cudaStream_t);
 
 cudaError_t configure_front_kernels() {
   const int lim = 227 * 1024;
   cudaError_t e;
-  if ((e = cudaFuncSetAttribute(k_front_small<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
-  if ((e = cudaFuncSetAttribute(k_front_small<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
   if ((e = cudaFuncSetAttribute(k_potrf<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
   if ((e = cudaFuncSetAttribute(k_potrf<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
-  if ((e = cudaFuncSetAttribute(k_potrf_warp<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
   if ((e = cudaFuncSetAttribute(k_chol_trsm<float, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
   if ((e = cudaFuncSetAttribute(k_chol_trsm<float, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
   if ((e = cudaFuncSetAttribute(k_chol_trsm<double, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;

@@ -5,10 +5,9 @@
 // the refinement sweeps) and the Schur complement of the subtree's root go to
 // global memory.  Nodes of one level are shared out among warp groups:
 //   * fronts of at most 32 rows handled by a single warp: one row per lane in
-//     registers, Cholesky with shuffles (as in k_front_warp);
-//   * otherwise a group of warps per front in shared memory with the blocked
-//     right-looking partial Cholesky of k_front_small, synchronised by a named
-//     barrier per group.
+//     registers, Cholesky with shuffles;
+//   * otherwise a group of warps per front in shared memory with a blocked
+//     right-looking partial Cholesky, synchronised by a named barrier per group.
 // Schur blocks inside the subtree are stored as full symmetric squares.
 #include "launch.h"
 

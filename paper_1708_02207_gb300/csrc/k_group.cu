@@ -16,8 +16,6 @@
 //      L_Bg; y_g^T] to the factor store.
 // Barriers are per group (a warp barrier when W = 1), so the groups of a CTA
 // never wait for one another.
-#include <cstdlib>
-
 #include "launch.h"
 
 namespace hdd {
@@ -109,21 +107,8 @@ __device__ __forceinline__ void add_son(T* K, int ld, const NodeDev& ch, const i
 
 }  // namespace
 
-// Entry (a, b) of a son's lower Schur triangle (ld = son b + 1), in the son's own
-// precision, for the sample whose arena offsets are base32 / base64.
 template <typename T>
-__device__ __forceinline__ T son_at(const NodeDev& ch, const Arenas& A, int64_t base32, int64_t base64, int x, int y) {
-  const int lo = min(x, y), hi = max(x, y);
-  const int64_t idx = (int64_t)lo * (ch.b + 1) + hi + ch.s_off;
-  return ch.fp64 ? (T)A.s64[base64 + idx] : (T)A.s32[base32 + idx];
-}
-
-// gather != 0 (fathers with long interfaces): only the m gamma columns of the
-// front are held in shared memory (gathered from the sons through the position
-// maps); the Schur tiles gather their boundary-block entries from the sons
-// directly, so the front's B x B block never exists as such.
-template <typename T>
-__global__ void __launch_bounds__(256) k_front_group(StepArgs a, int W, int ld, int fr_elems, int gather) {
+__global__ void __launch_bounds__(256) k_front_group(StepArgs a, int W, int ld, int fr_elems) {
   const int node = a.list[blockIdx.x];
   const NodeDev nd = a.nodes[node];
   const int nf = nd.nf, m = nd.m, nb = nd.b + 1, N = a.N;
@@ -133,8 +118,7 @@ __global__ void __launch_bounds__(256) k_front_group(StepArgs a, int W, int ld, 
   const int s = blockIdx.y * G + gi;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* K = reinterpret_cast<T*>(smem_raw) + (size_t)gi * fr_elems;
-  const int kcols = gather ? m : ((nf + 3) & ~3);   // columns held in shared memory
-  T* dg = K + (size_t)kcols * ld;                   // pivots sqrt(p_k) of this front
+  T* dg = K + (size_t)((nf + 3) & ~3) * ld;   // pivots sqrt(p_k) of this front
   int* sh = reinterpret_cast<int*>(reinterpret_cast<T*>(smem_raw) + (size_t)G * fr_elems);
   const int32_t* map = a.maps + nd.map_off;
 
@@ -153,11 +137,6 @@ __global__ void __launch_bounds__(256) k_front_group(StepArgs a, int W, int ld, 
       sh[lj * tw + li] = r;
       loc[r] = (lj << 16) | li;
     }
-  } else if (gather) {
-    c0 = a.nodes[nd.child0];
-    c1 = a.nodes[nd.child1];
-    const int32_t* pos = map + (nf - 1);   // son row of each front row, son 0 then son 1
-    for (int i = threadIdx.x; i < 2 * nf; i += blockDim.x) sh[i] = pos[i];
   } else {
     c0 = a.nodes[nd.child0];
     c1 = a.nodes[nd.child1];
@@ -168,45 +147,15 @@ __global__ void __launch_bounds__(256) k_front_group(StepArgs a, int W, int ld, 
   }
   __syncthreads();
   if (s >= a.batch) return;
-  const int64_t sb32 = (int64_t)s * a.arenas.s32_stride, sb64 = (int64_t)s * a.arenas.s64_stride;
-  const int* pos0 = sh;
-  const int* pos1 = sh + nf;
-
-  if (gather) {
-    // 1'. gamma columns of the front from the sons, four rows per thread and pass
-    for (int c = 0; c < m; ++c) {
-      const int q0 = pos0[c], q1 = pos1[c];
-      for (int r = g.t; r < c; r += g.size) K[c * ld + r] = (T)0;   // above the diagonal
-      for (int r0 = c + g.t; r0 < nf; r0 += 4 * g.size) {
-        T v[4];
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          const int r = r0 + q * g.size;
-          v[q] = (T)0;
-          if (r < nf) {
-            const int x0 = pos0[r], x1 = pos1[r];
-            if (x0 >= 0 && q0 >= 0) v[q] += son_at<T>(c0, a.arenas, sb32, sb64, x0, q0);
-            if (x1 >= 0 && q1 >= 0) v[q] += son_at<T>(c1, a.arenas, sb32, sb64, x1, q1);
-          }
-        }
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          const int r = r0 + q * g.size;
-          if (r < nf) K[c * ld + r] = v[q];
-        }
-      }
-    }
-  }
 
   // 1. build (the front is zero outside its lower triangle's nonzeros)
-  if (!gather) {
+  {
     const int n16 = (int)(((size_t)((nf + 3) & ~3) * ld * sizeof(T)) / 16);
     uint4* z = reinterpret_cast<uint4*>(K);
     for (int i = g.t; i < n16; i += g.size) z[i] = make_uint4(0, 0, 0, 0);
   }
   g.sync();
-  if (gather) {
-  } else if (nd.leaf) {
+  if (nd.leaf) {
     const T* kap = kappa_of<T>(a.kappa, a.kappa32) + (int64_t)s * a.kap_stride;
     const int* loc = sh + tw * (nd.y1 - nd.y0 + 1);
     for (int r = g.t; r < nf - 1; r += g.size) {
@@ -288,34 +237,12 @@ __global__ void __launch_bounds__(256) k_front_group(StepArgs a, int W, int ld, 
 #pragma unroll
         for (int w = 0; w < 4; ++w) acc[q][w] += x[q] * y[w];
     }
-    // the front's boundary-block entries: from shared memory, or (gather mode)
-    // from the sons (Eq. block_equation4)
-    int x0[4], x1[4];
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const int r = i0 + q;
-      x0[q] = (gather && r < nf) ? pos0[r] : -1;
-      x1[q] = (gather && r < nf) ? pos1[r] : -1;
-    }
 #pragma unroll
     for (int w = 0; w < 4; ++w) {
       const int c = j0 + w;
       if (c < m || c >= nf) continue;
-      T kv[4];
-      if (gather) {
-        const int q0 = pos0[c], q1 = pos1[c];
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          T v = (T)0;
-          if (i0 + q >= c) {
-            if (x0[q] >= 0 && q0 >= 0) v += son_at<T>(c0, a.arenas, sb32, sb64, x0[q], q0);
-            if (x1[q] >= 0 && q1 >= 0) v += son_at<T>(c1, a.arenas, sb32, sb64, x1[q], q1);
-          }
-          kv[q] = v;
-        }
-      } else {
-        ld4(K + c * ld + i0, kv);
-      }
+      T kv[4];   // the front's boundary-block entries
+      ld4(K + c * ld + i0, kv);
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
         const int r = i0 + q;
@@ -327,14 +254,9 @@ __global__ void __launch_bounds__(256) k_front_group(StepArgs a, int W, int ld, 
 
 // Warps per front: enough that a group's rows and tiles keep its lanes busy,
 // few enough that several fronts share a CTA.
-static int env_or(const char* name, int dflt) {
-  const char* v = getenv(name);
-  return v && *v ? atoi(v) : dflt;
-}
 static int group_warps(int max_nf, bool fp64) {
-  static const int w1 = env_or("HDD_GW1", 48), w2 = env_or("HDD_GW2", 64);
-  if (max_nf <= w1) return 1;
-  if (max_nf <= w2) return 2;
+  if (max_nf <= 48) return 1;
+  if (max_nf <= 64) return 2;
   if (!fp64 || max_nf <= 128) return 4;
   return 8;
 }
@@ -345,33 +267,25 @@ static int group_ld(int nf) {   // multiple of 4, congruent to 4 modulo 8
   return ld;
 }
 
-size_t front_group_smem(int max_nf, int max_m, int max_rect, bool gather, size_t elem) {
-  const int W = gather ? 8 : group_warps(max_nf, elem == 8);
-  const int G = (W > 4 ? W : 4) / W;
-  const int ld = group_ld(max_nf);
-  const int fr_elems = ((gather ? max_m : ((max_nf + 3) & ~3)) * ld + max_m + 3) & ~3;
-  const int ints = max(max_rect + max_nf, 2 * max_nf + 2);
-  return (size_t)G * fr_elems * elem + (size_t)ints * sizeof(int);
-}
-
 template <typename T>
-cudaError_t launch_front_group(const StepArgs& a, int family, cudaStream_t st, bool gather) {
+cudaError_t launch_front_group(const StepArgs& a, int family, cudaStream_t st) {
   if (a.nlist == 0) return cudaSuccess;
-  const int W = gather ? 8 : group_warps(a.max_nf, sizeof(T) == 8);
+  const int W = group_warps(a.max_nf, sizeof(T) == 8);
   const int warps = W > 4 ? W : 4;
   const int G = warps / W;
   const int ld = group_ld(a.max_nf);
-  const int fr_elems = ((gather ? a.max_m : ((a.max_nf + 3) & ~3)) * ld + a.max_m + 3) & ~3;
-  const size_t smem = front_group_smem(a.max_nf, a.max_m, a.max_rect, gather, sizeof(T));
+  const int fr_elems = (((a.max_nf + 3) & ~3) * ld + a.max_m + 3) & ~3;
+  const int ints = max(a.max_rect + a.max_nf, 2 * a.max_nf + 2);
+  const size_t smem = (size_t)G * fr_elems * sizeof(T) + (size_t)ints * sizeof(int);
   if (smem > 227 * 1024) return cudaErrorInvalidConfiguration;
   dim3 grid(a.nlist, (a.batch + G - 1) / G);
   if (a.prof) a.prof->begin(family, a.fl_chol + a.fl_trsm + a.fl_syrk + a.fl_rhs, st);
-  k_front_group<T><<<grid, warps * 32, smem, st>>>(a, W, ld, fr_elems, gather ? 1 : 0);
+  k_front_group<T><<<grid, warps * 32, smem, st>>>(a, W, ld, fr_elems);
   if (a.prof) a.prof->end(st);
   return cudaGetLastError();
 }
-template cudaError_t launch_front_group<double>(const StepArgs&, int, cudaStream_t, bool);
-template cudaError_t launch_front_group<float>(const StepArgs&, int, cudaStream_t, bool);
+template cudaError_t launch_front_group<double>(const StepArgs&, int, cudaStream_t);
+template cudaError_t launch_front_group<float>(const StepArgs&, int, cudaStream_t);
 
 cudaError_t configure_group_kernels() {
   const int lim = 227 * 1024;

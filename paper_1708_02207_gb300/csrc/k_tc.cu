@@ -100,7 +100,7 @@ __global__ void __launch_bounds__(128, 3) k_syrk_tc(StepArgs a) {
     asm volatile("fence.mbarrier_init.release.cluster;");
     timed_out = 0;
   }
-  const bool gather = !nd.leaf && a.bb_gather;
+  const bool gather = !nd.leaf;
   const int32_t* pos0 = a.maps + nd.map_off + (nd.nf - 1);
   const int32_t* pos1 = pos0 + nd.nf;
   if (gather) {

@@ -1,7 +1,6 @@
-// Warp-per-front kernels: fronts of at most 32 rows held in registers (one row
-// per lane), and the right-hand-side / descent sweeps with one warp per
-// (node, sample).  A CTA of 8 warps serves 8 samples of the same node, which
-// share the node's index maps.
+// Right-hand-side and descent sweeps with one warp per (node, sample).  A CTA
+// of 8 warps serves 8 samples of the same node, which share the node's index
+// maps.
 #include "launch.h"
 
 namespace hdd {
@@ -22,128 +21,6 @@ template <> __device__ __forceinline__ double* warp_S<double>(const Arenas& A, c
 template <> __device__ __forceinline__ float* warp_S<float>(const Arenas& A, const NodeDev& nd, int s) {
   return A.s32 + (int64_t)s * A.s32_stride + nd.s_off;
 }
-
-// ---------------------------------------------------------------------------
-// Fronts with nf <= 32: lane r holds row r of the (symmetric) front.  Build
-// (leaf stiffness, or the sons' Schur complements through the gather maps),
-// partial Cholesky of the first m columns with shuffles (column k of L is
-// broadcast entry by entry), then the factor columns and the Schur block are
-// written with coalesced stores.
-template <typename T>
-__global__ void __launch_bounds__(256) k_front_warp(StepArgs a) {
-  const int node = a.list[blockIdx.x];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int s = blockIdx.y * 8 + warp;
-  if (s >= a.batch) return;
-  const NodeDev nd = a.nodes[node];
-  const int nf = nd.nf, m = nd.m, nb = nd.b + 1;
-  const int N = a.N;
-  const int32_t* map = a.maps + nd.map_off;
-  const int v = (lane < nf - 1) ? map[lane] : -1;
-  const T rv = (lane < m) ? (T)a.rhs(s, v) : (T)0;   // load of this lane's vertex if it is eliminated here
-  T row[32];
-#pragma unroll
-  for (int c = 0; c < 32; ++c) row[c] = (T)0;
-  if (nd.leaf) {
-    const T* kap = kappa_of<T>(a.kappa, a.kappa32) + (int64_t)s * a.kap_stride;
-    int vi = -7, vj = -7;
-    T wl = (T)0, wr = (T)0, wd = (T)0, wu = (T)0;
-    if (v >= 0) {
-      vi = v % N;
-      vj = v / N;
-      wl = w_horizontal(kap, N, nd, vi - 1, vj);
-      wr = w_horizontal(kap, N, nd, vi, vj);
-      wd = w_vertical(kap, N, nd, vi, vj - 1);
-      wu = w_vertical(kap, N, nd, vi, vj);
-    }
-#pragma unroll
-    for (int c = 0; c < 32; ++c) {
-      const int ci = __shfl_sync(kFull, vi, c), cj = __shfl_sync(kFull, vj, c);
-      const T rc = __shfl_sync(kFull, rv, c);
-      T val = (T)0;
-      if (c < nf && lane < nf) {
-        if (lane == nf - 1) {
-          val = (c < m) ? rc : (T)0;
-        } else if (c == nf - 1) {
-          val = rv;
-        } else if (c == lane) {
-          val = wl + wr + wd + wu;
-        } else if (cj == vj && ci == vi - 1) {
-          val = -wl;
-        } else if (cj == vj && ci == vi + 1) {
-          val = -wr;
-        } else if (ci == vi && cj == vj - 1) {
-          val = -wd;
-        } else if (ci == vi && cj == vj + 1) {
-          val = -wu;
-        }
-      }
-      row[c] = val;
-    }
-  } else {
-    const int32_t* pos0 = map + (nf - 1);
-    const int32_t* pos1 = pos0 + nf;
-    const NodeDev c0 = a.nodes[nd.child0], c1 = a.nodes[nd.child1];
-    const int p0 = (lane < nf) ? pos0[lane] : -1, p1 = (lane < nf) ? pos1[lane] : -1;
-#pragma unroll
-    for (int c = 0; c < 32; ++c) {
-      const int q0 = __shfl_sync(kFull, p0, c), q1 = __shfl_sync(kFull, p1, c);
-      const T rc = __shfl_sync(kFull, rv, c);
-      T val = (T)0;
-      if (p0 >= 0 && q0 >= 0) val += son_entry<T>(a.arenas, c0, s, p0, q0);
-      if (p1 >= 0 && q1 >= 0) val += son_entry<T>(a.arenas, c1, s, p1, q1);
-      if (lane == nf - 1 && c < m) val += rc;
-      if (c == nf - 1 && lane < m) val += rv;
-      row[c] = val;
-    }
-  }
-  bool bad = false;
-#pragma unroll
-  for (int k = 0; k < 32; ++k) {
-    if (k < m) {
-      T pk = __shfl_sync(kFull, row[k], k);
-      if (!(pk > (T)0) || !isfinite(pk)) {
-        bad = true;
-        pk = (T)1;
-      }
-      const T d = sqrt(pk), inv = (T)1 / d;
-      T lk = (lane == k) ? d : row[k] * inv;
-      if (lane < k) lk = (T)0;
-#pragma unroll
-      for (int j = k + 1; j < 32; ++j) {
-        const T lj = __shfl_sync(kFull, lk, j);
-        if (lane > k) row[j] -= lk * lj;
-      }
-      row[k] = lk;
-    }
-  }
-  if (bad && lane == 0) flag_status(a.status, s, -HDD_ENOTSPD, node);
-  T* F = warp_F<T>(a.arenas, nd, s);
-#pragma unroll
-  for (int c = 0; c < 32; ++c)
-    if (c < m && lane < nf) F[c * nf + lane] = row[c];
-  if (lane == nf - 1) {
-    T* Y = node_Y<T>(a.arenas, nd, s);
-#pragma unroll
-    for (int c = 0; c < 32; ++c)
-      if (c < m) Y[c] = row[c];
-  }
-  T* S = warp_S<T>(a.arenas, nd, s);
-#pragma unroll
-  for (int c = 0; c < 32; ++c)
-    if (c >= m && c < nf && lane >= m && lane < nf) S[(c - m) * nb + (lane - m)] = row[c];
-}
-
-template <typename T>
-cudaError_t launch_front_warp(const StepArgs& a, cudaStream_t st) {
-  if (a.nlist == 0) return cudaSuccess;
-  if (a.prof) a.prof->begin(kProfFrontWarp, a.fl_chol + a.fl_trsm + a.fl_syrk + a.fl_rhs, st);
-  k_front_warp<T><<<dim3(a.nlist, (a.batch + 7) / 8), 256, 0, st>>>(a);
-  if (a.prof) a.prof->end(st);
-  return cudaGetLastError();
-}
-template cudaError_t launch_front_warp<double>(const StepArgs&, cudaStream_t);
-template cudaError_t launch_front_warp<float>(const StepArgs&, cudaStream_t);
 
 // Warps per CTA of the sweeps: 8, or fewer when a warp's vector of nf entries
 // would not fit the shared memory of 8 warps.

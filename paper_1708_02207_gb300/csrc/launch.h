@@ -15,7 +15,7 @@ namespace hdd {
 // algorithmic flops of the launch.  Owned by a plan; not thread-safe.
 enum ProfFamily {
   kProfKappa, kProfFrontWarp, kProfFrontSmall, kProfFill, kProfPotrf, kProfTrsm, kProfSyrk, kProfSyrkTc,
-  kProfSyrkRhs, kProfForward, kProfDescent, kProfResidual, kProfMisc, kProfFused, kProfLeaf, kProfCholTrsm, kProfFrontGather, kProfCount
+  kProfSyrkRhs, kProfForward, kProfDescent, kProfResidual, kProfMisc, kProfFused, kProfLeaf, kProfCholTrsm, kProfCount
 };
 struct Profiler {
   bool on = false;
@@ -59,8 +59,6 @@ struct StepArgs {
   int32_t* status;
   int max_nf, max_m, max_b;
   int max_rect;             // leaves: vertices of the largest closed rectangle
-  int bb_gather;            // large FP32 fronts: the Schur update gathers the sons' boundary block
-  int syrk_simt;            // large FP32 fronts: SIMT Schur update instead of the tensor cores
   Profiler* prof;            // nullptr unless profiling
   double fl_chol, fl_trsm, fl_syrk, fl_rhs;   // algorithmic flops of this launch (whole batch)
 };
@@ -83,8 +81,6 @@ cudaError_t launch_kappa(const double* phi, const double* Z, int n_t, int n_z, i
 cudaError_t launch_kappa_df(const float* phi_hi, const float* phi_lo, const double* Z, int n_t, int n_z, int batch,
                             double* kappa, float* kappa32, int64_t kap_stride, cudaStream_t st);
 
-// fronts of at most 32 rows: one warp each, in registers
-template <typename T> cudaError_t launch_front_warp(const StepArgs& a, cudaStream_t st);
 // sweeps with one warp per (node, sample)
 template <typename T>
 cudaError_t launch_forward_warp(const NodeDev* nodes, const int32_t* maps, const int32_t* list, int nlist, int batch,
@@ -101,12 +97,7 @@ template <typename T>
 cudaError_t launch_descent_tiny(const NodeDev* nodes, const int32_t* maps, const int32_t* list, int nlist, int batch,
                                 const Arenas& A, double* u, int64_t u_stride, cudaStream_t st);
 // fronts of up to kSmallMax rows: W warps per front, several samples of a node per CTA
-template <typename T>
-cudaError_t launch_front_group(const StepArgs& a, int family, cudaStream_t st, bool gather = false);
-// shared memory of one CTA of the grouped front kernel (0 < result; > 227 KiB: does not fit)
-size_t front_group_smem(int max_nf, int max_m, int max_rect, bool gather, size_t elem);
-// fronts that fit in shared memory: build + partial Cholesky + store, one CTA each
-template <typename T> cudaError_t launch_front_small(const StepArgs& a, cudaStream_t st);
+template <typename T> cudaError_t launch_front_group(const StepArgs& a, int family, cudaStream_t st);
 // condensed leaves (K_gg^-1 and boundary couplings): upsweep, right-hand-side sweep, descent
 template <typename T> cudaError_t launch_leaf_front(const StepArgs& a, cudaStream_t st);
 template <typename T>
