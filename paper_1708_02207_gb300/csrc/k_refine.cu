@@ -112,35 +112,36 @@ template cudaError_t launch_forward<float>(const NodeDev*, const int32_t*, const
 // r = b - A u over the unknowns (FP64).  (A u)_v = sum over the four axis edges of
 // w_e (u_v - u_w), w_e = mean kappa of the two triangles having e as a leg;
 // Dirichlet neighbours contribute u_w = 0.  Boundary entries of r are set to 0.
-__global__ void k_residual(const double* __restrict__ kappa, int64_t kap_stride, const double* __restrict__ u,
-                           int64_t u_stride, int N, double load, double* __restrict__ r) {
-  const int s = blockIdx.y;
-  const int v = blockIdx.x * blockDim.x + threadIdx.x;
-  if (v >= N * N) return;
-  const int i = v % N, j = v / N;
-  double* rs = r + (int64_t)s * u_stride;
+// Grid: (row blocks of 128 vertices, rows j, samples); the two triangles of a
+// cell are adjacent in kappa, so a row of cells is one contiguous run.
+__global__ void __launch_bounds__(128) k_residual(const double* __restrict__ kappa, int64_t kap_stride,
+                                                  const double* __restrict__ u, int64_t u_stride, int N,
+                                                  double load, double* __restrict__ r) {
+  const int s = blockIdx.z, j = blockIdx.y;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  double* rs = r + (int64_t)s * u_stride + (int64_t)j * N;
   if (i < 1 || j < 1 || i > N - 2 || j > N - 2) {
-    rs[v] = 0.0;
+    rs[i] = 0.0;
     return;
   }
-  const double* k = kappa + (int64_t)s * kap_stride;
-  const double* us = u + (int64_t)s * u_stride;
-  auto kt = [&](int ci, int cj, int t) { return k[2 * ((int64_t)cj * (N - 1) + ci) + t]; };
-  auto uu = [&](int a, int c) { return (a < 1 || c < 1 || a > N - 2 || c > N - 2) ? 0.0 : us[c * N + a]; };
-  const double uv = us[v];
-  const double wr = 0.5 * (kt(i, j, 0) + kt(i, j - 1, 1));          // (i,j)-(i+1,j)
-  const double wl = 0.5 * (kt(i - 1, j, 0) + kt(i - 1, j - 1, 1));  // (i-1,j)-(i,j)
-  const double wu = 0.5 * (kt(i, j, 1) + kt(i - 1, j, 0));          // (i,j)-(i,j+1)
-  const double wd = 0.5 * (kt(i, j - 1, 1) + kt(i - 1, j - 1, 0));  // (i,j-1)-(i,j)
-  const double Au = wr * (uv - uu(i + 1, j)) + wl * (uv - uu(i - 1, j)) + wu * (uv - uu(i, j + 1)) +
-                    wd * (uv - uu(i, j - 1));
-  rs[v] = load - Au;
+  const double* k0 = kappa + (int64_t)s * kap_stride + 2 * (int64_t)j * (N - 1);   // cells of row j
+  const double* k1 = k0 - 2 * (N - 1);                                              // cells of row j - 1
+  const double* us = u + (int64_t)s * u_stride + (int64_t)j * N;
+  const double uv = us[i];
+  const double ue = (i + 1 <= N - 2) ? us[i + 1] : 0.0, uw = (i - 1 >= 1) ? us[i - 1] : 0.0;
+  const double un = (j + 1 <= N - 2) ? us[i + N] : 0.0, us_ = (j - 1 >= 1) ? us[i - N] : 0.0;
+  const double wr = 0.5 * (k0[2 * i] + k1[2 * i + 1]);                 // (i,j)-(i+1,j)
+  const double wl = 0.5 * (k0[2 * (i - 1)] + k1[2 * (i - 1) + 1]);     // (i-1,j)-(i,j)
+  const double wu = 0.5 * (k0[2 * i + 1] + k0[2 * (i - 1)]);           // (i,j)-(i,j+1)
+  const double wd = 0.5 * (k1[2 * i + 1] + k1[2 * (i - 1)]);           // (i,j-1)-(i,j)
+  const double Au = wr * (uv - ue) + wl * (uv - uw) + wu * (uv - un) + wd * (uv - us_);
+  rs[i] = load - Au;
 }
 
 cudaError_t launch_residual(const double* kappa, int64_t kap_stride, const double* u, int64_t u_stride, int N,
                             double load, double* r, int batch, cudaStream_t st) {
-  const int NN = N * N;
-  k_residual<<<dim3((NN + 255) / 256, batch), 256, 0, st>>>(kappa, kap_stride, u, u_stride, N, load, r);
+  k_residual<<<dim3((N + 127) / 128, N, batch), 128, 0, st>>>(kappa, kap_stride, u, u_stride, N, load, r);
   return cudaGetLastError();
 }
 
