@@ -178,37 +178,32 @@ __global__ void __launch_bounds__(256) k_front_group(StepArgs a, int W, int ld, 
   }
   g.sync();
 
-  // 2. left-looking Cholesky of the gamma columns by the group's first warp
-  // (rows of a column spread over its lanes; warp barriers only), while the
-  // other warps of the group wait once
+  // 2. left-looking Cholesky of the gamma columns; rows of a column are spread
+  // over the group
   bool bad = false;
-  if (g.t < 32) {
-    const int lane = g.t;
-    for (int k = 0; k < m; ++k) {
-      const T* rowk = K + k;   // entries (k, l) = K[l * ld + k]
-      for (int r = k + lane; r < nf; r += 32) {
-        T acc = K[k * ld + r];
-        if (r == nf - 1 && !nd.leaf) acc += (T)a.rhs(s, map[k]);   // father: load of its gamma vertex
-        // the products are summed first and subtracted once: the entry is usually much
-        // larger than what is left of it, and one rounding at its magnitude is enough
-        T dot = (T)0;
+  for (int k = 0; k < m; ++k) {
+    const T* rowk = K + k;   // entries (k, l) = K[l * ld + k]
+    for (int r = k + g.t; r < nf; r += g.size) {
+      T acc = K[k * ld + r];
+      if (r == nf - 1 && !nd.leaf) acc += (T)a.rhs(s, map[k]);   // father: load of its gamma vertex
+      // the products are summed first and subtracted once: the entry is usually much
+      // larger than what is left of it, and one rounding at its magnitude is enough
+      T dot = (T)0;
 #pragma unroll 4
-        for (int l = 0; l < k; ++l) dot += K[l * ld + r] * rowk[l * ld];
-        K[k * ld + r] = acc - dot;
-      }
-      __syncwarp();
-      T p = K[k * ld + k];
-      if (!(p > (T)0) || !isfinite(p)) {   // not SPD: record, continue with a unit pivot
-        bad = true;
-        p = (T)1;
-      }
-      const T d = sqrt(p), inv = (T)1 / d;
-      for (int r = k + 1 + lane; r < nf; r += 32) K[k * ld + r] *= inv;
-      if (lane == 0) dg[k] = d;
-      __syncwarp();
+      for (int l = 0; l < k; ++l) dot += K[l * ld + r] * rowk[l * ld];
+      K[k * ld + r] = acc - dot;
     }
+    g.sync();
+    T p = K[k * ld + k];
+    if (!(p > (T)0) || !isfinite(p)) {   // not SPD: record, continue with a unit pivot
+      bad = true;
+      p = (T)1;
+    }
+    const T d = sqrt(p), inv = (T)1 / d;
+    for (int r = k + 1 + g.t; r < nf; r += g.size) K[k * ld + r] *= inv;
+    if (g.t == 0) dg[k] = d;
+    g.sync();
   }
-  g.sync();
   if (bad && g.t == 0) flag_status(a.status, s, -HDD_ENOTSPD, node);
 
   // 3a. factor columns and y_g
