@@ -726,7 +726,8 @@ cudaError_t launch_front_large(const StepArgs& a, cudaStream_t st) {
     // FP32 fronts: the tensor-core Schur update gathers the sons' boundary block
     // itself, so only the gamma columns are filled
     const bool gamma_only = std::is_same<T, float>::value;
-    dim3 grid((a.max_nf + 7) / 8, a.nlist, a.batch);
+    const int cols = (gamma_only && a.max_rect == 0) ? a.max_m : a.max_nf;   // max_rect > 0: the list has leaves
+    dim3 grid((cols + 7) / 8, a.nlist, a.batch);
     if (a.prof) a.prof->begin(kProfFill, 0.0, st);
     k_front_fill<T><<<grid, 256, 0, st>>>(a, gamma_only ? 1 : 0);
     if (a.prof) a.prof->end(st);
