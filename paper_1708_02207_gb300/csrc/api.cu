@@ -658,7 +658,11 @@ hdd_status hdd_plan_info(hdd_plan_t plan, hdd_plan_info_t* info) {
   for (int h = 0; h <= p.height; ++h)
     for (int kind = 0; kind < 8; ++kind) {
       const hdd::ListInfo& li = p.lists[p.step_lists[h][kind]];
-      if (li.n) up += kind == 2 ? 4 : (kind == 5 ? 5 : 1);
+      if (!li.n) continue;
+      if (kind == 2) up += li.max_m <= 32 ? 3 : 4;        // fill, POTRF+TRSM or POTRF, TRSM, SYRK
+      else if (kind == 5)   // fill, POTRF+TRSM or POTRF, TRSM, tensor-core SYRK (b > 0), bordered row
+        up += (li.max_m <= 64 ? 3 : 4) + (li.max_b > 0 ? 1 : 0);
+      else up += 1;
     }
   for (const auto& fu : p.fusion) up += fu.height > 0;
   int down_all = 0, fwd = 0;
