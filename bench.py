@@ -50,6 +50,13 @@ def _measured_peaks():
 
 MEASURED = _measured_peaks()
 
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of a kernel family, summed over
+# the launches of one step of a 32-sample run of the same workload and divided by 32.
+MEASURED_TRAFFIC = {
+    "front_small": {"workload": "grid513", "leaf": 4, "precision": "mixed", "bytes_per_sample": 4.613e9 / 32,
+                    "source": "profiles/k_front_group_grid513_b32.md"},
+}
+
 
 def _env_int(name, default):
     try:
@@ -337,8 +344,15 @@ def run_hdd(args, cfg):
         dom = max((k for k in stages_roof if k in kernels), key=lambda k: stages_roof[k]["ms_per_step"])
         r = stages_roof[dom]
         if r["bound"] == "hbm":
+            # DRAM bytes per step from ncu (profiles/), per sample; only for the family and
+            # kernel version the counters were taken on
+            tr = MEASURED_TRAFFIC.get(dom)
+            same = tr and cfg.name == tr["workload"] and (args.leaf or cfg.leaf) == tr["leaf"] \
+                and args.precision == tr["precision"]
+            traffic = tr["bytes_per_sample"] * B if same else None
             roof = {"bound": "hbm", "achieved": r["gbs"], "peak": hbm, "unit": "GB/s", "frac": r["gbs"] / hbm,
-                    "traffic": None, "kernel": dom,
+                    "traffic": traffic, "traffic_unit": "bytes per step (all launches of the family)",
+                    "traffic_source": tr["source"] if traffic else None, "kernel": dom,
                     "peak_source": "of measured: MEASURED_PEAKS hbm_gbs (copy bandwidth)",
                     "algorithmic_bytes_per_step": r["bytes_per_step"],
                     "bytes_note": "per front and sample: sons' lower Schur triangles (leaves: kappa) read once; "
