@@ -6,9 +6,6 @@
 namespace hdd {
 
 constexpr unsigned kFull = 0xffffffffu;
-// samples per warp of the sweeps (each warp loops over them; the node's descriptor
-// and index maps are loaded once)
-constexpr int kSweepSpw = 4;
 
 template <typename T> __device__ __forceinline__ T* warp_F(const Arenas& A, const NodeDev& nd, int s);
 template <> __device__ __forceinline__ double* warp_F<double>(const Arenas& A, const NodeDev& nd, int s) {
@@ -54,16 +51,14 @@ __global__ void __launch_bounds__(256) k_forward_warp(const NodeDev* __restrict_
                                                       const int32_t* __restrict__ list, int batch, int wstride,
                                                       int stage, Arenas A, Rhs rhs) {
   const int node = list[blockIdx.x];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, wpb = blockDim.x >> 5;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int s = blockIdx.y * (blockDim.x >> 5) + warp;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* z = reinterpret_cast<T*>(smem_raw) + warp * wstride;
+  if (s >= batch) return;
   const NodeDev nd = nodes[node];
   const int m = nd.m, b = nd.b, nf = nd.nf;
   const int32_t* vid = maps + nd.map_off;
-  for (int k = 0; k < kSweepSpw; ++k) {   // several samples per warp: the node's setup is shared
-  const int s = (blockIdx.y * kSweepSpw + k) * wpb + warp;
-  if (s >= batch) break;
-  __syncwarp();
   const T* Fg = warp_F<T>(A, nd, s);
   const T* F = Fg;
   if (stage) {
@@ -100,7 +95,6 @@ __global__ void __launch_bounds__(256) k_forward_warp(const NodeDev* __restrict_
     T* S = warp_S<T>(A, nd, s);
     for (int r = lane; r < b; r += 32) S[r] = z[m + r];
   }
-  }
 }
 
 // Bytes of shared memory per warp of a sweep: the vector, plus the staged
@@ -120,8 +114,7 @@ cudaError_t launch_forward_warp(const NodeDev* nodes, const int32_t* maps, const
   int stage = 0;
   const int ws = sweep_stride<T>(max_nf, max_m, &stage);
   const int wpb = sweep_warps((size_t)ws * sizeof(T));
-  k_forward_warp<T><<<dim3(nlist, (batch + wpb * kSweepSpw - 1) / (wpb * kSweepSpw)), 32 * wpb,
-                      (size_t)wpb * ws * sizeof(T), st>>>(
+  k_forward_warp<T><<<dim3(nlist, (batch + wpb - 1) / wpb), 32 * wpb, (size_t)wpb * ws * sizeof(T), st>>>(
       nodes, maps, list, batch, ws, stage, A, rhs);
   return cudaGetLastError();
 }
@@ -141,16 +134,14 @@ __global__ void __launch_bounds__(256) k_descent_warp(const NodeDev* __restrict_
                                                       const int32_t* __restrict__ list, int batch, int wstride,
                                                       int stage, Arenas A, double* __restrict__ u, int64_t u_stride) {
   const int node = list[blockIdx.x];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, wpb = blockDim.x >> 5;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int s = blockIdx.y * (blockDim.x >> 5) + warp;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* wv = reinterpret_cast<T*>(smem_raw) + warp * wstride;
+  if (s >= batch) return;
   const NodeDev nd = nodes[node];
   const int m = nd.m, b = nd.b, nf = nd.nf;
   const int32_t* vid = maps + nd.map_off;
-  for (int k = 0; k < kSweepSpw; ++k) {   // several samples per warp: the node's setup is shared
-  const int s = (blockIdx.y * kSweepSpw + k) * wpb + warp;
-  if (s >= batch) break;
-  __syncwarp();
   const T* Fg = warp_F<T>(A, nd, s);
   const T* F = Fg;
   if (stage) {
@@ -173,7 +164,6 @@ __global__ void __launch_bounds__(256) k_descent_warp(const NodeDev* __restrict_
     __syncwarp();
   }
   for (int c = lane; c < m; c += 32) us[vid[c]] = (double)wv[c];
-  }
 }
 
 template <typename T>
@@ -184,8 +174,7 @@ cudaError_t launch_descent_warp(const NodeDev* nodes, const int32_t* maps, const
   int stage = 0;
   const int ws = sweep_stride<T>(max_nf, max_m, &stage);
   const int wpb = sweep_warps((size_t)ws * sizeof(T));
-  k_descent_warp<T><<<dim3(nlist, (batch + wpb * kSweepSpw - 1) / (wpb * kSweepSpw)), 32 * wpb,
-                      (size_t)wpb * ws * sizeof(T), st>>>(
+  k_descent_warp<T><<<dim3(nlist, (batch + wpb - 1) / wpb), 32 * wpb, (size_t)wpb * ws * sizeof(T), st>>>(
       nodes, maps, list, batch, ws, stage, A, u, u_stride);
   return cudaGetLastError();
 }
@@ -207,12 +196,11 @@ __global__ void __launch_bounds__(256) k_forward_tiny(const NodeDev* __restrict_
                                                       Rhs rhs) {
   const int node = list[blockIdx.x];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int s = blockIdx.y * 8 + warp;
+  if (s >= batch) return;
   const NodeDev nd = nodes[node];
   const int m = nd.m, b = nd.b, nf = nd.nf;
   const int32_t* vid = maps + nd.map_off;
-  for (int k = 0; k < kSweepSpw; ++k) {
-  const int s = (blockIdx.y * kSweepSpw + k) * 8 + warp;
-  if (s >= batch) break;
   const T* F = warp_F<T>(A, nd, s);
   T row[32];
 #pragma unroll
@@ -239,7 +227,6 @@ __global__ void __launch_bounds__(256) k_forward_tiny(const NodeDev* __restrict_
   if (lane < m) node_Y<T>(A, nd, s)[lane] = z;
   if (lane >= m && lane < nf - 1) warp_S<T>(A, nd, s)[lane - m] = z;
   (void)b;
-  }
 }
 
 template <typename T>
@@ -249,12 +236,11 @@ __global__ void __launch_bounds__(256) k_descent_tiny(const NodeDev* __restrict_
                                                       double* __restrict__ u, int64_t u_stride) {
   const int node = list[blockIdx.x];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int s = blockIdx.y * 8 + warp;
+  if (s >= batch) return;
   const NodeDev nd = nodes[node];
   const int m = nd.m, nf = nd.nf;
   const int32_t* vid = maps + nd.map_off;
-  for (int k = 0; k < kSweepSpw; ++k) {
-  const int s = (blockIdx.y * kSweepSpw + k) * 8 + warp;
-  if (s >= batch) break;
   const T* F = warp_F<T>(A, nd, s);
   double* us = u + (int64_t)s * u_stride;
   T row[32];
@@ -273,23 +259,20 @@ __global__ void __launch_bounds__(256) k_descent_tiny(const NodeDev* __restrict_
     if (lane == c) wv = uc;
   }
   if (lane < m) us[vid[lane]] = (double)wv;
-  }
 }
 
 template <typename T>
 cudaError_t launch_forward_tiny(const NodeDev* nodes, const int32_t* maps, const int32_t* list, int nlist, int batch,
                                 const Arenas& A, const Rhs& rhs, cudaStream_t st) {
   if (nlist == 0) return cudaSuccess;
-  k_forward_tiny<T><<<dim3(nlist, (batch + 8 * kSweepSpw - 1) / (8 * kSweepSpw)), 256, 0, st>>>(nodes, maps, list,
-                                                                                              batch, A, rhs);
+  k_forward_tiny<T><<<dim3(nlist, (batch + 7) / 8), 256, 0, st>>>(nodes, maps, list, batch, A, rhs);
   return cudaGetLastError();
 }
 template <typename T>
 cudaError_t launch_descent_tiny(const NodeDev* nodes, const int32_t* maps, const int32_t* list, int nlist, int batch,
                                 const Arenas& A, double* u, int64_t u_stride, cudaStream_t st) {
   if (nlist == 0) return cudaSuccess;
-  k_descent_tiny<T><<<dim3(nlist, (batch + 8 * kSweepSpw - 1) / (8 * kSweepSpw)), 256, 0, st>>>(nodes, maps, list,
-                                                                                              batch, A, u, u_stride);
+  k_descent_tiny<T><<<dim3(nlist, (batch + 7) / 8), 256, 0, st>>>(nodes, maps, list, batch, A, u, u_stride);
   return cudaGetLastError();
 }
 template cudaError_t launch_forward_tiny<double>(const NodeDev*, const int32_t*, const int32_t*, int, int,
