@@ -512,12 +512,11 @@ __global__ void __launch_bounds__(32 * kCholTrsmWarps, 3) k_chol_trsm(StepArgs a
 }
 
 template <typename T> struct TrsmShape;
-template <> struct TrsmShape<float> { static constexpr int rows = 64, cap = 760; };
+template <> struct TrsmShape<float> { static constexpr int rows = 32, cap = 760; };   // rows: measured best of 32/64/128
 template <> struct TrsmShape<double> { static constexpr int rows = 32, cap = 760; };
 
-template <typename T>
-__global__ void __launch_bounds__(256) k_trsm(StepArgs a) {
-  constexpr int R = TrsmShape<T>::rows;     // rows per CTA
+template <typename T, int R>
+__global__ void __launch_bounds__(256) k_trsm(StepArgs a) {   // R rows per CTA
   constexpr int RG = R / 4;                 // row groups of 4
   constexpr int CG = 256 / RG;              // column groups
   constexpr int CPT = 64 / CG;              // columns per thread in a 64-column chunk
@@ -754,7 +753,7 @@ cudaError_t launch_front_large(const StepArgs& a, cudaStream_t st) {
     const size_t smem = (xrows * R + 32 * 33 + 3 + 32 * 64) * sizeof(T) + 16;
     dim3 grid((a.max_b + 1 + R - 1) / R, a.nlist, a.batch);
     if (a.prof) a.prof->begin(kProfTrsm, a.fl_trsm, st);
-    k_trsm<T><<<grid, 256, smem, st>>>(a);
+    k_trsm<T, 32><<<grid, 256, smem, st>>>(a);
     if (a.prof) a.prof->end(st);
   }
   if (std::is_same<T, float>::value) {
@@ -790,8 +789,8 @@ cudaError_t configure_front_kernels() {
   if ((e = cudaFuncSetAttribute(k_chol_trsm<float, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
   if ((e = cudaFuncSetAttribute(k_chol_trsm<float, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
   if ((e = cudaFuncSetAttribute(k_chol_trsm<double, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
-  if ((e = cudaFuncSetAttribute(k_trsm<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
-  if ((e = cudaFuncSetAttribute(k_trsm<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
+  if ((e = cudaFuncSetAttribute(k_trsm<double, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
+  if ((e = cudaFuncSetAttribute(k_trsm<float, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
   return cudaSuccess;
 }
 
