@@ -112,36 +112,59 @@ template cudaError_t launch_forward<float>(const NodeDev*, const int32_t*, const
 // r = b - A u over the unknowns (FP64).  (A u)_v = sum over the four axis edges of
 // w_e (u_v - u_w), w_e = mean kappa of the two triangles having e as a leg;
 // Dirichlet neighbours contribute u_w = 0.  Boundary entries of r are set to 0.
-// Grid: (row blocks of 128 vertices, rows j, samples); the two triangles of a
-// cell are adjacent in kappa, so a row of cells is one contiguous run.
+// A thread owns one column i of vertices over kResRows consecutive rows and
+// slides up them, so that every row of u and of the cells' kappa is loaded once
+// per thread (the left and right neighbours come from the adjacent threads'
+// loads through L1).
+constexpr int kResRows = 8;
+
 __global__ void __launch_bounds__(128) k_residual(const double* __restrict__ kappa, int64_t kap_stride,
                                                   const double* __restrict__ u, int64_t u_stride, int N,
                                                   double load, double* __restrict__ r) {
-  const int s = blockIdx.z, j = blockIdx.y;
+  const int s = blockIdx.z;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j0 = blockIdx.y * kResRows;
   if (i >= N) return;
-  double* rs = r + (int64_t)s * u_stride + (int64_t)j * N;
-  if (i < 1 || j < 1 || i > N - 2 || j > N - 2) {
-    rs[i] = 0.0;
-    return;
+  const double* ks = kappa + (int64_t)s * kap_stride;
+  const double* us = u + (int64_t)s * u_stride;
+  double* rs = r + (int64_t)s * u_stride;
+  const bool col_in = i >= 1 && i <= N - 2;
+  auto urow = [&](int j, int di) {   // u at (i + di, j), 0 off the unknowns
+    const int ii = i + di;
+    return (ii >= 1 && ii <= N - 2 && j >= 1 && j <= N - 2) ? us[(int64_t)j * N + ii] : 0.0;
+  };
+  // kappa of the lower-right (t = 0) and upper-left (t = 1) triangles of cells (i, j) and (i - 1, j)
+  auto kc = [&](int ci, int j, int t) {
+    return (ci >= 0 && ci <= N - 2 && j >= 0 && j <= N - 2) ? ks[2 * ((int64_t)j * (N - 1) + ci) + t] : 0.0;
+  };
+  double u_c = urow(j0, 0), u_s = urow(j0 - 1, 0);
+  double kb0 = kc(i, j0 - 1, 1), kb1 = kc(i - 1, j0 - 1, 0), kb2 = kc(i - 1, j0 - 1, 1);   // cells of row j - 1
+  for (int j = j0; j < min(j0 + kResRows, N); ++j) {
+    const double u_n = urow(j + 1, 0);
+    const double ka0 = kc(i, j, 0), ka1 = kc(i, j, 1), ka2 = kc(i - 1, j, 0);       // cells of row j
+    if (!col_in || j < 1 || j > N - 2) {
+      rs[(int64_t)j * N + i] = 0.0;
+    } else {
+      const double ue = urow(j, 1), uw = urow(j, -1);
+      const double wr = 0.5 * (ka0 + kb0);   // (i,j)-(i+1,j): lower-right of (i,j), upper-left of (i,j-1)
+      const double wl = 0.5 * (ka2 + kb2);   // (i-1,j)-(i,j): lower-right of (i-1,j), upper-left of (i-1,j-1)
+      const double wu = 0.5 * (ka1 + ka2);   // (i,j)-(i,j+1): upper-left of (i,j), lower-right of (i-1,j)
+      const double wd = 0.5 * (kb0 + kb1);   // (i,j-1)-(i,j): upper-left of (i,j-1), lower-right of (i-1,j-1)
+      const double Au = wr * (u_c - ue) + wl * (u_c - uw) + wu * (u_c - u_n) + wd * (u_c - u_s);
+      rs[(int64_t)j * N + i] = load - Au;
+    }
+    u_s = u_c;
+    u_c = u_n;
+    kb0 = ka1;
+    kb1 = ka2;
+    kb2 = kc(i - 1, j, 1);
   }
-  const double* k0 = kappa + (int64_t)s * kap_stride + 2 * (int64_t)j * (N - 1);   // cells of row j
-  const double* k1 = k0 - 2 * (N - 1);                                              // cells of row j - 1
-  const double* us = u + (int64_t)s * u_stride + (int64_t)j * N;
-  const double uv = us[i];
-  const double ue = (i + 1 <= N - 2) ? us[i + 1] : 0.0, uw = (i - 1 >= 1) ? us[i - 1] : 0.0;
-  const double un = (j + 1 <= N - 2) ? us[i + N] : 0.0, us_ = (j - 1 >= 1) ? us[i - N] : 0.0;
-  const double wr = 0.5 * (k0[2 * i] + k1[2 * i + 1]);                 // (i,j)-(i+1,j)
-  const double wl = 0.5 * (k0[2 * (i - 1)] + k1[2 * (i - 1) + 1]);     // (i-1,j)-(i,j)
-  const double wu = 0.5 * (k0[2 * i + 1] + k0[2 * (i - 1)]);           // (i,j)-(i,j+1)
-  const double wd = 0.5 * (k1[2 * i + 1] + k1[2 * (i - 1)]);           // (i,j-1)-(i,j)
-  const double Au = wr * (uv - ue) + wl * (uv - uw) + wu * (uv - un) + wd * (uv - us_);
-  rs[i] = load - Au;
 }
 
 cudaError_t launch_residual(const double* kappa, int64_t kap_stride, const double* u, int64_t u_stride, int N,
                             double load, double* r, int batch, cudaStream_t st) {
-  k_residual<<<dim3((N + 127) / 128, N, batch), 128, 0, st>>>(kappa, kap_stride, u, u_stride, N, load, r);
+  k_residual<<<dim3((N + 127) / 128, (N + kResRows - 1) / kResRows, batch), 128, 0, st>>>(kappa, kap_stride, u,
+                                                                                            u_stride, N, load, r);
   return cudaGetLastError();
 }
 
