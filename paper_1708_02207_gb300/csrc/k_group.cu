@@ -61,12 +61,14 @@ __device__ __forceinline__ void tile_of(int t, int nt, int& ti, int& tj) {
 // Barrier of one group.  A CTA holds at most two groups of more than one warp,
 // which use the named barriers 1 and 2 (constant ids: the SM's barrier budget
 // per CTA is what the kernel names, and it bounds the CTAs per SM).
+template <int W>
 struct Group {
-  int id, size, t;   // named barrier id (1 or 2), threads, thread index in the group
+  static constexpr int size = 32 * W;   // threads of the group (W warps)
+  int id, t;                            // named barrier id (1 or 2), thread index in the group
   __device__ __forceinline__ void sync() const {
-    if (size == 32) __syncwarp();
-    else if (id == 1) asm volatile("bar.sync 1, %0;" ::"r"(size) : "memory");
-    else asm volatile("bar.sync 2, %0;" ::"r"(size) : "memory");
+    if (W == 1) __syncwarp();
+    else if (id == 1) asm volatile("bar.sync 1, %0;" ::"n"(size) : "memory");
+    else asm volatile("bar.sync 2, %0;" ::"n"(size) : "memory");
   }
 };
 
@@ -75,9 +77,9 @@ struct Group {
 // in packed column order: a thread starts at its rank and advances by the group
 // size, carrying its (row, column) along (no division); four entries per pass,
 // loads first.
-template <typename T>
+template <typename T, class Grp>
 __device__ __forceinline__ void add_son(T* K, int ld, const NodeDev& ch, const int* ups, const Arenas& A, int s,
-                                        const Group& g) {
+                                        const Grp& g) {
   const int ldc = ch.b + 1;
   const int total = ldc * (ldc + 1) / 2;
   const int64_t base = (int64_t)s * (ch.fp64 ? A.s64_stride : A.s32_stride) + ch.s_off;
@@ -107,14 +109,14 @@ __device__ __forceinline__ void add_son(T* K, int ld, const NodeDev& ch, const i
 
 }  // namespace
 
-template <typename T>
-__global__ void __launch_bounds__(256) k_front_group(StepArgs a, int W, int ld, int fr_elems) {
+template <typename T, int W>
+__global__ void __launch_bounds__(256) k_front_group(StepArgs a, int ld, int fr_elems) {
   const int node = a.list[blockIdx.x];
   const NodeDev nd = a.nodes[node];
   const int nf = nd.nf, m = nd.m, nb = nd.b + 1, N = a.N;
   const int G = (blockDim.x >> 5) / W;
   const int gi = (threadIdx.x >> 5) / W;
-  Group g{1 + gi, 32 * W, (int)threadIdx.x - gi * 32 * W};
+  const Group<W> g{1 + gi, (int)threadIdx.x - gi * 32 * W};
   const int s = blockIdx.y * G + gi;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* K = reinterpret_cast<T*>(smem_raw) + (size_t)gi * fr_elems;
@@ -280,7 +282,12 @@ cudaError_t launch_front_group(const StepArgs& a, int family, cudaStream_t st) {
   if (smem > 227 * 1024) return cudaErrorInvalidConfiguration;
   dim3 grid(a.nlist, (a.batch + G - 1) / G);
   if (a.prof) a.prof->begin(family, a.fl_chol + a.fl_trsm + a.fl_syrk + a.fl_rhs, st);
-  k_front_group<T><<<grid, warps * 32, smem, st>>>(a, W, ld, fr_elems);
+  switch (W) {
+    case 1: k_front_group<T, 1><<<grid, warps * 32, smem, st>>>(a, ld, fr_elems); break;
+    case 2: k_front_group<T, 2><<<grid, warps * 32, smem, st>>>(a, ld, fr_elems); break;
+    case 4: k_front_group<T, 4><<<grid, warps * 32, smem, st>>>(a, ld, fr_elems); break;
+    default: k_front_group<T, 8><<<grid, warps * 32, smem, st>>>(a, ld, fr_elems); break;
+  }
   if (a.prof) a.prof->end(st);
   return cudaGetLastError();
 }
@@ -290,16 +297,17 @@ template cudaError_t launch_front_group<float>(const StepArgs&, int, cudaStream_
 cudaError_t configure_group_kernels() {
   const int lim = 227 * 1024;
   cudaError_t e;
-  if ((e = cudaFuncSetAttribute(k_front_group<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
-  if ((e = cudaFuncSetAttribute(k_front_group<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
   // the whole unified L1 / shared-memory array as shared memory: the residency of
   // these CTAs is bounded by their fronts, not by L1
-  if ((e = cudaFuncSetAttribute(k_front_group<double>, cudaFuncAttributePreferredSharedMemoryCarveout,
-                                cudaSharedmemCarveoutMaxShared)))
-    return e;
-  if ((e = cudaFuncSetAttribute(k_front_group<float>, cudaFuncAttributePreferredSharedMemoryCarveout,
-                                cudaSharedmemCarveoutMaxShared)))
-    return e;
+  const void* fns[] = {(const void*)k_front_group<double, 1>, (const void*)k_front_group<double, 2>,
+                       (const void*)k_front_group<double, 4>, (const void*)k_front_group<double, 8>,
+                       (const void*)k_front_group<float, 1>,  (const void*)k_front_group<float, 2>,
+                       (const void*)k_front_group<float, 4>,  (const void*)k_front_group<float, 8>};
+  for (const void* f : fns) {
+    if ((e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
+    if ((e = cudaFuncSetAttribute(f, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared)))
+      return e;
+  }
   return cudaSuccess;
 }
 
