@@ -207,13 +207,23 @@ __global__ void k_descent(const NodeDev* __restrict__ nodes, const int32_t* __re
   for (int i = threadIdx.x; i < b; i += blockDim.x) uB[i] = (T)us[vid[m + i]];
   __syncthreads();
   const T* Y = fac_Y<T>(A, nd, s);
-  for (int c = warp; c < m; c += nwarp) {
-    const T* col = F + (int64_t)c * nf;
-    T acc = (T)0;
-    for (int i = lane; i < b; i += 32) acc += col[m + i] * uB[i];
+  // four columns per warp and pass, their loads in flight together
+  for (int c0 = 4 * warp; c0 < m; c0 += 4 * nwarp) {
+    T acc[4] = {(T)0, (T)0, (T)0, (T)0};
+    for (int i = lane; i < b; i += 32) {
+      const T ub = uB[i];
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-    if (lane == 0) t[c] = Y[c] - acc;
+      for (int q = 0; q < 4; ++q)
+        if (c0 + q < m) acc[q] += F[(int64_t)(c0 + q) * nf + m + i] * ub;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) acc[q] += __shfl_xor_sync(0xffffffffu, acc[q], o);
+    if (lane == 0)
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+        if (c0 + q < m) t[c0 + q] = Y[c0 + q] - acc[q];
   }
   T* Ld = t + ((m + 3) & ~3);   // [32][33] diagonal block of L_gg, staged per block
   for (int cb = ((m - 1) / 32) * 32; cb >= 0; cb -= 32) {
@@ -235,12 +245,20 @@ __global__ void k_descent(const NodeDev* __restrict__ nodes, const int32_t* __re
       if (lane < jb) t[cb + lane] = x;    // now u_g
     }
     __syncthreads();
-    for (int c = warp; c < cb; c += nwarp) {
-      const T* col = F + (int64_t)c * nf + cb;
-      T acc = (lane < jb) ? col[lane] * t[cb + lane] : (T)0;
+    const T ul = (lane < jb) ? t[cb + lane] : (T)0;
+    for (int c0 = 4 * warp; c0 < cb; c0 += 4 * nwarp) {   // four columns per pass, loads first
+      T acc[4];
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-      if (lane == 0) t[c] -= acc;
+      for (int q = 0; q < 4; ++q)
+        acc[q] = (c0 + q < cb && lane < jb) ? F[(int64_t)(c0 + q) * nf + cb + lane] * ul : (T)0;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) acc[q] += __shfl_xor_sync(0xffffffffu, acc[q], o);
+      if (lane == 0)
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+          if (c0 + q < cb) t[c0 + q] -= acc[q];
     }
   }
   __syncthreads();
