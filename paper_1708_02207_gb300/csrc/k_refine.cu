@@ -83,15 +83,7 @@ __global__ void k_forward(const NodeDev* __restrict__ nodes, const int32_t* __re
     __syncthreads();
     for (int i = cb + jb + threadIdx.x; i < nf - 1; i += blockDim.x) {
       T acc = (T)0;
-      if (jb == 32) {   // a full block: all 32 loads issued before the products
-        T f[32];
-#pragma unroll
-        for (int c = 0; c < 32; ++c) f[c] = F[(int64_t)(cb + c) * nf + i];
-#pragma unroll
-        for (int c = 0; c < 32; ++c) acc += f[c] * z[cb + c];
-      } else {
-        for (int c = 0; c < jb; ++c) acc += F[(int64_t)(cb + c) * nf + i] * z[cb + c];
-      }
+      for (int c = 0; c < jb; ++c) acc += F[(int64_t)(cb + c) * nf + i] * z[cb + c];
       z[i] -= acc;
     }
   }
