@@ -103,8 +103,9 @@ template <typename T>
 static int sweep_stride(int max_nf, int max_m, int* stage) {
   const size_t vec = (size_t)((max_nf + 3) & ~3);
   const size_t fac = (size_t)max_nf * max_m;
-  *stage = (vec + fac) * sizeof(T) <= 64 * 1024;
-  return (int)(*stage ? vec + fac : vec);
+  const size_t yg = (size_t)((max_m + 3) & ~3);   // y_g (descent)
+  *stage = (vec + fac + yg) * sizeof(T) <= 64 * 1024;
+  return (int)(*stage ? vec + fac + yg : vec + yg);
 }
 
 template <typename T>
@@ -152,6 +153,8 @@ __global__ void __launch_bounds__(256) k_descent_warp(const NodeDev* __restrict_
   const T* Y = node_Y<T>(A, nd, s);
   double* us = u + (int64_t)s * u_stride;
   for (int i = lane; i < b; i += 32) wv[m + i] = (T)us[vid[m + i]];
+  T* ys = wv + ((nf + 3) & ~3) + (stage ? nf * m : 0);   // y_g, staged with the rest
+  for (int c = lane; c < m; c += 32) ys[c] = Y[c];
   __syncwarp();
   for (int c = m - 1; c >= 0; --c) {
     const T* col = F + (int64_t)c * nf;
@@ -159,7 +162,7 @@ __global__ void __launch_bounds__(256) k_descent_warp(const NodeDev* __restrict_
     for (int r = c + 1 + lane; r < nf - 1; r += 32) acc += col[r] * wv[r];
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(kFull, acc, o);
-    const T uc = (Y[c] - acc) / col[c];
+    const T uc = (ys[c] - acc) / col[c];
     if (lane == 0) wv[c] = uc;
     __syncwarp();
   }
