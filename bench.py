@@ -53,7 +53,7 @@ MEASURED = _measured_peaks()
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of a kernel family, summed over
 # the launches of one step of a 32-sample run of the same workload and divided by 32.
 MEASURED_TRAFFIC = {
-    "front_small": {"workload": "grid513", "leaf": 4, "precision": "mixed", "bytes_per_sample": 4.613e9 / 32,
+    "front_small": {"workload": "grid513", "leaf": 4, "precision": "mixed", "bytes_per_sample": 4.615e9 / 32,
                     "source": "profiles/k_front_group_grid513_b32.md"},
 }
 
