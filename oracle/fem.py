@@ -138,6 +138,37 @@ def solve_full(N: int, kappa: np.ndarray, f=1.0, refine: bool = False) -> np.nda
     return full
 
 
+def solve_load(N: int, kappa: np.ndarray, c: np.ndarray, refine: bool = False) -> np.ndarray:
+    """FE solution for an assembled load vector c [N*N] (entries at boundary vertices
+    ignored): A_II u_I = c_I, zero on the boundary.  The operators are independent of
+    the load, so one factorisation serves many right-hand sides (Sec. 2); here every
+    call simply solves again."""
+    A, _ = assemble(N, kappa)
+    I = interior_ids(N)
+    AI = A[I][:, I].tocsr()
+    cI = np.asarray(c, dtype=np.float64)[I]
+    u = solve_banded_cholesky(AI, cI, N - 1)
+    if refine:
+        u = refine_longdouble(AI, cI, u, N - 1)
+    full = np.zeros(N * N)
+    full[I] = u
+    return full
+
+
+def subdomain_mean(N: int, u: np.ndarray, x0: int, x1: int, y0: int, y1: int) -> float:
+    """Mean of the piecewise linear u over the rectangle [x0, x1] x [y0, y1] (vertex
+    indices), Sec. 5, Eq. mean: sum over its triangles of |t|/3 (u_1 + u_2 + u_3),
+    divided by the summed area of those triangles."""
+    coords, tris = mesh(N)
+    _, area = element_matrices(coords, tris, np.ones(tris.shape[0]))
+    cj, ci = np.meshgrid(np.arange(y0, y1), np.arange(x0, x1), indexing="ij")
+    cell = (cj * (N - 1) + ci).ravel()
+    t = np.concatenate([2 * cell, 2 * cell + 1])
+    u = np.asarray(u, dtype=np.float64)
+    integral = np.sum(area[t] / 3.0 * u[tris[t]].sum(axis=1))
+    return float(integral / np.sum(area[t]))
+
+
 def loglik(u_obs: np.ndarray, y: np.ndarray, sigma: float) -> float:
     """Gaussian log-likelihood of Sec. 1.2 with i.i.d. N(0, sigma^2) noise."""
     r = np.asarray(y, dtype=np.float64) - np.asarray(u_obs, dtype=np.float64)

@@ -221,3 +221,71 @@ def test_refinement_does_not_move_an_accurate_solve():
     u0 = fem.solve_full(N, kap)
     u1 = fem.solve_full(N, kap, refine=True)
     assert np.max(np.abs(u1 - u0)) < 1e-12 * np.max(np.abs(u0))
+
+
+@pytest.mark.parametrize("N", [9, 17, 33])
+def test_solve_load_eigenvector_closed_form(N):
+    # an assembled load c = h^2 sin(pi x) sin(pi y) at kappa = 1 gives
+    # u = c / (4 - 4 cos(pi h)) (the (1,1) eigenvector of the 5-point matrix);
+    # values at boundary vertices are not part of the load and must be ignored
+    h = 1.0 / (N - 1)
+    x = np.arange(N) * h
+    F = np.outer(np.sin(np.pi * x), np.sin(np.pi * x)).ravel()
+    c = h * h * F
+    bnd = np.setdiff1d(np.arange(N * N), fem.interior_ids(N))
+    c_noisy = c.copy()
+    c_noisy[bnd] = np.random.default_rng(N).standard_normal(bnd.size)
+    u = fem.solve_load(N, np.ones(2 * (N - 1) ** 2), c_noisy)
+    ref = c / (4.0 - 4.0 * np.cos(np.pi * h))
+    ref[bnd] = 0.0
+    assert np.max(np.abs(u - ref)) < 1e-13 * np.max(np.abs(ref))
+
+
+def test_solve_load_superposition_and_vertex_quadrature():
+    # the load of f = 1 by vertex quadrature (Eq. coefc) reproduces the constant-f
+    # solve; the solve is linear in c
+    N = 17
+    kap = _kappa_random(N, 3, amp=1.5)
+    _, c1 = fem.assemble(N, kap, 1.0)
+    u1 = fem.solve_load(N, kap, c1)
+    assert np.max(np.abs(u1 - fem.solve_full(N, kap))) < 1e-14 * np.max(np.abs(u1))
+    c2 = np.random.default_rng(4).random(N * N) / (N - 1) ** 2
+    u2 = fem.solve_load(N, kap, c2)
+    u12 = fem.solve_load(N, kap, c1 - 3.0 * c2)
+    assert np.max(np.abs(u12 - (u1 - 3.0 * u2))) < 1e-12 * np.max(np.abs(u12))
+
+
+def test_subdomain_mean_of_an_affine_field():
+    # P1 reproduces affine functions: the mean over a rectangle is the value at its centre
+    N = 17
+    h = 1.0 / (N - 1)
+    jj, ii = np.meshgrid(np.arange(N), np.arange(N), indexing="ij")
+    u = (0.3 + 1.7 * ii * h - 0.9 * jj * h).ravel()
+    for x0, x1, y0, y1 in [(0, 16, 0, 16), (3, 7, 2, 11), (5, 6, 9, 10), (0, 8, 8, 16)]:
+        ref = 0.3 + 1.7 * 0.5 * (x0 + x1) * h - 0.9 * 0.5 * (y0 + y1) * h
+        assert abs(fem.subdomain_mean(N, u, x0, x1, y0, y1) - ref) < 1e-14
+
+
+def test_subdomain_mean_of_the_domain_is_the_load_pairing():
+    # int_Omega u_h = sum_i u_i int b_i = sum_i u_i sum_{t containing i} |t|/3 = c . u with
+    # c the f = 1 load by vertex quadrature (Eq. coefc), whatever u is (boundary included)
+    N = 13
+    u = np.random.default_rng(5).standard_normal(N * N)
+    _, c = fem.assemble(N, np.ones(2 * (N - 1) ** 2), 1.0)
+    assert abs(fem.subdomain_mean(N, u, 0, N - 1, 0, N - 1) - np.dot(c, u)) < 1e-14 * np.abs(u).sum()
+
+
+def test_subdomain_means_follow_the_tree_recursion():
+    # Sec. 5.1: the mean over a father is c_1 mean_1 + c_2 mean_2 with c_i = |omega_i| / |omega|
+    from oracle import hdd_dense
+    N = 21
+    u = np.random.default_rng(6).standard_normal(N * N)
+    nodes = hdd_dense.build_tree(N, 4)
+    area = lambda nd: (nd.x1 - nd.x0) * (nd.y1 - nd.y0)
+    mean = [fem.subdomain_mean(N, u, nd.x0, nd.x1, nd.y0, nd.y1) for nd in nodes]
+    for k, nd in enumerate(nodes):
+        if nd.leaf:
+            continue
+        a, b = nd.children
+        ref = (area(nodes[a]) * mean[a] + area(nodes[b]) * mean[b]) / area(nd)
+        assert abs(mean[k] - ref) < 1e-14 * max(1.0, abs(ref))
