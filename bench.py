@@ -374,6 +374,52 @@ def run_hdd(args, cfg):
     upsweep_roof = {"achieved": up_flops / (stage_ms["upsweep"] / 1e3) / 1e12, "unit": "TFLOP/s",
                     "note": "whole hdd_upsweep call"}
 
+    # many loads at a fixed coefficient field (hdd_solve_loads on the factors of one upsweep)
+    # and the subdomain means of the result; timed after the headline step, not part of it
+    loads = None
+    if args.loads > 0:
+        NN = cfg.N * cfg.N
+        gen = torch.Generator(device=dev)
+        gen.manual_seed(1708_02207)
+        c_l = torch.rand(B, args.loads, NN, dtype=torch.float64, device=dev, generator=gen) / (cfg.N - 1) ** 2
+        u_l = torch.empty_like(c_l)
+        s_l = torch.empty(B, dtype=torch.int32, device=dev)
+        means = torch.empty(B, info["n_nodes"], dtype=torch.float64, device=dev)
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        with torch.cuda.stream(stream):
+            plan.assemble(Z, ws, stream)
+            plan.upsweep(B, ws, stream)
+            for _ in range(args.warmup):
+                plan.solve_loads(B, ws, c_l, u_l, s_l, stream)
+                plan.subdomain_means(u_l[:, 0, :], means, stream)
+            ev[0].record(stream)
+            for _ in range(args.steps):
+                plan.solve_loads(B, ws, c_l, u_l, s_l, stream)
+            ev[1].record(stream)
+            for _ in range(args.steps):
+                plan.subdomain_means(u_l[:, 0, :], means, stream)
+            ev[2].record(stream)
+        stream.synchronize()
+        t_l = ev[0].elapsed_time(ev[1]) / args.steps
+        t_m = ev[1].elapsed_time(ev[2]) / args.steps
+        v8 = 8.0 * NN   # one FP64 vertex vector
+        # per load and sample: zero u; (1 + K) sweeps and full descents; K residuals (kappa, u
+        # and c in, r out), updates (u, du in, u out) and correction maxima (du in; u at the last)
+        by_load = v8 + (1 + K) * (info["bytes_forward"] + info["bytes_descent_all"]) \
+            + K * (info["bytes_residual"] + v8) + K * 3 * v8 + (K * v8 + v8 if K else 0.0)
+        by_l = by_load * B * args.loads
+        by_m = (v8 + 8.0 * info["n_nodes"]) * B
+        loads = {"loads_per_sample": args.loads, "ms_per_call": t_l,
+                 "load_solves_per_s": world * B * args.loads / (t_l / 1e3),
+                 "failed_samples": int((s_l != 0).sum().item()),
+                 "roofline": {"bound": "hbm", "achieved": by_l / (t_l / 1e3) / 1e9, "peak": hbm, "unit": "GB/s",
+                              "frac": by_l / (t_l / 1e3) / 1e9 / hbm, "algorithmic_bytes_per_call": by_l},
+                 "subdomain_means": {"ms_per_call": t_m, "nodes": info["n_nodes"],
+                                     "achieved_gbs": by_m / (t_m / 1e3) / 1e9,
+                                     "frac": by_m / (t_m / 1e3) / 1e9 / hbm}}
+        del c_l, u_l
+        torch.cuda.empty_cache()
+
     # the plain FP64 path on the same inputs (the speedup of the mixed path is over it)
     fp64 = None
     if precision != hdd.HDD_FP64 and args.fp64_steps > 0:
@@ -427,6 +473,7 @@ def run_hdd(args, cfg):
         "stage_ms": stage_ms, "failed_samples": bad,
         "latency_ms": {"p50": pct(0.5), "p99": pct(0.99), "note": "per step (one batch of samples)"},
         "fp64_path": fp64,
+        "solve_loads": loads,
         "roofline": roof,
         "upsweep": upsweep_roof,
         "stages": stages_roof,
@@ -460,6 +507,8 @@ def main(argv=None):
     ap.add_argument("--ir-iters", type=int, default=2)
     ap.add_argument("--ir-tol", type=float, default=1e-8)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--loads", type=int, default=1,
+                    help="load vectors per sample of the hdd_solve_loads measurement (0: skip)")
     args = ap.parse_args(argv)
     cfg = w.CONFIGS[args.config]
     if args.impl == "reference":

@@ -13,6 +13,9 @@
  *   hdd_upsweep      "Leaves to Root": Schur maps of every node    (Sec. 2.4, 3.3, 3.4)
  *   hdd_point_solve  pruned "Root to Leaves" to the observation vertices (Sec. 3.4, 5.3)
  *   hdd_loglik       Gaussian data-misfit log-likelihood           (Sec. 1.2)
+ * and, on the same factors:
+ *   hdd_solve_loads      many load vectors at a fixed kappa         (Sec. 2)
+ *   hdd_subdomain_means  mean of u over every subdomain of the tree (Sec. 5, 5.1)
  *
  * Conventions shared by every call
  *   - Vertex (i, j) of the grid sits at (i h, j h), h = 1/(N-1), flat id j*N + i.
@@ -162,7 +165,9 @@ hdd_status hdd_upsweep(hdd_plan_t plan, int32_t batch, void* workspace, void* st
 /* Pruned "Root to Leaves" (Sec. 3.4, Sec. 5.3): from the root down the nodes on
  * the paths to the observation vertices, u_gamma = L_gg^-T (y_g - L_Bg^T u_B);
  * then u at the observation vertices.  Mixed precision adds FP64-residual
- * iterative refinement (full descents).  u_obs: device, [batch x n_obs] FP64. */
+ * iterative refinement (full descents).  u_obs: device, [batch x n_obs] FP64.
+ * Refinement reuses the stored y_gamma for its correction sweeps, so on mixed
+ * plans call it once per hdd_upsweep (FP64 plans leave y_gamma unchanged). */
 hdd_status hdd_point_solve(hdd_plan_t plan, int32_t batch, void* workspace, double* u_obs,
                            void* stream);
 
@@ -187,6 +192,44 @@ hdd_status hdd_evaluate_host(hdd_plan_t plan, int32_t batch, void* workspace,
                              const double* Z, const double* y, int32_t y_per_sample,
                              double* loglik, double* u_obs, int32_t* sample_status,
                              void* stream);
+
+/* Multiple loads at a fixed coefficient field (Sec. 2: the operators of every
+ * node are computed once, by hdd_upsweep, and then applied to any number of
+ * right-hand sides).  For each sample and each of its n_loads load vectors c,
+ * solves K u = c over the unknowns through the stored factors: a right-hand-side
+ * sweep ("Leaves to Root" with the stored L_gg, L_Bg: y_g = L_gg^-1 c_g,
+ * condensed load c_B - L_Bg y_g), then "Root to Leaves" over every node.  Mixed
+ * plans add ir_max_iter refinement steps (FP64 residual c - K u over all
+ * unknowns, a correction solve through the same factors) and mark a sample
+ * HDD_ENOCONV when the last correction, scaled by the observed contraction,
+ * exceeds ir_tol * max |u| (the test hdd_point_solve applies at the
+ * observation vertices).
+ *   c: device [batch x n_loads x N^2] FP64, the assembled load per vertex
+ *      c_i = sum_{t containing x_i} |t|/3 f(x_i) (Eq. coefc), i.e. h^2 f(x_i)
+ *      at the interior vertices of this mesh; entries at boundary vertices are
+ *      ignored.
+ *   u: device [batch x n_loads x N^2] FP64, written at every vertex (0 on the
+ *      boundary: Dirichlet data g = 0).
+ *   sample_status: device [batch] int32 or NULL, as in hdd_loglik (it also
+ *      carries the HDD_ENOTSPD flags of the upsweep).
+ * Needs the workspace of hdd_assemble + hdd_upsweep with the same batch.  It
+ * overwrites the stored y_gamma and the workspace's solution vectors: run
+ * hdd_point_solve for the plan's own load before it, or hdd_upsweep again
+ * after it. */
+hdd_status hdd_solve_loads(hdd_plan_t plan, int32_t batch, void* workspace, const double* c, int32_t n_loads,
+                           double* u, int32_t* sample_status, void* stream);
+
+/* Mean of u over every subdomain omega of the tree (Sec. 5, Eq. mean):
+ * mean(omega) = sum_{t in omega} |t|/3 (u_1 + u_2 + u_3) / |omega|, computed at
+ * the leaves from u and at each father from its sons as in Sec. 5.1,
+ * mean(omega) = c_1 mean(omega_1) + c_2 mean(omega_2), c_i = |omega_i| / |omega|.
+ *   u: device FP64, sample s at u + s * u_stride, N^2 values (vertex j*N + i),
+ *      e.g. from hdd_solve_loads; u_stride >= N^2.
+ *   means: device [batch x n_nodes] FP64, in the node numbering of
+ *      hdd_node_info (node 0 = the root, the whole domain).
+ * Needs no workspace.  One launch per tree height. */
+hdd_status hdd_subdomain_means(hdd_plan_t plan, int32_t batch, const double* u, int64_t u_stride, double* means,
+                               void* stream);
 
 /* Evaluation without any allocation and without a caller workspace.  The paper
  * has no counterpart: this entry point exists for callers that cannot allocate

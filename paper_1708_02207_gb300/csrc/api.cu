@@ -226,19 +226,18 @@ cudaError_t run_upsweep(const hdd::Plan& p, int batch, void* ws, const hdd::Rhs&
 
 // "Root to Leaves" over the given per-depth lists, writing u (FP64).
 cudaError_t run_descent(const hdd::Plan& p, int batch, void* ws, const std::vector<std::array<int, 3>>& per_depth,
-                        double* u, cudaStream_t st, hdd::Profiler* prof) {
+                        double* u, int64_t u_stride, cudaStream_t st, hdd::Profiler* prof) {
   const hdd::Layout L = hdd::layout(p, batch);
   const hdd::Arenas A = arenas(p, L, ws);
-  const int64_t NN = (int64_t)p.N * p.N;
   for (int d = 0; d <= p.depth; ++d) {
     for (int kind = 1; kind < 3; ++kind) {   // condensed leaves of this depth
       const hdd::ListInfo& ll = p.lists[per_depth[d][kind]];
       if (ll.n == 0) continue;
       ProfScope ps(prof, hdd::kProfDescent, 0.0, st);
       cudaError_t e = kind == 1 ? hdd::launch_leaf_descent<double>(p.d_nodes, p.d_maps, p.d_lists + ll.off, ll.n,
-                                                                   batch, A, u, NN, st)
+                                                                   batch, A, u, u_stride, st)
                                 : hdd::launch_leaf_descent<float>(p.d_nodes, p.d_maps, p.d_lists + ll.off, ll.n,
-                                                                  batch, A, u, NN, st);
+                                                                  batch, A, u, u_stride, st);
       if (e != cudaSuccess) return e;
     }
     const hdd::ListInfo& li = p.lists[per_depth[d][0]];
@@ -251,17 +250,17 @@ cudaError_t run_descent(const hdd::Plan& p, int batch, void* ws, const std::vect
     ProfScope ps(prof, hdd::kProfDescent, 0.0, st);
     cudaError_t e;
     if (li.max_nf <= hdd::kTinyMax)
-      e = fp64 ? hdd::launch_descent_tiny<double>(p.d_nodes, p.d_maps, p.d_lists + li.off, li.n, batch, A, u, NN, st)
-               : hdd::launch_descent_tiny<float>(p.d_nodes, p.d_maps, p.d_lists + li.off, li.n, batch, A, u, NN, st);
+      e = fp64 ? hdd::launch_descent_tiny<double>(p.d_nodes, p.d_maps, p.d_lists + li.off, li.n, batch, A, u, u_stride, st)
+               : hdd::launch_descent_tiny<float>(p.d_nodes, p.d_maps, p.d_lists + li.off, li.n, batch, A, u, u_stride, st);
     else if (cta)
-      e = fp64 ? hdd::launch_descent<double>(p.d_nodes, p.d_maps, p.d_lists + li.off, li.n, batch, A, u, NN,
+      e = fp64 ? hdd::launch_descent<double>(p.d_nodes, p.d_maps, p.d_lists + li.off, li.n, batch, A, u, u_stride,
                                              li.max_b, li.max_m, st)
-               : hdd::launch_descent<float>(p.d_nodes, p.d_maps, p.d_lists + li.off, li.n, batch, A, u, NN,
+               : hdd::launch_descent<float>(p.d_nodes, p.d_maps, p.d_lists + li.off, li.n, batch, A, u, u_stride,
                                             li.max_b, li.max_m, st);
     else
-      e = fp64 ? hdd::launch_descent_warp<double>(p.d_nodes, p.d_maps, p.d_lists + li.off, li.n, batch, A, u, NN,
+      e = fp64 ? hdd::launch_descent_warp<double>(p.d_nodes, p.d_maps, p.d_lists + li.off, li.n, batch, A, u, u_stride,
                                                   li.max_nf, li.max_m, st)
-               : hdd::launch_descent_warp<float>(p.d_nodes, p.d_maps, p.d_lists + li.off, li.n, batch, A, u, NN,
+               : hdd::launch_descent_warp<float>(p.d_nodes, p.d_maps, p.d_lists + li.off, li.n, batch, A, u, u_stride,
                                                  li.max_nf, li.max_m, st);
     if (e != cudaSuccess) return e;
   }
@@ -323,23 +322,56 @@ cudaError_t run_refined_solve(const hdd::Plan& p, int batch, void* ws, double* u
   const int64_t NN = (int64_t)p.N * p.N;
   const double load = p.h * p.h * p.f;
   const int K = p.ir_max_iter;
-  cudaError_t e = run_descent(p, batch, ws, K > 0 ? p.down_all_lists : p.down_vis_lists, u, st, prof);
+  cudaError_t e = run_descent(p, batch, ws, K > 0 ? p.down_all_lists : p.down_vis_lists, u, NN, st, prof);
   for (int it = 1; it <= K && e == cudaSuccess; ++it) {
     const bool last = it == K;
     {
       ProfScope ps(prof, hdd::kProfResidual, 0.0, st);
-      e = hdd::launch_residual(kappa, p.n_t, u, NN, p.N, load, r, batch, st);
+      e = hdd::launch_residual(kappa, p.n_t, u, NN, p.N, load, nullptr, 0, r, NN, batch, st);
     }
     if (e == cudaSuccess) e = run_forward(p, batch, ws, hdd::Rhs{r, NN, 0.0}, st, prof);
-    if (e == cudaSuccess) e = run_descent(p, batch, ws, last ? p.down_vis_lists : p.down_all_lists, du, st, prof);
+    if (e == cudaSuccess) e = run_descent(p, batch, ws, last ? p.down_vis_lists : p.down_all_lists, du, NN, st, prof);
     ProfScope ps(prof, hdd::kProfMisc, 0.0, st);
     if (e == cudaSuccess && !last) e = hdd::launch_delta_obs(du, NN, p.d_obs, p.n_obs, dprev, batch, st);
-    if (e == cudaSuccess && !last) e = hdd::launch_update(u, du, NN, p.N, batch, st);
+    if (e == cudaSuccess && !last) e = hdd::launch_update(u, NN, du, NN, p.N, batch, st);
   }
   if (e == cudaSuccess) {
     ProfScope ps(prof, hdd::kProfMisc, 0.0, st);
     e = hdd::launch_final_obs(u, K > 0 ? du : nullptr, NN, p.d_obs, p.n_obs, K > 0 ? p.ir_tol : -1.0, dprev, u_obs,
                               status, batch, st);
+  }
+  return e;
+}
+
+// One load vector per sample through the stored factors (the operators of every
+// node are computed once and applied to any right-hand side): right-hand-side
+// sweep with b = c, full descent into u; mixed plans then take ir_max_iter FP64
+// refinement steps over every unknown.
+cudaError_t run_load_solve(const hdd::Plan& p, int batch, void* ws, const double* c, int64_t c_stride, double* u,
+                           int64_t u_stride, cudaStream_t st, hdd::Profiler* prof) {
+  const hdd::Layout L = hdd::layout(p, batch);
+  char* w = static_cast<char*>(ws);
+  double* r = reinterpret_cast<double*>(w + L.r);
+  double* du = reinterpret_cast<double*>(w + L.du);
+  const double* kappa = reinterpret_cast<const double*>(w + L.kappa);
+  int32_t* status = reinterpret_cast<int32_t*>(w + L.status);
+  double* dprev = reinterpret_cast<double*>(w + L.conv);
+  const int64_t NN = (int64_t)p.N * p.N;
+  cudaError_t e = run_forward(p, batch, ws, hdd::Rhs{c, c_stride, 0.0}, st, prof);
+  if (e == cudaSuccess) e = run_descent(p, batch, ws, p.down_all_lists, u, u_stride, st, prof);
+  if (p.precision != HDD_MIXED_FP32) return e;
+  const int K = p.ir_max_iter;
+  if (e == cudaSuccess && K > 0) e = cudaMemsetAsync(dprev, 0, (size_t)batch * 8, st);
+  for (int it = 1; it <= K && e == cudaSuccess; ++it) {
+    {
+      ProfScope ps(prof, hdd::kProfResidual, 0.0, st);
+      e = hdd::launch_residual(kappa, p.n_t, u, u_stride, p.N, 0.0, c, c_stride, r, NN, batch, st);
+    }
+    if (e == cudaSuccess) e = run_forward(p, batch, ws, hdd::Rhs{r, NN, 0.0}, st, prof);
+    if (e == cudaSuccess) e = run_descent(p, batch, ws, p.down_all_lists, du, NN, st, prof);
+    ProfScope ps(prof, hdd::kProfMisc, 0.0, st);
+    if (e == cudaSuccess) e = hdd::launch_update(u, u_stride, du, NN, p.N, batch, st);
+    if (e == cudaSuccess) e = hdd::launch_conv_full(du, NN, u, u_stride, p.N, p.ir_tol, dprev, status, it == K, batch, st);
   }
   return e;
 }
@@ -503,7 +535,7 @@ hdd_status hdd_point_solve(hdd_plan_t plan, int32_t batch, void* workspace, doub
   if (p.precision == HDD_MIXED_FP32) {
     e = run_refined_solve(p, batch, workspace, u_obs, st, profiler(plan));
   } else {
-    e = run_descent(p, batch, workspace, p.down_vis_lists, u, st, profiler(plan));
+    e = run_descent(p, batch, workspace, p.down_vis_lists, u, NN, st, profiler(plan));
     ProfScope ps(profiler(plan), hdd::kProfMisc, 0.0, st);
     if (e == cudaSuccess) e = hdd::launch_gather_obs(u, NN, p.d_obs, p.n_obs, batch, u_obs, st);
   }
@@ -563,6 +595,52 @@ hdd_status hdd_evaluate_host(hdd_plan_t plan, int32_t batch, void* workspace, co
     e = cudaMemcpyAsync(sample_status, w + L.status, (size_t)batch * 4, cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   return e == cudaSuccess ? HDD_OK : fail_cuda(e, "hdd_evaluate_host");
+}
+
+hdd_status hdd_solve_loads(hdd_plan_t plan, int32_t batch, void* workspace, const double* c, int32_t n_loads,
+                           double* u, int32_t* sample_status, void* stream) {
+  hdd_status s = check_call(plan, batch, workspace);
+  if (s != HDD_OK) return s;
+  if (!c || !u) return fail_inval("c or u is NULL");
+  if (n_loads < 1) return fail_inval("n_loads must be >= 1");
+  const hdd::Plan& p = plan->p;
+  DeviceScope ds(p.device);
+  if (ds.err != cudaSuccess) return fail_cuda(ds.err, "cudaSetDevice");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const int64_t NN = (int64_t)p.N * p.N;
+  const int64_t stride = (int64_t)n_loads * NN;   // elements between samples of c and u
+  cudaError_t e = cudaMemsetAsync(u, 0, (size_t)batch * stride * 8, st);   // Dirichlet vertices: g = 0
+  for (int k = 0; k < n_loads && e == cudaSuccess; ++k)
+    e = run_load_solve(p, batch, workspace, c + k * NN, stride, u + k * NN, stride, st, profiler(plan));
+  if (e == cudaSuccess && sample_status)
+    e = cudaMemcpyAsync(sample_status, static_cast<char*>(workspace) + hdd::layout(p, batch).status,
+                        (size_t)batch * 4, cudaMemcpyDeviceToDevice, st);
+  return e == cudaSuccess ? HDD_OK : fail_cuda(e, "hdd_solve_loads");
+}
+
+hdd_status hdd_subdomain_means(hdd_plan_t plan, int32_t batch, const double* u, int64_t u_stride, double* means,
+                               void* stream) {
+  if (!plan) return fail_inval("plan is NULL");
+  const hdd::Plan& p = plan->p;
+  if (p.device < 0) {
+    g_err = "host-only plan";
+    return HDD_ESTATE;
+  }
+  if (batch < 1 || batch > 65535) return fail_inval("batch must be in 1..65535");
+  if (!u || !means) return fail_inval("u or means is NULL");
+  if (u_stride < (int64_t)p.N * p.N) return fail_inval("u_stride must be >= N*N");
+  DeviceScope ds(p.device);
+  if (ds.err != cudaSuccess) return fail_cuda(ds.err, "cudaSetDevice");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const int64_t ms = (int64_t)p.nodes.size();
+  ProfScope ps(profiler(plan), hdd::kProfMisc, 0.0, st);
+  cudaError_t e = cudaSuccess;
+  for (int h = 0; h <= p.height && e == cudaSuccess; ++h) {
+    const hdd::ListInfo& li = p.lists[p.height_lists[h]];
+    e = h == 0 ? hdd::launch_leaf_means(p.d_nodes, p.d_lists + li.off, li.n, u, u_stride, p.N, means, ms, batch, st)
+               : hdd::launch_father_means(p.d_nodes, p.d_lists + li.off, li.n, means, ms, batch, st);
+  }
+  return e == cudaSuccess ? HDD_OK : fail_cuda(e, "hdd_subdomain_means");
 }
 
 hdd_status hdd_kappa(hdd_plan_t plan, int32_t batch, void* workspace, double* kappa, void* stream) {

@@ -112,6 +112,8 @@ template cudaError_t launch_forward<float>(const NodeDev*, const int32_t*, const
 // r = b - A u over the unknowns (FP64).  (A u)_v = sum over the four axis edges of
 // w_e (u_v - u_w), w_e = mean kappa of the two triangles having e as a leg;
 // Dirichlet neighbours contribute u_w = 0.  Boundary entries of r are set to 0.
+// b is the constant vertex load `load`, or the vector loadv [batch x load_stride]
+// when it is not null.
 // A thread owns one column i of vertices over kResRows consecutive rows and
 // slides up them, so that every row of u and of the cells' kappa is loaded once
 // per thread (the left and right neighbours come from the adjacent threads'
@@ -120,14 +122,16 @@ constexpr int kResRows = 8;
 
 __global__ void __launch_bounds__(128) k_residual(const double* __restrict__ kappa, int64_t kap_stride,
                                                   const double* __restrict__ u, int64_t u_stride, int N,
-                                                  double load, double* __restrict__ r) {
+                                                  double load, const double* __restrict__ loadv,
+                                                  int64_t load_stride, double* __restrict__ r, int64_t r_stride) {
   const int s = blockIdx.z;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int j0 = blockIdx.y * kResRows;
   if (i >= N) return;
   const double* ks = kappa + (int64_t)s * kap_stride;
   const double* us = u + (int64_t)s * u_stride;
-  double* rs = r + (int64_t)s * u_stride;
+  double* rs = r + (int64_t)s * r_stride;
+  const double* bs = loadv ? loadv + (int64_t)s * load_stride : nullptr;
   const bool col_in = i >= 1 && i <= N - 2;
   auto urow = [&](int j, int di) {   // u at (i + di, j), 0 off the unknowns
     const int ii = i + di;
@@ -151,7 +155,7 @@ __global__ void __launch_bounds__(128) k_residual(const double* __restrict__ kap
       const double wu = 0.5 * (ka1 + ka2);   // (i,j)-(i,j+1): upper-left of (i,j), lower-right of (i-1,j)
       const double wd = 0.5 * (kb0 + kb1);   // (i,j-1)-(i,j): upper-left of (i,j-1), lower-right of (i-1,j-1)
       const double Au = wr * (u_c - ue) + wl * (u_c - uw) + wu * (u_c - u_n) + wd * (u_c - u_s);
-      rs[(int64_t)j * N + i] = load - Au;
+      rs[(int64_t)j * N + i] = (bs ? bs[(int64_t)j * N + i] : load) - Au;
     }
     u_s = u_c;
     u_c = u_n;
@@ -162,25 +166,74 @@ __global__ void __launch_bounds__(128) k_residual(const double* __restrict__ kap
 }
 
 cudaError_t launch_residual(const double* kappa, int64_t kap_stride, const double* u, int64_t u_stride, int N,
-                            double load, double* r, int batch, cudaStream_t st) {
-  k_residual<<<dim3((N + 127) / 128, (N + kResRows - 1) / kResRows, batch), 128, 0, st>>>(kappa, kap_stride, u,
-                                                                                            u_stride, N, load, r);
+                            double load, const double* loadv, int64_t load_stride, double* r, int64_t r_stride,
+                            int batch, cudaStream_t st) {
+  k_residual<<<dim3((N + 127) / 128, (N + kResRows - 1) / kResRows, batch), 128, 0, st>>>(
+      kappa, kap_stride, u, u_stride, N, load, loadv, load_stride, r, r_stride);
   return cudaGetLastError();
 }
 
 // u += du at every interior vertex
-__global__ void k_update(double* __restrict__ u, const double* __restrict__ du, int64_t stride, int N) {
+__global__ void k_update(double* __restrict__ u, int64_t u_stride, const double* __restrict__ du,
+                         int64_t du_stride, int N) {
   const int s = blockIdx.y;
   const int v = blockIdx.x * blockDim.x + threadIdx.x;
   if (v >= N * N) return;
   const int i = v % N, j = v / N;
   if (i < 1 || j < 1 || i > N - 2 || j > N - 2) return;
-  u[(int64_t)s * stride + v] += du[(int64_t)s * stride + v];
+  u[(int64_t)s * u_stride + v] += du[(int64_t)s * du_stride + v];
 }
 
-cudaError_t launch_update(double* u, const double* du, int64_t stride, int N, int batch, cudaStream_t st) {
+cudaError_t launch_update(double* u, int64_t u_stride, const double* du, int64_t du_stride, int N, int batch,
+                          cudaStream_t st) {
   const int NN = N * N;
-  k_update<<<dim3((NN + 255) / 256, batch), 256, 0, st>>>(u, du, stride, N);
+  k_update<<<dim3((NN + 255) / 256, batch), 256, 0, st>>>(u, u_stride, du, du_stride, N);
+  return cudaGetLastError();
+}
+
+// Size of a refinement correction over every unknown (full-field solves):
+// d = max_v |du_v| per sample.  Before the last step d is kept in dprev; after
+// the last update the remaining error, estimated as d_K min(1, d_K / d_{K-1})
+// (no contraction credit when d_{K-1} = 0), is compared with tol * max_v |u_v|
+// and a sample above it is marked HDD_ENOCONV.
+constexpr int kConvThreads = 512;
+__global__ void __launch_bounds__(kConvThreads) k_conv_full(const double* __restrict__ du, int64_t du_stride,
+                                                           const double* __restrict__ u, int64_t u_stride, int N,
+                                                           double tol, double* __restrict__ dprev,
+                                                           int32_t* status, int last) {
+  __shared__ double red_d[kConvThreads], red_u[kConvThreads];
+  const int s = blockIdx.x;
+  const int n = N - 2;   // unknowns per row and column
+  double md = 0.0, mu = 0.0;
+  for (int q = threadIdx.x; q < n * n; q += kConvThreads) {
+    const int64_t v = (int64_t)(q / n + 1) * N + (q % n + 1);
+    md = fmax(md, fabs(du[(int64_t)s * du_stride + v]));
+    if (last) mu = fmax(mu, fabs(u[(int64_t)s * u_stride + v]));
+  }
+  red_d[threadIdx.x] = md;
+  red_u[threadIdx.x] = mu;
+  __syncthreads();
+  for (int w = kConvThreads / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) {
+      red_d[threadIdx.x] = fmax(red_d[threadIdx.x], red_d[threadIdx.x + w]);
+      red_u[threadIdx.x] = fmax(red_u[threadIdx.x], red_u[threadIdx.x + w]);
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x != 0) return;
+  const double dK = red_d[0];
+  if (!last) {
+    dprev[s] = dK;
+    return;
+  }
+  const double dp = dprev[s];
+  const double est = (dp > 0.0) ? dK * fmin(1.0, dK / dp) : dK;
+  if (tol >= 0.0 && !(est <= tol * red_u[0])) flag_status(status, s, -HDD_ENOCONV, 0);
+}
+
+cudaError_t launch_conv_full(const double* du, int64_t du_stride, const double* u, int64_t u_stride, int N,
+                             double tol, double* dprev, int32_t* status, bool last, int batch, cudaStream_t st) {
+  k_conv_full<<<batch, kConvThreads, 0, st>>>(du, du_stride, u, u_stride, N, tol, dprev, status, last ? 1 : 0);
   return cudaGetLastError();
 }
 

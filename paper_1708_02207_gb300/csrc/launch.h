@@ -120,9 +120,20 @@ cudaError_t launch_descent(const NodeDev* nodes, const int32_t* maps, const int3
 template <typename T>
 cudaError_t launch_forward(const NodeDev* nodes, const int32_t* maps, const int32_t* list, int nlist, int batch,
                            const Arenas& A, const Rhs& rhs, int max_nf, cudaStream_t st);
+// r = b - A u with b = load (loadv == nullptr) or the vertex vector loadv
 cudaError_t launch_residual(const double* kappa, int64_t kap_stride, const double* u, int64_t u_stride, int N,
-                            double load, double* r, int batch, cudaStream_t st);
-cudaError_t launch_update(double* u, const double* du, int64_t stride, int N, int batch, cudaStream_t st);
+                            double load, const double* loadv, int64_t load_stride, double* r, int64_t r_stride,
+                            int batch, cudaStream_t st);
+cudaError_t launch_update(double* u, int64_t u_stride, const double* du, int64_t du_stride, int N, int batch,
+                          cudaStream_t st);
+// refinement of full-field solves: correction size over every unknown, convergence test at the last step
+cudaError_t launch_conv_full(const double* du, int64_t du_stride, const double* u, int64_t u_stride, int N,
+                             double tol, double* dprev, int32_t* status, bool last, int batch, cudaStream_t st);
+// subdomain means (Sec. 5, Eq. mean): leaves from u, fathers from their sons
+cudaError_t launch_leaf_means(const NodeDev* nodes, const int32_t* list, int n, const double* u, int64_t u_stride,
+                              int N, double* means, int64_t m_stride, int batch, cudaStream_t st);
+cudaError_t launch_father_means(const NodeDev* nodes, const int32_t* list, int n, double* means, int64_t m_stride,
+                                int batch, cudaStream_t st);
 cudaError_t launch_delta_obs(const double* du, int64_t stride, const int32_t* obs, int n_obs, double* dprev,
                              int batch, cudaStream_t st);
 cudaError_t launch_final_obs(const double* u, const double* du, int64_t stride, const int32_t* obs, int n_obs,

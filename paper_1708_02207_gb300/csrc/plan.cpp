@@ -441,6 +441,13 @@ std::string build_plan(const hdd_plan_desc& d, Plan& p) {
     for (int hgt = 0; hgt <= p.height; ++hgt)
       p.fwd_lists[hgt] = {add_list(l[0][hgt]), add_list(l[1][hgt]), add_list(l[2][hgt]), add_list(l[3][hgt])};
   }
+  // subdomain means: every node, by height
+  {
+    std::vector<std::vector<int>> l(p.height + 1);
+    for (int k = 0; k < nn; ++k) l[p.nodes[k].height].push_back(k);
+    p.height_lists.assign(p.height + 1, 0);
+    for (int hgt = 0; hgt <= p.height; ++hgt) p.height_lists[hgt] = add_list(l[hgt]);
+  }
   p.down_vis_lists.assign(p.depth + 1, {0, 0, 0});
   p.down_all_lists.assign(p.depth + 1, {0, 0, 0});
   for (int d = 0; d <= p.depth; ++d) {

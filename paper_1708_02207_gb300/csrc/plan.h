@@ -126,6 +126,7 @@ struct Plan {
   std::vector<std::array<int, 3>> down_vis_lists, down_all_lists;
   // [height][fp64, fp32, condensed fp64, condensed fp32]: right-hand-side sweep
   std::vector<std::array<int, 4>> fwd_lists;
+  std::vector<int> height_lists;   // per height: every node (subdomain means)
 
   // device copies
   double* d_phi = nullptr;

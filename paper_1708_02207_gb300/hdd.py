@@ -22,7 +22,7 @@ EXPORTED = [
     "hdd_plan", "hdd_plan_destroy", "hdd_workspace_size", "hdd_assemble", "hdd_upsweep",
     "hdd_point_solve", "hdd_loglik", "hdd_evaluate_host", "hdd_plan_info", "hdd_node_info",
     "hdd_node_indices", "hdd_status_string", "hdd_last_error", "hdd_evaluate_static",
-    "hdd_profile_begin", "hdd_profile_end", "hdd_kappa",
+    "hdd_profile_begin", "hdd_profile_end", "hdd_kappa", "hdd_solve_loads", "hdd_subdomain_means",
 ]
 STATIC_WORKSPACE_BYTES = 32 << 20
 
@@ -86,6 +86,8 @@ def load_library() -> C.CDLL:
     lib.hdd_evaluate_host.argtypes = [vp, i32, vp, pd, pd, i32, pd, pd, pi32, vp]
     lib.hdd_evaluate_static.argtypes = [vp, i32, vp, vp, i32, vp, vp, vp, vp]
     lib.hdd_kappa.argtypes = [vp, i32, vp, vp, vp]
+    lib.hdd_solve_loads.argtypes = [vp, i32, vp, vp, i32, vp, vp, vp]
+    lib.hdd_subdomain_means.argtypes = [vp, i32, vp, C.c_int64, vp, vp]
     lib.hdd_profile_begin.argtypes = [vp]
     lib.hdd_profile_end.argtypes = [vp, C.POINTER(KernelStat), i32, C.POINTER(i32)]
     lib.hdd_plan_info.argtypes = [vp, C.POINTER(PlanInfo)]
@@ -232,6 +234,20 @@ class Plan:
     def point_solve(self, batch: int, ws, u_obs, stream=None):
         _check(self.lib.hdd_point_solve(self._h, batch, _ptr(ws), _ptr(u_obs), _stream_ptr(stream)),
                "hdd_point_solve")
+
+    def solve_loads(self, batch: int, ws, c, u, status=None, stream=None):
+        """hdd_solve_loads: c and u device [batch, n_loads, N*N] FP64 (after assemble + upsweep on ws)."""
+        if c.shape != u.shape or c.dim() != 3 or c.shape[0] != batch or c.shape[2] != self.N * self.N:
+            raise ValueError("c and u must both be [batch, n_loads, N*N]")
+        _check(self.lib.hdd_solve_loads(self._h, batch, _ptr(ws), _ptr(c), int(c.shape[1]), _ptr(u), _ptr(status),
+                                        _stream_ptr(stream)), "hdd_solve_loads")
+
+    def subdomain_means(self, u, means, stream=None):
+        """hdd_subdomain_means: u device [batch, N*N] (any row stride), means device [batch, n_nodes]."""
+        if u.dim() != 2 or u.stride(1) != 1 or u.shape[1] != self.N * self.N:
+            raise ValueError("u must be [batch, N*N] with unit column stride")
+        _check(self.lib.hdd_subdomain_means(self._h, int(u.shape[0]), _ptr(u), int(u.stride(0)), _ptr(means),
+                                            _stream_ptr(stream)), "hdd_subdomain_means")
 
     def loglik(self, batch: int, ws, u_obs, y, loglik, status=None, stream=None):
         per_sample = 1 if y.dim() == 2 else 0
