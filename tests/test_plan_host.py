@@ -87,6 +87,16 @@ def test_invalid_arguments(hdd):
     with pytest.raises(hdd.HDDError) as e:
         plan.upsweep(1, None)
     assert e.value.status == hdd.HDD_ESTATE
+    torch = pytest.importorskip("torch")
+    c = torch.zeros(1, 2, 33 * 33, dtype=torch.float64)
+    with pytest.raises(hdd.HDDError) as e:   # host-only plans refuse device calls before touching buffers
+        plan.solve_loads(1, None, c, c.clone())
+    assert e.value.status == hdd.HDD_ESTATE
+    with pytest.raises(hdd.HDDError) as e:
+        plan.subdomain_means(c[:, 0, :], torch.zeros(1, plan.info()["n_nodes"], dtype=torch.float64))
+    assert e.value.status == hdd.HDD_ESTATE
+    with pytest.raises(ValueError):
+        plan.solve_loads(1, None, c, c[:, :1])
 
 
 def test_flop_count_matches_front_sizes(hdd):
