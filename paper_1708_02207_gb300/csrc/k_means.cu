@@ -9,30 +9,37 @@
 
 namespace hdd {
 
-// One thread per (leaf, sample).  Cell (i, j) holds the lower-right triangle
-// (i,j), (i+1,j), (i+1,j+1) and the upper-left one (i,j), (i+1,j+1), (i,j+1),
-// each of area h^2 / 2: the cell adds h^2 / 6 times the two corner sums, and
-// the leaf's area is cells * h^2, so h^2 cancels.
-__global__ void k_leaf_means(const NodeDev* __restrict__ nodes, const int32_t* __restrict__ list, int n,
-                             const double* __restrict__ u, int64_t u_stride, int N, double* __restrict__ means,
-                             int64_t m_stride) {
-  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+// One warp per (leaf, sample), lanes over the leaf's cells (row by row, so that
+// the lanes of one cell row read consecutive vertices).  Cell (i, j) holds the
+// lower-right triangle (i,j), (i+1,j), (i+1,j+1) and the upper-left one (i,j),
+// (i+1,j+1), (i,j+1), each of area h^2 / 2: the cell adds h^2 / 6 times the two
+// corner sums, and the leaf's area is cells * h^2, so h^2 cancels.  The lane sums
+// are combined by a fixed butterfly, so the result does not depend on timing.
+constexpr int kMeanWarps = 8;
+__global__ void __launch_bounds__(32 * kMeanWarps) k_leaf_means(const NodeDev* __restrict__ nodes,
+                                                                const int32_t* __restrict__ list, int n,
+                                                                const double* __restrict__ u, int64_t u_stride,
+                                                                int N, double* __restrict__ means,
+                                                                int64_t m_stride) {
+  const int q = blockIdx.x * kMeanWarps + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
   const int s = blockIdx.y;
-  if (q >= n) return;
+  if (q >= n) return;   // uniform per warp
   const int node = list[q];
   const NodeDev nd = nodes[node];
   const double* us = u + (int64_t)s * u_stride;
+  const int w = nd.x1 - nd.x0, cells = w * (nd.y1 - nd.y0);
   double acc = 0.0;
-  for (int j = nd.y0; j < nd.y1; ++j) {
-    const double* lo = us + (int64_t)j * N;
+  for (int c = lane; c < cells; c += 32) {
+    const int i = nd.x0 + c % w, j = nd.y0 + c / w;
+    const double* lo = us + (int64_t)j * N + i;
     const double* hi = lo + N;
-    for (int i = nd.x0; i < nd.x1; ++i) {
-      const double a = lo[i], b = lo[i + 1], c = hi[i + 1], d = hi[i];
-      acc += (a + b + c) + (a + c + d);
-    }
+    const double a = lo[0], b = lo[1], cc = hi[1], d = hi[0];
+    acc += (a + b + cc) + (a + cc + d);
   }
-  const double cells = (double)(nd.x1 - nd.x0) * (double)(nd.y1 - nd.y0);
-  means[(int64_t)s * m_stride + node] = acc / (6.0 * cells);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if (lane == 0) means[(int64_t)s * m_stride + node] = acc / (6.0 * (double)cells);
 }
 
 // One thread per (father, sample) of one height: mean = c_1 mean_1 + c_2 mean_2.
@@ -53,7 +60,9 @@ __global__ void k_father_means(const NodeDev* __restrict__ nodes, const int32_t*
 cudaError_t launch_leaf_means(const NodeDev* nodes, const int32_t* list, int n, const double* u, int64_t u_stride,
                               int N, double* means, int64_t m_stride, int batch, cudaStream_t st) {
   if (n == 0) return cudaSuccess;
-  k_leaf_means<<<dim3((n + 127) / 128, batch), 128, 0, st>>>(nodes, list, n, u, u_stride, N, means, m_stride);
+  k_leaf_means<<<dim3((n + kMeanWarps - 1) / kMeanWarps, batch), 32 * kMeanWarps, 0, st>>>(nodes, list, n, u,
+                                                                                          u_stride, N, means,
+                                                                                          m_stride);
   return cudaGetLastError();
 }
 
