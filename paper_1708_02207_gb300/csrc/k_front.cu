@@ -574,14 +574,25 @@ __global__ void __launch_bounds__(256) k_trsm(StepArgs a) {   // R rows per CTA
         for (int q = 0; q < CPB; ++q)
           if (cbase + q < jb) X[(j0 + cbase + q) * ldx + r] = acc[q];
     }
-    for (int c0 = j0 + jb; c0 < m; c0 += 64) {
-      const int nc = min(64, m - c0);
-      __syncthreads();
-      for (int idx = threadIdx.x; idx < jb * 64; idx += blockDim.x) {
-        const int l = idx >> 6, cc = idx & 63;
-        Lc[idx] = (cc < nc) ? A[(int64_t)(j0 + l) * nf + c0 + cc] : (T)0;
+    // trailing chunks of 64 columns; a chunk exists only after a full 32-column panel
+    // (jb == 32), so every chunk of L below the panel is 32 x 64 = 8 values per thread.
+    // The next chunk is loaded into registers while the current one is applied.
+    constexpr int kPre = 32 * 64 / 256;
+    T pre[kPre];
+    auto fetch = [&](int cn) {
+#pragma unroll
+      for (int k = 0; k < kPre; ++k) {
+        const int idx = threadIdx.x + k * 256, l = idx >> 6, cc = idx & 63;
+        pre[k] = (cn + cc < m) ? A[(int64_t)(j0 + l) * nf + cn + cc] : (T)0;
       }
+    };
+    if (j0 + jb < m) fetch(j0 + jb);
+    for (int c0 = j0 + jb; c0 < m; c0 += 64) {
       __syncthreads();
+#pragma unroll
+      for (int k = 0; k < kPre; ++k) Lc[threadIdx.x + k * 256] = pre[k];
+      __syncthreads();
+      if (c0 + 64 < m) fetch(c0 + 64);
       T acc[4][CPT];
 #pragma unroll
       for (int q = 0; q < 4; ++q)

@@ -9,37 +9,34 @@
 
 namespace hdd {
 
-// One warp per (leaf, sample), lanes over the leaf's cells (row by row, so that
-// the lanes of one cell row read consecutive vertices).  Cell (i, j) holds the
-// lower-right triangle (i,j), (i+1,j), (i+1,j+1) and the upper-left one (i,j),
-// (i+1,j+1), (i,j+1), each of area h^2 / 2: the cell adds h^2 / 6 times the two
-// corner sums, and the leaf's area is cells * h^2, so h^2 cancels.  The lane sums
-// are combined by a fixed butterfly, so the result does not depend on timing.
-constexpr int kMeanWarps = 8;
-__global__ void __launch_bounds__(32 * kMeanWarps) k_leaf_means(const NodeDev* __restrict__ nodes,
-                                                                const int32_t* __restrict__ list, int n,
-                                                                const double* __restrict__ u, int64_t u_stride,
-                                                                int N, double* __restrict__ means,
-                                                                int64_t m_stride) {
-  const int q = blockIdx.x * kMeanWarps + (threadIdx.x >> 5);
-  const int lane = threadIdx.x & 31;
+// One thread per (leaf, sample).  Cell (i, j) holds the lower-right triangle
+// (i,j), (i+1,j), (i+1,j+1) and the upper-left one (i,j), (i+1,j+1), (i,j+1),
+// each of area h^2 / 2, so the cell adds h^2 / 6 times (2 u(i,j) + u(i+1,j) +
+// 2 u(i+1,j+1) + u(i,j+1)).  Summed over the leaf's cells every vertex enters
+// once with the sum of those corner weights over the cells it belongs to (6 at an
+// inner vertex); the leaf's area is cells * h^2, so h^2 cancels.
+__global__ void k_leaf_means(const NodeDev* __restrict__ nodes, const int32_t* __restrict__ list, int n,
+                             const double* __restrict__ u, int64_t u_stride, int N, double* __restrict__ means,
+                             int64_t m_stride) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
   const int s = blockIdx.y;
-  if (q >= n) return;   // uniform per warp
+  if (q >= n) return;
   const int node = list[q];
   const NodeDev nd = nodes[node];
   const double* us = u + (int64_t)s * u_stride;
-  const int w = nd.x1 - nd.x0, cells = w * (nd.y1 - nd.y0);
   double acc = 0.0;
-  for (int c = lane; c < cells; c += 32) {
-    const int i = nd.x0 + c % w, j = nd.y0 + c / w;
-    const double* lo = us + (int64_t)j * N + i;
-    const double* hi = lo + N;
-    const double a = lo[0], b = lo[1], cc = hi[1], d = hi[0];
-    acc += (a + b + cc) + (a + cc + d);
+  for (int j = nd.y0; j <= nd.y1; ++j) {
+    const double* row = us + (int64_t)j * N;
+    const bool up = j < nd.y1, down = j > nd.y0;   // cells above / below this vertex row
+    for (int i = nd.x0; i <= nd.x1; ++i) {
+      const bool right = i < nd.x1, left = i > nd.x0;
+      // corner (i,j) of cell (i,j): 2; of cell (i-1,j): 1; of cell (i-1,j-1): 2; of cell (i,j-1): 1
+      const int wgt = (up ? (right ? 2 : 0) + (left ? 1 : 0) : 0) + (down ? (left ? 2 : 0) + (right ? 1 : 0) : 0);
+      acc += (double)wgt * row[i];
+    }
   }
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-  if (lane == 0) means[(int64_t)s * m_stride + node] = acc / (6.0 * (double)cells);
+  const double cells = (double)(nd.x1 - nd.x0) * (double)(nd.y1 - nd.y0);
+  means[(int64_t)s * m_stride + node] = acc / (6.0 * cells);
 }
 
 // One thread per (father, sample) of one height: mean = c_1 mean_1 + c_2 mean_2.
@@ -60,9 +57,7 @@ __global__ void k_father_means(const NodeDev* __restrict__ nodes, const int32_t*
 cudaError_t launch_leaf_means(const NodeDev* nodes, const int32_t* list, int n, const double* u, int64_t u_stride,
                               int N, double* means, int64_t m_stride, int batch, cudaStream_t st) {
   if (n == 0) return cudaSuccess;
-  k_leaf_means<<<dim3((n + kMeanWarps - 1) / kMeanWarps, batch), 32 * kMeanWarps, 0, st>>>(nodes, list, n, u,
-                                                                                          u_stride, N, means,
-                                                                                          m_stride);
+  k_leaf_means<<<dim3((n + 127) / 128, batch), 128, 0, st>>>(nodes, list, n, u, u_stride, N, means, m_stride);
   return cudaGetLastError();
 }
 
