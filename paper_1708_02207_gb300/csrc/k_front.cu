@@ -542,16 +542,37 @@ __global__ void __launch_bounds__(256) k_trsm(StepArgs a) {   // R rows per CTA
       Xs[idx] = (r < nr) ? A[(int64_t)c * nf + r0 + r] : (T)0;
     }
   const int rg = threadIdx.x % RG, cg = threadIdx.x / RG;
+  // Global loads are issued ahead of their use, into registers: the inverse of the
+  // next diagonal block during the current panel, the first 64-column chunk of L
+  // below a panel before the panel's diagonal product, and each further chunk
+  // while the previous one is applied.  A chunk exists only after a full 32-column
+  // panel (jb == 32), so every chunk is 32 x 64 = 8 values per thread.
+  // inv(L_jj), written by POTRF: column c at G[c * 32 .. c * 32 + 31]; L[l * 33 + c] = inv[c][l]
+  const T* G0 = reinterpret_cast<const T*>(a.arenas.inv + (int64_t)s * a.arenas.inv_stride + nd.inv_off);
+  constexpr int kInv = 1024 / 256, kPre = 32 * 64 / 256;
+  T gin[kInv], pre[kPre];
+#pragma unroll
+  for (int k = 0; k < kInv; ++k) gin[k] = G0[threadIdx.x + k * 256];
+  auto fetch = [&](int j0, int cn) {
+#pragma unroll
+    for (int k = 0; k < kPre; ++k) {
+      const int idx = threadIdx.x + k * 256, l = idx >> 6, cc = idx & 63;
+      pre[k] = (cn + cc < m) ? A[(int64_t)(j0 + l) * nf + cn + cc] : (T)0;
+    }
+  };
   for (int j0 = 0; j0 < m; j0 += 32) {
     const int jb = min(32, m - j0);
     __syncthreads();
-    // inv(L_jj), written by POTRF: column c at G[c * 32 .. c * 32 + 31]; L[l * 33 + c] = inv[c][l]
-    {
-      const T* G = reinterpret_cast<const T*>(a.arenas.inv + (int64_t)s * a.arenas.inv_stride + nd.inv_off) +
-                   (j0 / 32) * 1024;
-      for (int idx = threadIdx.x; idx < 1024; idx += blockDim.x) L[(idx >> 5) * 33 + (idx & 31)] = G[idx];
+#pragma unroll
+    for (int k = 0; k < kInv; ++k) {
+      const int idx = threadIdx.x + k * 256;
+      L[(idx >> 5) * 33 + (idx & 31)] = gin[k];
     }
     __syncthreads();
+    if (j0 + 32 < m)
+#pragma unroll
+      for (int k = 0; k < kInv; ++k) gin[k] = G0[(j0 / 32 + 1) * 1024 + threadIdx.x + k * 256];
+    if (j0 + jb < m) fetch(j0, j0 + jb);
     // X_blk <- X_blk inv(L_jj)^T: x_c = sum_{l <= c} x_l inv[c][l]; each thread one row and a
     // group of columns, results kept in registers until all threads have read X_blk
     {
@@ -574,25 +595,13 @@ __global__ void __launch_bounds__(256) k_trsm(StepArgs a) {   // R rows per CTA
         for (int q = 0; q < CPB; ++q)
           if (cbase + q < jb) X[(j0 + cbase + q) * ldx + r] = acc[q];
     }
-    // trailing chunks of 64 columns; a chunk exists only after a full 32-column panel
-    // (jb == 32), so every chunk of L below the panel is 32 x 64 = 8 values per thread.
-    // The next chunk is loaded into registers while the current one is applied.
-    constexpr int kPre = 32 * 64 / 256;
-    T pre[kPre];
-    auto fetch = [&](int cn) {
-#pragma unroll
-      for (int k = 0; k < kPre; ++k) {
-        const int idx = threadIdx.x + k * 256, l = idx >> 6, cc = idx & 63;
-        pre[k] = (cn + cc < m) ? A[(int64_t)(j0 + l) * nf + cn + cc] : (T)0;
-      }
-    };
-    if (j0 + jb < m) fetch(j0 + jb);
+    // trailing chunks of 64 columns
     for (int c0 = j0 + jb; c0 < m; c0 += 64) {
       __syncthreads();
 #pragma unroll
       for (int k = 0; k < kPre; ++k) Lc[threadIdx.x + k * 256] = pre[k];
       __syncthreads();
-      if (c0 + 64 < m) fetch(c0 + 64);
+      if (c0 + 64 < m) fetch(j0, c0 + 64);
       T acc[4][CPT];
 #pragma unroll
       for (int q = 0; q < 4; ++q)
