@@ -148,17 +148,17 @@ __global__ void __launch_bounds__(256) k_potrf(StepArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* piv = reinterpret_cast<T*>(smem_raw);                 // [kPanel]
   T* W = piv + kPanel;                                      // [32][33] inverse of a diagonal block
-  T* Ps = W + 32 * 33;                                      // panel, ld = rows
+  T* Ps = W + 32 * 33;                                      // panel, ld = rows rounded up to 4 (16 B aligned)
   const bool in_smem = m <= SmemCap<T>::rows;
   for (int k0 = 0; k0 < m; k0 += kPanel) {
     const int kb = min(kPanel, m - k0), rows = m - k0;
     T* P = in_smem ? Ps : A + (int64_t)k0 * nf + k0;
-    const int ld = in_smem ? rows : nf;
+    const int ld = in_smem ? ((rows + 3) & ~3) : nf;
     __syncthreads();
     if (in_smem)
       for (int idx = threadIdx.x; idx < kb * rows; idx += blockDim.x) {
         const int l = idx / rows, i = idx - l * rows;
-        Ps[idx] = A[(int64_t)(k0 + l) * nf + k0 + i];
+        Ps[l * ld + i] = A[(int64_t)(k0 + l) * nf + k0 + i];
       }
     // factor the panel (rows k0..m-1, columns k0..k0+kb-1): per column, scale it,
     // then one warp per remaining panel column applies the rank-1 update
@@ -204,7 +204,7 @@ __global__ void __launch_bounds__(256) k_potrf(StepArgs a) {
     if (in_smem)
       for (int idx = threadIdx.x; idx < kb * rows; idx += blockDim.x) {
         const int l = idx / rows, i = idx - l * rows;
-        if (i >= l) A[(int64_t)(k0 + l) * nf + k0 + i] = Ps[idx];
+        if (i >= l) A[(int64_t)(k0 + l) * nf + k0 + i] = Ps[l * ld + i];
       }
     // trailing update of K_gg[k0+kb:m, k0+kb:m] (lower): 4 x 4 register tiles,
     // one warp per column of tiles, lanes down the rows (coalesced in global memory)
@@ -222,10 +222,16 @@ __global__ void __launch_bounds__(256) k_potrf(StepArgs a) {
           for (int w = 0; w < 4; ++w) acc[q][w] = (T)0;
         for (int l = 0; l < kb; ++l) {
           T x[4], y[4];
+          if (in_smem) {   // kb = 32 here (a trailing block exists), so i0, j0 and ld are multiples of 4;
+                           // the padding rows beyond `rows` only reach products that are not stored
+            load4(P + l * ld + i0, x);
+            load4(P + l * ld + j0, y);
+          } else {
 #pragma unroll
-          for (int q = 0; q < 4; ++q) {
-            x[q] = (i0 + q < rows) ? P[(int64_t)l * ld + i0 + q] : (T)0;
-            y[q] = (j0 + q < rows) ? P[(int64_t)l * ld + j0 + q] : (T)0;
+            for (int q = 0; q < 4; ++q) {
+              x[q] = (i0 + q < rows) ? P[(int64_t)l * ld + i0 + q] : (T)0;
+              y[q] = (j0 + q < rows) ? P[(int64_t)l * ld + j0 + q] : (T)0;
+            }
           }
 #pragma unroll
           for (int q = 0; q < 4; ++q)
@@ -762,7 +768,7 @@ cudaError_t launch_front_large(const StepArgs& a, cudaStream_t st) {
       k_chol_trsm<T, 2><<<grid, 32 * kCholTrsmWarps, kCholTrsmWarps * sizeof(CholTrsmSmem<T, 2>), st>>>(a);
     if (a.prof) a.prof->end(st);
   } else {
-    const size_t smem = (rows_smem * kPanel + kPanel + 32 * 33) * sizeof(T);
+    const size_t smem = (((rows_smem + 3) & ~(size_t)3) * kPanel + kPanel + 32 * 33) * sizeof(T);
     if (a.prof) a.prof->begin(kProfPotrf, a.fl_chol, st);
     k_potrf<T><<<dim3(a.nlist, a.batch), 256, smem, st>>>(a);
     if (a.prof) a.prof->end(st);
