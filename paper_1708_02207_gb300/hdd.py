@@ -237,15 +237,24 @@ class Plan:
 
     def solve_loads(self, batch: int, ws, c, u, status=None, stream=None):
         """hdd_solve_loads: c and u device [batch, n_loads, N*N] FP64 (after assemble + upsweep on ws)."""
+        import torch
         if c.shape != u.shape or c.dim() != 3 or c.shape[0] != batch or c.shape[2] != self.N * self.N:
             raise ValueError("c and u must both be [batch, n_loads, N*N]")
+        if c.dtype != torch.float64 or u.dtype != torch.float64 or not (c.is_contiguous() and u.is_contiguous()):
+            raise ValueError("c and u must be contiguous float64 tensors")
+        if status is not None and (status.dtype != torch.int32 or status.numel() < batch):
+            raise ValueError("status must be an int32 tensor of at least batch entries")
         _check(self.lib.hdd_solve_loads(self._h, batch, _ptr(ws), _ptr(c), int(c.shape[1]), _ptr(u), _ptr(status),
                                         _stream_ptr(stream)), "hdd_solve_loads")
 
     def subdomain_means(self, u, means, stream=None):
         """hdd_subdomain_means: u device [batch, N*N] (any row stride), means device [batch, n_nodes]."""
-        if u.dim() != 2 or u.stride(1) != 1 or u.shape[1] != self.N * self.N:
-            raise ValueError("u must be [batch, N*N] with unit column stride")
+        import torch
+        if u.dim() != 2 or u.stride(1) != 1 or u.shape[1] != self.N * self.N or u.dtype != torch.float64:
+            raise ValueError("u must be float64 [batch, N*N] with unit column stride")
+        n_nodes = self.info()["n_nodes"]
+        if means.dtype != torch.float64 or not means.is_contiguous() or tuple(means.shape) != (u.shape[0], n_nodes):
+            raise ValueError("means must be a contiguous float64 [batch, n_nodes] tensor")
         _check(self.lib.hdd_subdomain_means(self._h, int(u.shape[0]), _ptr(u), int(u.stride(0)), _ptr(means),
                                             _stream_ptr(stream)), "hdd_subdomain_means")
 
