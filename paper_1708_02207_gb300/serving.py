@@ -1,0 +1,208 @@
+"""Continuous-batching request loop for likelihood evaluations.
+
+Plans (one per grid, KL basis and observation set) stay resident on the device.  Each
+request carries one parameter vector Z and its data y and names its plan.  Requests wait in
+arrival order; a scheduling pass first collects the batches whose completion event has
+fired, then admits new batches: it takes the plan of the oldest waiting request and gathers
+up to `max_batch` waiting requests of that plan, shrinking the batch until the device memory
+of its workspace (hdd_workspace_size: the Schur stacks, factors and vectors of that many
+samples) fits into what the batches in flight leave of the budget.  An admitted batch runs
+on a free stream, so batches of different plans overlap on the device, and requests that
+arrive while others run are admitted as soon as memory and a stream are free.  Latency is
+measured per request from submission to collection.
+
+Every sample of a batch is computed independently of the others (the library's kernels
+never combine samples), so a result does not depend on what it was batched with.
+
+The loop itself is host logic over a small backend interface: `CudaBackend` runs batches
+through the C ABI (paper_1708_02207_gb300.hdd); tests drive the same loop with a fake.
+"""
+from __future__ import annotations
+
+import time
+from collections import deque
+from dataclasses import dataclass
+
+import numpy as np
+
+
+@dataclass
+class Request:
+    rid: int
+    plan: str
+    Z: np.ndarray
+    y: np.ndarray
+    t_submit: float
+    t_done: float = float("nan")
+    loglik: float = float("nan")
+    u_obs: np.ndarray | None = None
+    status: int = 0
+    rejected: str = ""
+
+    @property
+    def latency(self) -> float:
+        return self.t_done - self.t_submit
+
+
+@dataclass
+class _Batch:
+    handle: object
+    plan: str
+    requests: list
+    bytes: int
+    slot: int
+
+
+class Server:
+    """The request loop.  `backend` provides workspace_bytes(plan, batch),
+    launch(plan, Z[B, n_z], y[B, n_obs], slot) -> handle, done(handle) -> bool,
+    collect(handle) -> (loglik[B], u_obs[B, n_obs], status[B]) and release(handle)."""
+
+    def __init__(self, backend, budget_bytes: int, max_batch: int = 64, n_slots: int = 4, clock=time.perf_counter):
+        if budget_bytes <= 0 or max_batch < 1 or n_slots < 1:
+            raise ValueError("budget_bytes, max_batch and n_slots must be positive")
+        self.backend = backend
+        self.budget = int(budget_bytes)
+        self.max_batch = int(max_batch)
+        self.clock = clock
+        self.waiting: deque = deque()
+        self.in_flight: list = []
+        self.free_slots = list(range(n_slots))
+        self.done: list = []
+        self.bytes_in_flight = 0
+        self.peak_bytes = 0
+        self.batches = 0
+        self._next = 0
+
+    # ---- requests ------------------------------------------------------
+    def submit(self, plan: str, Z, y, t: float | None = None) -> Request:
+        self.backend.workspace_bytes(plan, 1)   # an unknown plan raises here, not in the loop
+        r = Request(self._next, plan, np.asarray(Z, dtype=np.float64), np.asarray(y, dtype=np.float64),
+                    self.clock() if t is None else t)
+        self._next += 1
+        self.waiting.append(r)
+        return r
+
+    # ---- scheduling ----------------------------------------------------
+    def _collect(self):
+        still = []
+        for b in self.in_flight:
+            if not self.backend.done(b.handle):
+                still.append(b)
+                continue
+            ll, u, st = self.backend.collect(b.handle)
+            t = self.clock()
+            for k, r in enumerate(b.requests):
+                r.loglik, r.u_obs, r.status, r.t_done = float(ll[k]), np.array(u[k]), int(st[k]), t
+                self.done.append(r)
+            self.backend.release(b.handle)
+            self.bytes_in_flight -= b.bytes
+            self.free_slots.append(b.slot)
+        self.in_flight = still
+
+    def _admit(self):
+        while self.waiting and self.free_slots:
+            plan = self.waiting[0].plan
+            group = [r for r in self.waiting if r.plan == plan][: self.max_batch]
+            n = len(group)
+            left = self.budget - self.bytes_in_flight
+            while n > 0 and self.backend.workspace_bytes(plan, n) > left:
+                n -= 1
+            if n == 0:
+                if not self.in_flight and self.backend.workspace_bytes(plan, 1) > self.budget:
+                    r = self.waiting.popleft()   # can never fit: refuse it rather than wait forever
+                    r.rejected = "workspace of one sample exceeds the budget"
+                    r.t_done = self.clock()
+                    self.done.append(r)
+                    continue
+                return   # wait for memory to free up
+            group = group[:n]
+            ids = {r.rid for r in group}
+            self.waiting = deque(r for r in self.waiting if r.rid not in ids)
+            nbytes = self.backend.workspace_bytes(plan, n)
+            slot = self.free_slots.pop()
+            Z = np.stack([r.Z for r in group])
+            y = np.stack([r.y for r in group])
+            handle = self.backend.launch(plan, Z, y, slot)
+            self.in_flight.append(_Batch(handle, plan, group, nbytes, slot))
+            self.bytes_in_flight += nbytes
+            self.peak_bytes = max(self.peak_bytes, self.bytes_in_flight)
+            self.batches += 1
+
+    def step(self):
+        """One scheduling pass: collect finished batches, then admit what fits."""
+        self._collect()
+        self._admit()
+
+    def idle(self) -> bool:
+        return not self.waiting and not self.in_flight
+
+    def run_until_idle(self, poll_s: float = 0.0):
+        while not self.idle():
+            self.step()
+            if poll_s:
+                time.sleep(poll_s)
+
+    def latency_percentiles(self, qs=(0.5, 0.99)) -> dict:
+        lat = sorted(r.latency for r in self.done if not r.rejected)
+        if not lat:
+            return {q: float("nan") for q in qs}
+        return {q: lat[min(len(lat) - 1, int(round(q * (len(lat) - 1))))] for q in qs}
+
+
+class CudaBackend:
+    """Batches through the C ABI on one device: per plan a resident hdd.Plan, per in-flight
+    batch its own workspace (from PyTorch's caching allocator, returned when the batch is
+    collected), one CUDA stream per slot, inputs copied from pinned host memory and results
+    copied back on that stream, and a CUDA event that marks completion."""
+
+    def __init__(self, plans: dict, n_slots: int = 4, device: int = 0):
+        import torch
+        self.torch = torch
+        self.plans = plans
+        self.dev = torch.device("cuda", device)
+        self.streams = [torch.cuda.Stream(device=self.dev) for _ in range(n_slots)]
+
+    def workspace_bytes(self, plan: str, batch: int) -> int:
+        return self.plans[plan].workspace_size(batch)
+
+    def launch(self, plan: str, Z: np.ndarray, y: np.ndarray, slot: int):
+        torch = self.torch
+        p = self.plans[plan]
+        B = Z.shape[0]
+        st = self.streams[slot]
+        with torch.cuda.stream(st):
+            ws = p.workspace(B)
+        Zh = torch.from_numpy(np.ascontiguousarray(Z)).pin_memory()
+        yh = torch.from_numpy(np.ascontiguousarray(y)).pin_memory()
+        out = {"ll": torch.empty(B, dtype=torch.float64).pin_memory(),
+               "u": torch.empty(B, p.n_obs, dtype=torch.float64).pin_memory(),
+               "st": torch.empty(B, dtype=torch.int32).pin_memory()}
+        with torch.cuda.stream(st):
+            Zd = Zh.to(self.dev, non_blocking=True)
+            yd = yh.to(self.dev, non_blocking=True)
+            u = torch.empty(B, p.n_obs, dtype=torch.float64, device=self.dev)
+            ll = torch.empty(B, dtype=torch.float64, device=self.dev)
+            sd = torch.empty(B, dtype=torch.int32, device=self.dev)
+            p.assemble(Zd, ws, st)
+            p.upsweep(B, ws, st)
+            p.point_solve(B, ws, u, st)
+            p.loglik(B, ws, u, yd, ll, sd, st)
+            out["ll"].copy_(ll, non_blocking=True)
+            out["u"].copy_(u, non_blocking=True)
+            out["st"].copy_(sd, non_blocking=True)
+            ev = torch.cuda.Event()
+            ev.record(st)
+        # the device tensors of this batch stay alive until it is released
+        return {"ev": ev, "out": out, "keep": (ws, Zh, yh, Zd, yd, u, ll, sd)}
+
+    def done(self, h) -> bool:
+        return h["ev"].query()
+
+    def collect(self, h):
+        h["ev"].synchronize()
+        o = h["out"]
+        return o["ll"].numpy(), o["u"].numpy(), o["st"].numpy()
+
+    def release(self, h):
+        h["keep"] = None   # collected, so the stream is past every use of these buffers

@@ -1,0 +1,140 @@
+"""Host logic of the continuous-batching request loop (paper_1708_02207_gb300.serving),
+driven by a fake backend on a manual clock: every request gets its own result whatever it
+was batched with, the memory budget holds at every instant, requests that arrive while
+batches run are admitted as soon as a batch completes, and a request that can never fit is
+refused instead of blocking the queue."""
+import numpy as np
+import pytest
+
+from paper_1708_02207_gb300.serving import Server
+
+
+class Clock:
+    def __init__(self):
+        self.t = 0.0
+
+    def __call__(self):
+        return self.t
+
+
+class FakeBackend:
+    """workspace = fixed + per-sample bytes; a batch of n samples of a plan finishes
+    `dur[plan] * (1 + n / 8)` after launch; loglik is a fixed function of each row."""
+
+    def __init__(self, clock, per_sample, fixed=100, dur=None):
+        self.clock, self.per_sample, self.fixed = clock, per_sample, fixed
+        self.dur = dur or {k: 1.0 for k in per_sample}
+        self.launches = []
+        self.budget_seen = []
+
+    def workspace_bytes(self, plan, n):
+        return self.fixed + self.per_sample[plan] * n
+
+    def launch(self, plan, Z, y, slot):
+        h = {"t_end": self.clock() + self.dur[plan] * (1 + Z.shape[0] / 8), "Z": Z, "y": y}
+        self.launches.append((plan, Z.shape[0], slot, self.clock()))
+        return h
+
+    def done(self, h):
+        return self.clock() >= h["t_end"]
+
+    def collect(self, h):
+        ll = -(h["Z"] ** 2).sum(axis=1) + h["y"].sum(axis=1)
+        return ll, h["Z"][:, :2] * 3.0, np.zeros(len(ll), dtype=np.int32)
+
+    def release(self, h):
+        pass
+
+
+def drive(server, clock, dt=0.25, limit=10000):
+    for _ in range(limit):
+        if server.idle():
+            return
+        server.step()
+        assert server.bytes_in_flight <= server.budget
+        clock.t += dt
+    raise AssertionError("the loop did not drain")
+
+
+def test_results_belong_to_their_requests():
+    clock = Clock()
+    be = FakeBackend(clock, {"a": 10, "b": 30})
+    srv = Server(be, budget_bytes=1000, max_batch=5, n_slots=3, clock=clock)
+    rng = np.random.default_rng(0)
+    reqs = []
+    for k in range(37):
+        plan = "a" if rng.random() < 0.6 else "b"
+        Z, y = rng.standard_normal(4), rng.standard_normal(3)
+        reqs.append((srv.submit(plan, Z, y), Z, y))
+        if k % 5 == 0:
+            srv.step()
+            clock.t += 0.1
+    drive(srv, clock)
+    assert len(srv.done) == 37
+    for r, Z, y in reqs:
+        assert r.rejected == ""
+        assert r.loglik == pytest.approx(-(Z ** 2).sum() + y.sum(), abs=1e-12)
+        assert np.allclose(r.u_obs, Z[:2] * 3.0)
+        assert r.t_done >= r.t_submit
+    assert max(n for _, n, _, _ in be.launches) <= 5
+
+
+def test_batches_shrink_to_the_memory_budget():
+    clock = Clock()
+    be = FakeBackend(clock, {"a": 100}, fixed=50)
+    srv = Server(be, budget_bytes=400, max_batch=16, n_slots=4, clock=clock)   # room for 3 samples
+    for _ in range(10):
+        srv.submit("a", np.zeros(2), np.zeros(1))
+    drive(srv, clock)
+    assert all(n <= 3 for _, n, _, _ in be.launches)
+    assert srv.peak_bytes <= 400
+    assert len(srv.done) == 10
+
+
+def test_arrivals_are_admitted_while_other_batches_run():
+    clock = Clock()
+    be = FakeBackend(clock, {"slow": 10, "fast": 10}, dur={"slow": 50.0, "fast": 1.0})
+    srv = Server(be, budget_bytes=10_000, max_batch=4, n_slots=2, clock=clock)
+    srv.submit("slow", np.zeros(2), np.zeros(1))
+    srv.submit("fast", np.zeros(2), np.zeros(1))
+    srv.step()                                  # both slots busy
+    assert len(srv.in_flight) == 2
+    clock.t = 5.0
+    late = srv.submit("fast", np.ones(2), np.zeros(1))
+    srv.step()                                  # the fast batch is done: its slot takes the new request
+    assert late not in srv.waiting and any(late in b.requests for b in srv.in_flight)
+    assert any(b.plan == "slow" for b in srv.in_flight)   # still running beside it
+    drive(srv, clock)
+    assert late.t_done < 50.0
+
+
+def test_oversized_request_is_refused_not_blocking():
+    clock = Clock()
+    be = FakeBackend(clock, {"small": 10, "huge": 10_000})
+    srv = Server(be, budget_bytes=1000, max_batch=4, n_slots=2, clock=clock)
+    big = srv.submit("huge", np.zeros(2), np.zeros(1))
+    ok = [srv.submit("small", np.zeros(2), np.zeros(1)) for _ in range(3)]
+    drive(srv, clock)
+    assert big.rejected and np.isnan(big.loglik)
+    assert all(r.rejected == "" and np.isfinite(r.loglik) for r in ok)
+    assert srv.latency_percentiles()[0.5] >= 0.0
+
+
+def test_oldest_request_chooses_the_plan():
+    clock = Clock()
+    be = FakeBackend(clock, {"a": 10, "b": 10})
+    srv = Server(be, budget_bytes=10_000, max_batch=8, n_slots=1, clock=clock)
+    for plan in ("b", "a", "b", "a", "a"):
+        srv.submit(plan, np.zeros(2), np.zeros(1))
+    drive(srv, clock)
+    assert [(p, n) for p, n, _, _ in be.launches] == [("b", 2), ("a", 3)]
+
+
+def test_unknown_plan_and_bad_settings_raise():
+    clock = Clock()
+    be = FakeBackend(clock, {"a": 10})
+    srv = Server(be, budget_bytes=100, clock=clock)
+    with pytest.raises(KeyError):
+        srv.submit("nope", np.zeros(2), np.zeros(1))
+    with pytest.raises(ValueError):
+        Server(be, budget_bytes=0)
