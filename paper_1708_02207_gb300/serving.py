@@ -206,3 +206,79 @@ class CudaBackend:
 
     def release(self, h):
         h["keep"] = None   # collected, so the stream is past every use of these buffers
+
+
+class MetropolisChain:
+    """Random-walk Metropolis on Z with prior N(0, I) and the served log-likelihood:
+    propose Z' = Z + step * xi (xi ~ N(0, I)); once l(Z') is back, accept with probability
+    min(1, exp(l(Z') - |Z'|^2 / 2 - l(Z) + |Z|^2 / 2)).  A chain has at most one request in
+    flight; its first request evaluates its starting point, which is always taken."""
+
+    def __init__(self, plan: str, Z0, y, step: float, rng: np.random.Generator):
+        self.plan, self.y, self.step, self.rng = plan, np.asarray(y, dtype=np.float64), float(step), rng
+        self.Z = np.asarray(Z0, dtype=np.float64)
+        self.logpost = None          # log-likelihood + log-prior at Z, once known
+        self.pending = None          # (request, proposal) in flight
+        self.accepted = 0
+        self.steps = 0
+
+    def propose(self) -> np.ndarray:
+        if self.logpost is None:
+            return self.Z.copy()
+        return self.Z + self.step * self.rng.standard_normal(self.Z.shape)
+
+    def update(self, Zp: np.ndarray, loglik: float, status: int):
+        lp = loglik - 0.5 * float(Zp @ Zp) if status == 0 else -np.inf
+        if self.logpost is None:
+            self.logpost = lp
+            return
+        self.steps += 1
+        if np.log(self.rng.random()) < lp - self.logpost:
+            self.Z, self.logpost = Zp, lp
+            self.accepted += 1
+
+
+def run_offered_load(server: Server, chains: list, rate: float, n_requests: int, rng: np.random.Generator,
+                     tick=None) -> dict:
+    """Requests arrive as a Poisson process of `rate` per second over all chains; at an arrival
+    the longest-idle chain without a request in flight proposes and submits (if every chain
+    is waiting for a result, the arrival waits for the first one to come back).  Runs until
+    `n_requests` results are back and returns their throughput, p50/p99 latency and the
+    acceptance rate.  `rate` = inf submits whenever a chain is free (saturation).
+    `tick()` is called when a pass did nothing (default: sleep 50 us)."""
+    clock = server.clock
+    tick = tick or (lambda: time.sleep(5e-5))
+    idle = deque(chains)
+    t0 = clock()
+    next_arrival = t0 if np.isinf(rate) else t0 + rng.exponential(1.0 / rate)
+    submitted, seen, results = 0, len(server.done), []
+    while len(results) < n_requests:
+        busy = False
+        while submitted < n_requests and idle and clock() >= next_arrival:
+            c = idle.popleft()
+            Zp = c.propose()
+            c.pending = (server.submit(c.plan, Zp, c.y), Zp)
+            submitted += 1
+            busy = True
+            if not np.isinf(rate):
+                next_arrival += rng.exponential(1.0 / rate)
+        server.step()
+        while seen < len(server.done):
+            r = server.done[seen]
+            seen += 1
+            for c in chains:
+                if c.pending is not None and c.pending[0] is r:
+                    c.update(c.pending[1], r.loglik, r.status if not r.rejected else -1)
+                    c.pending = None
+                    idle.append(c)
+                    results.append(r)
+                    busy = True
+        if not busy:
+            tick()
+    t1 = clock()
+    lat = sorted(r.latency for r in results)
+    pick = lambda q: lat[min(len(lat) - 1, int(round(q * (len(lat) - 1))))]
+    steps = sum(c.steps for c in chains)
+    return {"offered_per_s": rate, "evals_per_s": len(results) / (t1 - t0) if t1 > t0 else float("inf"),
+            "p50_s": pick(0.5), "p99_s": pick(0.99), "requests": len(results),
+            "accept_rate": sum(c.accepted for c in chains) / steps if steps else float("nan")}

@@ -138,3 +138,34 @@ def test_unknown_plan_and_bad_settings_raise():
         srv.submit("nope", np.zeros(2), np.zeros(1))
     with pytest.raises(ValueError):
         Server(be, budget_bytes=0)
+
+
+def test_offered_load_run_with_metropolis_chains():
+    from paper_1708_02207_gb300.serving import MetropolisChain, run_offered_load
+
+    class GaussBackend(FakeBackend):
+        # log-likelihood of a Gaussian centred at 1 in every coordinate
+        def collect(self, h):
+            ll = -0.5 * ((h["Z"] - 1.0) ** 2).sum(axis=1)
+            return ll, h["Z"][:, :2], np.zeros(len(ll), dtype=np.int32)
+
+    clock = Clock()
+    be = GaussBackend(clock, {"a": 10, "b": 10}, dur={"a": 0.01, "b": 0.02})
+    srv = Server(be, budget_bytes=10_000, max_batch=8, n_slots=2, clock=clock)
+    rng = np.random.default_rng(3)
+    chains = [MetropolisChain("a" if k % 2 else "b", np.zeros(3), np.zeros(1), 0.5, np.random.default_rng(k))
+              for k in range(6)]
+
+    def tick():
+        clock.t += 0.001
+
+    out = run_offered_load(srv, chains, rate=200.0, n_requests=600, rng=rng, tick=tick)
+    assert out["requests"] == 600 and len(srv.done) == 600
+    assert 0.05 < out["accept_rate"] < 0.95
+    assert 0.0 <= out["p50_s"] <= out["p99_s"]
+    # offered 200/s for 600 requests: about 3 s of arrivals on the fake clock
+    assert 120.0 < out["evals_per_s"] < 260.0
+    # the chains drift to the likelihood's centre (posterior mean 0.5 per coordinate)
+    assert np.mean([c.Z.mean() for c in chains]) > 0.1
+    sat = run_offered_load(srv, chains, rate=float("inf"), n_requests=120, rng=rng, tick=tick)
+    assert sat["evals_per_s"] > out["evals_per_s"]
