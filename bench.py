@@ -400,8 +400,9 @@ def run_hdd(args, cfg):
                 plan.subdomain_means(u_l[:, 0, :], means, stream)
             ev[2].record(stream)
         stream.synchronize()
-        t_l = ev[0].elapsed_time(ev[1]) / args.steps
-        t_m = ev[1].elapsed_time(ev[2]) / args.steps
+        # slowest rank (replicas: the same reduction as the headline)
+        t_l = aggregate(ev[0].elapsed_time(ev[1]), 1, 1, dist, dev)[0] / args.steps
+        t_m = aggregate(ev[1].elapsed_time(ev[2]), 1, 1, dist, dev)[0] / args.steps
         v8 = 8.0 * NN   # one FP64 vertex vector
         # per load and sample: zero u; (1 + K) sweeps and full descents; K residuals (kappa, u
         # and c in, r out), updates (u, du in, u out) and correction maxima (du in; u at the last)
