@@ -127,3 +127,28 @@ def test_tree_shape_rules():
     u8, *_ = hd.solve(33, kap, 8)
     u4, *_ = hd.solve(33, kap, 4)
     assert np.max(np.abs(u8 - u4)) < 1e-13 * np.max(np.abs(u8))
+
+
+@pytest.mark.parametrize("N,leaf", [(17, 4), (21, 3), (33, 8), (30, 5)])
+def test_leaf_boundary_rows_couple_to_one_interior_vertex(N, leaf):
+    # The condensed leaves store K_gg^-1 and one weight per boundary row: on this mesh (each
+    # cell cut by its "/" diagonal, hypotenuse couplings zero) a boundary vertex of a leaf
+    # rectangle couples to at most one interior vertex, and that weight is the only nonzero
+    # of its row of K_Bg.  Corner vertices couple to none.
+    rng = np.random.default_rng(N + leaf)
+    kap = np.exp(rng.standard_normal(2 * (N - 1) ** 2))
+    for nd in hd.build_tree(N, leaf):
+        if not nd.leaf:
+            continue
+        A, ids = hd.local_neumann(N, kap, nd)
+        pos = {v: a for a, v in enumerate(ids)}
+        bset = set(nd.bnd)
+        I = [pos[v] for v in ids if v not in bset]
+        for v in nd.bnd:
+            row = A[pos[v], I]
+            nz = np.flatnonzero(np.abs(row) > 1e-14 * np.abs(A).max())
+            assert nz.size <= 1, (nd.x0, nd.y0, v)
+            i, j = v % N, v // N
+            corner = i in (nd.x0, nd.x1) and j in (nd.y0, nd.y1)
+            if corner:
+                assert nz.size == 0
