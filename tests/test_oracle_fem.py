@@ -223,6 +223,25 @@ def test_refinement_does_not_move_an_accurate_solve():
     assert np.max(np.abs(u1 - u0)) < 1e-12 * np.max(np.abs(u0))
 
 
+@pytest.mark.parametrize("N", [17, 65])
+def test_refinement_step_removes_a_known_perturbation(N):
+    # One step u <- u + A^-1 (c - A u) maps u* + e to u* exactly in exact arithmetic (and a
+    # residual of the wrong sign, A u - c, would give u* + 2e).  kappa spans four decades.
+    rng = np.random.default_rng(N)
+    kap = np.exp(rng.uniform(0.0, np.log(1e4), 2 * (N - 1) ** 2))
+    assert kap.max() / kap.min() > 1e3
+    A, c, _ = fem.reduced_system(N, kap)
+    u_star = fem.solve_banded_cholesky(A, c, N - 1)
+    scale = np.max(np.abs(u_star))
+    e = 1e-3 * scale * rng.standard_normal(u_star.size)
+    u1 = fem.refine_longdouble(A, c, u_star + e, N - 1)
+    assert np.max(np.abs(u1 - u_star)) <= 1e-12 * scale
+    # the step shrinks the long-double residual by the size of the perturbation
+    def res(u):
+        return np.max(np.abs(c - A @ u))
+    assert res(u1) <= 1e-6 * res(u_star + e)
+
+
 @pytest.mark.parametrize("N", [9, 17, 33])
 def test_solve_load_eigenvector_closed_form(N):
     # an assembled load c = h^2 sin(pi x) sin(pi y) at kappa = 1 gives

@@ -104,16 +104,24 @@ def test_appendix_a_sizes():
 
 def test_figure_ex_points_sizes():
     # Fig. ex_points: a floating subdomain with 12 nodes has 10 boundary nodes and 2 interior
-    nd = hd.Node(4, 6, 4, 7, 0)          # 2 x 3 cells = 3 x 4 vertices
-    tree_like = hd.build_tree(33, 32)    # single leaf: only to reuse the set logic below
-    assert len(tree_like) == 1
-    N = 33
-    bnd = [j * N + i for j in range(nd.y0, nd.y1 + 1) for i in range(nd.x0, nd.x1 + 1)
-           if i in (nd.x0, nd.x1) or j in (nd.y0, nd.y1)]
-    inner = [j * N + i for j in range(nd.y0 + 1, nd.y1) for i in range(nd.x0 + 1, nd.x1)]
+    # ones.  The oracle's own tree builds such a subdomain: on the 11 x 11 grid with leaves of
+    # at most 3 cells the bisection (Sec. 2.1) leaves floating 2 x 3-cell leaves, whose index
+    # sets I(d omega) and I(omega) \ I(d omega) must have the figure's sizes.
     g = _golden("fig_ex_points.json")
-    assert len(bnd) + len(inner) == g["nodes"]
-    assert len(bnd) == g["boundary"] and len(inner) == g["interior"]
+    N = 11
+    nodes = hd.build_tree(N, 3)
+    found = 0
+    for nd in nodes:
+        floating = nd.x0 > 0 and nd.y0 > 0 and nd.x1 < N - 1 and nd.y1 < N - 1
+        if nd.leaf and floating and {nd.x1 - nd.x0, nd.y1 - nd.y0} == {2, 3}:
+            assert len(nd.bnd) == g["boundary"] and len(nd.gamma) == g["interior"]
+            assert len(set(nd.bnd) | set(nd.gamma)) == g["nodes"]
+            # the two interior vertices are the ones off the rectangle's edges
+            for v in nd.gamma:
+                i, j = v % N, v // N
+                assert nd.x0 < i < nd.x1 and nd.y0 < j < nd.y1
+            found += 1
+    assert found >= 1
 
 
 def test_tree_shape_rules():

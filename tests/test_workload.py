@@ -27,6 +27,26 @@ def test_kl_nystrom_reproduces_dense_on_coarse_set():
     assert np.allclose(a, b, atol=1e-10)
 
 
+def test_kl_nystrom_agrees_with_dense_at_65():
+    # At N = 65 (8,192 triangles) the dense covariance over every centroid is still
+    # tractable, so the Nystrom basis used above 33^2 (32 x 32-cell coarse set) can be set
+    # against it, with the 513^2 workload's field parameters (40 terms, corr. length 0.1,
+    # variance 2).  Pairs of eigenvalues are degenerate (the square's symmetry), so the
+    # subspaces and the rank-40 covariances are compared, not single columns.
+    N, nz, lc, var = 65, 40, 0.1, 2.0
+    a = w.kl_basis(N, nz, lc, var, method="dense")
+    b = w.kl_basis(N, nz, lc, var, method="nystrom")
+    la, lb = (a ** 2).sum(axis=0), (b ** 2).sum(axis=0)
+    assert np.max(np.abs(la - lb) / la) < 1e-2                     # eigenvalues within 1%
+    Qa, _ = np.linalg.qr(a)
+    Qb, _ = np.linalg.qr(b)
+    cosines = np.linalg.svd(Qa.T @ Qb, compute_uv=False)
+    assert cosines.min() > 0.9999                                   # same 40-dim subspace
+    Ca, Cb = a @ a.T, b @ b.T
+    assert np.linalg.norm(Ca - Cb) <= 5e-3 * np.linalg.norm(Ca)     # rank-40 covariance
+    assert np.max(np.abs(np.diag(Ca) - np.diag(Cb))) <= 1e-2 * np.max(np.diag(Ca))
+
+
 def test_obs_lattice():
     assert list(w.obs_lattice_indices(33, 3)) == [8, 16, 24]
     from fractions import Fraction
