@@ -54,7 +54,7 @@ typedef enum {
   HDD_ECUDA = -3,     /* a CUDA call failed; hdd_last_error() has the text */
   HDD_ENOTSPD = -4,   /* per sample: a pivot of a Schur block was not positive */
   HDD_ENOCONV = -5,   /* per sample: iterative refinement did not reach ir_tol */
-  HDD_ETIMEOUT = -6,  /* reserved for bounded device waits */
+  HDD_ETIMEOUT = -6,  /* per sample: a bounded device wait gave up (hdd_set_wait_bound) */
   HDD_ESTATE = -7     /* call needs a device plan but the plan is host-only */
 } hdd_status;
 
@@ -176,8 +176,8 @@ hdd_status hdd_point_solve(hdd_plan_t plan, int32_t batch, void* workspace, doub
  * u_obs: device [batch x n_obs] from hdd_point_solve.  y: device, [n_obs]
  * (y_per_sample = 0) or [batch x n_obs] (y_per_sample = 1).  loglik: device
  * [batch] FP64.  sample_status: device [batch] int32 or NULL; 0 = ok, otherwise
- * (-code) | (node << 8) with code a negative hdd_status (HDD_ENOTSPD, HDD_ENOCONV)
- * and node the first failing tree node.  A failed sample gets
+ * (-code) | (node << 8) with code a negative hdd_status (HDD_ENOTSPD, HDD_ENOCONV,
+ * HDD_ETIMEOUT) and node the first failing tree node.  A failed sample gets
  * loglik = -inf. */
 hdd_status hdd_loglik(hdd_plan_t plan, int32_t batch, void* workspace, const double* u_obs,
                       const double* y, int32_t y_per_sample, double* loglik,
@@ -261,6 +261,21 @@ hdd_status hdd_evaluate_static(hdd_plan_t plan, int32_t batch, const double* Z, 
  * kappa: device [batch x n_t] FP64 (triangle order as above).  For inspection
  * and tests. */
 hdd_status hdd_kappa(hdd_plan_t plan, int32_t batch, void* workspace, double* kappa, void* stream);
+
+/* Bounded device waits.  The tensor-core Schur update (large FP32 fronts of mixed
+ * plans) waits on shared-memory barriers for its operand copies and its MMAs; each
+ * wait polls at most `polls` times (default 2^24, far above any real wait) and then
+ * gives up: the kernel issues no further copies or MMAs, waits with the same bound
+ * for what it already issued, skips its output tile and marks the sample
+ * HDD_ETIMEOUT (loglik = -inf).  No call of the library waits without a bound and
+ * none traps.
+ *   polls:        >= 1.
+ *   stall_node, stall_sample: test hook, -1 = off.  When set, the copies of the
+ *                 second operand chunk of that (node, sample) are never issued, so
+ *                 its wait is certain to run out: this is how the timeout path is
+ *                 tested without any fault.  Leave it off in production.
+ * Applies to the plan's later hdd_upsweep calls.  Errors: HDD_EINVAL. */
+hdd_status hdd_set_wait_bound(hdd_plan_t plan, uint32_t polls, int32_t stall_node, int32_t stall_sample);
 
 /* Per-kernel timing, for benchmarks.  Between hdd_profile_begin and
  * hdd_profile_end every kernel the library launches for this plan is bracketed

@@ -42,6 +42,18 @@ hdd_status fail_inval(const std::string& msg) {
   return HDD_EINVAL;
 }
 
+}  // namespace
+
+namespace hdd {
+// Error text for hdd_last_error() from the other translation units of the library.
+hdd_status set_error(hdd_status status, const std::string& msg) {
+  g_err = msg;
+  return status;
+}
+}  // namespace hdd
+
+namespace {
+
 // Makes the plan's device current for the duration of a call.
 struct DeviceScope {
   int prev = -1;
@@ -152,8 +164,6 @@ struct ProfScope {
   }
 };
 
-// Previous front kernels for fronts of up to kSmallMax rows (register rows per
-// warp / one CTA per front), selected with HDD_LEGACY_FRONTS=1 for comparison.
 // One pass of "Leaves to Root" over all heights with the given right-hand side.
 cudaError_t run_upsweep(const hdd::Plan& p, int batch, void* ws, const hdd::Rhs& rhs, cudaStream_t st,
                         hdd::Profiler* prof) {
@@ -171,6 +181,9 @@ cudaError_t run_upsweep(const hdd::Plan& p, int batch, void* ws, const hdd::Rhs&
   a.arenas = arenas(p, L, ws);
   a.status = reinterpret_cast<int32_t*>(w + L.status);
   a.prof = prof;
+  a.wait_limit = p.wait_limit;
+  a.stall_node = p.stall_node;
+  a.stall_sample = p.stall_sample;
   // fused bottom subtrees first (their roots' Schur blocks feed the regular steps)
   for (int prec = 0; prec < 2; ++prec) {
     const hdd::Plan::Fusion& fu = p.fusion[prec];
@@ -654,6 +667,18 @@ hdd_status hdd_kappa(hdd_plan_t plan, int32_t batch, void* workspace, double* ka
   cudaError_t e = cudaMemcpyAsync(kappa, static_cast<char*>(workspace) + L.kappa, (size_t)batch * p.n_t * 8,
                                   cudaMemcpyDeviceToDevice, static_cast<cudaStream_t>(stream));
   return e == cudaSuccess ? HDD_OK : fail_cuda(e, "hdd_kappa");
+}
+
+hdd_status hdd_set_wait_bound(hdd_plan_t plan, uint32_t polls, int32_t stall_node, int32_t stall_sample) {
+  if (!plan) return fail_inval("plan is NULL");
+  if (polls == 0) return fail_inval("polls must be >= 1");
+  hdd::Plan& p = plan->p;
+  if (stall_node < -1 || stall_node >= (int32_t)p.nodes.size()) return fail_inval("stall_node out of range");
+  if (stall_sample < -1) return fail_inval("stall_sample out of range");
+  p.wait_limit = polls;
+  p.stall_node = stall_node;
+  p.stall_sample = stall_node < 0 ? -1 : stall_sample;
+  return HDD_OK;
 }
 
 hdd_status hdd_profile_begin(hdd_plan_t plan) {

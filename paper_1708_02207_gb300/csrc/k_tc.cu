@@ -14,7 +14,11 @@
 //     three times per step, hi*hi + hi*lo + lo*hi ("3xTF32", about FP32
 //     accuracy), with the accumulator in tensor memory (128 lanes x 128 columns);
 //     tcgen05.commit frees a stage for the next copy;
-//   * every wait is bounded; a timeout marks the sample HDD_ETIMEOUT;
+//   * every wait is bounded (StepArgs::wait_limit polls); after a wait runs out
+//     the thread issues no further copies or MMAs, waits (with the same bound)
+//     for the MMAs already issued (one more tcgen05.commit on a drain barrier)
+//     and for every copy already issued, and marks the sample HDD_ETIMEOUT; the
+//     tensor memory is released only once no MMA can still write it;
 //   * the four warps read their 32 accumulator lanes with tcgen05.ld and subtract
 //     them from S (coalesced along the rows of S).
 #include "launch.h"
@@ -28,7 +32,6 @@ constexpr int kChunk = kTcChunk;      // contraction columns staged per buffer
 constexpr int kTileBytes = (int)kTcBlockBytes;          // one operand part (4 KiB)
 constexpr int kStageBytes = 4 * kTileBytes;             // A hi/lo, B hi/lo (16 KiB)
 constexpr int kStages = 4;                              // pipeline depth: 64 KiB, 3 CTAs per SM
-constexpr uint32_t kWaitLimit = 1u << 24;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -52,8 +55,8 @@ __device__ __forceinline__ void mma_tf32(uint32_t tmem, uint64_t da, uint64_t db
       "l"(da), "l"(db), "r"(idesc), "r"(acc));
 }
 
-__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t phase) {
-  for (uint32_t it = 0; it < kWaitLimit; ++it) {
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t phase, uint32_t limit) {
+  for (uint32_t it = 0; it < limit; ++it) {
     uint32_t done;
     asm volatile(
         "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}"
@@ -81,9 +84,9 @@ __global__ void __launch_bounds__(128, 3) k_syrk_tc(StepArgs a) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* stage =
       reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  __shared__ __align__(8) uint64_t full[kStages], empty[kStages];
+  __shared__ __align__(8) uint64_t full[kStages], empty[kStages], drain;
   __shared__ uint32_t tmem_slot;
-  __shared__ int timed_out;
+  __shared__ int timed_out, mma_live;
   __shared__ int cpos[2][kTile];   // sons' rows of this tile's columns (fathers)
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -97,8 +100,10 @@ __global__ void __launch_bounds__(128, 3) k_syrk_tc(StepArgs a) {
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&full[b])));
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&empty[b])));
     }
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&drain)));
     asm volatile("fence.mbarrier_init.release.cluster;");
     timed_out = 0;
+    mma_live = 0;
   }
   const bool gather = !nd.leaf;
   const int32_t* pos0 = a.maps + nd.map_off + (nd.nf - 1);
@@ -177,8 +182,13 @@ __global__ void __launch_bounds__(128, 3) k_syrk_tc(StepArgs a) {
     const unsigned char* base = a.arenas.tc + (int64_t)s * a.arenas.tc_stride + nd.tc_off;
     const uint32_t idesc = idesc_tf32();
     const uint32_t sbo = (kChunk / 4) * 128;
+    const uint32_t limit = a.wait_limit;
+    // test hook: the copies of one chunk of one (node, sample) are never issued, so
+    // the wait for them runs out (the stage's barrier still expects their bytes)
+    const int stall_chunk = (node == a.stall_node && s == a.stall_sample) ? min(1, nchunks - 1) : -1;
     uint32_t ph_full[kStages] = {}, ph_empty[kStages] = {};
-    bool ok = true;
+    uint32_t pending = 0;   // bit b: copies into stage b issued, their completion not yet waited for
+    bool ok = true, any_mma = false;
     auto load = [&](int c) {
       const int b = c % kStages;
       const uint32_t dst = smem_u32(stage + b * kStageBytes);
@@ -186,6 +196,7 @@ __global__ void __launch_bounds__(128, 3) k_syrk_tc(StepArgs a) {
       const unsigned char* srcA = base + ((int64_t)TI * nchunks + c) * 2 * kTileBytes;
       const unsigned char* srcB = base + ((int64_t)TJ * nchunks + c) * 2 * kTileBytes;
       asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(kStageBytes));
+      if (c == stall_chunk) return;
       asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
                    "l"(srcA), "r"(2 * kTileBytes), "r"(bar)
                    : "memory");
@@ -193,12 +204,14 @@ __global__ void __launch_bounds__(128, 3) k_syrk_tc(StepArgs a) {
                        dst + 2 * kTileBytes),
                    "l"(srcB), "r"(2 * kTileBytes), "r"(bar)
                    : "memory");
+      pending |= 1u << b;
     };
     for (int c = 0; c < nchunks && c < kStages; ++c) load(c);
     for (int c = 0; c < nchunks; ++c) {
       const int b = c % kStages;
-      if (!mbar_wait(smem_u32(&full[b]), ph_full[b])) { ok = false; break; }
+      if (!mbar_wait(smem_u32(&full[b]), ph_full[b], limit)) { ok = false; break; }
       ph_full[b] ^= 1u;
+      pending &= ~(1u << b);
       asm volatile("tcgen05.fence::after_thread_sync;");
       const uint32_t Ah = smem_u32(stage + b * kStageBytes);
       const uint32_t Al = Ah + kTileBytes, Bh = Ah + 2 * kTileBytes, Bl = Ah + 3 * kTileBytes;
@@ -211,6 +224,7 @@ __global__ void __launch_bounds__(128, 3) k_syrk_tc(StepArgs a) {
         mma_tf32(tmem, dah, dbl, idesc, 1u);
         mma_tf32(tmem, dal, dbh, idesc, 1u);
       }
+      any_mma = true;
       asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
           smem_u32(&empty[b])));
       // refill the stage of the previous chunk (its MMAs were queued one step
@@ -218,7 +232,7 @@ __global__ void __launch_bounds__(128, 3) k_syrk_tc(StepArgs a) {
       const int cp = c - 1;
       if (cp >= 0 && cp + kStages < nchunks) {
         const int bp = cp % kStages;
-        if (!mbar_wait(smem_u32(&empty[bp]), ph_empty[bp])) { ok = false; break; }
+        if (!mbar_wait(smem_u32(&empty[bp]), ph_empty[bp], limit)) { ok = false; break; }
         ph_empty[bp] ^= 1u;
         load(cp + kStages);
       }
@@ -228,10 +242,22 @@ __global__ void __launch_bounds__(128, 3) k_syrk_tc(StepArgs a) {
     if (ok)
       for (int c = max(0, nchunks - kStages); c < nchunks; ++c) {
         const int b = c % kStages;
-        if (!mbar_wait(smem_u32(&empty[b]), ph_empty[b])) { ok = false; break; }
+        if (!mbar_wait(smem_u32(&empty[b]), ph_empty[b], limit)) { ok = false; break; }
         ph_empty[b] ^= 1u;
       }
-    if (!ok) timed_out = 1;
+    if (!ok) {
+      // Nothing more is issued.  A commit on the drain barrier completes once every
+      // MMA this thread issued has completed; copies already issued complete on their
+      // stage's barrier (a stage whose copies were never issued is not waited for).
+      timed_out = 1;
+      if (any_mma) {
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+            smem_u32(&drain)));
+        if (!mbar_wait(smem_u32(&drain), 0u, limit)) mma_live = 1;
+      }
+      for (int b = 0; b < kStages; ++b)
+        if (pending & (1u << b)) mbar_wait(smem_u32(&full[b]), ph_full[b], limit);
+    }
   }
   asm volatile("tcgen05.fence::before_thread_sync;");
   __syncthreads();
@@ -269,7 +295,10 @@ __global__ void __launch_bounds__(128, 3) k_syrk_tc(StepArgs a) {
   }
   asm volatile("tcgen05.fence::before_thread_sync;");
   __syncthreads();
-  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTile));
+  // an MMA that did not complete within the bound may still write this tensor
+  // memory: it stays allocated rather than being handed to another CTA under it
+  if (warp == 0 && !mma_live)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTile));
 }
 
 constexpr size_t kSyrkTcSmem = kStages * (size_t)kStageBytes + 1024;

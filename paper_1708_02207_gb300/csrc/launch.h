@@ -61,6 +61,8 @@ struct StepArgs {
   int max_rect;             // leaves: vertices of the largest closed rectangle
   Profiler* prof;            // nullptr unless profiling
   double fl_chol, fl_trsm, fl_syrk, fl_rhs;   // algorithmic flops of this launch (whole batch)
+  uint32_t wait_limit;       // polls of a bounded mbarrier wait before it gives up
+  int stall_node, stall_sample;   // test hook of the bounded waits (-1: off)
 };
 
 // Fused bottom subtrees of the upsweep (one CTA per subtree and sample)

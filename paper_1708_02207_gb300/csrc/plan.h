@@ -75,6 +75,10 @@ struct Plan {
   int precision = HDD_FP64, ir_max_iter = 0, fp64_top_levels = 0, fuse_height = 0;
   double f = 1.0, sigma = 1.0, h = 0.0, ir_tol = 1e-10;
   std::vector<int32_t> obs;
+  // bounded device waits: polls before a wait gives up, and the test hook that
+  // withholds the copies of one (node, sample) (hdd_set_wait_bound)
+  uint32_t wait_limit = 1u << 24;
+  int stall_node = -1, stall_sample = -1;
 
   // tree
   std::vector<Node> nodes;

@@ -7,6 +7,10 @@
 
 #include "plan.h"
 
+namespace hdd {
+hdd_status set_error(hdd_status status, const std::string& msg);
+}
+
 namespace {
 
 // The one workspace shared by every call on a device (held until process exit).
@@ -39,14 +43,18 @@ cudaError_t static_workspace(int dev, void** out) {
 extern "C" hdd_status hdd_evaluate_static(hdd_plan_t plan, int32_t batch, const double* Z, const double* y,
                                           int32_t y_per_sample, double* loglik, double* u_obs,
                                           int32_t* sample_status, void* stream) {
-  if (!plan || !Z || !y || !loglik) return HDD_EINVAL;
-  if (plan->p.device < 0) return HDD_ESTATE;
+  if (!plan) return hdd::set_error(HDD_EINVAL, "plan is NULL");
+  if (!Z || !y || !loglik) return hdd::set_error(HDD_EINVAL, "Z, y or loglik is NULL");
+  if (plan->p.device < 0) return hdd::set_error(HDD_ESTATE, "host-only plan");
   size_t need = 0;
   hdd_status s = hdd_workspace_size(plan, batch, &need);
   if (s != HDD_OK) return s;
-  if (need > HDD_STATIC_WORKSPACE_BYTES) return HDD_EINVAL;   // batch too large for the static workspace
+  if (need > HDD_STATIC_WORKSPACE_BYTES)
+    return hdd::set_error(HDD_EINVAL, "batch workspace of " + std::to_string(need) +
+                                          " bytes exceeds HDD_STATIC_WORKSPACE_BYTES");
   void* ws = nullptr;
-  if (static_workspace(plan->p.device, &ws) != cudaSuccess) return HDD_ECUDA;
+  const cudaError_t e = static_workspace(plan->p.device, &ws);
+  if (e != cudaSuccess) return hdd::set_error(HDD_ECUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
   double* uo = u_obs ? u_obs
                      : reinterpret_cast<double*>(static_cast<char*>(ws) + hdd::layout(plan->p, batch).uobs);
   if ((s = hdd_assemble(plan, Z, batch, ws, stream)) != HDD_OK) return s;

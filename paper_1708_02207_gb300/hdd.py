@@ -23,6 +23,7 @@ EXPORTED = [
     "hdd_point_solve", "hdd_loglik", "hdd_evaluate_host", "hdd_plan_info", "hdd_node_info",
     "hdd_node_indices", "hdd_status_string", "hdd_last_error", "hdd_evaluate_static",
     "hdd_profile_begin", "hdd_profile_end", "hdd_kappa", "hdd_solve_loads", "hdd_subdomain_means",
+    "hdd_set_wait_bound",
 ]
 STATIC_WORKSPACE_BYTES = 32 << 20
 
@@ -88,6 +89,7 @@ def load_library() -> C.CDLL:
     lib.hdd_kappa.argtypes = [vp, i32, vp, vp, vp]
     lib.hdd_solve_loads.argtypes = [vp, i32, vp, vp, i32, vp, vp, vp]
     lib.hdd_subdomain_means.argtypes = [vp, i32, vp, C.c_int64, vp, vp]
+    lib.hdd_set_wait_bound.argtypes = [vp, C.c_uint32, i32, i32]
     lib.hdd_profile_begin.argtypes = [vp]
     lib.hdd_profile_end.argtypes = [vp, C.POINTER(KernelStat), i32, C.POINTER(i32)]
     lib.hdd_plan_info.argtypes = [vp, C.POINTER(PlanInfo)]
@@ -119,6 +121,21 @@ def _check(status: int, where: str):
 
 def _ptr(t) -> int:
     return 0 if t is None else int(t.data_ptr())
+
+
+def _need(t, name: str, dtype: str, shape: tuple, device=None):
+    """Raise ValueError unless t is a contiguous tensor of that dtype, exact shape and
+    (if given) device: the C ABI takes bare pointers, so a wrong tensor would be read
+    or written out of bounds."""
+    import torch
+    dt = {"f64": torch.float64, "i32": torch.int32}[dtype]
+    if t is None or not isinstance(t, torch.Tensor):
+        raise ValueError(f"{name} must be a torch tensor")
+    if t.dtype != dt or not t.is_contiguous() or tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name} must be a contiguous {dt} tensor of shape {tuple(shape)} "
+                         f"(got {t.dtype}, {tuple(t.shape)}, contiguous={t.is_contiguous()})")
+    if device is not None and t.device != device:
+        raise ValueError(f"{name} must be on {device} (got {t.device})")
 
 
 def _stream_ptr(stream) -> int:
@@ -179,6 +196,11 @@ class Plan:
         except Exception:
             pass
 
+    def set_wait_bound(self, polls: int = 1 << 24, stall_node: int = -1, stall_sample: int = -1):
+        """hdd_set_wait_bound: polls of each bounded device wait; (stall_node, stall_sample)
+        is the test hook that makes one wait run out (-1: off)."""
+        _check(self.lib.hdd_set_wait_bound(self._h, polls, stall_node, stall_sample), "hdd_set_wait_bound")
+
     # ---- per-kernel timing ---------------------------------------------
     def profile_begin(self):
         _check(self.lib.hdd_profile_begin(self._h), "hdd_profile_begin")
@@ -220,8 +242,18 @@ class Plan:
         import torch
         return torch.empty(self.workspace_size(batch), dtype=torch.uint8, device=f"cuda:{self.device}")
 
+    def _dev(self):
+        import torch
+        return torch.device("cuda", self.device)
+
+    def _check_y(self, y, batch):
+        if y is None or y.dim() not in (1, 2):
+            raise ValueError("y must be [n_obs] or [batch, n_obs]")
+        _need(y, "y", "f64", (self.n_obs,) if y.dim() == 1 else (batch, self.n_obs), self._dev())
+
     def assemble(self, Z, ws, stream=None):
-        batch = Z.shape[0]
+        batch = Z.shape[0] if Z is not None and Z.dim() == 2 else 0
+        _need(Z, "Z", "f64", (batch, self.n_z), self._dev())
         _check(self.lib.hdd_assemble(self._h, _ptr(Z), batch, _ptr(ws), _stream_ptr(stream)), "hdd_assemble")
 
     def kappa(self, batch: int, ws, out, stream=None):
@@ -232,6 +264,7 @@ class Plan:
         _check(self.lib.hdd_upsweep(self._h, batch, _ptr(ws), _stream_ptr(stream)), "hdd_upsweep")
 
     def point_solve(self, batch: int, ws, u_obs, stream=None):
+        _need(u_obs, "u_obs", "f64", (batch, self.n_obs), self._dev())
         _check(self.lib.hdd_point_solve(self._h, batch, _ptr(ws), _ptr(u_obs), _stream_ptr(stream)),
                "hdd_point_solve")
 
@@ -259,6 +292,11 @@ class Plan:
                                             _stream_ptr(stream)), "hdd_subdomain_means")
 
     def loglik(self, batch: int, ws, u_obs, y, loglik, status=None, stream=None):
+        _need(u_obs, "u_obs", "f64", (batch, self.n_obs), self._dev())
+        self._check_y(y, batch)
+        _need(loglik, "loglik", "f64", (batch,), self._dev())
+        if status is not None:
+            _need(status, "status", "i32", (batch,), self._dev())
         per_sample = 1 if y.dim() == 2 else 0
         _check(self.lib.hdd_loglik(self._h, batch, _ptr(ws), _ptr(u_obs), _ptr(y), per_sample, _ptr(loglik),
                                    _ptr(status), _stream_ptr(stream)), "hdd_loglik")
@@ -282,7 +320,14 @@ class Plan:
     def evaluate_static(self, Z, y, loglik, u_obs=None, status=None, stream=None):
         """hdd_evaluate_static: same result as evaluate(), workspace in the library's
         static device array (no allocation); device tensors in and out."""
-        batch = Z.shape[0]
+        batch = Z.shape[0] if Z is not None and Z.dim() == 2 else 0
+        _need(Z, "Z", "f64", (batch, self.n_z), self._dev())
+        self._check_y(y, batch)
+        _need(loglik, "loglik", "f64", (batch,), self._dev())
+        if u_obs is not None:
+            _need(u_obs, "u_obs", "f64", (batch, self.n_obs), self._dev())
+        if status is not None:
+            _need(status, "status", "i32", (batch,), self._dev())
         per_sample = 1 if y.dim() == 2 else 0
         _check(self.lib.hdd_evaluate_static(self._h, batch, _ptr(Z), _ptr(y), per_sample, _ptr(loglik),
                                             _ptr(u_obs), _ptr(status), _stream_ptr(stream)), "hdd_evaluate_static")

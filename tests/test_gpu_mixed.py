@@ -136,3 +136,40 @@ def test_double_float_assembly_matches_fp64_exp(hdd):
     q2 = phi @ Z[2]
     assert np.isinf(kdf[2][q2 > 710.0]).all() and np.isinf(k64[2][q2 > 710.0]).all()
     assert (kdf[2][q2 < -750.0] == 0.0).all()
+
+
+def test_bounded_wait_runs_out_and_flags_only_its_sample(hdd):
+    # The tensor-core Schur update waits on shared-memory barriers for its operand
+    # copies.  The plan's test hook withholds the copies of one operand chunk of one
+    # (node, sample), so that wait is certain to run out after the given number of polls
+    # (every other wait of the launch has the same bound and completes well within it):
+    # the sample must read HDD_ETIMEOUT at that node with loglik = -inf, and every other
+    # sample must still match the oracle.  Nothing faults or hangs: the kernel drains
+    # what it issued and returns.
+    N, leaf = 129, 8
+    phi, Z = small_problem(N, n_z=20, corr_len=0.2, variance=2.0, batch=3, seed=21)
+    obs = w.obs_vertices(N, 8)
+    y = np.zeros(obs.size)
+    plan = hdd.Plan(N, leaf, phi, obs, 0.1, precision=hdd.HDD_MIXED_FP32, ir_max_iter=3)
+    n_nodes = plan.info()["n_nodes"]
+    # a front on the tensor-core path (more than 128 rows, boundary rows) with at least
+    # two 8-column operand chunks
+    node = next(k for k in range(n_nodes)
+                if plan.node(k)["m"] + plan.node(k)["b"] + 1 > 128 and plan.node(k)["b"] > 0
+                and plan.node(k)["m"] > 8)
+    Zt = torch.from_numpy(Z).cuda()
+    yt = torch.from_numpy(y).cuda()
+    plan.set_wait_bound(1 << 16, node, 1)
+    ll, u, st = (t.cpu().numpy() for t in plan.evaluate(Zt, yt))
+    assert st[1] & 0xFF == -hdd.HDD_ETIMEOUT and st[1] >> 8 == node
+    assert np.isneginf(ll[1])
+    u_ref, ll_ref = oracle_eval(N, phi, Z, obs, y, 0.1)
+    ok = [0, 2]
+    assert (st[ok] == 0).all()
+    assert rel_err_field(u[ok], u_ref[ok]).max() <= TOL
+    assert rel_err_scalar(ll[ok], ll_ref[ok]).max() <= TOL
+    # back to the default bound: the same plan evaluates every sample again
+    plan.set_wait_bound()
+    ll, u, st = (t.cpu().numpy() for t in plan.evaluate(Zt, yt))
+    assert (st == 0).all()
+    assert rel_err_field(u, u_ref).max() <= TOL
