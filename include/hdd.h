@@ -63,6 +63,12 @@ typedef enum {
   HDD_MIXED_FP32 = 1  /* FP32 Schur factorisation + FP64-residual iterative refinement */
 } hdd_precision;
 
+typedef enum {
+  HDD_OBS_VERTEX = 0,  /* observations are u at vertices (obs_vertex: flat vertex ids) */
+  HDD_OBS_MEANS = 1    /* observations are the mean values of u over subdomains of the tree
+                          (Sec. 5, Eq. mean); obs_vertex then holds tree node ids */
+} hdd_obs_kind;
+
 typedef struct {
   int32_t N;                  /* vertices per side, N >= 3 */
   int32_t leaf;               /* leaf size in cells per side, >= 1 */
@@ -85,6 +91,13 @@ typedef struct {
                                  by one CTA each with their Schur complements kept on chip */
   int32_t device;             /* CUDA device ordinal, or -1 for a host-only plan that supports
                                  the hdd_plan_info / hdd_node_info queries and nothing else */
+  int32_t obs_kind;           /* hdd_obs_kind.  HDD_OBS_MEANS: obs_vertex[k] is a node id of the
+                                 decomposition tree (the numbering of hdd_node_info, which a
+                                 host-only plan of the same N and leaf reports; node 0 = Omega),
+                                 and observation k is the mean of u over that node's rectangle.
+                                 The point solve then computes the mean functionals of Sec. 5.1
+                                 (Lemma, Eq. prop1/prop2) and descends only to the observed
+                                 nodes' ancestors (Sec. 5.2 Remark b): see hdd_point_solve. */
 } hdd_plan_desc;
 
 typedef struct {
@@ -166,6 +179,15 @@ hdd_status hdd_upsweep(hdd_plan_t plan, int32_t batch, void* workspace, void* st
  * the paths to the observation vertices, u_gamma = L_gg^-T (y_g - L_Bg^T u_B);
  * then u at the observation vertices.  Mixed precision adds FP64-residual
  * iterative refinement (full descents).  u_obs: device, [batch x n_obs] FP64.
+ * Plans that observe subdomain means (HDD_OBS_MEANS) descend only to the observed
+ * nodes' ancestors, which gives u on each observed node's boundary, build the mean
+ * functionals of the observed nodes and their subtrees leaves to root through the
+ * stored factors (Sec. 5.1 Lemma with c_i = |omega_i| / |omega|: w = L_gg^-1 z_gamma,
+ * lambda^g = z_B - L_Bg w, (lambda^f, c) = sum_i c_i (lambda^f_i, c) + w . y_g), and
+ * return mean(omega) = (lambda^g, u on d omega) + (lambda^f, c) (Eq. prop1).  On refined
+ * mixed plans the mean is Eq. mean of the refined iterate plus the functional of the
+ * last correction; the refinement's convergence test runs on the observed nodes'
+ * boundary unknowns.
  * Refinement reuses the stored y_gamma for its correction sweeps, so on mixed
  * plans call it once per hdd_upsweep (FP64 plans leave y_gamma unchanged). */
 hdd_status hdd_point_solve(hdd_plan_t plan, int32_t batch, void* workspace, double* u_obs,
@@ -256,6 +278,22 @@ hdd_status hdd_subdomain_means(hdd_plan_t plan, int32_t batch, const double* u, 
 hdd_status hdd_evaluate_static(hdd_plan_t plan, int32_t batch, const double* Z, const double* y,
                                int32_t y_per_sample, double* loglik, double* u_obs, int32_t* sample_status,
                                void* stream);
+
+/* The mean functionals of the observed nodes of a plan with obs_kind = HDD_OBS_MEANS
+ * (Sec. 5.1 Lemma: mean(omega) = (lambda^g, u on the boundary unknowns of omega) +
+ * (lambda^f, load inside omega), Eq. prop1), as the last hdd_point_solve on this
+ * workspace left them:
+ *   lambda_g: device [batch x sum_k b_k] FP64 or NULL: lambda^g of each observed node,
+ *             nodes in observation order, b_k entries each in the order of
+ *             hdd_node_indices(bnd);
+ *   mu_f:     device [batch x n_nodes] FP64 or NULL: mu^f = (lambda^f, c) of every node
+ *             whose functional was built (the observed nodes and their subtrees), with c
+ *             the load the stored y_g carry: the plan's load on FP64 plans and on mixed
+ *             plans without refinement, the last refinement residual otherwise (the
+ *             functional of the last correction).
+ * On mixed plans both come from the FP32 factors.  Errors: HDD_ESTATE for other plans. */
+hdd_status hdd_mean_functionals(hdd_plan_t plan, int32_t batch, void* workspace, double* lambda_g, double* mu_f,
+                                void* stream);
 
 /* Copy of the coefficient field of the last hdd_assemble on this workspace:
  * kappa: device [batch x n_t] FP64 (triangle order as above).  For inspection

@@ -22,6 +22,7 @@ cudaError_t configure_tc_kernels();
 cudaError_t configure_fused_kernels();
 cudaError_t configure_group_kernels();
 cudaError_t configure_leaf_kernels();
+cudaError_t configure_func_kernels();
 }  // namespace hdd
 
 namespace {
@@ -83,6 +84,7 @@ cudaError_t configure_device(int dev) {
   if (e == cudaSuccess) e = hdd::configure_fused_kernels();
   if (e == cudaSuccess) e = hdd::configure_group_kernels();
   if (e == cudaSuccess) e = hdd::configure_leaf_kernels();
+  if (e == cudaSuccess) e = hdd::configure_func_kernels();
   if (e == cudaSuccess) g_configured[dev] = true;
   return e;
 }
@@ -103,6 +105,9 @@ void free_device(hdd::Plan& p) {
   }
   cudaFree(p.d_fuse_soff);
   p.d_fuse_soff = nullptr;
+  cudaFree(p.d_lam_off);
+  cudaFree(p.d_obs_nodes);
+  p.d_lam_off = p.d_obs_nodes = nullptr;
   p.d_phi = nullptr; p.d_nodes = nullptr; p.d_maps = nullptr; p.d_lists = nullptr; p.d_obs = nullptr;
 }
 
@@ -319,6 +324,61 @@ cudaError_t run_forward(const hdd::Plan& p, int batch, void* ws, const hdd::Rhs&
   return cudaSuccess;
 }
 
+hdd::FuncArgs func_args(const hdd::Plan& p, int batch, void* ws) {
+  const hdd::Layout L = hdd::layout(p, batch);
+  char* w = static_cast<char*>(ws);
+  hdd::FuncArgs f{};
+  f.nodes = p.d_nodes;
+  f.maps = p.d_maps;
+  f.batch = batch;
+  f.N = p.N;
+  f.A = arenas(p, L, ws);
+  f.fmu = reinterpret_cast<double*>(w + L.fmu);
+  f.n_nodes = (int64_t)p.nodes.size();
+  f.lam = reinterpret_cast<double*>(w + L.lam);
+  f.lam_stride = p.lam_stride;
+  f.lam_off = p.d_lam_off;
+  return f;
+}
+
+// Mean functionals (Sec. 5.1 Lemma; the algorithms of Sec. 5.2) of the observed
+// nodes and their subtrees, leaves to root, through the stored factors; mu^f
+// uses the stored y_g, i.e. the load of the last upsweep or right-hand-side sweep.
+cudaError_t run_functional(const hdd::Plan& p, int batch, void* ws, cudaStream_t st, hdd::Profiler* prof) {
+  hdd::FuncArgs f = func_args(p, batch, ws);
+  for (int h = 0; h <= p.height; ++h)
+    for (int k = 0; k < 4; ++k) {
+      const hdd::ListInfo& li = p.lists[p.func_lists[h][k]];
+      if (li.n == 0) continue;
+      f.list = p.d_lists + li.off;
+      f.nlist = li.n;
+      ProfScope ps(prof, hdd::kProfFunc, 0.0, st);
+      cudaError_t e;
+      switch (k) {
+        case 0: e = hdd::launch_func_warp<double>(f, li.max_nf, st); break;
+        case 1: e = hdd::launch_func_warp<float>(f, li.max_nf, st); break;
+        case 2: e = hdd::launch_func_leaf<double>(f, st); break;
+        default: e = hdd::launch_func_leaf<float>(f, st); break;
+      }
+      if (e != cudaSuccess) return e;
+    }
+  return cudaSuccess;
+}
+
+// Subdomain means of every node of one vertex field per sample (Eq. mean; fathers
+// from their sons as in Sec. 5.1).
+cudaError_t run_means(const hdd::Plan& p, int batch, const double* u, int64_t u_stride, double* means,
+                      cudaStream_t st) {
+  const int64_t ms = (int64_t)p.nodes.size();
+  cudaError_t e = cudaSuccess;
+  for (int h = 0; h <= p.height && e == cudaSuccess; ++h) {
+    const hdd::ListInfo& li = p.lists[p.height_lists[h]];
+    e = h == 0 ? hdd::launch_leaf_means(p.d_nodes, p.d_lists + li.off, li.n, u, u_stride, p.N, means, ms, batch, st)
+               : hdd::launch_father_means(p.d_nodes, p.d_lists + li.off, li.n, means, ms, batch, st);
+  }
+  return e;
+}
+
 // Mixed precision point solve: full descent, then ir_max_iter refinement steps
 // (FP64 residual, sweep through the FP32/FP64 factors, update); the last step's
 // descent is pruned to the observation paths and checked against ir_tol.
@@ -335,7 +395,12 @@ cudaError_t run_refined_solve(const hdd::Plan& p, int batch, void* ws, double* u
   const int64_t NN = (int64_t)p.N * p.N;
   const double load = p.h * p.h * p.f;
   const int K = p.ir_max_iter;
-  cudaError_t e = run_descent(p, batch, ws, K > 0 ? p.down_all_lists : p.down_vis_lists, u, NN, st, prof);
+  cudaError_t e = cudaSuccess;
+  // mean plans average the refined iterate over whole rectangles (Eq. mean), whose
+  // Dirichlet vertices the descents never write: they hold g = 0
+  if (p.obs_kind == HDD_OBS_MEANS && K > 0) e = cudaMemsetAsync(u, 0, (size_t)batch * NN * 8, st);
+  if (e == cudaSuccess)
+    e = run_descent(p, batch, ws, K > 0 ? p.down_all_lists : p.down_vis_lists, u, NN, st, prof);
   for (int it = 1; it <= K && e == cudaSuccess; ++it) {
     const bool last = it == K;
     {
@@ -345,13 +410,33 @@ cudaError_t run_refined_solve(const hdd::Plan& p, int batch, void* ws, double* u
     if (e == cudaSuccess) e = run_forward(p, batch, ws, hdd::Rhs{r, NN, 0.0}, st, prof);
     if (e == cudaSuccess) e = run_descent(p, batch, ws, last ? p.down_vis_lists : p.down_all_lists, du, NN, st, prof);
     ProfScope ps(prof, hdd::kProfMisc, 0.0, st);
-    if (e == cudaSuccess && !last) e = hdd::launch_delta_obs(du, NN, p.d_obs, p.n_obs, dprev, batch, st);
+    if (e == cudaSuccess && !last) e = hdd::launch_delta_obs(du, NN, p.d_obs, p.n_conv, dprev, batch, st);
     if (e == cudaSuccess && !last) e = hdd::launch_update(u, NN, du, NN, p.N, batch, st);
   }
+  const bool means = p.obs_kind == HDD_OBS_MEANS;
   if (e == cudaSuccess) {
     ProfScope ps(prof, hdd::kProfMisc, 0.0, st);
-    e = hdd::launch_final_obs(u, K > 0 ? du : nullptr, NN, p.d_obs, p.n_obs, K > 0 ? p.ir_tol : -1.0, dprev, u_obs,
+    // mean plans: the convergence test runs on the observed nodes' boundary unknowns
+    double* out = means ? reinterpret_cast<double*>(w + L.conv_u) : u_obs;
+    e = hdd::launch_final_obs(u, K > 0 ? du : nullptr, NN, p.d_obs, p.n_conv, K > 0 ? p.ir_tol : -1.0, dprev, out,
                               status, batch, st);
+  }
+  if (means && e == cudaSuccess) {
+    // mean = Eq. mean of the refined iterate + the functional of the last correction
+    // (its boundary values from the pruned descent, its load the last residual,
+    // which the last right-hand-side sweep left in y_g); without refinement the
+    // functional of the solution itself
+    double* mfull = K > 0 ? reinterpret_cast<double*>(w + L.mfull) : nullptr;
+    if (K > 0) {
+      ProfScope ps(prof, hdd::kProfMisc, 0.0, st);
+      e = run_means(p, batch, u, NN, mfull, st);
+    }
+    if (e == cudaSuccess) e = run_functional(p, batch, ws, st, prof);
+    if (e == cudaSuccess) {
+      ProfScope ps(prof, hdd::kProfMisc, 0.0, st);
+      e = hdd::launch_mean_obs(func_args(p, batch, ws), p.d_obs_nodes, p.n_obs, K > 0 ? du : u, NN, mfull, u_obs,
+                               st);
+    }
   }
   return e;
 }
@@ -458,6 +543,8 @@ hdd_status hdd_plan(const hdd_plan_desc* desc, hdd_plan_t* out) {
     if (e == cudaSuccess) e = upload(&p.d_lists, p.list_data.data(), p.list_data.size());
     if (e == cudaSuccess) e = upload(&p.d_obs, p.obs.data(), p.obs.size());
     if (e == cudaSuccess) e = upload(&p.d_fuse_soff, p.fuse_soff.data(), p.fuse_soff.size());
+    if (e == cudaSuccess) e = upload(&p.d_lam_off, p.lam_off.data(), p.lam_off.size());
+    if (e == cudaSuccess) e = upload(&p.d_obs_nodes, p.obs_nodes.data(), p.obs_nodes.size());
     for (auto& fu : p.fusion)
       if (e == cudaSuccess && fu.height > 0) {
         e = upload(&fu.d_roots, fu.roots.data(), fu.roots.size());
@@ -547,6 +634,14 @@ hdd_status hdd_point_solve(hdd_plan_t plan, int32_t batch, void* workspace, doub
   cudaError_t e;
   if (p.precision == HDD_MIXED_FP32) {
     e = run_refined_solve(p, batch, workspace, u_obs, st, profiler(plan));
+  } else if (p.obs_kind == HDD_OBS_MEANS) {
+    // descent to the observed nodes' ancestors only, then Eq. prop1 with the mean
+    // functionals of the observed nodes (Sec. 5.1-5.2)
+    e = run_descent(p, batch, workspace, p.down_vis_lists, u, NN, st, profiler(plan));
+    if (e == cudaSuccess) e = run_functional(p, batch, workspace, st, profiler(plan));
+    ProfScope ps(profiler(plan), hdd::kProfMisc, 0.0, st);
+    if (e == cudaSuccess)
+      e = hdd::launch_mean_obs(func_args(p, batch, workspace), p.d_obs_nodes, p.n_obs, u, NN, nullptr, u_obs, st);
   } else {
     e = run_descent(p, batch, workspace, p.down_vis_lists, u, NN, st, profiler(plan));
     ProfScope ps(profiler(plan), hdd::kProfMisc, 0.0, st);
@@ -645,15 +740,31 @@ hdd_status hdd_subdomain_means(hdd_plan_t plan, int32_t batch, const double* u, 
   DeviceScope ds(p.device);
   if (ds.err != cudaSuccess) return fail_cuda(ds.err, "cudaSetDevice");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  const int64_t ms = (int64_t)p.nodes.size();
   ProfScope ps(profiler(plan), hdd::kProfMisc, 0.0, st);
-  cudaError_t e = cudaSuccess;
-  for (int h = 0; h <= p.height && e == cudaSuccess; ++h) {
-    const hdd::ListInfo& li = p.lists[p.height_lists[h]];
-    e = h == 0 ? hdd::launch_leaf_means(p.d_nodes, p.d_lists + li.off, li.n, u, u_stride, p.N, means, ms, batch, st)
-               : hdd::launch_father_means(p.d_nodes, p.d_lists + li.off, li.n, means, ms, batch, st);
-  }
+  const cudaError_t e = run_means(p, batch, u, u_stride, means, st);
   return e == cudaSuccess ? HDD_OK : fail_cuda(e, "hdd_subdomain_means");
+}
+
+hdd_status hdd_mean_functionals(hdd_plan_t plan, int32_t batch, void* workspace, double* lambda_g, double* mu_f,
+                                void* stream) {
+  hdd_status s = check_call(plan, batch, workspace);
+  if (s != HDD_OK) return s;
+  const hdd::Plan& p = plan->p;
+  if (p.obs_kind != HDD_OBS_MEANS) {
+    g_err = "the plan does not observe subdomain means";
+    return HDD_ESTATE;
+  }
+  DeviceScope ds(p.device);
+  if (ds.err != cudaSuccess) return fail_cuda(ds.err, "cudaSetDevice");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const hdd::Layout L = hdd::layout(p, batch);
+  const char* w = static_cast<const char*>(workspace);
+  cudaError_t e = cudaSuccess;
+  if (lambda_g && p.lam_stride > 0)
+    e = cudaMemcpyAsync(lambda_g, w + L.lam, (size_t)batch * p.lam_stride * 8, cudaMemcpyDeviceToDevice, st);
+  if (e == cudaSuccess && mu_f)
+    e = cudaMemcpyAsync(mu_f, w + L.fmu, (size_t)batch * p.nodes.size() * 8, cudaMemcpyDeviceToDevice, st);
+  return e == cudaSuccess ? HDD_OK : fail_cuda(e, "hdd_mean_functionals");
 }
 
 hdd_status hdd_kappa(hdd_plan_t plan, int32_t batch, void* workspace, double* kappa, void* stream) {
@@ -701,7 +812,8 @@ hdd_status hdd_profile_end(hdd_plan_t plan, hdd_kernel_stat_t* stats, int32_t ma
   pr->on = false;
   static const char* names[hdd::kProfCount] = {"kappa", "front_warp", "front_small", "front_fill", "potrf", "trsm",
                                                 "syrk_simt", "syrk_tc", "syrk_rhs", "forward", "descent",
-                                                "residual", "misc", "subtree", "leaf_front", "chol_trsm"};
+                                                "residual", "misc", "subtree", "leaf_front", "chol_trsm",
+                                                "functional"};
   int launches[hdd::kProfCount] = {};
   double ms[hdd::kProfCount] = {}, fl[hdd::kProfCount] = {};
   DeviceScope ds(plan->p.device);
@@ -777,10 +889,16 @@ hdd_status hdd_plan_info(hdd_plan_t plan, hdd_plan_info_t* info) {
   for (int h = 0; h <= p.height; ++h)
     for (int k = 0; k < 4; ++k) fwd += p.lists[p.fwd_lists[h][k]].n > 0;
   int solve = down + 1;
+  int func = 0;
+  for (int h = 0; h <= p.height && p.obs_kind == HDD_OBS_MEANS; ++h)
+    for (int k = 0; k < 4; ++k) func += p.lists[p.func_lists[h][k]].n > 0;
   if (p.precision == HDD_MIXED_FP32) {
     const int K = p.ir_max_iter;
     solve = (K > 0 ? down_all : down) + 1;
     for (int it = 1; it <= K; ++it) solve += 1 + fwd + (it == K ? down : down_all) + (it == K ? 0 : 2);
+    if (p.obs_kind == HDD_OBS_MEANS) solve += func + 1 + (K > 0 ? p.height + 1 : 0);
+  } else if (p.obs_kind == HDD_OBS_MEANS) {
+    solve += func;
   }
   info->launches_upsweep = up;
   info->launches_evaluate = 1 + up + solve + 1;

@@ -95,6 +95,8 @@ template <typename T>
 __global__ void __launch_bounds__(256) k_front_fill(StepArgs a, int gamma_only) {
   const int node = a.list[blockIdx.y];
   const int s = blockIdx.z;
+  bind_plan(a, node);
+  if (s >= a.batch) return;
   const NodeDev nd = a.nodes[node];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int c = blockIdx.x * (blockDim.x >> 5) + warp;
@@ -142,6 +144,8 @@ template <typename T>
 __global__ void __launch_bounds__(256) k_potrf(StepArgs a) {
   const int node = a.list[blockIdx.x];
   const int s = blockIdx.y;
+  bind_plan(a, node);
+  if (s >= a.batch) return;
   const NodeDev nd = a.nodes[node];
   const int nf = nd.nf, m = nd.m;
   T* A = node_F<T>(a.arenas, nd, s);
@@ -394,6 +398,7 @@ constexpr int kCholTrsmWarps = 4;   // samples of one node per CTA, one warp eac
 template <typename T, int NB>
 __global__ void __launch_bounds__(32 * kCholTrsmWarps, 3) k_chol_trsm(StepArgs a) {
   const int node = a.list[blockIdx.x];
+  bind_plan(a, node);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int s = blockIdx.y * kCholTrsmWarps + warp;
   if (s >= a.batch) return;
@@ -528,6 +533,8 @@ __global__ void __launch_bounds__(256) k_trsm(StepArgs a) {   // R rows per CTA
   constexpr int CPT = 64 / CG;              // columns per thread in a 64-column chunk
   const int node = a.list[blockIdx.y];
   const int s = blockIdx.z;
+  bind_plan(a, node);
+  if (s >= a.batch) return;
   const NodeDev nd = a.nodes[node];
   const int nf = nd.nf, m = nd.m;
   const int r0 = m + blockIdx.x * R;
@@ -660,6 +667,8 @@ template <typename T>
 __global__ void k_syrk(StepArgs a) {
   const int node = a.list[blockIdx.y];
   const int s = blockIdx.z;
+  bind_plan(a, node);
+  if (s >= a.batch) return;
   const NodeDev nd = a.nodes[node];
   const int nf = nd.nf, m = nd.m, nb = nd.b + 1;
   const int nt = (nb + kSyrkTile - 1) / kSyrkTile;
@@ -724,6 +733,8 @@ __global__ void k_syrk(StepArgs a) {
 __global__ void k_syrk_rhs(StepArgs a) {
   const int node = a.list[blockIdx.x];
   const int s = blockIdx.y;
+  bind_plan(a, node);
+  if (s >= a.batch) return;
   const NodeDev nd = a.nodes[node];
   const int nf = nd.nf, m = nd.m, b = nd.b, nb = b + 1;
   if (m == 0) return;

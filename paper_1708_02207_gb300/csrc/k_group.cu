@@ -109,9 +109,12 @@ __device__ __forceinline__ void add_son(T* K, int ld, const NodeDev& ch, const i
 
 }  // namespace
 
-template <typename T, int W>
+// MP: the launch covers several plans (the per-plan fields are bound per CTA; a
+// separate instantiation keeps the single-plan kernel's registers as they are)
+template <typename T, int W, bool MP>
 __global__ void __launch_bounds__(256) k_front_group(StepArgs a, int ld, int fr_elems) {
   const int node = a.list[blockIdx.x];
+  if (MP) bind_plan(a, node);
   const NodeDev nd = a.nodes[node];
   const int nf = nd.nf, m = nd.m, nb = nd.b + 1, N = a.N;
   const int G = (blockDim.x >> 5) / W;
@@ -282,11 +285,20 @@ cudaError_t launch_front_group(const StepArgs& a, int family, cudaStream_t st) {
   if (smem > 227 * 1024) return cudaErrorInvalidConfiguration;
   dim3 grid(a.nlist, (a.batch + G - 1) / G);
   if (a.prof) a.prof->begin(family, a.fl_chol + a.fl_trsm + a.fl_syrk + a.fl_rhs, st);
-  switch (W) {
-    case 1: k_front_group<T, 1><<<grid, warps * 32, smem, st>>>(a, ld, fr_elems); break;
-    case 2: k_front_group<T, 2><<<grid, warps * 32, smem, st>>>(a, ld, fr_elems); break;
-    case 4: k_front_group<T, 4><<<grid, warps * 32, smem, st>>>(a, ld, fr_elems); break;
-    default: k_front_group<T, 8><<<grid, warps * 32, smem, st>>>(a, ld, fr_elems); break;
+  if (a.plan_of) {
+    switch (W) {
+      case 1: k_front_group<T, 1, true><<<grid, warps * 32, smem, st>>>(a, ld, fr_elems); break;
+      case 2: k_front_group<T, 2, true><<<grid, warps * 32, smem, st>>>(a, ld, fr_elems); break;
+      case 4: k_front_group<T, 4, true><<<grid, warps * 32, smem, st>>>(a, ld, fr_elems); break;
+      default: k_front_group<T, 8, true><<<grid, warps * 32, smem, st>>>(a, ld, fr_elems); break;
+    }
+  } else {
+    switch (W) {
+      case 1: k_front_group<T, 1, false><<<grid, warps * 32, smem, st>>>(a, ld, fr_elems); break;
+      case 2: k_front_group<T, 2, false><<<grid, warps * 32, smem, st>>>(a, ld, fr_elems); break;
+      case 4: k_front_group<T, 4, false><<<grid, warps * 32, smem, st>>>(a, ld, fr_elems); break;
+      default: k_front_group<T, 8, false><<<grid, warps * 32, smem, st>>>(a, ld, fr_elems); break;
+    }
   }
   if (a.prof) a.prof->end(st);
   return cudaGetLastError();
@@ -299,10 +311,15 @@ cudaError_t configure_group_kernels() {
   cudaError_t e;
   // the whole unified L1 / shared-memory array as shared memory: the residency of
   // these CTAs is bounded by their fronts, not by L1
-  const void* fns[] = {(const void*)k_front_group<double, 1>, (const void*)k_front_group<double, 2>,
-                       (const void*)k_front_group<double, 4>, (const void*)k_front_group<double, 8>,
-                       (const void*)k_front_group<float, 1>,  (const void*)k_front_group<float, 2>,
-                       (const void*)k_front_group<float, 4>,  (const void*)k_front_group<float, 8>};
+  const void* fns[] = {
+      (const void*)k_front_group<double, 1, false>, (const void*)k_front_group<double, 2, false>,
+      (const void*)k_front_group<double, 4, false>, (const void*)k_front_group<double, 8, false>,
+      (const void*)k_front_group<float, 1, false>,  (const void*)k_front_group<float, 2, false>,
+      (const void*)k_front_group<float, 4, false>,  (const void*)k_front_group<float, 8, false>,
+      (const void*)k_front_group<double, 1, true>,  (const void*)k_front_group<double, 2, true>,
+      (const void*)k_front_group<double, 4, true>,  (const void*)k_front_group<double, 8, true>,
+      (const void*)k_front_group<float, 1, true>,   (const void*)k_front_group<float, 2, true>,
+      (const void*)k_front_group<float, 4, true>,   (const void*)k_front_group<float, 8, true>};
   for (const void* f : fns) {
     if ((e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
     if ((e = cudaFuncSetAttribute(f, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared)))

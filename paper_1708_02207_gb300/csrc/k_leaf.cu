@@ -54,6 +54,7 @@ constexpr int kLeafSamples = 16;   // samples per CTA: two per warp, one per hal
 template <typename T>
 __global__ void __launch_bounds__(256) k_leaf_front(StepArgs a) {
   const int node = a.list[blockIdx.x];
+  bind_plan(a, node);
   const NodeDev nd = a.nodes[node];
   const int m = nd.m, b = nd.b, nf = nd.nf, nb = b + 1, N = a.N;
   const int hw = threadIdx.x >> 4, r = threadIdx.x & 15;   // half-warp = sample, lane r = row

@@ -72,6 +72,8 @@ __device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t phase, uint32_
 __global__ void __launch_bounds__(128, 3) k_syrk_tc(StepArgs a) {
   const int node = a.list[blockIdx.y];
   const int s = blockIdx.z;
+  bind_plan(a, node);
+  if (s >= a.batch) return;
   const NodeDev nd = a.nodes[node];
   const int m = nd.m, nb = nd.b + 1, nbt = nd.b;   // tiles cover the b boundary rows
   const int nt = (nbt + kTile - 1) / kTile;

@@ -15,7 +15,8 @@ namespace hdd {
 // algorithmic flops of the launch.  Owned by a plan; not thread-safe.
 enum ProfFamily {
   kProfKappa, kProfFrontWarp, kProfFrontSmall, kProfFill, kProfPotrf, kProfTrsm, kProfSyrk, kProfSyrkTc,
-  kProfSyrkRhs, kProfForward, kProfDescent, kProfResidual, kProfMisc, kProfFused, kProfLeaf, kProfCholTrsm, kProfCount
+  kProfSyrkRhs, kProfForward, kProfDescent, kProfResidual, kProfMisc, kProfFused, kProfLeaf, kProfCholTrsm,
+  kProfFunc, kProfCount
 };
 struct Profiler {
   bool on = false;
@@ -44,6 +45,18 @@ struct Profiler {
   }
 };
 
+// One plan's part of a launch over several plans (hdd_multi_*): the workspace
+// arenas, coefficient field, status words, load and sizes of that plan's batch.
+struct PlanDev {
+  Arenas arenas;
+  const double* kappa;
+  const float* kappa32;
+  int64_t kap_stride;
+  int32_t* status;
+  Rhs rhs;
+  int N, batch;
+};
+
 struct StepArgs {
   const NodeDev* nodes;
   const int32_t* maps;
@@ -63,7 +76,27 @@ struct StepArgs {
   double fl_chol, fl_trsm, fl_syrk, fl_rhs;   // algorithmic flops of this launch (whole batch)
   uint32_t wait_limit;       // polls of a bounded mbarrier wait before it gives up
   int stall_node, stall_sample;   // test hook of the bounded waits (-1: off)
+  // launches over several plans: the nodes and maps are the plans' tables
+  // concatenated, plan_of[node] names the node's plan and plans[] its part (null
+  // for a single plan)
+  const PlanDev* plans;
+  const int32_t* plan_of;
 };
+
+// Take the per-plan fields of `a` from the node's plan (no-op for one plan).  After
+// it, a.batch is that plan's batch: CTAs of samples beyond it have no work.
+__device__ __forceinline__ void bind_plan(StepArgs& a, int node) {
+  if (!a.plan_of) return;
+  const PlanDev& P = a.plans[a.plan_of[node]];
+  a.arenas = P.arenas;
+  a.kappa = P.kappa;
+  a.kappa32 = P.kappa32;
+  a.kap_stride = P.kap_stride;
+  a.status = P.status;
+  a.rhs = P.rhs;
+  a.N = P.N;
+  a.batch = P.batch;
+}
 
 // Fused bottom subtrees of the upsweep (one CTA per subtree and sample)
 struct FuseArgs {
@@ -75,6 +108,28 @@ struct FuseArgs {
   int front_elems;            // elements of the front workspace shared by the warp groups
 };
 template <typename T> cudaError_t launch_subtree(const FuseArgs& f, int nroots, size_t smem_bytes, cudaStream_t st);
+
+// mean functionals of the subdomains (Sec. 5.1 Lemma, Sec. 5.2): lambda^g of every node in
+// the list (to the node's Schur slot, and to lam for observed nodes) and mu^f = (lambda^f, c)
+struct FuncArgs {
+  const NodeDev* nodes;
+  const int32_t* maps;
+  const int32_t* list;
+  int nlist;
+  int batch;
+  int N;
+  Arenas A;
+  double* fmu;              // [batch x n_nodes]
+  int64_t n_nodes;
+  double* lam;              // [batch x lam_stride]: lambda^g of the observed nodes
+  int64_t lam_stride;
+  const int32_t* lam_off;   // per node, offset into a sample's lam row, or -1
+};
+template <typename T> cudaError_t launch_func_leaf(const FuncArgs& f, cudaStream_t st);
+template <typename T> cudaError_t launch_func_warp(const FuncArgs& f, int max_nf, cudaStream_t st);
+// observation k = mean over obs_nodes[k]: (lambda^g, x on its boundary) + mu^f (+ base)
+cudaError_t launch_mean_obs(const FuncArgs& f, const int32_t* obs_nodes, int n_obs, const double* x,
+                            int64_t x_stride, const double* base, double* u_obs, cudaStream_t st);
 
 // assembly: kappa = exp(Phi Z) (Sec. 3.1; kappa = e^q)
 cudaError_t launch_kappa(const double* phi, const double* Z, int n_t, int n_z, int batch, double* kappa,

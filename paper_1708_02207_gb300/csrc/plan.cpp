@@ -102,15 +102,35 @@ std::string build_plan(const hdd_plan_desc& d, Plan& p) {
   p.fp64_top_levels = d.fp64_top_levels;
   p.fuse_height = d.fuse_height;
   p.device = d.device;
-  p.obs.assign(d.obs_vertex, d.obs_vertex + d.n_obs);
-  for (int v : p.obs) {
-    if (v < 0 || v >= d.N * d.N) return "observation vertex out of range";
-    if (!unknown(d.N, v % d.N, v / d.N)) return "observation vertex on the Dirichlet boundary";
+  if (d.obs_kind != HDD_OBS_VERTEX && d.obs_kind != HDD_OBS_MEANS) return "unknown obs_kind";
+  p.obs_kind = d.obs_kind;
+  if (p.obs_kind == HDD_OBS_VERTEX) {
+    p.obs.assign(d.obs_vertex, d.obs_vertex + d.n_obs);
+    for (int v : p.obs) {
+      if (v < 0 || v >= d.N * d.N) return "observation vertex out of range";
+      if (!unknown(d.N, v % d.N, v / d.N)) return "observation vertex on the Dirichlet boundary";
+    }
   }
 
   build_tree(p);
   const int N = p.N;
   const int nn = (int)p.nodes.size();
+
+  if (p.obs_kind == HDD_OBS_MEANS) {
+    // observations are node means; the vertices whose values they need are the
+    // boundary unknowns of the observed nodes (their owners are the ancestors, so
+    // the pruned descent below visits exactly the ancestors, Sec. 5.2 Remark b)
+    p.obs_nodes.assign(d.obs_vertex, d.obs_vertex + d.n_obs);
+    std::vector<char> seen((size_t)N * N, 0);
+    for (int k : p.obs_nodes) {
+      if (k < 0 || k >= nn) return "observed node out of range";
+      for (int v : p.nodes[k].bnd)
+        if (!seen[v]) { seen[v] = 1; p.obs.push_back(v); }
+    }
+    std::sort(p.obs.begin(), p.obs.end());
+    if (p.obs.empty()) p.obs = p.nodes[0].gamma;   // only Omega observed: the root's interface
+  }
+  p.n_conv = (int)p.obs.size();
 
   // owner of every unknown: each is eliminated exactly once
   p.owner.assign((size_t)N * N, -1);
@@ -441,6 +461,29 @@ std::string build_plan(const hdd_plan_desc& d, Plan& p) {
     for (int hgt = 0; hgt <= p.height; ++hgt)
       p.fwd_lists[hgt] = {add_list(l[0][hgt]), add_list(l[1][hgt]), add_list(l[2][hgt]), add_list(l[3][hgt])};
   }
+  // mean functionals (mean plans): the observed nodes and their subtrees, by height,
+  // precision and format; lambda^g offsets of the observed nodes
+  p.func_lists.assign(p.height + 1, {0, 0, 0, 0});
+  p.lam_off.assign(nn, -1);
+  p.lam_stride = 0;
+  if (p.obs_kind == HDD_OBS_MEANS) {
+    std::vector<char> need(nn, 0);
+    for (int k : p.obs_nodes) {
+      need[k] = 1;
+      if (p.lam_off[k] < 0) { p.lam_off[k] = (int32_t)p.lam_stride; p.lam_stride += p.nodes[k].b; }
+    }
+    for (int k = 1; k < nn; ++k)   // children have larger indices than their parent
+      if (need[p.nodes[k].parent]) need[k] = 1;
+    std::vector<std::vector<int>> l[4];
+    for (auto& v : l) v.assign(p.height + 1, {});
+    for (int k = 0; k < nn; ++k) {
+      if (!need[k]) continue;
+      const Node& nd = p.nodes[k];
+      l[(nd.linv ? 2 : 0) + (nd.fp64 ? 0 : 1)][nd.height].push_back(k);
+    }
+    for (int hgt = 0; hgt <= p.height; ++hgt)
+      p.func_lists[hgt] = {add_list(l[0][hgt]), add_list(l[1][hgt]), add_list(l[2][hgt]), add_list(l[3][hgt])};
+  }
   // subdomain means: every node, by height
   {
     std::vector<std::vector<int>> l(p.height + 1);
@@ -559,6 +602,12 @@ Layout layout(const Plan& p, int batch) {
   L.ll = take(B * 8);
   L.z = take(B * p.n_z * 8);
   L.y = take(B * p.n_obs * 8);
+  if (p.obs_kind == HDD_OBS_MEANS) {
+    L.fmu = take(B * p.nodes.size() * 8);
+    L.lam = take(B * (size_t)p.lam_stride * 8);
+    L.conv_u = take(B * (size_t)p.n_conv * 8);
+    if (p.precision == HDD_MIXED_FP32 && p.ir_max_iter > 0) L.mfull = take(B * p.nodes.size() * 8);
+  }
   L.total = off;
   return L;
 }

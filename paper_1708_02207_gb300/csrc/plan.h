@@ -72,6 +72,12 @@ struct Step {
 struct Plan {
   // problem
   int N = 0, leaf = 0, n_z = 0, n_obs = 0, n_t = 0, device = -1;
+  int obs_kind = HDD_OBS_VERTEX;
+  // n_conv = obs.size(): the vertices whose corrections drive the refinement's
+  // convergence test (vertex plans: the observations; mean plans: the boundary
+  // unknowns of the observed nodes, or the root's interface)
+  int n_conv = 0;
+  std::vector<int32_t> obs_nodes;   // mean plans: the observed tree nodes
   int precision = HDD_FP64, ir_max_iter = 0, fp64_top_levels = 0, fuse_height = 0;
   double f = 1.0, sigma = 1.0, h = 0.0, ir_tol = 1e-10;
   std::vector<int32_t> obs;
@@ -131,6 +137,14 @@ struct Plan {
   // [height][fp64, fp32, condensed fp64, condensed fp32]: right-hand-side sweep
   std::vector<std::array<int, 4>> fwd_lists;
   std::vector<int> height_lists;   // per height: every node (subdomain means)
+  // mean plans: per height [fp64, fp32, condensed fp64, condensed fp32] nodes whose mean
+  // functional is needed (the observed nodes and their subtrees), and per node the
+  // offset of its functional lambda^g in the workspace's observation block (-1: none)
+  std::vector<std::array<int, 4>> func_lists;
+  std::vector<int32_t> lam_off;
+  int64_t lam_stride = 0;          // sum of b over the observed nodes
+  int32_t* d_lam_off = nullptr;
+  int32_t* d_obs_nodes = nullptr;
 
   // device copies
   double* d_phi = nullptr;
@@ -169,6 +183,11 @@ struct Layout {
   size_t u = 0, r = 0, du = 0;        // FP64 vertex vectors [batch x N^2]
   size_t f64 = 0, f32 = 0, s64 = 0, s32 = 0, y64 = 0, y32 = 0, tc = 0, inv = 0;
   size_t uobs = 0, ll = 0, z = 0, y = 0, conv = 0;
+  // mean plans: mu^f of every node [batch x n_nodes], lambda^g of the observed nodes
+  // [batch x lam_stride], the corrected vertices of the convergence test
+  // [batch x n_conv], and (mixed plans with refinement) the means of the refined
+  // iterate [batch x n_nodes]
+  size_t fmu = 0, lam = 0, conv_u = 0, mfull = 0;
   size_t total = 0;
 };
 Layout layout(const Plan& p, int batch);

@@ -17,13 +17,14 @@ LIB_PATH = os.path.join(_PKG, "_build", "libhdd.so")
 
 HDD_OK, HDD_EINVAL, HDD_ENOMEM, HDD_ECUDA, HDD_ENOTSPD, HDD_ENOCONV, HDD_ETIMEOUT, HDD_ESTATE = 0, -1, -2, -3, -4, -5, -6, -7
 HDD_FP64, HDD_MIXED_FP32 = 0, 1
+HDD_OBS_VERTEX, HDD_OBS_MEANS = 0, 1
 
 EXPORTED = [
     "hdd_plan", "hdd_plan_destroy", "hdd_workspace_size", "hdd_assemble", "hdd_upsweep",
     "hdd_point_solve", "hdd_loglik", "hdd_evaluate_host", "hdd_plan_info", "hdd_node_info",
     "hdd_node_indices", "hdd_status_string", "hdd_last_error", "hdd_evaluate_static",
     "hdd_profile_begin", "hdd_profile_end", "hdd_kappa", "hdd_solve_loads", "hdd_subdomain_means",
-    "hdd_set_wait_bound",
+    "hdd_set_wait_bound", "hdd_mean_functionals",
 ]
 STATIC_WORKSPACE_BYTES = 32 << 20
 
@@ -35,7 +36,7 @@ class PlanDesc(C.Structure):
         ("n_obs", C.c_int32), ("obs_vertex", C.POINTER(C.c_int32)),
         ("sigma", C.c_double), ("precision", C.c_int32), ("ir_max_iter", C.c_int32),
         ("ir_tol", C.c_double), ("fp64_top_levels", C.c_int32), ("fuse_height", C.c_int32),
-        ("device", C.c_int32),
+        ("device", C.c_int32), ("obs_kind", C.c_int32),
     ]
 
 
@@ -90,6 +91,7 @@ def load_library() -> C.CDLL:
     lib.hdd_solve_loads.argtypes = [vp, i32, vp, vp, i32, vp, vp, vp]
     lib.hdd_subdomain_means.argtypes = [vp, i32, vp, C.c_int64, vp, vp]
     lib.hdd_set_wait_bound.argtypes = [vp, C.c_uint32, i32, i32]
+    lib.hdd_mean_functionals.argtypes = [vp, i32, vp, vp, vp, vp]
     lib.hdd_profile_begin.argtypes = [vp]
     lib.hdd_profile_end.argtypes = [vp, C.POINTER(KernelStat), i32, C.POINTER(i32)]
     lib.hdd_plan_info.argtypes = [vp, C.POINTER(PlanInfo)]
@@ -155,7 +157,9 @@ class Plan:
 
     def __init__(self, N: int, leaf: int, phi: np.ndarray | None, obs: np.ndarray, sigma: float,
                  f: float = 1.0, precision: int = HDD_FP64, ir_max_iter: int = 2, ir_tol: float = 1e-8,
-                 fp64_top_levels: int = 0, fuse_height: int = 0, device: int = 0):
+                 fp64_top_levels: int = 0, fuse_height: int = 0, device: int = 0, obs_kind: int = HDD_OBS_VERTEX):
+        """obs: vertex ids (obs_kind HDD_OBS_VERTEX) or tree node ids whose mean values are
+        observed (HDD_OBS_MEANS; node ids as reported by node() of a plan of the same N, leaf)."""
         self.lib = load_library()
         self.N, self.leaf, self.sigma, self.f = N, leaf, float(sigma), float(f)
         self.obs = np.ascontiguousarray(obs, dtype=np.int32)
@@ -179,6 +183,8 @@ class Plan:
         desc.fp64_top_levels = fp64_top_levels
         desc.fuse_height = fuse_height
         desc.device = device
+        desc.obs_kind = obs_kind
+        self.obs_kind = obs_kind
         self.precision = precision
         h = C.c_void_p()
         _check(self.lib.hdd_plan(C.byref(desc), C.byref(h)), "hdd_plan")
@@ -290,6 +296,22 @@ class Plan:
             raise ValueError("means must be a contiguous float64 [batch, n_nodes] tensor")
         _check(self.lib.hdd_subdomain_means(self._h, int(u.shape[0]), _ptr(u), int(u.stride(0)), _ptr(means),
                                             _stream_ptr(stream)), "hdd_subdomain_means")
+
+    def mean_functionals(self, batch: int, ws, stream=None):
+        """hdd_mean_functionals: (lambda^g of the observed nodes [batch, sum b], mu^f of every
+        node [batch, n_nodes]) as the last point_solve on ws left them (mean plans only)."""
+        import torch
+        nb = sum(self.node(int(k))["b"] for k in self.obs)
+        lam = torch.empty(batch, nb, dtype=torch.float64, device=self._dev())
+        mu = torch.empty(batch, self.info()["n_nodes"], dtype=torch.float64, device=self._dev())
+        _check(self.lib.hdd_mean_functionals(self._h, batch, _ptr(ws), _ptr(lam) if nb else None, _ptr(mu),
+                                             _stream_ptr(stream)), "hdd_mean_functionals")
+        return lam, mu
+
+    def nodes_at_depth(self, depth: int) -> np.ndarray:
+        """Ids of the tree nodes at one depth (the cells of a coarse level), ascending."""
+        n = self.info()["n_nodes"]
+        return np.array([k for k in range(n) if self.node(k)["depth"] == depth], dtype=np.int32)
 
     def loglik(self, batch: int, ws, u_obs, y, loglik, status=None, stream=None):
         _need(u_obs, "u_obs", "f64", (batch, self.n_obs), self._dev())

@@ -167,3 +167,34 @@ def test_condensed_leaves_follow_the_leaf_size(hdd):
     assert hdd.Plan(65, 8, None, obs, 0.01, device=-1).info()["n_condensed_leaves"] == 0
     fused = hdd.Plan(65, 4, None, obs, 0.01, precision=hdd.HDD_MIXED_FP32, fuse_height=2, device=-1)
     assert fused.info()["n_condensed_leaves"] == 0
+
+
+@pytest.mark.parametrize("N,leaf,depth", [(33, 4, 4), (65, 8, 3), (50, 5, 5)])
+def test_mean_plan_visits_exactly_the_ancestors(hdd, N, leaf, depth):
+    # Sec. 5.2 Remark b: a functional supported in omega_0 needs Phi of the nodes above
+    # omega_0 only, so the descent of a plan observing node means stops at their ancestors
+    # (the root is always solved)
+    probe = hdd.Plan(N, leaf, None, np.array([0], dtype=np.int32), 0.1, device=-1, obs_kind=hdd.HDD_OBS_MEANS)
+    ids = probe.nodes_at_depth(depth)[::2]
+    plan = hdd.Plan(N, leaf, None, ids, 0.1, device=-1, obs_kind=hdd.HDD_OBS_MEANS)
+    nodes = hd.build_tree(N, leaf)
+    expect = {0}
+    for k in ids:
+        a = nodes[k].parent
+        while a >= 0:
+            expect.add(a)
+            a = nodes[a].parent
+    got = {k for k in range(len(nodes)) if plan.node(k)["visited"]}
+    assert got == {k for k in expect if nodes[k].gamma}
+    # mean plans hold more per sample than vertex plans (functionals, conv. vertices)
+    vplan = hdd.Plan(N, leaf, None, w.obs_vertices(N, 2), 0.1, device=-1)
+    assert plan.workspace_size(4) > vplan.workspace_size(4)
+
+
+def test_mean_plan_refuses_bad_nodes(hdd):
+    with pytest.raises(hdd.HDDError):
+        hdd.Plan(33, 8, None, np.array([99], dtype=np.int32), 0.1, device=-1, obs_kind=hdd.HDD_OBS_MEANS)
+    with pytest.raises(hdd.HDDError):
+        hdd.Plan(33, 8, None, np.array([-1], dtype=np.int32), 0.1, device=-1, obs_kind=hdd.HDD_OBS_MEANS)
+    with pytest.raises(hdd.HDDError):
+        hdd.Plan(33, 8, None, np.array([3], dtype=np.int32), 0.1, device=-1, obs_kind=7)
