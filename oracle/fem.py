@@ -155,6 +155,57 @@ def solve_load(N: int, kappa: np.ndarray, c: np.ndarray, refine: bool = False) -
     return full
 
 
+def prolongate(N: int, f_coarse: np.ndarray) -> np.ndarray:
+    """Nodal values on the fine N x N grid of the coarse P1 function with nodal values
+    f_coarse [NH*NH], NH = (N+1)/2, H = 2h (Sec. 3.5: a right-hand side in V_H, a subspace
+    of V_h).  Evaluated at each fine vertex from the coarse triangle that contains it, by its
+    barycentric coordinates (the coarse mesh is the same "/" triangulation with step H)."""
+    if N % 2 == 0:
+        raise ValueError("the two-grid load needs an odd N (the coarse grid has (N+1)/2 vertices per side)")
+    NH = (N + 1) // 2
+    fH = np.asarray(f_coarse, dtype=np.float64).reshape(NH * NH)
+    cc, ct = mesh(NH)
+    out = np.empty(N * N)
+    hH = 1.0 / (NH - 1)
+    for j in range(N):
+        for i in range(N):
+            x, y = i / (N - 1), j / (N - 1)
+            ci, cj = min(int(x / hH), NH - 2), min(int(y / hH), NH - 2)
+            fx, fy = x / hH - ci, y / hH - cj
+            t = 2 * (cj * (NH - 1) + ci) + (0 if fx >= fy else 1)   # lower-right below the "/" diagonal
+            p = cc[ct[t]]
+            T = np.array([[p[0, 0], p[1, 0], p[2, 0]], [p[0, 1], p[1, 1], p[2, 1]], [1.0, 1.0, 1.0]])
+            lam = np.linalg.solve(T, np.array([x, y, 1.0]))
+            out[j * N + i] = lam @ fH[ct[t]]
+    return out
+
+
+def solve_data(N: int, kappa: np.ndarray, c=None, f_coarse=None, g=None, refine: bool = False) -> np.ndarray:
+    """FE solution for one load and Dirichlet data (Sec. 2: the solution as a function of the
+    right-hand side and of the boundary values, u|_gamma = Phi(u|_dOmega, f)): the load is
+    the assembled vector c [N*N] (interior entries used) or, for f given on the coarse grid
+    (Sec. 3.5), the vertex-quadrature load of its fine interpolant, c_i = sum_t |t|/3 f(x_i);
+    g [N*N] gives u on the boundary vertices (interior entries ignored; None = 0).  Solves
+    A_II u_I = c_I - A_IB g_B by banded Cholesky and returns u at every vertex."""
+    A, _ = assemble(N, kappa)
+    if (c is None) == (f_coarse is None):
+        raise ValueError("give exactly one of c and f_coarse")
+    if f_coarse is not None:
+        _, c = assemble(N, np.ones(2 * (N - 1) ** 2), prolongate(N, f_coarse))
+    I = interior_ids(N)
+    Bd = np.setdiff1d(np.arange(N * N), I)
+    gv = np.zeros(N * N) if g is None else np.asarray(g, dtype=np.float64)
+    AII = A[I][:, I].tocsr()
+    rhs = np.asarray(c, dtype=np.float64)[I] - A[I][:, Bd] @ gv[Bd]
+    u = solve_banded_cholesky(AII, rhs, N - 1)
+    if refine:
+        u = refine_longdouble(AII, rhs, u, N - 1)
+    full = np.zeros(N * N)
+    full[I] = u
+    full[Bd] = gv[Bd]
+    return full
+
+
 def subdomain_mean(N: int, u: np.ndarray, x0: int, x1: int, y0: int, y1: int) -> float:
     """Mean of the piecewise linear u over the rectangle [x0, x1] x [y0, y1] (vertex
     indices), Sec. 5, Eq. mean: sum over its triangles of |t|/3 (u_1 + u_2 + u_3),

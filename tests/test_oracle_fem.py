@@ -308,3 +308,77 @@ def test_subdomain_means_follow_the_tree_recursion():
         a, b = nd.children
         ref = (area(nodes[a]) * mean[a] + area(nodes[b]) * mean[b]) / area(nd)
         assert abs(mean[k] - ref) < 1e-14 * max(1.0, abs(ref))
+
+
+# --- Dirichlet data and coarse-grid loads (Sec. 2, Sec. 3.5) ---------------------------------
+
+def _bnd(N):
+    return np.setdiff1d(np.arange(N * N), fem.interior_ids(N))
+
+
+def test_constant_dirichlet_data_gives_a_constant_for_any_kappa():
+    # constants are in the kernel of every stiffness (rows of A sum to zero), so g = 1, c = 0
+    # gives u = 1 whatever kappa is
+    N = 17
+    u = fem.solve_data(N, _kappa_random(N, 21, amp=2.0), c=np.zeros(N * N), g=np.ones(N * N))
+    assert np.abs(u - 1.0).max() < 1e-12
+
+
+def test_linear_dirichlet_data_is_reproduced_at_constant_kappa():
+    # at constant kappa the P1 (five-point) operator annihilates affine functions
+    N = 21
+    coords, _ = fem.mesh(N)
+    gl = 0.3 + 1.7 * coords[:, 0] - 0.9 * coords[:, 1]
+    u = fem.solve_data(N, np.full(2 * (N - 1) ** 2, 2.5), c=np.zeros(N * N), g=gl)
+    assert np.abs(u - gl).max() < 1e-12
+
+
+def test_data_superposition_and_maximum_principle():
+    N = 17
+    kap = _kappa_random(N, 22, amp=1.5)
+    rng = np.random.default_rng(23)
+    c = rng.random(N * N) / (N - 1) ** 2
+    g = rng.random(N * N)
+    u = fem.solve_data(N, kap, c=c, g=g)
+    u0 = fem.solve_data(N, kap, c=c)
+    ug = fem.solve_data(N, kap, c=np.zeros(N * N), g=g)
+    assert np.abs(u - (u0 + ug)).max() < 1e-12 * np.abs(u).max()
+    assert np.array_equal(u[_bnd(N)], g[_bnd(N)])
+    # an M-matrix: harmonic data stay within the range of their boundary values
+    B = _bnd(N)
+    assert ug.min() >= g[B].min() - 1e-13 and ug.max() <= g[B].max() + 1e-13
+
+
+def test_prolongation_is_exact_for_affine_coarse_functions():
+    N, NH = 17, 9
+    cH, _ = fem.mesh(NH)
+    cF, _ = fem.mesh(N)
+    a = lambda xy: 0.5 - 2.0 * xy[:, 0] + 3.0 * xy[:, 1]
+    assert np.abs(fem.prolongate(N, a(cH)) - a(cF)).max() < 1e-13
+
+
+def test_prolongation_matches_the_coarse_function_between_coarse_vertices():
+    # coarse vertices keep their values; a fine vertex on a coarse edge (axis or "/" diagonal)
+    # is the mean of the edge's two coarse ends
+    N, NH = 9, 5
+    fH = np.random.default_rng(24).standard_normal(NH * NH)
+    f = fem.prolongate(N, fH)
+    F = lambda i, j: f[j * N + i]
+    C = lambda a, b: fH[b * NH + a]
+    for b in range(NH):
+        for a in range(NH):
+            assert F(2 * a, 2 * b) == pytest.approx(C(a, b), abs=1e-14)
+    for b in range(NH - 1):
+        for a in range(NH - 1):
+            assert F(2 * a + 1, 2 * b) == pytest.approx(0.5 * (C(a, b) + C(a + 1, b)), abs=1e-14)
+            assert F(2 * a, 2 * b + 1) == pytest.approx(0.5 * (C(a, b) + C(a, b + 1)), abs=1e-14)
+            assert F(2 * a + 1, 2 * b + 1) == pytest.approx(0.5 * (C(a, b) + C(a + 1, b + 1)), abs=1e-14)
+
+
+def test_coarse_constant_load_is_the_fine_constant_load():
+    N = 17
+    kap = _kappa_random(N, 25)
+    NH = (N + 1) // 2
+    u1 = fem.solve_data(N, kap, f_coarse=np.full(NH * NH, 1.0))
+    u2 = fem.solve_full(N, kap, 1.0)
+    assert np.abs(u1 - u2).max() < 1e-13 * np.abs(u2).max()
