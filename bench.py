@@ -184,6 +184,196 @@ def run_reference(args, cfg):
     return 0
 
 
+# Uneven batch (the north-star's batching workload): samples over four grids, 40/30/20/10 %
+# by count, n_Z uniform in {10, 20, 40}, per plan an m x m observation lattice with m
+# uniform in 4..32 (16 to 1024 points); KL field with correlation length 0.2, variance 1.
+UNEVEN_MIX = ((129, 0.4), (257, 0.3), (513, 0.2), (1025, 0.1))
+
+
+def uneven_groups(total: int):
+    """The plans of the uneven batch: one per (grid, n_Z) with its sample count and lattice."""
+    rng = np.random.default_rng(np.random.SeedSequence(w.ROOT_SEED).spawn(4)[3])
+    counts = [int(round(total * f)) for _, f in UNEVEN_MIX]
+    counts[-1] = total - sum(counts[:-1])
+    groups = []
+    for (N, _), cnt in zip(UNEVEN_MIX, counts):
+        nz = rng.choice([10, 20, 40], size=cnt)
+        for z in (10, 20, 40):
+            k = int((nz == z).sum())
+            if k:
+                groups.append({"N": N, "n_z": z, "count": k, "m": int(rng.integers(4, 33))})
+    return groups, rng
+
+
+def run_uneven(args, hdd, torch, dev, stream, local):
+    """The uneven batch through hdd_multi_* (one launch per tree height and front class over
+    all plans) against the same samples evaluated plan by plan, leaves and refinement steps
+    from the autotuner's table."""
+    from paper_1708_02207_gb300 import autotune
+    prec_name = args.precision
+    prec = hdd.HDD_MIXED_FP32 if prec_name == "mixed" else hdd.HDD_FP64
+    groups, rng = uneven_groups(args.uneven_samples)
+    grids = sorted({g["N"] for g in groups})
+    tuned = {N: autotune.choose(N, prec_name) for N in grids}
+    phis = {N: w.kl_basis(N, 40, 0.2, 1.0) for N in grids}
+    plans = []
+    for g in groups:
+        t = tuned[g["N"]]
+        phi = np.ascontiguousarray(phis[g["N"]][:, :g["n_z"]])
+        plans.append(hdd.Plan(g["N"], t["leaf"], phi, w.obs_vertices(g["N"], g["m"]), 0.01, precision=prec,
+                              ir_max_iter=t["ir_max_iter"], ir_tol=args.ir_tol, device=local))
+    free = torch.cuda.mem_get_info(dev)[0]
+    chunks = 1
+    while sum(p.workspace_size(-(-g["count"] // chunks)) for p, g in zip(plans, groups)) > 0.6 * free:
+        chunks += 1
+    batches = [-(-g["count"] // chunks) for g in groups]
+    mp = hdd.MultiPlan(plans, batches)
+    Zs = [[torch.from_numpy(rng.standard_normal((b, g["n_z"]))).to(dev) for b, g in zip(batches, groups)]
+          for _ in range(chunks)]
+    ys = [torch.from_numpy(0.01 * rng.standard_normal(p.n_obs)).to(dev) for p in plans]
+    failed = 0
+
+    def multi():
+        nonlocal failed
+        for c in range(chunks):
+            outs = mp.evaluate(Zs[c], ys, stream)
+        failed = sum(int((o[2] != 0).sum().item()) for o in outs)
+
+    def alone():
+        for c in range(chunks):
+            for q, p in enumerate(plans):
+                p.evaluate(Zs[c][q], ys[q], ws=mp.ws[q], stream=stream)
+
+    def timed(fn, steps):
+        with torch.cuda.stream(stream):
+            fn()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(steps):
+                fn()
+            e1.record(stream)
+        stream.synchronize()
+        return e0.elapsed_time(e1) / steps
+
+    t_multi = timed(multi, args.uneven_steps)
+    t_alone = timed(alone, args.uneven_steps)
+    evaluated = sum(batches) * chunks
+    info = mp.info()
+    out = {"samples": args.uneven_samples, "evaluated_per_step": evaluated, "plans": len(plans), "chunks": chunks,
+           "grids": {str(N): sum(g["count"] for g in groups if g["N"] == N) for N in grids},
+           "precision": prec_name, "tuned": {str(N): tuned[N] for N in grids},
+           "ms_per_step": t_multi, "evals_per_s": args.uneven_samples / (t_multi / 1e3),
+           "ms_per_step_plans_alone": t_alone, "evals_per_s_plans_alone": args.uneven_samples / (t_alone / 1e3),
+           "launches_per_chunk": info["launches_evaluate"],
+           "launches_per_chunk_plans_alone": sum(p.info()["launches_evaluate"] for p in plans),
+           "failed_samples": failed,
+           "note": "one step = every sample once (chunks of per-plan batches that fit 60% of free HBM; "
+                   "padded samples of the last chunk count as work, not as evaluations)"}
+    del mp, Zs
+    torch.cuda.empty_cache()
+    return out
+
+
+def run_policy(args, cfg, hdd, torch, dev, stream, local, prob, Z, y):
+    """North-star precision split (FP64 Cholesky of the top two tree levels) beside the
+    benched all-FP32 factorisation: per setting the fewest refinement steps with no sample
+    flagged HDD_ENOCONV at the tolerance, and its speed."""
+    B = Z.shape[0]
+    res = {}
+    for top in (0, 2):
+        for K in (1, 2, 3):
+            plan = hdd.Plan(cfg.N, args.leaf or cfg.leaf, prob.phi, prob.obs, cfg.sigma, f=cfg.f,
+                            precision=hdd.HDD_MIXED_FP32, ir_max_iter=K, ir_tol=args.ir_tol, fp64_top_levels=top,
+                            device=local)
+            ws = plan.workspace(B)
+            with torch.cuda.stream(stream):
+                ll, u, st = plan.evaluate(Z, y, ws=ws, stream=stream)
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                for _ in range(2):
+                    plan.evaluate(Z, y, ws=ws, stream=stream)
+                e1.record(stream)
+            stream.synchronize()
+            bad = int((st != 0).sum().item())
+            ms = e0.elapsed_time(e1) / 2
+            del ws
+            torch.cuda.empty_cache()
+            if bad == 0 or K == 3:
+                res[f"fp64_top_levels_{top}"] = {"ir_steps": K, "failed_samples": bad, "ms_per_step": ms,
+                                                 "evals_per_s": B / (ms / 1e3)}
+                break
+    return res
+
+
+def run_means_leg(args, cfg, hdd, torch, dev, stream, local, prob, Z):
+    """Subdomain means as the observation operator (Sec. 5.1-5.2): the 256 cells of depth 8
+    (32 x 32 cells each) of the same grid and samples."""
+    B = Z.shape[0]
+    probe = hdd.Plan(cfg.N, args.leaf or cfg.leaf, None, np.array([0], dtype=np.int32), cfg.sigma,
+                     device=-1, obs_kind=hdd.HDD_OBS_MEANS)
+    ids = probe.nodes_at_depth(8)
+    plan = hdd.Plan(cfg.N, args.leaf or cfg.leaf, prob.phi, ids, cfg.sigma, f=cfg.f, precision=hdd.HDD_MIXED_FP32,
+                    ir_max_iter=args.ir_iters, ir_tol=args.ir_tol, device=local, obs_kind=hdd.HDD_OBS_MEANS)
+    ws = plan.workspace(B)
+    yv = torch.zeros(ids.size, dtype=torch.float64, device=dev)
+    with torch.cuda.stream(stream):
+        ll, m, st = plan.evaluate(Z, yv, ws=ws, stream=stream)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(2):
+            plan.evaluate(Z, yv, ws=ws, stream=stream)
+        e1.record(stream)
+    stream.synchronize()
+    ms = e0.elapsed_time(e1) / 2
+    out = {"observed_nodes": int(ids.size), "depth": 8, "ms_per_step": ms, "evals_per_s": B / (ms / 1e3),
+           "failed_samples": int((st != 0).sum().item()), "visited_nodes": plan.info()["n_visited"],
+           "launches_per_evaluation": plan.info()["launches_evaluate"]}
+    del ws
+    torch.cuda.empty_cache()
+    return out
+
+
+def run_serving(args, hdd, torch, dev, local):
+    """The serving workload: 64 random-walk Metropolis chains (step 0.1, n_Z 40) spread over the
+    grids, each with one request in flight, Poisson arrivals at offered loads that are
+    fractions of the measured saturation rate; continuous batching admitted by workspace
+    bytes (paper_1708_02207_gb300.serving).  Per load point: offered rate, throughput and
+    per-request p50/p99 latency."""
+    from paper_1708_02207_gb300 import autotune, serving
+    rng = np.random.default_rng(np.random.SeedSequence(w.ROOT_SEED).spawn(5)[4])
+    grids = args.serve_grids
+    out = {"chains": 64, "grids": grids, "step": 0.1, "n_z": 40, "points": {}}
+    for prec_name in args.serve_precisions:
+        prec = hdd.HDD_MIXED_FP32 if prec_name == "mixed" else hdd.HDD_FP64
+        plans, ydata = {}, {}
+        for N in grids:
+            t = autotune.choose(N, prec_name)
+            obs = w.obs_vertices(N, 16)
+            plans[str(N)] = hdd.Plan(N, t["leaf"], w.kl_basis(N, 40, 0.1, 2.0), obs, 0.01, precision=prec,
+                                     ir_max_iter=t["ir_max_iter"], ir_tol=args.ir_tol, device=local)
+            ydata[str(N)] = 0.05 + 0.01 * rng.standard_normal(obs.size)
+        budget = int(min(80e9, 0.5 * torch.cuda.mem_get_info(dev)[0]))
+        backend = serving.CudaBackend(plans, n_slots=4, device=local)
+        server = serving.Server(backend, budget_bytes=budget, max_batch=64, n_slots=4)
+        chains = [serving.MetropolisChain(str(grids[k % len(grids)]), rng.standard_normal(40),
+                                          ydata[str(grids[k % len(grids)])], 0.1, rng) for k in range(64)]
+        n_req = args.serve_requests if prec_name == "mixed" else max(1, args.serve_requests // 5)
+        serving.run_offered_load(server, chains, float("inf"), min(n_req, 256), rng)   # warm-up
+        sat = serving.run_offered_load(server, chains, float("inf"), n_req, rng)
+        pts = [{"load": "saturation", "offered_per_s": None, "evals_per_s": sat["evals_per_s"],
+                "p50_ms": 1e3 * sat["p50_s"], "p99_ms": 1e3 * sat["p99_s"], "requests": sat["requests"]}]
+        for f in args.serve_loads:
+            r = serving.run_offered_load(server, chains, f * sat["evals_per_s"], n_req, rng)
+            pts.append({"load": f, "offered_per_s": f * sat["evals_per_s"], "evals_per_s": r["evals_per_s"],
+                        "p50_ms": 1e3 * r["p50_s"], "p99_ms": 1e3 * r["p99_s"], "requests": r["requests"]})
+        out["points"][prec_name] = {"budget_bytes": budget, "peak_admitted_bytes": server.peak_bytes,
+                                    "batches": server.batches, "requests_per_point": n_req, "sweep": pts,
+                                    "failed": sum(1 for r in server.done if r.status != 0 or r.rejected)}
+        del server, backend, plans
+        torch.cuda.empty_cache()
+    return out
+
+
 def run_hdd(args, cfg):
     import torch
     from paper_1708_02207_gb300 import build as hdd_build, hdd
@@ -402,6 +592,7 @@ def run_hdd(args, cfg):
         s_l = torch.empty(B, dtype=torch.int32, device=dev)
         means = torch.empty(B, info["n_nodes"], dtype=torch.float64, device=dev)
         ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        ws_l = ws
         with torch.cuda.stream(stream):
             plan.assemble(Z, ws, stream)
             plan.upsweep(B, ws, stream)
@@ -426,7 +617,37 @@ def run_hdd(args, cfg):
             + K * (info["bytes_residual"] + v8) + K * 3 * v8 + (K * v8 + v8 if K else 0.0)
         by_l = by_load * B * args.loads
         by_m = (v8 + 8.0 * info["n_nodes"]) * B
-        loads = {"loads_per_sample": args.loads, "ms_per_call": t_l,
+        # four loads per sample: hdd_solve_loads (one load per sweep) against hdd_solve_data
+        # (four right-hand sides per factor read), with Dirichlet data, and with coarse-grid loads
+        data = None
+        if args.data:
+            c4 = torch.rand(B, 4, NN, dtype=torch.float64, device=dev, generator=gen) / (cfg.N - 1) ** 2
+            g4 = torch.rand(B, 4, NN, dtype=torch.float64, device=dev, generator=gen)
+            NH = (cfg.N + 1) // 2
+            f4 = torch.rand(B, 4, NH * NH, dtype=torch.float64, device=dev, generator=gen)
+            u4 = torch.empty_like(c4)
+            scratch = torch.empty(plan.data_scratch_size(B), dtype=torch.uint8, device=dev)
+            runs = {"solve_loads": lambda: plan.solve_loads(B, ws_l, c4, u4, s_l, stream),
+                    "solve_data": lambda: plan.solve_data(B, ws_l, u4, c=c4, g=g4, status=s_l, scratch=scratch,
+                                                          stream=stream),
+                    "solve_data_coarse": lambda: plan.solve_data(B, ws_l, u4, f_coarse=f4, g=g4, status=s_l,
+                                                                 scratch=scratch, stream=stream)}
+            data = {"loads_per_sample": 4}
+            for name, fn in runs.items():
+                with torch.cuda.stream(stream):
+                    fn()
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    e0.record(stream)
+                    for _ in range(args.steps):
+                        fn()
+                    e1.record(stream)
+                stream.synchronize()
+                ms = e0.elapsed_time(e1) / args.steps
+                data[name] = {"ms_per_call": ms, "load_solves_per_s": 4 * B / (ms / 1e3),
+                              "failed_samples": int((s_l != 0).sum().item())}
+            data["speedup_of_grouped_sweeps"] = data["solve_loads"]["ms_per_call"] / data["solve_data"]["ms_per_call"]
+            del c4, g4, f4, u4, scratch
+        loads = {"loads_per_sample": args.loads, "ms_per_call": t_l, "four_loads_with_data": data,
                  "load_solves_per_s": world * B * args.loads / (t_l / 1e3),
                  "failed_samples": int((s_l != 0).sum().item()),
                  "roofline": {"bound": "hbm", "achieved": by_l / (t_l / 1e3) / 1e9, "peak": hbm, "unit": "GB/s",
@@ -437,11 +658,22 @@ def run_hdd(args, cfg):
         del c_l, u_l
         torch.cuda.empty_cache()
 
+    # legs beside the headline (each after the headline's workspace is released)
+    del ws
+    torch.cuda.empty_cache()
+    policy = means_leg = uneven = serve = None
+    if precision != hdd.HDD_FP64 and args.policy:
+        policy = run_policy(args, cfg, hdd, torch, dev, stream, local, prob, Z, y)
+    if precision != hdd.HDD_FP64 and args.means and cfg.N >= 257:
+        means_leg = run_means_leg(args, cfg, hdd, torch, dev, stream, local, prob, Z)
+    if args.uneven_samples > 0:
+        uneven = run_uneven(args, hdd, torch, dev, stream, local)
+    if args.serve_requests > 0:
+        serve = run_serving(args, hdd, torch, dev, local)
+
     # the plain FP64 path on the same inputs (the speedup of the mixed path is over it)
     fp64 = None
     if precision != hdd.HDD_FP64 and args.fp64_steps > 0:
-        del ws
-        torch.cuda.empty_cache()
         plan64 = hdd.Plan(cfg.N, args.leaf or cfg.leaf, prob.phi, prob.obs, cfg.sigma, f=cfg.f,
                           precision=hdd.HDD_FP64, device=local)
         ws64 = plan64.workspace(B)
@@ -492,6 +724,10 @@ def run_hdd(args, cfg):
                              "note": "device time of one whole batch step; per-request latency is in 'serving'"},
         "profiled_ms_per_step": profiled_ms,
         "fp64_path": fp64,
+        "precision_policy": policy,
+        "subdomain_means": means_leg,
+        "uneven": uneven,
+        "serving": serve,
         "solve_loads": loads,
         "roofline": roof,
         "upsweep": upsweep_roof,
@@ -526,6 +762,16 @@ def main(argv=None):
     ap.add_argument("--ir-iters", type=int, default=2)
     ap.add_argument("--ir-tol", type=float, default=1e-8)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--policy", type=int, default=1, help="precision-policy leg (FP64 top levels; 0: skip)")
+    ap.add_argument("--means", type=int, default=1, help="subdomain-means leg (0: skip)")
+    ap.add_argument("--data", type=int, default=1, help="loads-with-data leg inside the loads leg (0: skip)")
+    ap.add_argument("--uneven-samples", type=int, default=4096, help="samples of the uneven batch (0: skip)")
+    ap.add_argument("--uneven-steps", type=int, default=2)
+    ap.add_argument("--serve-requests", type=int, default=1000,
+                    help="requests per load point of the serving leg (0: skip; FP64 takes a fifth)")
+    ap.add_argument("--serve-grids", type=int, nargs="+", default=[513])
+    ap.add_argument("--serve-precisions", nargs="+", default=["mixed"], choices=["mixed", "fp64"])
+    ap.add_argument("--serve-loads", type=float, nargs="+", default=[0.25, 0.75, 1.25])
     ap.add_argument("--loads", type=int, default=1,
                     help="load vectors per sample of the hdd_solve_loads measurement (0: skip)")
     args = ap.parse_args(argv)

@@ -241,6 +241,41 @@ hdd_status hdd_evaluate_host(hdd_plan_t plan, int32_t batch, void* workspace,
 hdd_status hdd_solve_loads(hdd_plan_t plan, int32_t batch, void* workspace, const double* c, int32_t n_loads,
                            double* u, int32_t* sample_status, void* stream);
 
+/* Many loads AND Dirichlet data at a fixed coefficient field, the load given on the
+ * fine grid or on the coarse grid H = 2h (Sec. 2: the operators of every node are
+ * computed once and applied to any number of right-hand sides and boundary data,
+ * u|_gamma = Phi(u|_dOmega, f); Sec. 3.5: a smooth right-hand side discretised on a
+ * coarser mesh, f in V_H, a subspace of V_h).  For each sample and each of its n_loads
+ * data sets it solves A_II u_I = c_I - A_IB g_B and sets u_B = g_B, in correction form:
+ * u = g on the boundary, 0 inside; r = c - A u (FP64 five-point residual, boundary
+ * neighbours contributing g); d = the HDD solve of r through the stored factors (a
+ * right-hand-side sweep "Leaves to Root", then "Root to Leaves" over every node);
+ * u += d.  Mixed plans repeat the last three steps ir_max_iter more times (iterative
+ * refinement) and flag HDD_ENOCONV as hdd_solve_loads does.  The loads of a sample go
+ * through the sweeps in groups of four: each node's factors are read once per group and
+ * applied to all four right-hand sides.
+ *   c:        device [batch x n_loads x N^2] FP64 assembled loads c_i = sum_{t at x_i}
+ *             |t|/3 f(x_i) (Eq. coefc; h^2 f(x_i) on this mesh), boundary entries ignored;
+ *             or NULL when f_coarse is given.
+ *   f_coarse: device [batch x n_loads x NH^2] FP64 nodal values of f on the coarse grid,
+ *             NH = (N+1)/2 vertices per side (N odd), coarse vertex (a, b) at fine vertex
+ *             (2a, 2b); the load is the vertex quadrature of its fine P1 interpolant; or
+ *             NULL when c is given.  Exactly one of c and f_coarse.
+ *   g:        device [batch x n_loads x N^2] FP64 Dirichlet data at the boundary vertices
+ *             (interior entries ignored), or NULL for g = 0.
+ *   u:        device [batch x n_loads x N^2] FP64, the solution at every vertex.
+ *   scratch:  device, >= hdd_data_scratch_size(plan, batch) bytes, 256-byte aligned,
+ *             caller-owned (the group's residuals and corrections).
+ *   sample_status: device [batch] int32 or NULL, as in hdd_loglik.
+ * Needs the workspace of hdd_assemble + hdd_upsweep with the same batch; it overwrites
+ * the slots the right-hand-side sweep uses (not y_g, not the factors).
+ * Errors: HDD_EINVAL (both or neither of c and f_coarse, f_coarse with an even N,
+ * n_loads < 1, NULL or unaligned buffers). */
+hdd_status hdd_data_scratch_size(hdd_plan_t plan, int32_t batch, size_t* bytes);
+hdd_status hdd_solve_data(hdd_plan_t plan, int32_t batch, void* workspace, void* scratch, const double* c,
+                          const double* f_coarse, const double* g, int32_t n_loads, double* u,
+                          int32_t* sample_status, void* stream);
+
 /* Mean of u over every subdomain omega of the tree (Sec. 5, Eq. mean):
  * mean(omega) = sum_{t in omega} |t|/3 (u_1 + u_2 + u_3) / |omega|, computed at
  * the leaves from u and at each father from its sons as in Sec. 5.1,
@@ -294,6 +329,39 @@ hdd_status hdd_evaluate_static(hdd_plan_t plan, int32_t batch, const double* Z, 
  * On mixed plans both come from the FP32 factors.  Errors: HDD_ESTATE for other plans. */
 hdd_status hdd_mean_functionals(hdd_plan_t plan, int32_t batch, void* workspace, double* lambda_g, double* mu_f,
                                 void* stream);
+
+/* Uneven batches: several plans evaluated together, "Leaves to Root" as one launch
+ * per tree height and front class over the nodes of all of them.  The north-star
+ * workload mixes grids of 129^2 to 1025^2 with different KL bases and observation
+ * sets; run one plan at a time, the upper tree levels of each leave most of the GPU
+ * idle, while one launch per height over every plan fills it.  The paper has no
+ * counterpart (its algorithms treat one problem): the arithmetic per sample is the
+ * same as for the plan alone, so every result equals the plan's own.
+ *
+ * hdd_multi_create binds n_plans plans (same device, no fused subtrees), each with its
+ * batch size and its workspace (>= hdd_workspace_size(plan, batch) bytes, 256-byte
+ * aligned, caller-owned, used by later calls until hdd_multi_destroy).  It copies the
+ * plans' node tables and maps into one device table; the plans must outlive it.
+ * Errors: HDD_EINVAL, HDD_ENOMEM, HDD_ECUDA. */
+typedef struct hdd_multi_s* hdd_multi_t;
+hdd_status hdd_multi_create(const hdd_plan_t* plans, int32_t n_plans, const int32_t* batches,
+                            void* const* workspaces, hdd_multi_t* out);
+hdd_status hdd_multi_destroy(hdd_multi_t multi);
+/* "Leaves to Root" of every bound plan on its workspace (after hdd_assemble of each):
+ * the same factors and Schur complements as hdd_upsweep per plan. */
+hdd_status hdd_multi_upsweep(hdd_multi_t multi, void* stream);
+/* End to end on device buffers, arrays of n_plans pointers in binding order:
+ * hdd_assemble per plan, hdd_multi_upsweep, then hdd_point_solve and hdd_loglik per
+ * plan.  The per-plan phases run on streams that hdd_multi_create made (one per plan),
+ * forked from `stream` and joined back to it by events, so the call is ordered on
+ * `stream` like any other and the plans' small launches overlap on the device.  Z[q]: [batch_q x n_z_q]; y[q]: [n_obs_q] or [batch_q x n_obs_q] per
+ * y_per_sample[q]; loglik[q]: [batch_q]; u_obs[q]: [batch_q x n_obs_q] (required);
+ * sample_status: NULL or an array whose entries are NULL or [batch_q]. */
+hdd_status hdd_multi_evaluate(hdd_multi_t multi, const double* const* Z, const double* const* y,
+                              const int32_t* y_per_sample, double* const* loglik, double* const* u_obs,
+                              int32_t* const* sample_status, void* stream);
+/* Kernel launches of one hdd_multi_upsweep and of one hdd_multi_evaluate. */
+hdd_status hdd_multi_info(hdd_multi_t multi, int32_t* launches_upsweep, int32_t* launches_evaluate);
 
 /* Copy of the coefficient field of the last hdd_assemble on this workspace:
  * kappa: device [batch x n_t] FP64 (triangle order as above).  For inspection

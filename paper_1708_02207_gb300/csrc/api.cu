@@ -2,6 +2,7 @@
 // schedule of the HDD likelihood path.  No exceptions cross this boundary.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <array>
 #include <cstdlib>
 #include <cstring>
@@ -23,6 +24,7 @@ cudaError_t configure_fused_kernels();
 cudaError_t configure_group_kernels();
 cudaError_t configure_leaf_kernels();
 cudaError_t configure_func_kernels();
+cudaError_t configure_data_kernels();
 }  // namespace hdd
 
 namespace {
@@ -50,6 +52,44 @@ namespace hdd {
 hdd_status set_error(hdd_status status, const std::string& msg) {
   g_err = msg;
   return status;
+}
+
+// The sizes and algorithmic flops of one node list on a launch's arguments
+// (flops per sample of the list, times `scale`).
+void set_list(StepArgs& a, const ListInfo& li, double scale) {
+  a.nlist = li.n;
+  a.max_nf = li.max_nf;
+  a.max_m = li.max_m;
+  a.max_b = li.max_b;
+  a.max_rect = li.max_rect;
+  a.fl_chol = li.fl_chol * scale;
+  a.fl_trsm = li.fl_trsm * scale;
+  a.fl_syrk = li.fl_syrk * scale;
+  a.fl_rhs = li.fl_rhs * scale;
+}
+
+// One upsweep launch (or launch sequence, for the large fronts) over a node list of
+// one height and one class: 0-2 FP64 fronts of up to 32 rows / in shared memory /
+// in global memory, 3-5 the same in FP32, 6-7 condensed leaves (FP64, FP32).
+cudaError_t launch_step(int kind, StepArgs& a, cudaStream_t st) {
+  switch (kind) {
+    case 0: return launch_front_group<double>(a, kProfFrontWarp, st);
+    case 1: return launch_front_group<double>(a, kProfFrontSmall, st);
+    case 2: return launch_front_large<double>(a, st);
+    case 3: return launch_front_group<float>(a, kProfFrontWarp, st);
+    case 4: return launch_front_group<float>(a, kProfFrontSmall, st);
+    case 5: return launch_front_large<float>(a, st);
+    case 6: return launch_leaf_front<double>(a, st);
+    default: return launch_leaf_front<float>(a, st);
+  }
+}
+
+// Launches of one upsweep list of the given class (the large fronts take a sequence).
+int step_launches(int kind, const ListInfo& li) {
+  if (li.n == 0) return 0;
+  if (kind == 2) return li.max_m <= 32 ? 3 : 4;   // fill, POTRF+TRSM or POTRF, TRSM, SYRK
+  if (kind == 5) return (li.max_m <= 64 ? 3 : 4) + (li.max_b > 0 ? 1 : 0);   // + bordered row
+  return 1;
 }
 }  // namespace hdd
 
@@ -85,6 +125,7 @@ cudaError_t configure_device(int dev) {
   if (e == cudaSuccess) e = hdd::configure_group_kernels();
   if (e == cudaSuccess) e = hdd::configure_leaf_kernels();
   if (e == cudaSuccess) e = hdd::configure_func_kernels();
+  if (e == cudaSuccess) e = hdd::configure_data_kernels();
   if (e == cudaSuccess) g_configured[dev] = true;
   return e;
 }
@@ -140,6 +181,27 @@ hdd::Arenas arenas(const hdd::Plan& p, const hdd::Layout& L, void* ws) {
   A.inv_stride = p.inv_stride;
   return A;
 }
+
+}  // namespace
+
+namespace hdd {
+PlanDev plan_part(const Plan& p, int batch, void* ws) {
+  const Layout L = layout(p, batch);
+  char* w = static_cast<char*>(ws);
+  PlanDev d{};
+  d.arenas = arenas(p, L, ws);
+  d.kappa = reinterpret_cast<const double*>(w + L.kappa);
+  d.kappa32 = L.kappa32 ? reinterpret_cast<const float*>(w + L.kappa32) : nullptr;
+  d.kap_stride = p.n_t;
+  d.status = reinterpret_cast<int32_t*>(w + L.status);
+  d.rhs = Rhs{nullptr, 0, p.h * p.h * p.f};
+  d.N = p.N;
+  d.batch = batch;
+  return d;
+}
+}  // namespace hdd
+
+namespace {
 
 hdd_status check_call(hdd_plan_t plan, int32_t batch, void* ws) {
   if (!plan) return fail_inval("plan is NULL");
@@ -216,26 +278,8 @@ cudaError_t run_upsweep(const hdd::Plan& p, int batch, void* ws, const hdd::Rhs&
       const hdd::ListInfo& li = p.lists[p.step_lists[h][kind]];
       if (li.n == 0) continue;
       a.list = p.d_lists + li.off;
-      a.nlist = li.n;
-      a.max_nf = li.max_nf;
-      a.max_m = li.max_m;
-      a.max_b = li.max_b;
-      a.max_rect = li.max_rect;
-      a.fl_chol = li.fl_chol * batch;
-      a.fl_trsm = li.fl_trsm * batch;
-      a.fl_syrk = li.fl_syrk * batch;
-      a.fl_rhs = li.fl_rhs * batch;
-      cudaError_t e;
-      switch (kind) {
-        case 0: e = hdd::launch_front_group<double>(a, hdd::kProfFrontWarp, st); break;
-        case 1: e = hdd::launch_front_group<double>(a, hdd::kProfFrontSmall, st); break;
-        case 2: e = hdd::launch_front_large<double>(a, st); break;
-        case 3: e = hdd::launch_front_group<float>(a, hdd::kProfFrontWarp, st); break;
-        case 4: e = hdd::launch_front_group<float>(a, hdd::kProfFrontSmall, st); break;
-        case 5: e = hdd::launch_front_large<float>(a, st); break;
-        case 6: e = hdd::launch_leaf_front<double>(a, st); break;
-        default: e = hdd::launch_leaf_front<float>(a, st); break;
-      }
+      hdd::set_list(a, li, batch);
+      cudaError_t e = hdd::launch_step(kind, a, st);
       if (e != cudaSuccess) return e;
     }
   }
@@ -726,6 +770,91 @@ hdd_status hdd_solve_loads(hdd_plan_t plan, int32_t batch, void* workspace, cons
   return e == cudaSuccess ? HDD_OK : fail_cuda(e, "hdd_solve_loads");
 }
 
+hdd_status hdd_data_scratch_size(hdd_plan_t plan, int32_t batch, size_t* bytes) {
+  if (!plan || !bytes) return fail_inval("NULL argument");
+  if (batch < 1 || batch > 65535) return fail_inval("batch must be in 1..65535");
+  const size_t NN = (size_t)plan->p.N * plan->p.N;
+  *bytes = (2 * (size_t)hdd::kData * batch * NN + 4 * (size_t)batch) * 8;
+  return HDD_OK;
+}
+
+hdd_status hdd_solve_data(hdd_plan_t plan, int32_t batch, void* workspace, void* scratch, const double* c,
+                          const double* f_coarse, const double* g, int32_t n_loads, double* u,
+                          int32_t* sample_status, void* stream) {
+  hdd_status s = check_call(plan, batch, workspace);
+  if (s != HDD_OK) return s;
+  const hdd::Plan& p = plan->p;
+  if (!u || !scratch) return fail_inval("u or scratch is NULL");
+  if (reinterpret_cast<uintptr_t>(scratch) % 256 != 0) return fail_inval("scratch must be 256-byte aligned");
+  if ((c == nullptr) == (f_coarse == nullptr)) return fail_inval("give exactly one of c and f_coarse");
+  if (f_coarse && p.N % 2 == 0) return fail_inval("a coarse-grid load needs an odd N");
+  if (n_loads < 1) return fail_inval("n_loads must be >= 1");
+  DeviceScope ds(p.device);
+  if (ds.err != cudaSuccess) return fail_cuda(ds.err, "cudaSetDevice");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const hdd::Layout L = hdd::layout(p, batch);
+  char* w = static_cast<char*>(workspace);
+  const size_t NN = (size_t)p.N * p.N;
+  hdd::DataArgs D{};
+  D.nodes = p.d_nodes;
+  D.maps = p.d_maps;
+  D.A = arenas(p, L, workspace);
+  D.N = p.N;
+  D.batch = batch;
+  D.n_loads = n_loads;
+  D.h2 = p.h * p.h;
+  D.u = u;
+  D.d = static_cast<double*>(scratch);
+  D.r = D.d + (size_t)hdd::kData * batch * NN;
+  D.conv = D.r + (size_t)hdd::kData * batch * NN;
+  D.status = reinterpret_cast<int32_t*>(w + L.status);
+  const double* kappa = reinterpret_cast<const double*>(w + L.kappa);
+  const int K = p.precision == HDD_MIXED_FP32 ? p.ir_max_iter : 0;
+  hdd::Profiler* prof = profiler(plan);
+  cudaError_t e = cudaMemsetAsync(D.conv, 0, (size_t)batch * 4 * 8, st);
+  for (int k0 = 0; k0 < n_loads && e == cudaSuccess; k0 += hdd::kData) {
+    D.nk = std::min(hdd::kData, n_loads - k0);
+    e = hdd::launch_data_init(D, g, k0, st);
+    for (int it = 0; it <= K && e == cudaSuccess; ++it) {
+      {
+        ProfScope ps(prof, hdd::kProfResidual, 0.0, st);
+        e = hdd::launch_data_residual(D, kappa, p.n_t, c, f_coarse, k0, st);
+      }
+      for (int h = 0; h <= p.height && e == cudaSuccess; ++h)   // leaves to root, every node
+        for (int k = 0; k < 4 && e == cudaSuccess; ++k) {
+          const hdd::ListInfo& li = p.lists[p.fwd_lists[h][k]];
+          if (li.n == 0) continue;
+          ProfScope ps(prof, hdd::kProfForward, 0.0, st);
+          const int32_t* l = p.d_lists + li.off;
+          e = k == 0 ? hdd::launch_data_sweep<double>(D, l, li.n, li.max_nf, false, st)
+            : k == 1 ? hdd::launch_data_sweep<float>(D, l, li.n, li.max_nf, false, st)
+            : k == 2 ? hdd::launch_data_leaf<double>(D, l, li.n, false, st)
+                     : hdd::launch_data_leaf<float>(D, l, li.n, false, st);
+        }
+      for (int d = 0; d <= p.depth && e == cudaSuccess; ++d)    // root to leaves, every node
+        for (int k = 0; k < 3 && e == cudaSuccess; ++k) {
+          const hdd::ListInfo& li = p.lists[p.down_all_lists[d][k]];
+          if (li.n == 0) continue;
+          ProfScope ps(prof, hdd::kProfDescent, 0.0, st);
+          const int32_t* l = p.d_lists + li.off;
+          if (k == 0)
+            e = p.nodes[p.list_data[li.off]].fp64 ? hdd::launch_data_sweep<double>(D, l, li.n, li.max_nf, true, st)
+                                                  : hdd::launch_data_sweep<float>(D, l, li.n, li.max_nf, true, st);
+          else
+            e = k == 1 ? hdd::launch_data_leaf<double>(D, l, li.n, true, st)
+                       : hdd::launch_data_leaf<float>(D, l, li.n, true, st);
+        }
+      if (e == cudaSuccess) {
+        ProfScope ps(prof, hdd::kProfMisc, 0.0, st);
+        e = hdd::launch_data_update(D, k0, p.ir_tol, it == K, it > 0, st);
+      }
+    }
+  }
+  if (e == cudaSuccess && sample_status)
+    e = cudaMemcpyAsync(sample_status, D.status, (size_t)batch * 4, cudaMemcpyDeviceToDevice, st);
+  return e == cudaSuccess ? HDD_OK : fail_cuda(e, "hdd_solve_data");
+}
+
 hdd_status hdd_subdomain_means(hdd_plan_t plan, int32_t batch, const double* u, int64_t u_stride, double* means,
                                void* stream) {
   if (!plan) return fail_inval("plan is NULL");
@@ -871,14 +1000,7 @@ hdd_status hdd_plan_info(hdd_plan_t plan, hdd_plan_info_t* info) {
   for (const hdd::Node& nd : p.nodes) info->n_condensed_leaves += nd.linv;
   int up = 0, down = 0;
   for (int h = 0; h <= p.height; ++h)
-    for (int kind = 0; kind < 8; ++kind) {
-      const hdd::ListInfo& li = p.lists[p.step_lists[h][kind]];
-      if (!li.n) continue;
-      if (kind == 2) up += li.max_m <= 32 ? 3 : 4;        // fill, POTRF+TRSM or POTRF, TRSM, SYRK
-      else if (kind == 5)   // fill, POTRF+TRSM or POTRF, TRSM, tensor-core SYRK (b > 0), bordered row
-        up += (li.max_m <= 64 ? 3 : 4) + (li.max_b > 0 ? 1 : 0);
-      else up += 1;
-    }
+    for (int kind = 0; kind < 8; ++kind) up += hdd::step_launches(kind, p.lists[p.step_lists[h][kind]]);
   for (const auto& fu : p.fusion) up += fu.height > 0;
   int down_all = 0, fwd = 0;
   for (int d = 0; d <= p.depth; ++d)

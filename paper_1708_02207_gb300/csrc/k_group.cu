@@ -259,7 +259,7 @@ __global__ void __launch_bounds__(256) k_front_group(StepArgs a, int ld, int fr_
 
 // Warps per front: enough that a group's rows and tiles keep its lanes busy,
 // few enough that several fronts share a CTA.
-static int group_warps(int max_nf, bool fp64) {
+int group_warps(int max_nf, bool fp64) {
   if (max_nf <= 48) return 1;
   if (max_nf <= 64) return 2;
   if (!fp64 || max_nf <= 128) return 4;

@@ -31,7 +31,11 @@ constexpr int kTile = kTcTile;        // M = N of the MMA and of the output tile
 constexpr int kChunk = kTcChunk;      // contraction columns staged per buffer
 constexpr int kTileBytes = (int)kTcBlockBytes;          // one operand part (4 KiB)
 constexpr int kStageBytes = 4 * kTileBytes;             // A hi/lo, B hi/lo (16 KiB)
-constexpr int kStages = 4;                              // pipeline depth: 64 KiB, 3 CTAs per SM
+// Pipeline depth: 2 stages (32 KiB).  The contraction is short (K = m = 31..511
+// columns), so the epilogue's gather of the sons' entries, a chain of dependent
+// loads, bounds the kernel: it wants CTAs in flight more than deep prefetch.  Four
+// CTAs of 128 tensor-memory columns fill an SM's 512 columns.
+constexpr int kStages = 2;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -69,7 +73,7 @@ __device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t phase, uint32_
 
 }  // namespace
 
-__global__ void __launch_bounds__(128, 3) k_syrk_tc(StepArgs a) {
+__global__ void __launch_bounds__(128, 4) k_syrk_tc(StepArgs a) {
   const int node = a.list[blockIdx.y];
   const int s = blockIdx.z;
   bind_plan(a, node);
@@ -122,7 +126,7 @@ __global__ void __launch_bounds__(128, 3) k_syrk_tc(StepArgs a) {
 
   // Epilogue operands.  The values subtracted from are loaded chunk by chunk
   // (32 columns), the first chunk before the MMAs so that its loads overlap
-  // them, each later one while the previous chunk is stored.
+  // them.
   float* S = a.arenas.s32 + (int64_t)s * a.arenas.s32_stride + nd.s_off;
   const int i = TI * kTile + warp * 32 + lane;   // accumulator lane = tile row
   // fathers: the boundary block of the front is the sum of the sons' Schur
@@ -280,18 +284,12 @@ __global__ void __launch_bounds__(128, 3) k_syrk_tc(StepArgs a) {
             "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
             "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
           : "r"(taddr));
+      if (c0 > 0) load_chunk(c0, sv);
       asm volatile("tcgen05.wait::ld.sync.aligned;");
-      const bool more = c0 + 32 < kTile && !(TI == TJ && c0 + 32 > warp * 32 + 31);
-      float nx[32];
-      if (more) load_chunk(c0 + 32, nx);
 #pragma unroll
       for (int q = 0; q < 32; ++q) {
         const int j = TJ * kTile + c0 + q;
         if (i < nbt && j < nbt && i >= j) S[(int64_t)j * nb + i] = sv[q] - __uint_as_float(r[q]);
-      }
-      if (more) {
-#pragma unroll
-        for (int q = 0; q < 32; ++q) sv[q] = nx[q];
       }
     }
   }

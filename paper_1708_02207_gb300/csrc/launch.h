@@ -131,6 +131,41 @@ template <typename T> cudaError_t launch_func_warp(const FuncArgs& f, int max_nf
 cudaError_t launch_mean_obs(const FuncArgs& f, const int32_t* obs_nodes, int n_obs, const double* x,
                             int64_t x_stride, const double* base, double* u_obs, cudaStream_t st);
 
+// warps per front of the grouped front kernel for a list's largest front (k_group.cu)
+int group_warps(int max_nf, bool fp64);
+// one upsweep list (api.cu): its sizes on the arguments, its launch(es), their count
+void set_list(StepArgs& a, const ListInfo& li, double scale);
+cudaError_t launch_step(int kind, StepArgs& a, cudaStream_t st);
+int step_launches(int kind, const ListInfo& li);
+// a plan's workspace as one part of a launch over several plans (api.cu)
+PlanDev plan_part(const Plan& p, int batch, void* ws);
+
+// many loads and Dirichlet data through the stored factors (k_data.cu): groups of
+// kData right-hand sides share each factor read
+constexpr int kData = 4;
+struct DataArgs {
+  const NodeDev* nodes;
+  const int32_t* maps;
+  Arenas A;
+  int N, batch, n_loads;
+  int nk;                 // loads of the current group (<= kData)
+  double h2;              // h^2: vertex-quadrature weight of a nodal load on this mesh
+  double* u;              // [batch x n_loads x N^2] the solutions (Dirichlet data at the boundary)
+  double* d;              // [kData x batch x N^2] y_g during the sweep, then the correction
+  double* r;              // [kData x batch x N^2] residuals of the group
+  double* conv;           // [batch x 4] refinement bookkeeping
+  int32_t* status;        // [batch] per-sample status words
+};
+cudaError_t launch_data_init(const DataArgs& D, const double* g, int k0, cudaStream_t st);
+cudaError_t launch_data_residual(const DataArgs& D, const double* kappa, int64_t kap_stride, const double* c,
+                                 const double* fH, int k0, cudaStream_t st);
+template <typename T>
+cudaError_t launch_data_sweep(const DataArgs& D, const int32_t* list, int nlist, int max_nf, bool descent,
+                              cudaStream_t st);
+template <typename T>
+cudaError_t launch_data_leaf(const DataArgs& D, const int32_t* list, int nlist, bool descent, cudaStream_t st);
+cudaError_t launch_data_update(const DataArgs& D, int k0, double tol, bool last, bool test, cudaStream_t st);
+
 // assembly: kappa = exp(Phi Z) (Sec. 3.1; kappa = e^q)
 cudaError_t launch_kappa(const double* phi, const double* Z, int n_t, int n_z, int batch, double* kappa,
                          float* kappa32, int64_t kap_stride, cudaStream_t st);

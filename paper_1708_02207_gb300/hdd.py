@@ -24,7 +24,8 @@ EXPORTED = [
     "hdd_point_solve", "hdd_loglik", "hdd_evaluate_host", "hdd_plan_info", "hdd_node_info",
     "hdd_node_indices", "hdd_status_string", "hdd_last_error", "hdd_evaluate_static",
     "hdd_profile_begin", "hdd_profile_end", "hdd_kappa", "hdd_solve_loads", "hdd_subdomain_means",
-    "hdd_set_wait_bound", "hdd_mean_functionals",
+    "hdd_set_wait_bound", "hdd_mean_functionals", "hdd_multi_create", "hdd_multi_destroy", "hdd_multi_upsweep",
+    "hdd_multi_evaluate", "hdd_multi_info", "hdd_data_scratch_size", "hdd_solve_data",
 ]
 STATIC_WORKSPACE_BYTES = 32 << 20
 
@@ -92,6 +93,14 @@ def load_library() -> C.CDLL:
     lib.hdd_subdomain_means.argtypes = [vp, i32, vp, C.c_int64, vp, vp]
     lib.hdd_set_wait_bound.argtypes = [vp, C.c_uint32, i32, i32]
     lib.hdd_mean_functionals.argtypes = [vp, i32, vp, vp, vp, vp]
+    lib.hdd_multi_create.argtypes = [C.POINTER(vp), i32, pi32, C.POINTER(vp), C.POINTER(vp)]
+    lib.hdd_multi_destroy.argtypes = [vp]
+    lib.hdd_multi_upsweep.argtypes = [vp, vp]
+    lib.hdd_multi_evaluate.argtypes = [vp, C.POINTER(vp), C.POINTER(vp), pi32, C.POINTER(vp), C.POINTER(vp),
+                                       C.POINTER(vp), vp]
+    lib.hdd_multi_info.argtypes = [vp, pi32, pi32]
+    lib.hdd_data_scratch_size.argtypes = [vp, i32, C.POINTER(C.c_size_t)]
+    lib.hdd_solve_data.argtypes = [vp, i32, vp, vp, vp, vp, vp, i32, vp, vp, vp]
     lib.hdd_profile_begin.argtypes = [vp]
     lib.hdd_profile_end.argtypes = [vp, C.POINTER(KernelStat), i32, C.POINTER(i32)]
     lib.hdd_plan_info.argtypes = [vp, C.POINTER(PlanInfo)]
@@ -286,6 +295,41 @@ class Plan:
         _check(self.lib.hdd_solve_loads(self._h, batch, _ptr(ws), _ptr(c), int(c.shape[1]), _ptr(u), _ptr(status),
                                         _stream_ptr(stream)), "hdd_solve_loads")
 
+    def solve_data(self, batch: int, ws, u, c=None, f_coarse=None, g=None, status=None, scratch=None, stream=None):
+        """hdd_solve_data (after assemble + upsweep on ws): exactly one of c [batch, n_loads, N*N]
+        and f_coarse [batch, n_loads, NH*NH] (NH = (N+1)/2), optional g [batch, n_loads, N*N];
+        u [batch, n_loads, N*N] out.  scratch: a uint8 device tensor of at least
+        data_scratch_size(batch) bytes (allocated here when None)."""
+        import torch
+        if u.dim() != 3:
+            raise ValueError("u must be [batch, n_loads, N*N]")
+        nl = int(u.shape[1])
+        NN = self.N * self.N
+        _need(u, "u", "f64", (batch, nl, NN), self._dev())
+        if (c is None) == (f_coarse is None):
+            raise ValueError("give exactly one of c and f_coarse")
+        if c is not None:
+            _need(c, "c", "f64", (batch, nl, NN), self._dev())
+        else:
+            NH = (self.N + 1) // 2
+            _need(f_coarse, "f_coarse", "f64", (batch, nl, NH * NH), self._dev())
+        if g is not None:
+            _need(g, "g", "f64", (batch, nl, NN), self._dev())
+        if status is not None:
+            _need(status, "status", "i32", (batch,), self._dev())
+        need = self.data_scratch_size(batch)
+        if scratch is None:
+            scratch = torch.empty(need, dtype=torch.uint8, device=self._dev())
+        elif scratch.numel() < need or scratch.device != self._dev():
+            raise ValueError(f"scratch must hold {need} bytes on {self._dev()}")
+        _check(self.lib.hdd_solve_data(self._h, batch, _ptr(ws), _ptr(scratch), _ptr(c), _ptr(f_coarse), _ptr(g), nl,
+                                       _ptr(u), _ptr(status), _stream_ptr(stream)), "hdd_solve_data")
+
+    def data_scratch_size(self, batch: int) -> int:
+        n = C.c_size_t()
+        _check(self.lib.hdd_data_scratch_size(self._h, batch, C.byref(n)), "hdd_data_scratch_size")
+        return int(n.value)
+
     def subdomain_means(self, u, means, stream=None):
         """hdd_subdomain_means: u device [batch, N*N] (any row stride), means device [batch, n_nodes]."""
         import torch
@@ -378,3 +422,69 @@ class Plan:
                                           st.ctypes.data_as(C.POINTER(C.c_int32)), _stream_ptr(stream)),
                "hdd_evaluate_host")
         return ll, u_obs, st
+
+
+class MultiPlan:
+    """Several plans evaluated together (hdd_multi_*): an uneven batch whose "Leaves to Root"
+    runs as one launch per tree height and front class over every plan.  Each plan keeps
+    its own workspace (allocated here for its batch size)."""
+
+    def __init__(self, plans: list, batches: list):
+        import torch
+        if len(plans) != len(batches) or not plans:
+            raise ValueError("plans and batches must be non-empty lists of the same length")
+        self.lib = load_library()
+        self.plans = list(plans)
+        self.batches = [int(b) for b in batches]
+        self.ws = [p.workspace(b) for p, b in zip(self.plans, self.batches)]
+        n = len(self.plans)
+        hs = (C.c_void_p * n)(*[p._h.value for p in self.plans])
+        bs = (C.c_int32 * n)(*self.batches)
+        ws = (C.c_void_p * n)(*[w.data_ptr() for w in self.ws])
+        h = C.c_void_p()
+        _check(self.lib.hdd_multi_create(hs, n, bs, ws, C.byref(h)), "hdd_multi_create")
+        self._h = h
+        self.outputs = []
+        for p, b in zip(self.plans, self.batches):
+            dev = p._dev()
+            self.outputs.append((torch.empty(b, dtype=torch.float64, device=dev),
+                                 torch.empty(b, p.n_obs, dtype=torch.float64, device=dev),
+                                 torch.empty(b, dtype=torch.int32, device=dev)))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self.lib.hdd_multi_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def info(self) -> dict:
+        up, ev = C.c_int32(), C.c_int32()
+        _check(self.lib.hdd_multi_info(self._h, C.byref(up), C.byref(ev)), "hdd_multi_info")
+        return {"launches_upsweep": up.value, "launches_evaluate": ev.value}
+
+    def upsweep(self, stream=None):
+        _check(self.lib.hdd_multi_upsweep(self._h, _stream_ptr(stream)), "hdd_multi_upsweep")
+
+    def evaluate(self, Zs: list, ys: list, stream=None):
+        """Device tensors Z_q [batch_q, n_z_q], y_q [n_obs_q] or [batch_q, n_obs_q] in; per plan
+        (loglik [batch_q], u_obs [batch_q, n_obs_q], status [batch_q]) out (views of buffers
+        that the next call overwrites)."""
+        n = len(self.plans)
+        if len(Zs) != n or len(ys) != n:
+            raise ValueError("one Z and one y per plan")
+        for p, b, Z, y in zip(self.plans, self.batches, Zs, ys):
+            _need(Z, "Z", "f64", (b, p.n_z), p._dev())
+            p._check_y(y, b)
+        P = C.c_void_p * n
+        ll = P(*[o[0].data_ptr() for o in self.outputs])
+        uo = P(*[o[1].data_ptr() for o in self.outputs])
+        st = P(*[o[2].data_ptr() for o in self.outputs])
+        yps = (C.c_int32 * n)(*[1 if y.dim() == 2 else 0 for y in ys])
+        _check(self.lib.hdd_multi_evaluate(self._h, P(*[Z.data_ptr() for Z in Zs]), P(*[y.data_ptr() for y in ys]),
+                                           yps, ll, uo, st, _stream_ptr(stream)), "hdd_multi_evaluate")
+        return self.outputs
