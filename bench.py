@@ -366,9 +366,15 @@ def run_serving(args, hdd, torch, dev, local):
             r = serving.run_offered_load(server, chains, f * sat["evals_per_s"], n_req, rng)
             pts.append({"load": f, "offered_per_s": f * sat["evals_per_s"], "evals_per_s": r["evals_per_s"],
                         "p50_ms": 1e3 * r["p50_s"], "p99_ms": 1e3 * r["p99_s"], "requests": r["requests"]})
+        fails = {}
+        for r in server.done:
+            if r.status != 0 or r.rejected:
+                key = f"{r.plan}:" + ("rejected" if r.rejected else str(-(r.status & 0xFF)))
+                fails[key] = fails.get(key, 0) + 1
         out["points"][prec_name] = {"budget_bytes": budget, "peak_admitted_bytes": server.peak_bytes,
                                     "batches": server.batches, "requests_per_point": n_req, "sweep": pts,
-                                    "failed": sum(1 for r in server.done if r.status != 0 or r.rejected)}
+                                    "requests": len(server.done),
+                                    "failed": sum(fails.values()), "failed_by_grid_and_status": fails}
         del server, backend, plans
         torch.cuda.empty_cache()
     return out

@@ -137,131 +137,6 @@ template <typename T> struct SmemCap;
 template <> struct SmemCap<double> { static constexpr int rows = 800; };
 template <> struct SmemCap<float> { static constexpr int rows = 1600; };
 
-// POTRF of K_gg (m x m, in F with ld nf): one CTA per (node, sample), blocked
-// right-looking with 32-column panels staged in shared memory; the trailing
-// update uses 4 x 4 register tiles over the lower triangle.
-template <typename T>
-__global__ void __launch_bounds__(256) k_potrf(StepArgs a) {
-  const int node = a.list[blockIdx.x];
-  const int s = blockIdx.y;
-  bind_plan(a, node);
-  if (s >= a.batch) return;
-  const NodeDev nd = a.nodes[node];
-  const int nf = nd.nf, m = nd.m;
-  T* A = node_F<T>(a.arenas, nd, s);
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* piv = reinterpret_cast<T*>(smem_raw);                 // [kPanel]
-  T* W = piv + kPanel;                                      // [32][33] inverse of a diagonal block
-  T* Ps = W + 32 * 33;                                      // panel, ld = rows rounded up to 4 (16 B aligned)
-  const bool in_smem = m <= SmemCap<T>::rows;
-  for (int k0 = 0; k0 < m; k0 += kPanel) {
-    const int kb = min(kPanel, m - k0), rows = m - k0;
-    T* P = in_smem ? Ps : A + (int64_t)k0 * nf + k0;
-    const int ld = in_smem ? ((rows + 3) & ~3) : nf;
-    __syncthreads();
-    if (in_smem)
-      for (int idx = threadIdx.x; idx < kb * rows; idx += blockDim.x) {
-        const int l = idx / rows, i = idx - l * rows;
-        Ps[l * ld + i] = A[(int64_t)(k0 + l) * nf + k0 + i];
-      }
-    // factor the panel (rows k0..m-1, columns k0..k0+kb-1): per column, scale it,
-    // then one warp per remaining panel column applies the rank-1 update
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarp = blockDim.x >> 5;
-    for (int kk = 0; kk < kb; ++kk) {
-      __syncthreads();
-      T p = P[(int64_t)kk * ld + kk];
-      if (!(p > (T)0) || !isfinite(p)) {
-        if (threadIdx.x == 0) flag_status(a.status, s, -HDD_ENOTSPD, node);
-        p = (T)1;
-      }
-      const T d = sqrt(p), inv = (T)1 / d;
-      T* colk = P + (int64_t)kk * ld;
-      for (int i = kk + 1 + threadIdx.x; i < rows; i += blockDim.x) colk[i] *= inv;
-      __syncthreads();
-      if (threadIdx.x == 0) colk[kk] = d;
-      for (int j = kk + 1 + warp; j < kb; j += nwarp) {
-        const T lj = colk[j];
-        T* colj = P + (int64_t)j * ld;
-        for (int i = j + lane; i < rows; i += 32) colj[i] -= colk[i] * lj;
-      }
-    }
-    __syncthreads();
-    // inverse of the diagonal block L_kk (lower), one column per lane of warp 0,
-    // by forward substitution on the unit vectors; TRSM applies it as a product
-    if (threadIdx.x < 32) {
-      T* Wc = W + threadIdx.x * 33;          // column c of inv(L_kk), rows c..kb-1
-      const int c = threadIdx.x;
-      if (c < kb) {
-        for (int r = 0; r < kb; ++r) {
-          if (r < c) { Wc[r] = (T)0; continue; }
-          T acc = (r == c) ? (T)1 : (T)0;
-          for (int l = c; l < r; ++l) acc -= P[(int64_t)l * ld + r] * Wc[l];
-          Wc[r] = acc / P[(int64_t)r * ld + r];
-        }
-        T* G = reinterpret_cast<T*>(a.arenas.inv + (int64_t)s * a.arenas.inv_stride + nd.inv_off) + (k0 / 32) * 1024;
-        for (int r = 0; r < 32; ++r) G[c * 32 + r] = (r < kb) ? Wc[r] : (T)0;
-      } else {
-        T* G = reinterpret_cast<T*>(a.arenas.inv + (int64_t)s * a.arenas.inv_stride + nd.inv_off) + (k0 / 32) * 1024;
-        for (int r = 0; r < 32; ++r) G[c * 32 + r] = (r == c) ? (T)1 : (T)0;
-      }
-    }
-    if (in_smem)
-      for (int idx = threadIdx.x; idx < kb * rows; idx += blockDim.x) {
-        const int l = idx / rows, i = idx - l * rows;
-        if (i >= l) A[(int64_t)(k0 + l) * nf + k0 + i] = Ps[l * ld + i];
-      }
-    // trailing update of K_gg[k0+kb:m, k0+kb:m] (lower): 4 x 4 register tiles,
-    // one warp per column of tiles, lanes down the rows (coalesced in global memory)
-    const int n = rows - kb;
-    if (n <= 0) continue;
-    const int nt = (n + 3) >> 2;
-    for (int tj = warp; tj < nt; tj += nwarp) {
-      const int j0 = kb + 4 * tj;
-      for (int ti = tj + lane; ti < nt; ti += 32) {
-        const int i0 = kb + 4 * ti;
-        T acc[4][4];
-#pragma unroll
-        for (int q = 0; q < 4; ++q)
-#pragma unroll
-          for (int w = 0; w < 4; ++w) acc[q][w] = (T)0;
-        for (int l = 0; l < kb; ++l) {
-          T x[4], y[4];
-          if (in_smem) {   // kb = 32 here (a trailing block exists), so i0, j0 and ld are multiples of 4;
-                           // the padding rows beyond `rows` only reach products that are not stored
-            load4(P + l * ld + i0, x);
-            load4(P + l * ld + j0, y);
-          } else {
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-              x[q] = (i0 + q < rows) ? P[(int64_t)l * ld + i0 + q] : (T)0;
-              y[q] = (j0 + q < rows) ? P[(int64_t)l * ld + j0 + q] : (T)0;
-            }
-          }
-#pragma unroll
-          for (int q = 0; q < 4; ++q)
-#pragma unroll
-            for (int w = 0; w < 4; ++w) acc[q][w] += x[q] * y[w];
-        }
-        T av[4][4];   // loads first (in flight together), then the stores
-#pragma unroll
-        for (int w = 0; w < 4; ++w)
-#pragma unroll
-          for (int q = 0; q < 4; ++q) {
-            const int j = j0 + w, i = i0 + q;
-            av[q][w] = (j < rows && i < rows && i >= j) ? A[(int64_t)(k0 + j) * nf + k0 + i] : (T)0;
-          }
-#pragma unroll
-        for (int w = 0; w < 4; ++w)
-#pragma unroll
-          for (int q = 0; q < 4; ++q) {
-            const int j = j0 + w, i = i0 + q;
-            if (j < rows && i < rows && i >= j) A[(int64_t)(k0 + j) * nf + k0 + i] = av[q][w] - acc[q][w];
-          }
-      }
-    }
-  }
-}
-
 // Staging for the tensor-core SYRK (k_syrk_tc): rows [row0, row0 + nr) of X
 // (= F[m:nf, 0:m], relative row numbers; the bordered right-hand-side row is
 // excluded, k_syrk_rhs handles it) split into TF32 hi and lo parts and written in
@@ -384,6 +259,125 @@ __device__ __forceinline__ void apply_inverse(T (&x)[NX], const T* W) {
     }
     x[O + c] = acc;
   }
+}
+
+// POTRF of K_gg (m x m, in F with ld nf): one CTA per (node, sample), blocked
+// right-looking with 32-column panels staged in shared memory.  Per panel, warp 0
+// factors the 32 x 32 diagonal block in registers and inverts it
+// (warp_chol_inverse: the pivot column by shuffles, no CTA barrier per column);
+// the panel rows below it become L21 = A21 L11^-T as products with that inverse,
+// one thread per row; the trailing update uses 4 x 4 register tiles over the
+// lower triangle.  The inverse also goes to the arena of inverted diagonal blocks,
+// which the TRSM applies as products.
+template <typename T>
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) k_potrf(StepArgs a) {   // FP64 panels fill the shared memory
+  const int node = a.list[blockIdx.x];
+  const int s = blockIdx.y;
+  bind_plan(a, node);
+  if (s >= a.batch) return;
+  const NodeDev nd = a.nodes[node];
+  const int nf = nd.nf, m = nd.m;
+  T* A = node_F<T>(a.arenas, nd, s);
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* Ls = reinterpret_cast<T*>(smem_raw);   // [32][kWs] scratch of warp_chol_inverse
+  T* W = Ls + 32 * kWs;                     // [32][kWs] inverse of the diagonal block, W[r * kWs + c]
+  T* dinv = W + 32 * kWs;                   // [32]
+  T* Ps = dinv + 32;                        // panel, ld = rows rounded up to 4 (16 B aligned)
+  const bool in_smem = m <= SmemCap<T>::rows;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarp = blockDim.x >> 5;
+  bool bad = false;
+  for (int k0 = 0; k0 < m; k0 += kPanel) {
+    const int kb = min(kPanel, m - k0), rows = m - k0;
+    T* P = in_smem ? Ps : A + (int64_t)k0 * nf + k0;
+    const int ld = in_smem ? ((rows + 3) & ~3) : nf;
+    __syncthreads();
+    if (in_smem)
+      for (int idx = threadIdx.x; idx < kb * rows; idx += blockDim.x) {
+        const int l = idx / rows, i = idx - l * rows;
+        Ps[l * ld + i] = A[(int64_t)(k0 + l) * nf + k0 + i];
+      }
+    __syncthreads();
+    if (warp == 0) {   // the diagonal block, lane r holding row r
+      T row[32];
+#pragma unroll
+      for (int c = 0; c < 32; ++c) row[c] = (c < kb && lane < kb && c <= lane) ? P[(int64_t)c * ld + lane] : (T)0;
+      warp_chol_inverse<T>(row, kb, Ls, W, dinv, bad);
+#pragma unroll
+      for (int c = 0; c < 32; ++c)
+        if (c < kb && lane < kb && c <= lane) P[(int64_t)c * ld + lane] = row[c];
+      // column c of the inverse at G[c * 32 .. c * 32 + 31] (identity beyond the block)
+      T* G = reinterpret_cast<T*>(a.arenas.inv + (int64_t)s * a.arenas.inv_stride + nd.inv_off) + (k0 / 32) * 1024;
+#pragma unroll 4
+      for (int r = 0; r < 32; ++r)
+        G[lane * 32 + r] = (lane < kb) ? ((r < kb) ? W[r * kWs + lane] : (T)0) : ((r == lane) ? (T)1 : (T)0);
+    }
+    __syncthreads();
+    // rows below the diagonal block (present only for full panels, kb = 32): x <- x W^T
+    for (int i = kb + threadIdx.x; i < rows; i += blockDim.x) {
+      T x[32];
+#pragma unroll
+      for (int l = 0; l < 32; ++l) x[l] = P[(int64_t)l * ld + i];
+      apply_inverse<T, 0, 32>(x, W);
+#pragma unroll
+      for (int c = 0; c < 32; ++c) P[(int64_t)c * ld + i] = x[c];
+    }
+    __syncthreads();
+    if (in_smem)
+      for (int idx = threadIdx.x; idx < kb * rows; idx += blockDim.x) {
+        const int l = idx / rows, i = idx - l * rows;
+        if (i >= l) A[(int64_t)(k0 + l) * nf + k0 + i] = Ps[l * ld + i];
+      }
+    // trailing update of K_gg[k0+kb:m, k0+kb:m] (lower): 4 x 4 register tiles,
+    // one warp per column of tiles, lanes down the rows (coalesced in global memory)
+    const int n = rows - kb;
+    if (n <= 0) continue;
+    const int nt = (n + 3) >> 2;
+    for (int tj = warp; tj < nt; tj += nwarp) {
+      const int j0 = kb + 4 * tj;
+      for (int ti = tj + lane; ti < nt; ti += 32) {
+        const int i0 = kb + 4 * ti;
+        T acc[4][4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+#pragma unroll
+          for (int w = 0; w < 4; ++w) acc[q][w] = (T)0;
+        for (int l = 0; l < kb; ++l) {
+          T x[4], y[4];
+          if (in_smem) {   // kb = 32 here (a trailing block exists), so i0, j0 and ld are multiples of 4;
+                           // the padding rows beyond `rows` only reach products that are not stored
+            load4(P + l * ld + i0, x);
+            load4(P + l * ld + j0, y);
+          } else {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+              x[q] = (i0 + q < rows) ? P[(int64_t)l * ld + i0 + q] : (T)0;
+              y[q] = (j0 + q < rows) ? P[(int64_t)l * ld + j0 + q] : (T)0;
+            }
+          }
+#pragma unroll
+          for (int q = 0; q < 4; ++q)
+#pragma unroll
+            for (int w = 0; w < 4; ++w) acc[q][w] += x[q] * y[w];
+        }
+        T av[4][4];   // loads first (in flight together), then the stores
+#pragma unroll
+        for (int w = 0; w < 4; ++w)
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            const int j = j0 + w, i = i0 + q;
+            av[q][w] = (j < rows && i < rows && i >= j) ? A[(int64_t)(k0 + j) * nf + k0 + i] : (T)0;
+          }
+#pragma unroll
+        for (int w = 0; w < 4; ++w)
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            const int j = j0 + w, i = i0 + q;
+            if (j < rows && i < rows && i >= j) A[(int64_t)(k0 + j) * nf + k0 + i] = av[q][w] - acc[q][w];
+          }
+      }
+    }
+  }
+  if (bad && threadIdx.x == 0) flag_status(a.status, s, -HDD_ENOTSPD, node);
 }
 
 template <typename T, int NB>
@@ -779,7 +773,7 @@ cudaError_t launch_front_large(const StepArgs& a, cudaStream_t st) {
       k_chol_trsm<T, 2><<<grid, 32 * kCholTrsmWarps, kCholTrsmWarps * sizeof(CholTrsmSmem<T, 2>), st>>>(a);
     if (a.prof) a.prof->end(st);
   } else {
-    const size_t smem = (((rows_smem + 3) & ~(size_t)3) * kPanel + kPanel + 32 * 33) * sizeof(T);
+    const size_t smem = (((rows_smem + 3) & ~(size_t)3) * kPanel + 2 * 32 * kWs + 32) * sizeof(T);
     if (a.prof) a.prof->begin(kProfPotrf, a.fl_chol, st);
     k_potrf<T><<<dim3(a.nlist, a.batch), 256, smem, st>>>(a);
     if (a.prof) a.prof->end(st);
