@@ -826,8 +826,8 @@ hdd_status hdd_solve_data(hdd_plan_t plan, int32_t batch, void* workspace, void*
           if (li.n == 0) continue;
           ProfScope ps(prof, hdd::kProfForward, 0.0, st);
           const int32_t* l = p.d_lists + li.off;
-          e = k == 0 ? hdd::launch_data_sweep<double>(D, l, li.n, li.max_nf, false, st)
-            : k == 1 ? hdd::launch_data_sweep<float>(D, l, li.n, li.max_nf, false, st)
+          e = k == 0 ? hdd::launch_data_sweep<double>(D, l, li.n, li.max_nf, li.max_m, false, st)
+            : k == 1 ? hdd::launch_data_sweep<float>(D, l, li.n, li.max_nf, li.max_m, false, st)
             : k == 2 ? hdd::launch_data_leaf<double>(D, l, li.n, false, st)
                      : hdd::launch_data_leaf<float>(D, l, li.n, false, st);
         }
@@ -838,8 +838,8 @@ hdd_status hdd_solve_data(hdd_plan_t plan, int32_t batch, void* workspace, void*
           ProfScope ps(prof, hdd::kProfDescent, 0.0, st);
           const int32_t* l = p.d_lists + li.off;
           if (k == 0)
-            e = p.nodes[p.list_data[li.off]].fp64 ? hdd::launch_data_sweep<double>(D, l, li.n, li.max_nf, true, st)
-                                                  : hdd::launch_data_sweep<float>(D, l, li.n, li.max_nf, true, st);
+            e = p.nodes[p.list_data[li.off]].fp64 ? hdd::launch_data_sweep<double>(D, l, li.n, li.max_nf, li.max_m, true, st)
+                                                  : hdd::launch_data_sweep<float>(D, l, li.n, li.max_nf, li.max_m, true, st);
           else
             e = k == 1 ? hdd::launch_data_leaf<double>(D, l, li.n, true, st)
                        : hdd::launch_data_leaf<float>(D, l, li.n, true, st);

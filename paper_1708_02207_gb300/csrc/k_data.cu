@@ -231,6 +231,211 @@ __global__ void __launch_bounds__(32 * kDataWarps) k_data_descent(const DataArgs
       if (k < D.nk) ds[k * rk + vid[c]] = (double)w[k * wstride + c];
 }
 
+// The same two sweeps for nodes with long interfaces (m >= kDataCtaMinM): one CTA
+// of 256 threads per (node, sample), the interface in 32-column blocks.  Forward:
+// warp 0 solves a block's diagonal triangle for the group's loads (shuffles), then
+// every thread folds the block into its rows below, reading each factor entry once
+// for all loads.  Descent: t = y_g - L_Bg^T d_B with four columns per warp and pass
+// (lanes down the boundary rows), then back substitution block by block (warp 0 on
+// the diagonal triangle, every warp folding the block into the columns before it).
+constexpr int kDataCtaMinM = 16;
+
+template <typename T, int R>
+__global__ void __launch_bounds__(256) k_data_forward_cta(const DataArgs D, const int32_t* __restrict__ list,
+                                                          int wstride) {
+  const int node = list[blockIdx.x];
+  const int s = blockIdx.y;
+  const NodeDev nd = D.nodes[node];
+  const int m = nd.m, b = nd.b, nf = nd.nf;
+  const int32_t* vid = D.maps + nd.map_off;
+  const int64_t NN = (int64_t)D.N * D.N, rk = (int64_t)D.batch * NN;
+  const double* rs = D.r + (int64_t)s * NN;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* z = reinterpret_cast<T*>(smem_raw);   // load k at z + k * wstride
+  T* Ld = z + R * wstride;                 // [32][33] diagonal block of L_gg
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (nd.leaf) {
+    for (int r = threadIdx.x; r < nf - 1; r += blockDim.x)
+#pragma unroll
+      for (int k = 0; k < R; ++k) z[k * wstride + r] = (r < m && k < D.nk) ? (T)rs[k * rk + vid[r]] : (T)0;
+  } else {
+    const NodeDev c0 = D.nodes[nd.child0], c1 = D.nodes[nd.child1];
+    const int32_t* pos0 = vid + (nf - 1);
+    const int32_t* pos1 = pos0 + nf;
+    for (int r = threadIdx.x; r < nf - 1; r += blockDim.x) {
+      const int q0 = pos0[r], q1 = pos1[r];
+#pragma unroll
+      for (int k = 0; k < R; ++k) {
+        double v = 0.0;
+        if (k < D.nk) {
+          if (r < m) v = rs[k * rk + vid[r]];
+          if (q0 >= 0) v += son_cond(D.A, c0, s, k, q0);
+          if (q1 >= 0) v += son_cond(D.A, c1, s, k, q1);
+        }
+        z[k * wstride + r] = (T)v;
+      }
+    }
+  }
+  const T* F = dat_F<T>(D.A, nd, s);
+  for (int cb = 0; cb < m; cb += 32) {
+    const int jb = min(32, m - cb);
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < 32 * jb; idx += blockDim.x) {
+      const int c = idx >> 5, l = idx & 31;
+      Ld[c * 33 + l] = (l < jb) ? F[(int64_t)(cb + c) * nf + cb + l] : (T)0;
+    }
+    __syncthreads();
+    if (warp == 0) {
+      T x[R];
+#pragma unroll
+      for (int k = 0; k < R; ++k) x[k] = (lane < jb) ? z[k * wstride + cb + lane] : (T)0;
+      for (int c = 0; c < jb; ++c) {
+        const T dc = Ld[c * 33 + c], lc = Ld[c * 33 + lane];
+#pragma unroll
+        for (int k = 0; k < R; ++k) {
+          const T yc = __shfl_sync(kAll, x[k], c) / dc;
+          if (lane == c) x[k] = yc;
+          if (lane > c && lane < jb) x[k] -= lc * yc;
+        }
+      }
+      if (lane < jb)
+#pragma unroll
+        for (int k = 0; k < R; ++k) z[k * wstride + cb + lane] = x[k];
+    }
+    __syncthreads();
+    for (int i = cb + jb + threadIdx.x; i < nf - 1; i += blockDim.x) {
+      T acc[R];
+#pragma unroll
+      for (int k = 0; k < R; ++k) acc[k] = (T)0;
+      for (int c = 0; c < jb; ++c) {
+        const T f = F[(int64_t)(cb + c) * nf + i];
+#pragma unroll
+        for (int k = 0; k < R; ++k) acc[k] += f * z[k * wstride + cb + c];
+      }
+#pragma unroll
+      for (int k = 0; k < R; ++k) z[k * wstride + i] -= acc[k];
+    }
+  }
+  __syncthreads();
+  double* ds = D.d + (int64_t)s * NN;
+  for (int c = threadIdx.x; c < m; c += blockDim.x)
+#pragma unroll
+    for (int k = 0; k < R; ++k)
+      if (k < D.nk) ds[k * rk + vid[c]] = (double)z[k * wstride + c];
+  if (b > 0) {
+    T* slot = dat_slot<T>(D.A, nd, s);
+    for (int r = threadIdx.x; r < b; r += blockDim.x)
+#pragma unroll
+      for (int k = 0; k < R; ++k)
+        if (k < D.nk) slot[k * b + r] = z[k * wstride + m + r];
+  }
+}
+
+template <typename T, int R>
+__global__ void __launch_bounds__(256) k_data_descent_cta(const DataArgs D, const int32_t* __restrict__ list,
+                                                          int wstride) {
+  const int node = list[blockIdx.x];
+  const int s = blockIdx.y;
+  const NodeDev nd = D.nodes[node];
+  const int m = nd.m, b = nd.b, nf = nd.nf;
+  const int32_t* vid = D.maps + nd.map_off;
+  const int64_t NN = (int64_t)D.N * D.N, rk = (int64_t)D.batch * NN;
+  double* ds = D.d + (int64_t)s * NN;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* w = reinterpret_cast<T*>(smem_raw);   // [gamma (t, then d_g), B (d_B)] of load k at w + k * wstride
+  T* Ld = w + R * wstride;                 // [32][33]
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarp = blockDim.x >> 5;
+  for (int r = threadIdx.x; r < nf - 1; r += blockDim.x)
+#pragma unroll
+    for (int k = 0; k < R; ++k) w[k * wstride + r] = (k < D.nk) ? (T)ds[k * rk + vid[r]] : (T)0;
+  __syncthreads();
+  const T* F = dat_F<T>(D.A, nd, s);
+  // t_c = y_c - sum_i F[m + i, c] d_B,i: four columns per warp and pass, lanes down the rows
+  for (int c0 = 4 * warp; c0 < m; c0 += 4 * nwarp) {
+    T acc[4][R];
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+#pragma unroll
+      for (int k = 0; k < R; ++k) acc[q][k] = (T)0;
+    for (int i = lane; i < b; i += 32) {
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const T f = (c0 + q < m) ? F[(int64_t)(c0 + q) * nf + m + i] : (T)0;
+#pragma unroll
+        for (int k = 0; k < R; ++k) acc[q][k] += f * w[k * wstride + m + i];
+      }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+#pragma unroll
+        for (int k = 0; k < R; ++k) acc[q][k] += __shfl_xor_sync(kAll, acc[q][k], o);
+    if (lane == 0)
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+        if (c0 + q < m)
+#pragma unroll
+          for (int k = 0; k < R; ++k) w[k * wstride + c0 + q] -= acc[q][k];
+  }
+  // back substitution L_gg^T d_g = t, last block first
+  for (int cb = ((m - 1) / 32) * 32; cb >= 0; cb -= 32) {
+    const int jb = min(32, m - cb);
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < 32 * jb; idx += blockDim.x) {
+      const int c = idx >> 5, l = idx & 31;
+      Ld[c * 33 + l] = (l < jb) ? F[(int64_t)(cb + c) * nf + cb + l] : (T)0;
+    }
+    __syncthreads();
+    if (warp == 0) {
+      T x[R];
+#pragma unroll
+      for (int k = 0; k < R; ++k) x[k] = (lane < jb) ? w[k * wstride + cb + lane] : (T)0;
+      for (int r = jb - 1; r >= 0; --r) {
+        const T dr = Ld[r * 33 + r], lr = Ld[lane * 33 + r];
+#pragma unroll
+        for (int k = 0; k < R; ++k) {
+          const T ur = __shfl_sync(kAll, x[k], r) / dr;
+          if (lane == r) x[k] = ur;
+          if (lane < r) x[k] -= lr * ur;
+        }
+      }
+      if (lane < jb)
+#pragma unroll
+        for (int k = 0; k < R; ++k) w[k * wstride + cb + lane] = x[k];
+    }
+    __syncthreads();
+    // fold the block into the columns before it: t_c -= sum_l F[cb + l, c] d_{cb + l}
+    for (int c0 = 4 * warp; c0 < cb; c0 += 4 * nwarp) {
+      T acc[4][R];
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+#pragma unroll
+        for (int k = 0; k < R; ++k) {
+          acc[q][k] = (c0 + q < cb && lane < jb) ? F[(int64_t)(c0 + q) * nf + cb + lane] * w[k * wstride + cb + lane]
+                                                 : (T)0;
+        }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+#pragma unroll
+          for (int k = 0; k < R; ++k) acc[q][k] += __shfl_xor_sync(kAll, acc[q][k], o);
+      if (lane == 0)
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+          if (c0 + q < cb)
+#pragma unroll
+            for (int k = 0; k < R; ++k) w[k * wstride + c0 + q] -= acc[q][k];
+    }
+  }
+  __syncthreads();
+  for (int c = threadIdx.x; c < m; c += blockDim.x)
+#pragma unroll
+    for (int k = 0; k < R; ++k)
+      if (k < D.nk) ds[k * rk + vid[c]] = (double)w[k * wstride + c];
+}
+
 // Condensed leaves (G = K_gg^-1 and one coupling weight per boundary row): one
 // half-warp per (leaf, sample), the group's loads in turn.  Forward: y = G r_g
 // (to d at the interior vertices), condensed -w_i y[c_i]; descent:
@@ -341,10 +546,18 @@ cudaError_t launch_data_residual(const DataArgs& D, const double* kappa, int64_t
   return cudaGetLastError();
 }
 template <typename T>
-cudaError_t launch_data_sweep(const DataArgs& D, const int32_t* list, int nlist, int max_nf, bool descent,
+cudaError_t launch_data_sweep(const DataArgs& D, const int32_t* list, int nlist, int max_nf, int max_m, bool descent,
                               cudaStream_t st) {
   if (nlist == 0) return cudaSuccess;
   const int ws = (max_nf + 3) & ~3;
+  if (max_m >= kDataCtaMinM) {   // long interfaces: one CTA per (node, sample)
+    const size_t smem = ((size_t)kData * ws + 32 * 33) * sizeof(T);
+    if (smem > 227 * 1024) return cudaErrorInvalidConfiguration;
+    const dim3 grid(nlist, D.batch);
+    if (descent) k_data_descent_cta<T, kData><<<grid, 256, smem, st>>>(D, list, ws);
+    else k_data_forward_cta<T, kData><<<grid, 256, smem, st>>>(D, list, ws);
+    return cudaGetLastError();
+  }
   const size_t per_warp = (size_t)kData * ws * sizeof(T);
   int wpb = kDataWarps;
   while (wpb > 1 && (size_t)wpb * per_warp > 227 * 1024) --wpb;
@@ -370,8 +583,8 @@ cudaError_t launch_data_update(const DataArgs& D, int k0, double tol, bool last,
   }
   return e;
 }
-template cudaError_t launch_data_sweep<double>(const DataArgs&, const int32_t*, int, int, bool, cudaStream_t);
-template cudaError_t launch_data_sweep<float>(const DataArgs&, const int32_t*, int, int, bool, cudaStream_t);
+template cudaError_t launch_data_sweep<double>(const DataArgs&, const int32_t*, int, int, int, bool, cudaStream_t);
+template cudaError_t launch_data_sweep<float>(const DataArgs&, const int32_t*, int, int, int, bool, cudaStream_t);
 template cudaError_t launch_data_leaf<double>(const DataArgs&, const int32_t*, int, bool, cudaStream_t);
 template cudaError_t launch_data_leaf<float>(const DataArgs&, const int32_t*, int, bool, cudaStream_t);
 
@@ -382,6 +595,10 @@ cudaError_t configure_data_kernels() {
   if ((e = cudaFuncSetAttribute(k_data_forward<float, kData>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
   if ((e = cudaFuncSetAttribute(k_data_descent<double, kData>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
   if ((e = cudaFuncSetAttribute(k_data_descent<float, kData>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
+  if ((e = cudaFuncSetAttribute(k_data_forward_cta<double, kData>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
+  if ((e = cudaFuncSetAttribute(k_data_forward_cta<float, kData>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
+  if ((e = cudaFuncSetAttribute(k_data_descent_cta<double, kData>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
+  if ((e = cudaFuncSetAttribute(k_data_descent_cta<float, kData>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
   return cudaSuccess;
 }
 

@@ -160,7 +160,7 @@ cudaError_t launch_data_init(const DataArgs& D, const double* g, int k0, cudaStr
 cudaError_t launch_data_residual(const DataArgs& D, const double* kappa, int64_t kap_stride, const double* c,
                                  const double* fH, int k0, cudaStream_t st);
 template <typename T>
-cudaError_t launch_data_sweep(const DataArgs& D, const int32_t* list, int nlist, int max_nf, bool descent,
+cudaError_t launch_data_sweep(const DataArgs& D, const int32_t* list, int nlist, int max_nf, int max_m, bool descent,
                               cudaStream_t st);
 template <typename T>
 cudaError_t launch_data_leaf(const DataArgs& D, const int32_t* list, int nlist, bool descent, cudaStream_t st);
