@@ -4,37 +4,43 @@
 // the bordered right-hand-side row is done by k_syrk_rhs), i.e. the SYRK of the
 // partial Cholesky of Sec. 2.4
 // (Eq. SchurC1: A11 - A12 A22^-1 A21 = K_BB - L_Bg L_Bg^T).  One CTA of 128
-// threads computes one 128 x 128 lower tile pair of one (node, sample):
+// threads computes one 128 x 64 tile (rows TI, columns TJ, on or below the
+// diagonal) of one (node, sample):
 //   * the TRSM that produced X also wrote it split into TF32 hi and lo parts,
 //     in 128-row x 8-column tiles in the K-major, no-swizzle core-matrix layout
 //     (8-row x 16-byte core matrices) that the MMA reads from shared memory;
 //   * one thread runs the pipeline: cp.async.bulk copies (completion counted in
 //     bytes on an mbarrier) fill kStages shared-memory stages, and for each
-//     8-column chunk it issues tcgen05.mma kind::tf32 (M = N = 128, K = 8)
+//     8-column chunk it issues tcgen05.mma kind::tf32 (M = 128, N = 64, K = 8)
 //     three times per step, hi*hi + hi*lo + lo*hi ("3xTF32", about FP32
-//     accuracy), with the accumulator in tensor memory (128 lanes x 128 columns);
+//     accuracy), with the accumulator in tensor memory (128 lanes x 64 columns);
+//     the B operand is one half (64 rows) of a 128-row staging tile;
 //     tcgen05.commit frees a stage for the next copy;
 //   * every wait is bounded (StepArgs::wait_limit polls); after a wait runs out
 //     the thread issues no further copies or MMAs, waits (with the same bound)
 //     for the MMAs already issued (one more tcgen05.commit on a drain barrier)
 //     and for every copy already issued, and marks the sample HDD_ETIMEOUT; the
 //     tensor memory is released only once no MMA can still write it;
-//   * the four warps read their 32 accumulator lanes with tcgen05.ld and subtract
-//     them from S (coalesced along the rows of S).
+//   * the four warps read their 32 accumulator lanes with tcgen05.ld, 16 columns at
+//     a time, and subtract them from S (coalesced along the rows of S).
+// The epilogue's gather of the sons' entries (Eq. block_equation4), a chain of
+// dependent loads, bounds the kernel, so the tile is 128 x 64: eight CTAs of 64
+// tensor-memory columns fill an SM's 512 columns and keep twice the warps of
+// 128 x 128 tiles in flight on the gather.
 #include "launch.h"
 
 namespace hdd {
 
 namespace {
 
-constexpr int kTile = kTcTile;        // M = N of the MMA and of the output tile
+constexpr int kTile = kTcTile;        // M of the MMA: rows of the output tile
+constexpr int kTileN = kTcTile / 2;   // N of the MMA: columns of the output tile
 constexpr int kChunk = kTcChunk;      // contraction columns staged per buffer
-constexpr int kTileBytes = (int)kTcBlockBytes;          // one operand part (4 KiB)
-constexpr int kStageBytes = 4 * kTileBytes;             // A hi/lo, B hi/lo (16 KiB)
-// Pipeline depth: 2 stages (32 KiB).  The contraction is short (K = m = 31..511
-// columns), so the epilogue's gather of the sons' entries, a chain of dependent
-// loads, bounds the kernel: it wants CTAs in flight more than deep prefetch.  Four
-// CTAs of 128 tensor-memory columns fill an SM's 512 columns.
+constexpr int kTileBytes = (int)kTcBlockBytes;          // one operand part of 128 rows (4 KiB)
+constexpr int kHalfBytes = kTileBytes / 2;              // its 64-row half (2 KiB)
+constexpr int kStageBytes = 2 * kTileBytes + 2 * kHalfBytes;   // A hi/lo, B hi/lo (12 KiB)
+// Pipeline depth: 2 stages (24 KiB).  The contraction is short (K = m = 31..511
+// columns): the kernel wants CTAs in flight more than deep prefetch.
 constexpr int kStages = 2;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -47,9 +53,9 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint
          ((uint64_t)((sbo >> 4) & 0x3FFF) << 32) | ((uint64_t)1 << 46);
 }
 
-// Instruction descriptor: D = F32, A = B = TF32, both K-major, N = M = 128.
+// Instruction descriptor: D = F32, A = B = TF32, both K-major, N = 64, M = 128.
 __device__ __forceinline__ uint32_t idesc_tf32() {
-  return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(kTile >> 3) << 17) | ((uint32_t)(kTile >> 4) << 24);
+  return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(kTileN >> 3) << 17) | ((uint32_t)(kTile >> 4) << 24);
 }
 
 __device__ __forceinline__ void mma_tf32(uint32_t tmem, uint64_t da, uint64_t db, uint32_t idesc, uint32_t acc) {
@@ -73,7 +79,7 @@ __device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t phase, uint32_
 
 }  // namespace
 
-__global__ void __launch_bounds__(128, 4) k_syrk_tc(StepArgs a) {
+__global__ void __launch_bounds__(128, 8) k_syrk_tc(StepArgs a) {
   const int node = a.list[blockIdx.y];
   const int s = blockIdx.z;
   bind_plan(a, node);
@@ -81,11 +87,13 @@ __global__ void __launch_bounds__(128, 4) k_syrk_tc(StepArgs a) {
   const NodeDev nd = a.nodes[node];
   const int m = nd.m, nb = nd.b + 1, nbt = nd.b;   // tiles cover the b boundary rows
   const int nt = (nbt + kTile - 1) / kTile;
-  if ((int)blockIdx.x >= nt * (nt + 1) / 2 || m == 0 || nd.tc_off < 0) return;
-  int TI = (int)((sqrtf(8.0f * (float)blockIdx.x + 1.0f) - 1.0f) * 0.5f);
-  while (TI * (TI + 1) / 2 > (int)blockIdx.x) --TI;
-  while ((TI + 1) * (TI + 2) / 2 <= (int)blockIdx.x) ++TI;
-  const int TJ = blockIdx.x - TI * (TI + 1) / 2;
+  // row tile TI holds the column tiles TJ = 0 .. 2 TI + 1 (x = TI (TI + 1) + TJ)
+  if ((int)blockIdx.x >= nt * (nt + 1) || m == 0 || nd.tc_off < 0) return;
+  int TI = (int)((sqrtf(4.0f * (float)blockIdx.x + 1.0f) - 1.0f) * 0.5f);
+  while (TI * (TI + 1) > (int)blockIdx.x) --TI;
+  while ((TI + 1) * (TI + 2) <= (int)blockIdx.x) ++TI;
+  const int TJ = blockIdx.x - TI * (TI + 1);
+  if (TJ * kTileN >= nbt) return;   // columns beyond the boundary rows
 
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* stage =
@@ -93,12 +101,12 @@ __global__ void __launch_bounds__(128, 4) k_syrk_tc(StepArgs a) {
   __shared__ __align__(8) uint64_t full[kStages], empty[kStages], drain;
   __shared__ uint32_t tmem_slot;
   __shared__ int timed_out, mma_live;
-  __shared__ int cpos[2][kTile];   // sons' rows of this tile's columns (fathers)
+  __shared__ int cpos[2][kTileN];   // sons' rows of this tile's columns (fathers)
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
-                 "r"(kTile));
+                 "r"(kTileN));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   if (tid == 0) {
@@ -114,8 +122,8 @@ __global__ void __launch_bounds__(128, 4) k_syrk_tc(StepArgs a) {
   const bool gather = !nd.leaf;
   const int32_t* pos0 = a.maps + nd.map_off + (nd.nf - 1);
   const int32_t* pos1 = pos0 + nd.nf;
-  if (gather) {
-    const int j = TJ * kTile + tid;
+  if (gather && tid < kTileN) {
+    const int j = TJ * kTileN + tid;
     cpos[0][tid] = j < nbt ? pos0[m + j] : -1;
     cpos[1][tid] = j < nbt ? pos1[m + j] : -1;
   }
@@ -150,17 +158,17 @@ __global__ void __launch_bounds__(128, 4) k_syrk_tc(StepArgs a) {
   }
   const int ld0 = ch0.b + 1, ld1 = ch1.b + 1;
   const int32_t* map = a.maps + nd.map_off;
-  auto load_chunk = [&](int c0, float (&sv)[32]) {
+  auto load_chunk = [&](int c0, float (&sv)[16]) {
     if (!gather) {
 #pragma unroll
-      for (int q = 0; q < 32; ++q) {
-        const int j = TJ * kTile + c0 + q;
+      for (int q = 0; q < 16; ++q) {
+        const int j = TJ * kTileN + c0 + q;
         sv[q] = (i < nbt && j < nbt && i >= j) ? S[(int64_t)j * nb + i] : 0.0f;
       }
     } else if (!mixed_sons) {
 #pragma unroll
-      for (int q = 0; q < 32; ++q) {
-        const int j = TJ * kTile + c0 + q;
+      for (int q = 0; q < 16; ++q) {
+        const int j = TJ * kTileN + c0 + q;
         const int q0 = cpos[0][c0 + q], q1 = cpos[1][c0 + q];
         const bool v = i < nbt && j < nbt && i >= j;
         float x = 0.0f;
@@ -170,15 +178,15 @@ __global__ void __launch_bounds__(128, 4) k_syrk_tc(StepArgs a) {
       }
     } else {
 #pragma unroll
-      for (int q = 0; q < 32; ++q) {
-        const int j = TJ * kTile + c0 + q;
+      for (int q = 0; q < 16; ++q) {
+        const int j = TJ * kTileN + c0 + q;
         sv[q] = (i < nbt && j < nbt && i >= j)
                     ? father_entry<float>(m + i, m + j, s, nd, map, ch0, ch1, a.arenas, a.rhs)
                     : 0.0f;
       }
     }
   };
-  float sv[32];
+  float sv[16];
   load_chunk(0, sv);
 
   if (tid == 0) {
@@ -200,7 +208,8 @@ __global__ void __launch_bounds__(128, 4) k_syrk_tc(StepArgs a) {
       const uint32_t dst = smem_u32(stage + b * kStageBytes);
       const uint32_t bar = smem_u32(&full[b]);
       const unsigned char* srcA = base + ((int64_t)TI * nchunks + c) * 2 * kTileBytes;
-      const unsigned char* srcB = base + ((int64_t)TJ * nchunks + c) * 2 * kTileBytes;
+      // B: the half (TJ & 1) of the 128-row tile TJ / 2, hi part then lo part
+      const unsigned char* srcB = base + ((int64_t)(TJ >> 1) * nchunks + c) * 2 * kTileBytes + (TJ & 1) * kHalfBytes;
       asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(kStageBytes));
       if (c == stall_chunk) return;
       asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
@@ -208,7 +217,11 @@ __global__ void __launch_bounds__(128, 4) k_syrk_tc(StepArgs a) {
                    : "memory");
       asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
                        dst + 2 * kTileBytes),
-                   "l"(srcB), "r"(2 * kTileBytes), "r"(bar)
+                   "l"(srcB), "r"(kHalfBytes), "r"(bar)
+                   : "memory");
+      asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                       dst + 2 * kTileBytes + kHalfBytes),
+                   "l"(srcB + kTileBytes), "r"(kHalfBytes), "r"(bar)
                    : "memory");
       pending |= 1u << b;
     };
@@ -220,7 +233,7 @@ __global__ void __launch_bounds__(128, 4) k_syrk_tc(StepArgs a) {
       pending &= ~(1u << b);
       asm volatile("tcgen05.fence::after_thread_sync;");
       const uint32_t Ah = smem_u32(stage + b * kStageBytes);
-      const uint32_t Al = Ah + kTileBytes, Bh = Ah + 2 * kTileBytes, Bl = Ah + 3 * kTileBytes;
+      const uint32_t Al = Ah + kTileBytes, Bh = Ah + 2 * kTileBytes, Bl = Bh + kHalfBytes;
 #pragma unroll
       for (int t = 0; t < kChunk / 8; ++t) {
         const uint32_t o = t * 256;   // two core matrices (128 bytes apart along K) per MMA
@@ -271,24 +284,22 @@ __global__ void __launch_bounds__(128, 4) k_syrk_tc(StepArgs a) {
   if (timed_out) {
     if (tid == 0) flag_status(a.status, s, -HDD_ETIMEOUT, node);
   } else {
+    const int row_last = TI * kTile + warp * 32 + 31;   // this warp's last row
 #pragma unroll 1
-    for (int c0 = 0; c0 < kTile; c0 += 32) {
-      if (TI == TJ && c0 > warp * 32 + 31) break;   // strictly above the diagonal of this warp's rows
-      uint32_t r[32];
+    for (int c0 = 0; c0 < kTileN; c0 += 16) {
+      if (TJ * kTileN + c0 > row_last) break;   // strictly above the diagonal of this warp's rows
+      uint32_t r[16];
       const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0;
       asm volatile(
-          "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-          "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+          "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
           : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-            "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
-            "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
-            "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+            "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
           : "r"(taddr));
       if (c0 > 0) load_chunk(c0, sv);
       asm volatile("tcgen05.wait::ld.sync.aligned;");
 #pragma unroll
-      for (int q = 0; q < 32; ++q) {
-        const int j = TJ * kTile + c0 + q;
+      for (int q = 0; q < 16; ++q) {
+        const int j = TJ * kTileN + c0 + q;
         if (i < nbt && j < nbt && i >= j) S[(int64_t)j * nb + i] = sv[q] - __uint_as_float(r[q]);
       }
     }
@@ -298,7 +309,7 @@ __global__ void __launch_bounds__(128, 4) k_syrk_tc(StepArgs a) {
   // an MMA that did not complete within the bound may still write this tensor
   // memory: it stays allocated rather than being handed to another CTA under it
   if (warp == 0 && !mma_live)
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTile));
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTileN));
 }
 
 constexpr size_t kSyrkTcSmem = kStages * (size_t)kStageBytes + 1024;
@@ -307,7 +318,7 @@ cudaError_t launch_syrk_tc(const StepArgs& a, cudaStream_t st) {
   if (a.nlist == 0) return cudaSuccess;
   const int nt = (a.max_b + kTile - 1) / kTile;
   if (nt == 0) return cudaSuccess;
-  dim3 grid(nt * (nt + 1) / 2, a.nlist, a.batch);
+  dim3 grid(nt * (nt + 1), a.nlist, a.batch);
   k_syrk_tc<<<grid, 128, kSyrkTcSmem, st>>>(a);
   return cudaGetLastError();
 }
