@@ -204,7 +204,20 @@ __global__ void k_descent(const NodeDev* __restrict__ nodes, const int32_t* __re
   T* uB = reinterpret_cast<T*>(smem_raw);   // [b]
   T* t = uB + b;                            // [m]
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarp = blockDim.x >> 5;
-  for (int i = threadIdx.x; i < b; i += blockDim.x) uB[i] = (T)us[vid[m + i]];
+  for (int i0 = 0; i0 < b; i0 += 4 * blockDim.x) {   // u_B: four gathers per thread in flight
+    int v[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int i = i0 + q * blockDim.x + threadIdx.x;
+      v[q] = i < b ? vid[m + i] : -1;
+    }
+    double x[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) x[q] = v[q] >= 0 ? us[v[q]] : 0.0;
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+      if (v[q] >= 0) uB[i0 + q * blockDim.x + threadIdx.x] = (T)x[q];
+  }
   __syncthreads();
   const T* Y = fac_Y<T>(A, nd, s);
   // four columns per warp and pass, their loads in flight together

@@ -22,6 +22,22 @@ template <> __device__ __forceinline__ float* warp_S<float>(const Arenas& A, con
   return A.s32 + (int64_t)s * A.s32_stride + nd.s_off;
 }
 
+// A warp copies n consecutive values from global to shared memory with eight
+// loads in flight per lane (all issued before the stores).
+template <typename T>
+__device__ __forceinline__ void warp_stage(T* dst, const T* __restrict__ src, int n, int lane) {
+  constexpr int U = 8;
+  int i = lane;
+  for (; i + 32 * (U - 1) < n; i += 32 * U) {
+    T v[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) v[u] = src[i + 32 * u];
+#pragma unroll
+    for (int u = 0; u < U; ++u) dst[i + 32 * u] = v[u];
+  }
+  for (; i < n; i += 32) dst[i] = src[i];
+}
+
 // Warps per CTA of the sweeps: 8, or fewer when a warp's vector of nf entries
 // would not fit the shared memory of 8 warps.
 static int sweep_warps(size_t bytes_per_warp) {
@@ -63,7 +79,7 @@ __global__ void __launch_bounds__(256) k_forward_warp(const NodeDev* __restrict_
   const T* F = Fg;
   if (stage) {
     T* Fs = z + ((nf + 3) & ~3);
-    for (int idx = lane; idx < nf * m; idx += 32) Fs[idx] = Fg[idx];
+    warp_stage(Fs, Fg, nf * m, lane);
     F = Fs;
   }
   if (nd.leaf) {
@@ -147,12 +163,22 @@ __global__ void __launch_bounds__(256) k_descent_warp(const NodeDev* __restrict_
   const T* F = Fg;
   if (stage) {
     T* Fs = wv + ((nf + 3) & ~3);
-    for (int idx = lane; idx < nf * m; idx += 32) Fs[idx] = Fg[idx];
+    warp_stage(Fs, Fg, nf * m, lane);
     F = Fs;
   }
   const T* Y = node_Y<T>(A, nd, s);
   double* us = u + (int64_t)s * u_stride;
-  for (int i = lane; i < b; i += 32) wv[m + i] = (T)us[vid[m + i]];
+  for (int i0 = 0; i0 < b; i0 += 128) {   // u_B: four gathers per lane in flight
+    int v[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) v[q] = (i0 + 32 * q + lane < b) ? vid[m + i0 + 32 * q + lane] : -1;
+    double x[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) x[q] = v[q] >= 0 ? us[v[q]] : 0.0;
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+      if (v[q] >= 0) wv[m + i0 + 32 * q + lane] = (T)x[q];
+  }
   T* ys = wv + ((nf + 3) & ~3) + (stage ? nf * m : 0);   // y_g, staged with the rest
   for (int c = lane; c < m; c += 32) ys[c] = Y[c];
   __syncwarp();
