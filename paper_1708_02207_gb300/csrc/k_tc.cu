@@ -9,8 +9,12 @@
 //   * the TRSM that produced X also wrote it split into TF32 hi and lo parts,
 //     in 128-row x 8-column tiles in the K-major, no-swizzle core-matrix layout
 //     (8-row x 16-byte core matrices) that the MMA reads from shared memory;
-//   * one thread runs the pipeline: cp.async.bulk copies (completion counted in
-//     bytes on an mbarrier) fill kStages shared-memory stages, and for each
+//   * one thread runs the pipeline: TMA copies (cp.async.bulk.tensor through two
+//     tensor maps over the batch's staging arena, viewed as rows of 1 KiB:
+//     8-row boxes for an A tile's hi and lo parts, 2-row boxes for a B half;
+//     completion counted in bytes on an mbarrier) fill kStages shared-memory
+//     stages (launches over several plans, whose arenas differ, use plain
+//     cp.async.bulk copies of the same bytes), and for each
 //     8-column chunk it issues tcgen05.mma kind::tf32 (M = 128, N = 64, K = 8)
 //     three times per step, hi*hi + hi*lo + lo*hi ("3xTF32", about FP32
 //     accuracy), with the accumulator in tensor memory (128 lanes x 64 columns);
@@ -27,6 +31,10 @@
 // dependent loads, bounds the kernel, so the tile is 128 x 64: eight CTAs of 64
 // tensor-memory columns fill an SM's 512 columns and keep twice the warps of
 // 128 x 128 tiles in flight on the gather.
+#include <cuda.h>   // CUtensorMap (the encoder is taken from the driver at run time)
+
+#include <mutex>
+
 #include "launch.h"
 
 namespace hdd {
@@ -79,7 +87,10 @@ __device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t phase, uint32_
 
 }  // namespace
 
-__global__ void __launch_bounds__(128, 8) k_syrk_tc(StepArgs a) {
+// use_tma: the tensor maps describe this launch's staging arena (rows of 1 KiB from
+// a.arenas.tc); otherwise the same bytes come by plain bulk copies.
+__global__ void __launch_bounds__(128, 8) k_syrk_tc(StepArgs a, const __grid_constant__ CUtensorMap mapA,
+                                                    const __grid_constant__ CUtensorMap mapB, int use_tma) {
   const int node = a.list[blockIdx.y];
   const int s = blockIdx.z;
   bind_plan(a, node);
@@ -203,6 +214,8 @@ __global__ void __launch_bounds__(128, 8) k_syrk_tc(StepArgs a) {
     uint32_t ph_full[kStages] = {}, ph_empty[kStages] = {};
     uint32_t pending = 0;   // bit b: copies into stage b issued, their completion not yet waited for
     bool ok = true, any_mma = false;
+    // tensor-map rows (1 KiB each) of this (node, sample)'s staging
+    const int row0 = (int)(((int64_t)s * a.arenas.tc_stride + nd.tc_off) >> 10);
     auto load = [&](int c) {
       const int b = c % kStages;
       const uint32_t dst = smem_u32(stage + b * kStageBytes);
@@ -212,6 +225,25 @@ __global__ void __launch_bounds__(128, 8) k_syrk_tc(StepArgs a) {
       const unsigned char* srcB = base + ((int64_t)(TJ >> 1) * nchunks + c) * 2 * kTileBytes + (TJ & 1) * kHalfBytes;
       asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(kStageBytes));
       if (c == stall_chunk) return;
+      if (use_tma) {
+        const int ya = row0 + (TI * nchunks + c) * 8;
+        const int yb = row0 + ((TJ >> 1) * nchunks + c) * 8 + (TJ & 1) * 2;
+        asm volatile(
+            "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
+            ::"r"(dst), "l"(reinterpret_cast<uint64_t>(&mapA)), "r"(0), "r"(ya), "r"(bar)
+            : "memory");
+        asm volatile(
+            "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
+            ::"r"(dst + 2 * kTileBytes), "l"(reinterpret_cast<uint64_t>(&mapB)), "r"(0), "r"(yb), "r"(bar)
+            : "memory");
+        asm volatile(
+            "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
+            ::"r"(dst + 2 * kTileBytes + kHalfBytes), "l"(reinterpret_cast<uint64_t>(&mapB)), "r"(0), "r"(yb + 4),
+              "r"(bar)
+            : "memory");
+        pending |= 1u << b;
+        return;
+      }
       asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
                    "l"(srcA), "r"(2 * kTileBytes), "r"(bar)
                    : "memory");
@@ -314,12 +346,52 @@ __global__ void __launch_bounds__(128, 8) k_syrk_tc(StepArgs a) {
 
 constexpr size_t kSyrkTcSmem = kStages * (size_t)kStageBytes + 1024;
 
+namespace {
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+EncodeTiledFn g_encode = nullptr;
+std::once_flag g_encode_once;
+
+EncodeTiledFn encoder() {
+  std::call_once(g_encode_once, [] {
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      g_encode = reinterpret_cast<EncodeTiledFn>(fn);
+  });
+  return g_encode;
+}
+
+// A 2D FP32 tensor of rows of 256 values (1 KiB) over `rows` rows from `base`,
+// read in boxes of 256 x box_rows.
+bool encode_rows(CUtensorMap* map, void* base, uint64_t rows, uint32_t box_rows) {
+  EncodeTiledFn enc = encoder();
+  if (!enc || rows == 0 || rows > 0xFFFFFFFFull || (reinterpret_cast<uintptr_t>(base) & 15)) return false;
+  const cuuint64_t dims[2] = {256, rows};
+  const cuuint64_t strides[1] = {1024};
+  const cuuint32_t box[2] = {256, box_rows};
+  const cuuint32_t estr[2] = {1, 1};
+  return enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+             CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE,
+             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+}  // namespace
+
 cudaError_t launch_syrk_tc(const StepArgs& a, cudaStream_t st) {
   if (a.nlist == 0) return cudaSuccess;
   const int nt = (a.max_b + kTile - 1) / kTile;
   if (nt == 0) return cudaSuccess;
   dim3 grid(nt * (nt + 1), a.nlist, a.batch);
-  k_syrk_tc<<<grid, 128, kSyrkTcSmem, st>>>(a);
+  // one plan: the staging arena of the batch as one tensor (row offsets of nodes and
+  // samples are multiples of 8 KiB); several plans: plain bulk copies
+  CUtensorMap mapA{}, mapB{};
+  const uint64_t rows = (uint64_t)a.batch * (uint64_t)a.arenas.tc_stride / 1024;
+  const bool tma = !a.plan_of && a.arenas.tc_stride % 1024 == 0 && encode_rows(&mapA, a.arenas.tc, rows, 8) &&
+                   encode_rows(&mapB, a.arenas.tc, rows, 2);
+  k_syrk_tc<<<grid, 128, kSyrkTcSmem, st>>>(a, mapA, mapB, tma ? 1 : 0);
   return cudaGetLastError();
 }
 
