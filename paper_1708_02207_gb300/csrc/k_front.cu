@@ -380,6 +380,118 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) k_potrf(StepArgs 
   if (bad && threadIdx.x == 0) flag_status(a.status, s, -HDD_ENOTSPD, node);
 }
 
+// POTRF of a K_gg whose whole lower triangle fits in shared memory: the same
+// blocked algorithm as k_potrf, with the trailing updates in shared memory (one
+// load of the triangle, one store of the factor).  Storage: column j holds rows
+// floor4(j) .. m4-1 (m4 = m rounded up to 4), columns packed one after another, so
+// that every 4-row group starts on a 16-byte boundary:
+//   (i, j) -> tri_off(j, m4) + i - floor4(j),
+//   tri_off(j, m4) = 4 q m4 - 8 q (q - 1) + r (m4 - 4 q),  j = 4 q + r.
+__host__ __device__ __forceinline__ int tri_off(int j, int m4) {
+  const int q = j >> 2, r = j & 3;
+  return 4 * q * m4 - 8 * q * (q - 1) + r * (m4 - 4 * q);
+}
+__host__ __device__ __forceinline__ int tri_elems(int m) {
+  const int m4 = (m + 3) & ~3;
+  return tri_off(m4, m4);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) k_potrf_smem(StepArgs a) {
+  const int node = a.list[blockIdx.x];
+  const int s = blockIdx.y;
+  bind_plan(a, node);
+  if (s >= a.batch) return;
+  const NodeDev nd = a.nodes[node];
+  const int nf = nd.nf, m = nd.m, m4 = (m + 3) & ~3;
+  T* A = node_F<T>(a.arenas, nd, s);
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* Ls = reinterpret_cast<T*>(smem_raw);   // [32][kWs] scratch of warp_chol_inverse
+  T* W = Ls + 32 * kWs;                     // [32][kWs] inverse of the diagonal block
+  T* dinv = W + 32 * kWs;                   // [32]
+  T* P = dinv + 32;                         // the lower triangle, 16-byte aligned 4-row groups
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarp = blockDim.x >> 5;
+  auto at = [&](int i, int j) -> T& { return P[tri_off(j, m4) + i - (j & ~3)]; };
+  // load: column by column, one warp per column, zeros above the diagonal and below m
+  for (int j = warp; j < m; j += nwarp)
+    for (int i = (j & ~3) + lane; i < m4; i += 32) at(i, j) = (i >= j && i < m) ? A[(int64_t)j * nf + i] : (T)0;
+  bool bad = false;
+  for (int k0 = 0; k0 < m; k0 += kPanel) {
+    const int kb = min(kPanel, m - k0);
+    __syncthreads();
+    if (warp == 0) {   // the diagonal block, lane r holding row k0 + r
+      T row[32];
+#pragma unroll
+      for (int c = 0; c < 32; ++c) row[c] = (c < kb && lane < kb && c <= lane) ? at(k0 + lane, k0 + c) : (T)0;
+      warp_chol_inverse<T>(row, kb, Ls, W, dinv, bad);
+#pragma unroll
+      for (int c = 0; c < 32; ++c)
+        if (c < kb && lane < kb && c <= lane) at(k0 + lane, k0 + c) = row[c];
+      T* G = reinterpret_cast<T*>(a.arenas.inv + (int64_t)s * a.arenas.inv_stride + nd.inv_off) + (k0 / 32) * 1024;
+#pragma unroll 4
+      for (int r = 0; r < 32; ++r)
+        G[lane * 32 + r] = (lane < kb) ? ((r < kb) ? W[r * kWs + lane] : (T)0) : ((r == lane) ? (T)1 : (T)0);
+    }
+    __syncthreads();
+    // rows below the diagonal block (full panels only): x <- x W^T
+    for (int i = k0 + kb + threadIdx.x; i < m; i += blockDim.x) {
+      T x[32];
+#pragma unroll
+      for (int l = 0; l < 32; ++l) x[l] = at(i, k0 + l);
+      apply_inverse<T, 0, 32>(x, W);
+#pragma unroll
+      for (int c = 0; c < 32; ++c) at(i, k0 + c) = x[c];
+    }
+    __syncthreads();
+    // trailing update of rows and columns k0+kb .. m4-1 in 4 x 4 tiles (rows past m
+    // are zero and stay unused); one warp per column of tiles, lanes down the rows
+    const int t0 = k0 + kb;   // a multiple of 32 whenever a trailing block exists
+    if (t0 >= m) continue;
+    const int nt = (m4 - t0) >> 2;
+    for (int tj = warp; tj < nt; tj += nwarp) {
+      const int j0 = t0 + 4 * tj;
+      for (int ti = tj + lane; ti < nt; ti += 32) {
+        const int i0 = t0 + 4 * ti;
+        T acc[4][4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+#pragma unroll
+          for (int w = 0; w < 4; ++w) acc[q][w] = (T)0;
+#pragma unroll 4
+        for (int l = 0; l < 32; ++l) {
+          T x[4], y[4];
+          load4(&at(i0, k0 + l), x);
+          load4(&at(j0, k0 + l), y);
+#pragma unroll
+          for (int q = 0; q < 4; ++q)
+#pragma unroll
+            for (int w = 0; w < 4; ++w) acc[q][w] += x[q] * y[w];
+        }
+#pragma unroll
+        for (int w = 0; w < 4; ++w) {
+          T v[4];
+          load4(&at(i0, j0 + w), v);
+#pragma unroll
+          for (int q = 0; q < 4; ++q)
+            if (i0 + q >= j0 + w) at(i0 + q, j0 + w) = v[q] - acc[q][w];
+        }
+      }
+    }
+  }
+  __syncthreads();
+  for (int j = warp; j < m; j += nwarp)
+    for (int i = j + lane; i < m; i += 32) A[(int64_t)j * nf + i] = at(i, j);
+  if (bad && threadIdx.x == 0) flag_status(a.status, s, -HDD_ENOTSPD, node);
+}
+
+// Largest interface whose triangle, with the diagonal-block scratch, fits the shared
+// memory of one CTA.
+template <typename T>
+static bool potrf_in_smem(int max_m, size_t* bytes) {
+  *bytes = ((size_t)2 * 32 * kWs + 32 + tri_elems(max_m)) * sizeof(T);
+  return *bytes <= 48 * 1024;   // larger triangles cost residency: measured slower
+}
+
 template <typename T, int NB>
 struct CholTrsmSmem {   // per warp (sample)
   T W[NB][32 * kWs];
@@ -773,9 +885,14 @@ cudaError_t launch_front_large(const StepArgs& a, cudaStream_t st) {
       k_chol_trsm<T, 2><<<grid, 32 * kCholTrsmWarps, kCholTrsmWarps * sizeof(CholTrsmSmem<T, 2>), st>>>(a);
     if (a.prof) a.prof->end(st);
   } else {
-    const size_t smem = (((rows_smem + 3) & ~(size_t)3) * kPanel + 2 * 32 * kWs + 32) * sizeof(T);
+    size_t tri_bytes = 0;
     if (a.prof) a.prof->begin(kProfPotrf, a.fl_chol, st);
-    k_potrf<T><<<dim3(a.nlist, a.batch), 256, smem, st>>>(a);
+    if (potrf_in_smem<T>(a.max_m, &tri_bytes)) {
+      k_potrf_smem<T><<<dim3(a.nlist, a.batch), 256, tri_bytes, st>>>(a);
+    } else {
+      const size_t smem = (((rows_smem + 3) & ~(size_t)3) * kPanel + 2 * 32 * kWs + 32) * sizeof(T);
+      k_potrf<T><<<dim3(a.nlist, a.batch), 256, smem, st>>>(a);
+    }
     if (a.prof) a.prof->end(st);
   }
   if (!fused_pt) {
@@ -817,6 +934,8 @@ cudaError_t configure_front_kernels() {
   cudaError_t e;
   if ((e = cudaFuncSetAttribute(k_potrf<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
   if ((e = cudaFuncSetAttribute(k_potrf<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
+  if ((e = cudaFuncSetAttribute(k_potrf_smem<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
+  if ((e = cudaFuncSetAttribute(k_potrf_smem<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
   if ((e = cudaFuncSetAttribute(k_chol_trsm<float, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
   if ((e = cudaFuncSetAttribute(k_chol_trsm<float, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
   if ((e = cudaFuncSetAttribute(k_chol_trsm<double, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
