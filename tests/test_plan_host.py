@@ -198,3 +198,11 @@ def test_mean_plan_refuses_bad_nodes(hdd):
         hdd.Plan(33, 8, None, np.array([-1], dtype=np.int32), 0.1, device=-1, obs_kind=hdd.HDD_OBS_MEANS)
     with pytest.raises(hdd.HDDError):
         hdd.Plan(33, 8, None, np.array([3], dtype=np.int32), 0.1, device=-1, obs_kind=7)
+
+
+def test_data_scratch_size_is_two_groups_of_four_vectors(hdd):
+    # hdd_solve_data keeps the residuals and corrections of four data sets per sample
+    # plus four words of refinement bookkeeping per sample
+    plan = hdd.Plan(33, 8, None, w.obs_vertices(33, 3), 0.1, device=-1)
+    for B in (1, 7, 256):
+        assert plan.data_scratch_size(B) == (2 * 4 * B * 33 * 33 + 4 * B) * 8
