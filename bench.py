@@ -354,12 +354,19 @@ def run_serving(args, hdd, torch, dev, local):
             # tuner saw, where the tuned minimum of refinement steps leaves requests above the
             # tolerance (flagged HDD_ENOCONV): serving plans take one step more
             K = t["ir_max_iter"] + (1 if prec_name == "mixed" else 0)
-            plans[str(N)] = hdd.Plan(N, t["leaf"], w.kl_basis(N, 40, 0.1, 2.0), obs, 0.01, precision=prec,
+            phi = w.kl_basis(N, 40, 0.1, 2.0)
+            plans[str(N)] = hdd.Plan(N, t["leaf"], phi, obs, 0.01, precision=prec,
                                      ir_max_iter=K, ir_tol=args.ir_tol, device=local)
             ydata[str(N)] = 0.05 + 0.01 * rng.standard_normal(obs.size)
+            if prec_name == "mixed":
+                # a request that still does not converge is answered by an FP64 plan
+                t64 = autotune.choose(N, "fp64")
+                plans[f"{N}-fp64"] = hdd.Plan(N, t64["leaf"], phi, obs, 0.01, precision=hdd.HDD_FP64,
+                                              ir_max_iter=0, device=local)
+        fallback = {str(N): f"{N}-fp64" for N in grids} if prec_name == "mixed" else None
         budget = int(min(80e9, 0.5 * torch.cuda.mem_get_info(dev)[0]))
         backend = serving.CudaBackend(plans, n_slots=4, device=local)
-        server = serving.Server(backend, budget_bytes=budget, max_batch=64, n_slots=4)
+        server = serving.Server(backend, budget_bytes=budget, max_batch=64, n_slots=4, fallback=fallback)
         chains = [serving.MetropolisChain(str(grids[k % len(grids)]), rng.standard_normal(40),
                                           ydata[str(grids[k % len(grids)])], 0.1, rng) for k in range(64)]
         n_req = args.serve_requests if prec_name == "mixed" else max(1, args.serve_requests // 5)
@@ -379,6 +386,7 @@ def run_serving(args, hdd, torch, dev, local):
         out["points"][prec_name] = {"budget_bytes": budget, "peak_admitted_bytes": server.peak_bytes,
                                     "batches": server.batches, "requests_per_point": n_req, "sweep": pts,
                                     "requests": len(server.done),
+                                    "escalated_to_fp64": server.escalated,
                                     "failed": sum(fails.values()), "failed_by_grid_and_status": fails}
         del server, backend, plans
         torch.cuda.empty_cache()

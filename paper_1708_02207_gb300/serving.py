@@ -14,6 +14,14 @@ measured per request from submission to collection.
 Every sample of a batch is computed independently of the others (the library's kernels
 never combine samples), so a result does not depend on what it was batched with.
 
+A plan may name a fallback plan (`fallback={"513": "513-fp64"}`): a request whose result comes
+back with one of the `escalate` codes (by default HDD_ENOCONV, a mixed-precision sample
+whose refinement did not reach the tolerance) goes back to the head of the queue under the
+fallback plan, keeping its submission time, and is reported once, with the fallback's result
+and `escalated_from` set.  An FP64 plan as the fallback of a mixed one turns the rare sample
+of high contrast that the FP32 factors cannot refine into a slower, exact answer instead of a
+failure.
+
 The loop itself is host logic over a small backend interface: `CudaBackend` runs batches
 through the C ABI (paper_1708_02207_gb300.hdd); tests drive the same loop with a fake.
 """
@@ -38,6 +46,7 @@ class Request:
     u_obs: np.ndarray | None = None
     status: int = 0
     rejected: str = ""
+    escalated_from: str = ""
 
     @property
     def latency(self) -> float:
@@ -58,9 +67,18 @@ class Server:
     launch(plan, Z[B, n_z], y[B, n_obs], slot) -> handle, done(handle) -> bool,
     collect(handle) -> (loglik[B], u_obs[B, n_obs], status[B]) and release(handle)."""
 
-    def __init__(self, backend, budget_bytes: int, max_batch: int = 64, n_slots: int = 4, clock=time.perf_counter):
+    def __init__(self, backend, budget_bytes: int, max_batch: int = 64, n_slots: int = 4, clock=time.perf_counter,
+                 fallback: dict | None = None, escalate=(-5,)):
         if budget_bytes <= 0 or max_batch < 1 or n_slots < 1:
             raise ValueError("budget_bytes, max_batch and n_slots must be positive")
+        self.fallback = dict(fallback or {})
+        for a, b in self.fallback.items():
+            backend.workspace_bytes(a, 1)   # unknown plans raise here
+            backend.workspace_bytes(b, 1)
+            if self.fallback.get(b) is not None:
+                raise ValueError(f"fallback plan {b!r} has a fallback of its own")
+        self.escalate = frozenset(int(e) for e in escalate)
+        self.escalated = 0
         self.backend = backend
         self.budget = int(budget_bytes)
         self.max_batch = int(max_batch)
@@ -92,9 +110,17 @@ class Server:
                 continue
             ll, u, st = self.backend.collect(b.handle)
             t = self.clock()
+            again = []
             for k, r in enumerate(b.requests):
+                code = -(int(st[k]) & 0xFF)   # a sample's status is (-code) | (node << 8)
+                if code in self.escalate and b.plan in self.fallback:
+                    r.escalated_from, r.plan = b.plan, self.fallback[b.plan]
+                    again.append(r)
+                    continue
                 r.loglik, r.u_obs, r.status, r.t_done = float(ll[k]), np.array(u[k]), int(st[k]), t
                 self.done.append(r)
+            self.waiting.extendleft(reversed(again))   # ahead of every later arrival, in order
+            self.escalated += len(again)
             self.backend.release(b.handle)
             self.bytes_in_flight -= b.bytes
             self.free_slots.append(b.slot)

@@ -169,3 +169,61 @@ def test_offered_load_run_with_metropolis_chains():
     assert np.mean([c.Z.mean() for c in chains]) > 0.1
     sat = run_offered_load(srv, chains, rate=float("inf"), n_requests=120, rng=rng, tick=tick)
     assert sat["evals_per_s"] > out["evals_per_s"]
+
+
+class FlakyBackend(FakeBackend):
+    """Plan "mixed" reports HDD_ENOCONV at tree node 7 ((5) | (7 << 8)) for rows whose first
+    entry is negative; plan "fp64" always succeeds and shifts loglik by +1000 so that the
+    test can tell which plan produced a result."""
+
+    def collect(self, h):
+        ll, u, st = super().collect(h)
+        if h["plan"] == "mixed":
+            st = np.where(h["Z"][:, 0] < 0, 5 | (7 << 8), 0).astype(np.int32)
+        else:
+            ll = ll + 1000.0
+        return ll, u, st
+
+    def launch(self, plan, Z, y, slot):
+        h = super().launch(plan, Z, y, slot)
+        h["plan"] = plan
+        return h
+
+
+def test_non_converged_requests_escalate_to_the_fallback_plan():
+    clock = Clock()
+    be = FlakyBackend(clock, {"mixed": 10, "fp64": 40}, dur={"mixed": 1.0, "fp64": 4.0})
+    srv = Server(be, budget_bytes=10_000, max_batch=8, clock=clock, fallback={"mixed": "fp64"})
+    rng = np.random.default_rng(3)
+    reqs = [srv.submit("mixed", rng.standard_normal(4), np.ones(2)) for _ in range(20)]
+    drive(srv, clock)
+    assert len(srv.done) == 20 and {r.rid for r in srv.done} == {r.rid for r in reqs}
+    bad = [r for r in reqs if r.Z[0] < 0]
+    assert bad and srv.escalated == len(bad)
+    for r in reqs:
+        ref = -(r.Z ** 2).sum() + 2.0
+        assert r.status == 0
+        if r.Z[0] < 0:
+            assert r.escalated_from == "mixed" and r.plan == "fp64" and r.loglik == pytest.approx(ref + 1000.0)
+        else:
+            assert r.escalated_from == "" and r.plan == "mixed" and r.loglik == pytest.approx(ref)
+        assert r.t_done > r.t_submit
+    # the re-run of a request never precedes its first attempt, and fp64 batches hold only escalated rows
+    assert all(p == "mixed" for p, _, _, t in be.launches if t == 0.0)
+    assert sum(n for p, n, _, _ in be.launches if p == "fp64") == len(bad)
+
+
+def test_escalation_only_for_the_named_codes_and_plans():
+    clock = Clock()
+    be = FlakyBackend(clock, {"mixed": 10, "fp64": 40})
+    # HDD_ENOTSPD (-4) is escalated, HDD_ENOCONV is not: the failures come back as they are
+    srv = Server(be, budget_bytes=10_000, max_batch=8, clock=clock, fallback={"mixed": "fp64"}, escalate=(-4,))
+    rng = np.random.default_rng(4)
+    reqs = [srv.submit("mixed", rng.standard_normal(4), np.ones(2)) for _ in range(12)]
+    drive(srv, clock)
+    assert srv.escalated == 0
+    assert all((r.status == (5 | (7 << 8))) == (r.Z[0] < 0) for r in reqs)
+    with pytest.raises(ValueError):
+        Server(be, budget_bytes=10_000, fallback={"mixed": "fp64", "fp64": "mixed"})
+    with pytest.raises(KeyError):
+        Server(be, budget_bytes=10_000, fallback={"mixed": "nope"})
