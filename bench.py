@@ -415,6 +415,8 @@ def run_hdd(args, cfg):
     precision = hdd.HDD_MIXED_FP32 if args.precision == "mixed" else hdd.HDD_FP64
     plan = hdd.Plan(cfg.N, args.leaf or cfg.leaf, prob.phi, prob.obs, cfg.sigma, f=cfg.f, precision=precision,
                     ir_max_iter=args.ir_iters, ir_tol=args.ir_tol, device=local)
+    if args.sweep_fusion is not None:
+        plan.set_sweep_fusion(args.sweep_fusion)
     info = plan.info()
     ws = plan.workspace(B)
     Z = torch.from_numpy(prob.Z).to(dev)
@@ -763,7 +765,8 @@ def run_hdd(args, cfg):
         "clocks": clk.summary(),
         "cpu_baseline": cpu,
         "plan": {"flops_upsweep_per_sample": info["flops_upsweep"], "nodes": info["n_nodes"],
-                 "visited": info["n_visited"], "workspace_gb": plan.workspace_size(B) / 1e9},
+                 "visited": info["n_visited"], "workspace_gb": plan.workspace_size(B) / 1e9,
+                 "sweep_fuse_height": info["sweep_fuse_height"]},
     }
     if rank == 0:
         print(json.dumps(line))
@@ -785,6 +788,9 @@ def main(argv=None):
     ap.add_argument("--leaf", type=int, default=0)
     ap.add_argument("--batch", type=int, default=0, help="samples per step (default: the workload's)")
     ap.add_argument("--ir-iters", type=int, default=2)
+    ap.add_argument("--sweep-fusion", type=int, default=None,
+                    help="largest height of the fused bottom subtrees of the full sweeps (0: level by level; "
+                         "default: the plan's own choice)")
     ap.add_argument("--ir-tol", type=float, default=1e-8)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--policy", type=int, default=1, help="precision-policy leg (FP64 top levels; 0: skip)")

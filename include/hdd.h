@@ -133,6 +133,8 @@ typedef struct {
   double bytes_upsweep_leaf;     /* condensed leaves (at most 16 interior vertices): kappa in; K_gg^-1,
                                     the boundary couplings, y_g and the lower Schur triangle out */
   int32_t n_condensed_leaves;    /* leaves stored as K_gg^-1 and boundary couplings instead of factors */
+  int32_t sweep_fuse_height;     /* height of the bottom subtrees whose full sweeps run fused (0: none;
+                                    hdd_set_sweep_fusion) */
 } hdd_plan_info_t;
 
 typedef struct {
@@ -382,6 +384,22 @@ hdd_status hdd_kappa(hdd_plan_t plan, int32_t batch, void* workspace, double* ka
  *                 tested without any fault.  Leave it off in production.
  * Applies to the plan's later hdd_upsweep calls.  Errors: HDD_EINVAL. */
 hdd_status hdd_set_wait_bound(hdd_plan_t plan, uint32_t polls, int32_t stall_node, int32_t stall_sample);
+
+/* Fused bottom subtrees of the full sweeps (the right-hand-side sweeps and the full
+ * descents of the refinement, hdd_solve_loads): "Leaves to Root" on a new load and
+ * "Root to Leaves" (Sec. 3.4) over every subtree of height <= h, where a subtree is a
+ * node of height <= h whose father is higher, with all its descendants, run as one
+ * kernel with one warp per (subtree, sample) that keeps the values of the subtree's
+ * rectangle on chip; the levels above run as before.  h is the largest height
+ * <= max_height whose subtrees qualify (every front with at most 32 eliminated
+ * vertices and 128 rows, or a condensed leaf; one precision; the shared memory of
+ * eight samples per CTA within 75 KiB); 0 = none.  Plans start with max_height = 2.
+ * The arithmetic per node is the same elimination in another order of operations, so
+ * results agree with the level-by-level sweeps to rounding.  Replaces device tables:
+ * call it when no work of the plan is in flight.  hdd_plan_info reports the height
+ * in use.  Errors: HDD_EINVAL (max_height outside 0..6), HDD_ENOMEM, HDD_ECUDA (the
+ * plan then runs its sweeps level by level). */
+hdd_status hdd_set_sweep_fusion(hdd_plan_t plan, int32_t max_height);
 
 /* Per-kernel timing, for benchmarks.  Between hdd_profile_begin and
  * hdd_profile_end every kernel the library launches for this plan is bracketed

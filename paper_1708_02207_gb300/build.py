@@ -18,7 +18,7 @@ LIB = os.path.join(BUILD, "libhdd.so")
 INCLUDE = os.path.join(os.path.dirname(PKG), "include")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-CU_SOURCES = ["api.cu", "k_front.cu", "k_group.cu", "k_leaf.cu", "k_solve.cu", "k_refine.cu", "k_warp.cu", "k_tc.cu", "k_fused.cu", "k_means.cu", "k_func.cu", "k_data.cu", "multi.cu", "static_ws.cu"]
+CU_SOURCES = ["api.cu", "k_front.cu", "k_group.cu", "k_leaf.cu", "k_solve.cu", "k_refine.cu", "k_warp.cu", "k_tc.cu", "k_fused.cu", "k_means.cu", "k_func.cu", "k_data.cu", "k_sweep.cu", "multi.cu", "static_ws.cu"]
 CXX_SOURCES = ["plan.cpp"]
 
 

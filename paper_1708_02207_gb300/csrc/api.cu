@@ -25,6 +25,7 @@ cudaError_t configure_group_kernels();
 cudaError_t configure_leaf_kernels();
 cudaError_t configure_func_kernels();
 cudaError_t configure_data_kernels();
+cudaError_t configure_sweep_kernels();
 }  // namespace hdd
 
 namespace {
@@ -126,8 +127,18 @@ cudaError_t configure_device(int dev) {
   if (e == cudaSuccess) e = hdd::configure_leaf_kernels();
   if (e == cudaSuccess) e = hdd::configure_func_kernels();
   if (e == cudaSuccess) e = hdd::configure_data_kernels();
+  if (e == cudaSuccess) e = hdd::configure_sweep_kernels();
   if (e == cudaSuccess) g_configured[dev] = true;
   return e;
+}
+
+void free_sweep(hdd::SweepSub& sw) {
+  cudaFree(sw.d_subs);
+  cudaFree(sw.d_sched);
+  cudaFree(sw.d_rec);
+  cudaFree(sw.d_top);
+  sw.d_subs = sw.d_sched = sw.d_top = nullptr;
+  sw.d_rec = nullptr;
 }
 
 void free_device(hdd::Plan& p) {
@@ -146,6 +157,7 @@ void free_device(hdd::Plan& p) {
   }
   cudaFree(p.d_fuse_soff);
   p.d_fuse_soff = nullptr;
+  free_sweep(p.sweep);
   cudaFree(p.d_lam_off);
   cudaFree(p.d_obs_nodes);
   p.d_lam_off = p.d_obs_nodes = nullptr;
@@ -157,6 +169,15 @@ cudaError_t upload(T** dst, const T* src, size_t n) {
   cudaError_t e = cudaMalloc((void**)dst, (n ? n : 1) * sizeof(T));
   if (e != cudaSuccess) return e;
   if (n) e = cudaMemcpy(*dst, src, n * sizeof(T), cudaMemcpyHostToDevice);
+  return e;
+}
+
+cudaError_t upload_sweep(hdd::SweepSub& sw) {
+  if (sw.height == 0) return cudaSuccess;
+  cudaError_t e = upload(&sw.d_subs, sw.subs.data(), sw.subs.size());
+  if (e == cudaSuccess) e = upload(&sw.d_sched, sw.sched.data(), sw.sched.size());
+  if (e == cudaSuccess) e = upload(&sw.d_rec, sw.rec.data(), sw.rec.size());
+  if (e == cudaSuccess) e = upload(&sw.d_top, sw.top_data.data(), sw.top_data.size());
   return e;
 }
 
@@ -286,55 +307,111 @@ cudaError_t run_upsweep(const hdd::Plan& p, int batch, void* ws, const hdd::Rhs&
   return cudaSuccess;
 }
 
-// "Root to Leaves" over the given per-depth lists, writing u (FP64).
-cudaError_t run_descent(const hdd::Plan& p, int batch, void* ws, const std::vector<std::array<int, 3>>& per_depth,
-                        double* u, int64_t u_stride, cudaStream_t st, hdd::Profiler* prof) {
-  const hdd::Layout L = hdd::layout(p, batch);
-  const hdd::Arenas A = arenas(p, L, ws);
-  for (int d = 0; d <= p.depth; ++d) {
+// The sweeps' fused bottom subtrees of a plan for one batch.
+hdd::SubArgs sub_args(const hdd::Plan& p, int batch, const hdd::Arenas& A, bool descent) {
+  const hdd::SweepSub& sw = p.sweep;
+  const size_t E = sw.fp64 ? 8 : 4;
+  auto al16 = [](size_t x) { return (int)((x + 15) & ~(size_t)15); };
+  hdd::SubArgs g{};
+  g.nodes = p.d_nodes;
+  g.maps = p.d_maps;
+  g.subs = sw.d_subs;
+  g.sched = sw.d_sched;
+  g.rec = sw.d_rec;
+  g.A = A;
+  g.N = p.N;
+  g.batch = batch;
+  g.fac_bytes = al16((size_t)sw.f_elems * E);
+  g.y_bytes = descent ? al16((size_t)sw.y_elems * E) : 0;
+  g.region_bytes = al16((size_t)sw.region_elems * E);
+  g.stack_bytes = descent ? 0 : al16((size_t)sw.stack_elems * E);
+  g.warp_bytes = g.fac_bytes + g.y_bytes + g.region_bytes + g.stack_bytes;
+  g.sched_bytes = al16((size_t)sw.max_nodes * hdd::kSchedInts * 4);
+  g.rec_bytes = al16((size_t)sw.max_rec * 2);
+  return g;
+}
+
+// "Root to Leaves" over per-depth lists (indices into `infos`; nodes in `data` on the
+// host and at d_base on the device, at each list's offset).
+cudaError_t descent_levels(const hdd::Plan& p, int batch, const hdd::Arenas& A,
+                           const std::vector<std::array<int, 3>>& per_depth, const std::vector<hdd::ListInfo>& infos,
+                           const std::vector<int32_t>& data, const int32_t* d_base, double* u, int64_t u_stride,
+                           cudaStream_t st, hdd::Profiler* prof) {
+  for (int d = 0; d < (int)per_depth.size(); ++d) {
     for (int kind = 1; kind < 3; ++kind) {   // condensed leaves of this depth
-      const hdd::ListInfo& ll = p.lists[per_depth[d][kind]];
+      const hdd::ListInfo& ll = infos[per_depth[d][kind]];
       if (ll.n == 0) continue;
       ProfScope ps(prof, hdd::kProfDescent, 0.0, st);
-      cudaError_t e = kind == 1 ? hdd::launch_leaf_descent<double>(p.d_nodes, p.d_maps, p.d_lists + ll.off, ll.n,
+      cudaError_t e = kind == 1 ? hdd::launch_leaf_descent<double>(p.d_nodes, p.d_maps, d_base + ll.off, ll.n,
                                                                    batch, A, u, u_stride, st)
-                                : hdd::launch_leaf_descent<float>(p.d_nodes, p.d_maps, p.d_lists + ll.off, ll.n,
+                                : hdd::launch_leaf_descent<float>(p.d_nodes, p.d_maps, d_base + ll.off, ll.n,
                                                                   batch, A, u, u_stride, st);
       if (e != cudaSuccess) return e;
     }
-    const hdd::ListInfo& li = p.lists[per_depth[d][0]];
+    const hdd::ListInfo& li = infos[per_depth[d][0]];
     if (li.n == 0) continue;
     // the lists hold one precision per depth in the plans built here
-    const bool fp64 = p.nodes[p.list_data[li.off]].fp64;
+    const bool fp64 = p.nodes[data[li.off]].fp64;
     // nodes with long interfaces: one CTA per (node, sample), blocked back substitution;
     // otherwise one warp per (node, sample)
     const bool cta = li.max_m >= kSweepCtaMinM;
+    const int32_t* list = d_base + li.off;
     ProfScope ps(prof, hdd::kProfDescent, 0.0, st);
     cudaError_t e;
     if (li.max_nf <= hdd::kTinyMax)
-      e = fp64 ? hdd::launch_descent_tiny<double>(p.d_nodes, p.d_maps, p.d_lists + li.off, li.n, batch, A, u, u_stride, st)
-               : hdd::launch_descent_tiny<float>(p.d_nodes, p.d_maps, p.d_lists + li.off, li.n, batch, A, u, u_stride, st);
+      e = fp64 ? hdd::launch_descent_tiny<double>(p.d_nodes, p.d_maps, list, li.n, batch, A, u, u_stride, st)
+               : hdd::launch_descent_tiny<float>(p.d_nodes, p.d_maps, list, li.n, batch, A, u, u_stride, st);
     else if (cta)
-      e = fp64 ? hdd::launch_descent<double>(p.d_nodes, p.d_maps, p.d_lists + li.off, li.n, batch, A, u, u_stride,
-                                             li.max_b, li.max_m, st)
-               : hdd::launch_descent<float>(p.d_nodes, p.d_maps, p.d_lists + li.off, li.n, batch, A, u, u_stride,
-                                            li.max_b, li.max_m, st);
+      e = fp64 ? hdd::launch_descent<double>(p.d_nodes, p.d_maps, list, li.n, batch, A, u, u_stride, li.max_b,
+                                             li.max_m, st)
+               : hdd::launch_descent<float>(p.d_nodes, p.d_maps, list, li.n, batch, A, u, u_stride, li.max_b,
+                                            li.max_m, st);
     else
-      e = fp64 ? hdd::launch_descent_warp<double>(p.d_nodes, p.d_maps, p.d_lists + li.off, li.n, batch, A, u, u_stride,
-                                                  li.max_nf, li.max_m, st)
-               : hdd::launch_descent_warp<float>(p.d_nodes, p.d_maps, p.d_lists + li.off, li.n, batch, A, u, u_stride,
-                                                 li.max_nf, li.max_m, st);
+      e = fp64 ? hdd::launch_descent_warp<double>(p.d_nodes, p.d_maps, list, li.n, batch, A, u, u_stride, li.max_nf,
+                                                  li.max_m, st)
+               : hdd::launch_descent_warp<float>(p.d_nodes, p.d_maps, list, li.n, batch, A, u, u_stride, li.max_nf,
+                                                 li.max_m, st);
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;
 }
 
-// Right-hand-side sweep (leaves to root) through the stored factors.
+// "Root to Leaves" over the given per-depth lists, writing u (FP64).  The full descent
+// of a plan with fused sweep subtrees runs the levels above them, then the subtrees.
+cudaError_t run_descent(const hdd::Plan& p, int batch, void* ws, const std::vector<std::array<int, 3>>& per_depth,
+                        double* u, int64_t u_stride, cudaStream_t st, hdd::Profiler* prof) {
+  const hdd::Layout L = hdd::layout(p, batch);
+  const hdd::Arenas A = arenas(p, L, ws);
+  const hdd::SweepSub& sw = p.sweep;
+  if (&per_depth == &p.down_all_lists && sw.height > 0 && sw.d_subs) {
+    cudaError_t e =
+        descent_levels(p, batch, A, sw.top_lists, sw.top_infos, sw.top_data, sw.d_top, u, u_stride, st, prof);
+    if (e != cudaSuccess) return e;
+    ProfScope ps(prof, hdd::kProfDescent, 0.0, st);
+    const hdd::SubArgs g = sub_args(p, batch, A, true);
+    return sw.fp64 ? hdd::launch_descent_sub<double>(g, sw.n_sub, sw.smem_desc, u, u_stride, st)
+                   : hdd::launch_descent_sub<float>(g, sw.n_sub, sw.smem_desc, u, u_stride, st);
+  }
+  return descent_levels(p, batch, A, per_depth, p.lists, p.list_data, p.d_lists, u, u_stride, st, prof);
+}
+
+// Right-hand-side sweep (leaves to root) through the stored factors; plans with fused
+// sweep subtrees run those first, then the heights above them.
 cudaError_t run_forward(const hdd::Plan& p, int batch, void* ws, const hdd::Rhs& rhs, cudaStream_t st,
                         hdd::Profiler* prof) {
   const hdd::Layout L = hdd::layout(p, batch);
   const hdd::Arenas A = arenas(p, L, ws);
-  for (int h = 0; h <= p.height; ++h)
+  const hdd::SweepSub& sw = p.sweep;
+  int h0 = 0;
+  if (sw.height > 0 && sw.d_subs) {
+    ProfScope ps(prof, hdd::kProfForward, 0.0, st);
+    const hdd::SubArgs g = sub_args(p, batch, A, false);
+    cudaError_t e = sw.fp64 ? hdd::launch_forward_sub<double>(g, sw.n_sub, sw.smem_fwd, rhs, st)
+                            : hdd::launch_forward_sub<float>(g, sw.n_sub, sw.smem_fwd, rhs, st);
+    if (e != cudaSuccess) return e;
+    h0 = sw.height + 1;
+  }
+  for (int h = h0; h <= p.height; ++h)
     for (int k = 0; k < 4; ++k) {
       const hdd::ListInfo& li = p.lists[p.fwd_lists[h][k]];
       if (li.n == 0) continue;
@@ -589,6 +666,7 @@ hdd_status hdd_plan(const hdd_plan_desc* desc, hdd_plan_t* out) {
     if (e == cudaSuccess) e = upload(&p.d_fuse_soff, p.fuse_soff.data(), p.fuse_soff.size());
     if (e == cudaSuccess) e = upload(&p.d_lam_off, p.lam_off.data(), p.lam_off.size());
     if (e == cudaSuccess) e = upload(&p.d_obs_nodes, p.obs_nodes.data(), p.obs_nodes.size());
+    if (e == cudaSuccess) e = upload_sweep(p.sweep);
     for (auto& fu : p.fusion)
       if (e == cudaSuccess && fu.height > 0) {
         e = upload(&fu.d_roots, fu.roots.data(), fu.roots.size());
@@ -909,6 +987,27 @@ hdd_status hdd_kappa(hdd_plan_t plan, int32_t batch, void* workspace, double* ka
   return e == cudaSuccess ? HDD_OK : fail_cuda(e, "hdd_kappa");
 }
 
+hdd_status hdd_set_sweep_fusion(hdd_plan_t plan, int32_t max_height) {
+  if (!plan) return fail_inval("plan is NULL");
+  if (max_height < 0 || max_height > hdd::kSweepMaxHeight) return fail_inval("max_height must be in 0..6");
+  hdd::Plan& p = plan->p;
+  hdd::SweepSub old = std::move(p.sweep);
+  p.sweep_max_height = max_height;
+  hdd::build_sweep(p, max_height);
+  if (p.device < 0) return HDD_OK;
+  DeviceScope ds(p.device);
+  if (ds.err != cudaSuccess) return fail_cuda(ds.err, "cudaSetDevice");
+  free_sweep(old);
+  const cudaError_t e = upload_sweep(p.sweep);
+  if (e != cudaSuccess) {
+    free_sweep(p.sweep);
+    p.sweep = hdd::SweepSub{};   // the level-by-level sweeps stay usable
+    return e == cudaErrorMemoryAllocation ? (g_err = "device allocation failed", HDD_ENOMEM)
+                                          : fail_cuda(e, "hdd_set_sweep_fusion upload");
+  }
+  return HDD_OK;
+}
+
 hdd_status hdd_set_wait_bound(hdd_plan_t plan, uint32_t polls, int32_t stall_node, int32_t stall_sample) {
   if (!plan) return fail_inval("plan is NULL");
   if (polls == 0) return fail_inval("polls must be >= 1");
@@ -1008,8 +1107,16 @@ hdd_status hdd_plan_info(hdd_plan_t plan, hdd_plan_info_t* info) {
       down += p.lists[p.down_vis_lists[d][kind]].n > 0;
       down_all += p.lists[p.down_all_lists[d][kind]].n > 0;
     }
-  for (int h = 0; h <= p.height; ++h)
+  const hdd::SweepSub& sw = p.sweep;
+  for (int h = sw.height > 0 ? sw.height + 1 : 0; h <= p.height; ++h)
     for (int k = 0; k < 4; ++k) fwd += p.lists[p.fwd_lists[h][k]].n > 0;
+  if (sw.height > 0) {   // fused sweep subtrees: one launch each way, plus the levels above
+    fwd += 1;
+    down_all = 1;
+    for (const auto& l : sw.top_lists)
+      for (int kind = 0; kind < 3; ++kind) down_all += sw.top_infos[l[kind]].n > 0;
+  }
+  info->sweep_fuse_height = sw.height;
   int solve = down + 1;
   int func = 0;
   for (int h = 0; h <= p.height && p.obs_kind == HDD_OBS_MEANS; ++h)

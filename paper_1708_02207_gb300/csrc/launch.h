@@ -203,6 +203,25 @@ cudaError_t launch_syrk_tc(const StepArgs& a, cudaStream_t st);
 // large fronts: fill in global memory, then POTRF of gamma, TRSM of the rest, SYRK into S
 template <typename T> cudaError_t launch_front_large(const StepArgs& a, cudaStream_t st);
 
+// sweeps over the fused bottom subtrees (k_sweep.cu): one warp per (subtree, sample)
+struct SubArgs {
+  const NodeDev* nodes;
+  const int32_t* maps;
+  const int32_t* subs;     // [n_sub x kSubInts]
+  const int32_t* sched;    // [nodes x kSchedInts], pre-order per subtree
+  const int16_t* rec;      // map records
+  Arenas A;
+  int N, batch;
+  // per warp: the subtree's factor range, y_g range (descent), rectangle, stack (sweep)
+  int fac_bytes, y_bytes, region_bytes, stack_bytes, warp_bytes;
+  int sched_bytes, rec_bytes;                  // per CTA
+};
+template <typename T>
+cudaError_t launch_descent_sub(const SubArgs& g, int n_sub, size_t smem, double* u, int64_t u_stride,
+                               cudaStream_t st);
+template <typename T>
+cudaError_t launch_forward_sub(const SubArgs& g, int n_sub, size_t smem, const Rhs& rhs, cudaStream_t st);
+
 // descent (Root to Leaves) over a list of nodes of one depth; u is FP64 [batch x N^2]
 template <typename T>
 cudaError_t launch_descent(const NodeDev* nodes, const int32_t* maps, const int32_t* list, int nlist, int batch,

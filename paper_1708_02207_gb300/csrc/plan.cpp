@@ -276,17 +276,25 @@ std::string build_plan(const hdd_plan_desc& d, Plan& p) {
     if (nd.visited) p.down_visited[nd.depth].push_back(k);
   }
 
-  // factor store offsets (all nodes keep their factors)
+  // factor store and y_g offsets (all nodes keep their factors), in depth-first
+  // pre-order (father, son 0's subtree, son 1's subtree), so that every subtree's
+  // blocks of one precision are contiguous; y_g blocks padded to four entries
   p.f64_stride = p.f32_stride = 0;
   p.y64_stride = p.y32_stride = 0;
-  for (Node& nd : p.nodes) {
-    int64_t& ys = nd.fp64 ? p.y64_stride : p.y32_stride;
-    nd.y_off = ys;
-    ys += nd.m;
-    int64_t sz = nd.linv ? (int64_t)nd.m * (nd.m + 1) / 2 + nd.b : (int64_t)nd.nf * nd.m;
-    int64_t& st = nd.fp64 ? p.f64_stride : p.f32_stride;
-    nd.f_off = st;
-    st += (sz + 31) / 32 * 32;
+  {
+    std::vector<int> todo{0};
+    while (!todo.empty()) {
+      Node& nd = p.nodes[todo.back()];
+      todo.pop_back();
+      if (!nd.leaf()) { todo.push_back(nd.child[1]); todo.push_back(nd.child[0]); }
+      int64_t& ys = nd.fp64 ? p.y64_stride : p.y32_stride;
+      nd.y_off = ys;
+      ys += (nd.m + 3) / 4 * 4;
+      int64_t sz = nd.linv ? (int64_t)nd.m * (nd.m + 1) / 2 + nd.b : (int64_t)nd.nf * nd.m;
+      int64_t& st = nd.fp64 ? p.f64_stride : p.f32_stride;
+      nd.f_off = st;
+      st += (sz + 31) / 32 * 32;
+    }
   }
 
   // tensor-core staging (large FP32 fronts): lives within one height step
@@ -423,23 +431,7 @@ std::string build_plan(const hdd_plan_desc& d, Plan& p) {
   p.list_data.clear();
   p.lists.clear();
   auto add_list = [&](const std::vector<int>& v) {
-    ListInfo li;
-    li.off = (int64_t)p.list_data.size();
-    li.n = (int)v.size();
-    for (int k : v) {
-      p.list_data.push_back(k);
-      const Node& nd = p.nodes[k];
-      li.max_nf = std::max(li.max_nf, nd.nf);
-      li.max_m = std::max(li.max_m, nd.m);
-      li.max_b = std::max(li.max_b, nd.b);
-      if (nd.leaf()) li.max_rect = std::max(li.max_rect, (nd.x1 - nd.x0 + 1) * (nd.y1 - nd.y0 + 1));
-      const double m = nd.m, b = nd.b;
-      li.fl_chol += 2.0 * m * m * m / 3.0;
-      li.fl_trsm += 2.0 * (b + 1.0) * m * m / 2.0;
-      li.fl_syrk += 2.0 * b * (b + 1.0) / 2.0 * m;
-      li.fl_rhs += 2.0 * (b + 1.0) * m;
-    }
-    p.lists.push_back(li);
+    p.lists.push_back(make_list(p, v, p.list_data));
     return (int)p.lists.size() - 1;
   };
   p.step_lists.assign(p.height + 1, {0, 0, 0, 0, 0, 0, 0, 0});
@@ -567,11 +559,161 @@ std::string build_plan(const hdd_plan_desc& d, Plan& p) {
     p.by_desc_all += down;
     if (nd.visited) p.by_desc_vis += down;
   }
+  build_sweep(p, p.sweep_max_height);
   const double NN = (double)p.N * p.N;
   p.by_residual = 2.0 * p.n_t * 8.0 + 2.0 * NN * 8.0;   // kappa and u in, r out
   p.by_assemble = p.n_z * 8.0 + p.n_t * (p.precision == HDD_MIXED_FP32 ? 12.0 : 8.0);
   p.by_kl_basis = (double)p.n_t * p.n_z * 8.0;
   return "";
+}
+
+ListInfo make_list(const Plan& p, const std::vector<int>& v, std::vector<int32_t>& data) {
+  ListInfo li;
+  li.off = (int64_t)data.size();
+  li.n = (int)v.size();
+  for (int k : v) {
+    data.push_back(k);
+    const Node& nd = p.nodes[k];
+    li.max_nf = std::max(li.max_nf, nd.nf);
+    li.max_m = std::max(li.max_m, nd.m);
+    li.max_b = std::max(li.max_b, nd.b);
+    if (nd.leaf()) li.max_rect = std::max(li.max_rect, (nd.x1 - nd.x0 + 1) * (nd.y1 - nd.y0 + 1));
+    const double m = nd.m, b = nd.b;
+    li.fl_chol += 2.0 * m * m * m / 3.0;
+    li.fl_trsm += 2.0 * (b + 1.0) * m * m / 2.0;
+    li.fl_syrk += 2.0 * b * (b + 1.0) / 2.0 * m;
+    li.fl_rhs += 2.0 * (b + 1.0) * m;
+  }
+  return li;
+}
+
+namespace {
+size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
+int64_t fac_block(const Node& nd) {   // padded factor block of a node (elements)
+  const int64_t sz = nd.linv ? (int64_t)nd.m * (nd.m + 1) / 2 + nd.b : (int64_t)nd.nf * nd.m;
+  return (sz + 31) / 32 * 32;
+}
+}  // namespace
+
+void build_sweep(Plan& p, int max_height) {
+  SweepSub out;
+  const int nn = (int)p.nodes.size();
+  auto eligible = [&](const Node& nd) {
+    if (nd.linv) return nd.m <= kLeafInvMax && nd.b <= kLeafInvMaxB;
+    return nd.m >= 1 && nd.m <= 32 && nd.nf - 1 <= 128;
+  };
+  for (int H = std::min(max_height, kSweepMaxHeight); H >= 1; --H) {
+    SweepSub sw;
+    sw.height = H;
+    std::vector<int> roots;
+    for (int k = 0; k < nn; ++k) {
+      const Node& nd = p.nodes[k];
+      if (nd.height <= H && (nd.parent < 0 || p.nodes[nd.parent].height > H)) roots.push_back(k);
+    }
+    bool ok = !roots.empty();
+    const bool fp64 = ok && p.nodes[roots[0]].fp64;
+    const size_t E = fp64 ? 8 : 4;
+    std::vector<char> fused(nn, 0);
+    for (size_t q = 0; q < roots.size() && ok; ++q) {
+      const int r = roots[q];
+      const Node& rt = p.nodes[r];
+      // pre-order: father, son 0's subtree, son 1's subtree
+      std::vector<int> order, todo{r};
+      while (!todo.empty()) {
+        const int k = todo.back();
+        todo.pop_back();
+        order.push_back(k);
+        const Node& nd = p.nodes[k];
+        if (!nd.leaf()) { todo.push_back(nd.child[1]); todo.push_back(nd.child[0]); }
+      }
+      const int w = rt.x1 - rt.x0 + 1, h = rt.y1 - rt.y0 + 1;
+      int32_t desc[kSubInts] = {(int32_t)(sw.sched.size() / kSchedInts), (int32_t)order.size(),
+                                (int32_t)sw.rec.size(), 0, rt.x0, rt.y0, w, h,
+                                (int32_t)(rt.f_off & 0xffffffff), (int32_t)(rt.f_off >> 32), 0,
+                                (int32_t)rt.y_off, 0, 0, 0, 0};
+      const size_t rec0 = sw.rec.size();
+      int64_t f_len = 0, y_len = 0;
+      for (int k : order) {
+        const Node& nd = p.nodes[k];
+        if (!eligible(nd) || nd.fp64 != fp64 || (!nd.leaf() && nd.linv)) { ok = false; break; }
+        fused[k] = 1;
+        const int nr = nd.nf - 1;
+        const int kind = nd.linv ? 2 : (nd.leaf() ? 1 : 0);
+        const int b0 = nd.leaf() ? 0 : p.nodes[nd.child[0]].b, b1 = nd.leaf() ? 0 : p.nodes[nd.child[1]].b;
+        // the depth-first layout puts the subtree's blocks one after the other
+        if (nd.f_off != rt.f_off + f_len || nd.y_off != rt.y_off + y_len) { ok = false; break; }
+        const int32_t ent[kSchedInts] = {k, kind | nd.m << 2 | nd.b << 8 | nd.nf << 20, (int32_t)(sw.rec.size() - rec0),
+                                         (int32_t)nd.y_off, (int32_t)f_len, (int32_t)y_len, b0, b1};
+        f_len += fac_block(nd);
+        y_len += (nd.m + 3) / 4 * 4;
+        sw.sched.insert(sw.sched.end(), ent, ent + kSchedInts);
+        const int32_t* vid = p.maps.data() + nd.map_off;
+        auto pad = [&]() { if (sw.rec.size() & 1) sw.rec.push_back(0); };
+        for (int i = 0; i < nr; ++i) {
+          const int x = vid[i] % p.N - rt.x0, y = vid[i] / p.N - rt.y0;
+          if (x < 0 || x >= w || y < 0 || y >= h) { ok = false; break; }
+          sw.rec.push_back((int16_t)(y * w + x));
+        }
+        pad();
+        if (kind == 0) {   // positions in the sons' condensed right-hand sides
+          for (int s = 0; s < 2; ++s) {
+            const int32_t* pos = vid + nr + s * nd.nf;
+            for (int i = 0; i < nr; ++i) sw.rec.push_back((int16_t)pos[i]);
+            pad();
+          }
+        } else if (kind == 2) {   // interior row coupled to each boundary row
+          for (int i = 0; i < nd.b; ++i) sw.rec.push_back((int16_t)vid[nr + i]);
+          pad();
+        }
+      }
+      if (!ok || (size_t)w * h > 32767 || f_len > (1 << 24)) { ok = false; break; }
+      desc[3] = (int32_t)(sw.rec.size() - rec0);
+      desc[10] = (int32_t)f_len;
+      desc[12] = (int32_t)y_len;
+      sw.f_elems = std::max(sw.f_elems, (int)f_len);
+      sw.y_elems = std::max(sw.y_elems, (int)y_len);
+      sw.subs.insert(sw.subs.end(), desc, desc + kSubInts);
+      sw.max_nodes = std::max(sw.max_nodes, (int)order.size());
+      sw.max_rec = std::max(sw.max_rec, desc[3]);
+      sw.region_elems = std::max(sw.region_elems, w * h);
+      // the sweep's stack of condensed right-hand sides (sons' on top of each other until
+      // their father takes them), in the sweep's order: reversed pre-order
+      int sp = 0, peak = 0;
+      for (size_t i = order.size(); i-- > 1;) {
+        const Node& nd = p.nodes[order[i]];
+        if (!nd.leaf()) sp -= p.nodes[nd.child[0]].b + p.nodes[nd.child[1]].b;
+        sp += nd.b;
+        peak = std::max(peak, sp);
+      }
+      sw.stack_elems = std::max(sw.stack_elems, peak);
+    }
+    if (!ok) continue;
+    sw.fp64 = fp64;
+    sw.n_sub = (int)roots.size();
+    const size_t shared = align16((size_t)sw.max_nodes * kSchedInts * 4) + align16((size_t)sw.max_rec * 2);
+    const size_t fac = align16((size_t)sw.f_elems * E), yg = align16((size_t)sw.y_elems * E);
+    const size_t region = align16((size_t)sw.region_elems * E), stack = align16((size_t)sw.stack_elems * E);
+    sw.smem_desc = shared + kSubWarps * (fac + yg + region);
+    sw.smem_fwd = shared + kSubWarps * (fac + region + stack);
+    if (std::max(sw.smem_desc, sw.smem_fwd) > (size_t)kSubSmemCap) continue;
+    // the descent's levels above the subtrees, by depth and kind
+    sw.top_lists.assign(p.depth + 1, {0, 0, 0});
+    for (int d = 0; d <= p.depth; ++d) {
+      std::vector<int> all[3];
+      for (int k : p.down_all[d]) {
+        if (fused[k]) continue;
+        const Node& nd = p.nodes[k];
+        all[nd.linv ? (nd.fp64 ? 1 : 2) : 0].push_back(k);
+      }
+      for (int kind = 0; kind < 3; ++kind) {
+        sw.top_infos.push_back(make_list(p, all[kind], sw.top_data));
+        sw.top_lists[d][kind] = (int)sw.top_infos.size() - 1;
+      }
+    }
+    out = std::move(sw);
+    break;
+  }
+  p.sweep = std::move(out);
 }
 
 static size_t align256(size_t x) { return (x + 255) / 256 * 256; }

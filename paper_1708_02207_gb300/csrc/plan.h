@@ -69,6 +69,47 @@ struct Step {
   std::vector<int> tiny64, small64, large64, tiny32, small32, large32, linv64, linv32;
 };
 
+// Fused bottom subtrees of the right-hand-side sweep and of the full descent: one warp
+// per (subtree, sample) keeps the vertex values of the subtree's rectangle in shared
+// memory and copies the subtree's factor blocks (contiguous in the depth-first factor
+// layout) into shared memory at once (k_sweep.cu).  A subtree is a node of height
+// <= height whose father is higher, with all its descendants; every node in it has
+// m <= 32 eliminated vertices and at most 128 front rows, or is a condensed leaf.
+constexpr int kSweepMaxHeight = 6;        // largest subtree height allowed
+constexpr int kSweepDefaultHeight = 2;    // a new plan's limit (fastest measured at 513^2 with 4 x 4-cell leaves)
+constexpr int kSubInts = 16;              // ints per subtree descriptor
+constexpr int kSchedInts = 8;             // ints per scheduled node
+constexpr int kSubWarps = 8;              // warps (samples) per CTA
+constexpr int kSubSmemCap = 75 * 1024;    // shared memory per CTA (three CTAs per SM)
+struct SweepSub {
+  int height = 0;            // 0: the sweeps run level by level
+  bool fp64 = false;
+  int n_sub = 0, max_nodes = 0, max_rec = 0;   // max_rec: int16 entries of one subtree's map records
+  int region_elems = 0, stack_elems = 0;
+  int f_elems = 0, y_elems = 0;                // largest factor and y_g ranges of a subtree
+  size_t smem_desc = 0, smem_fwd = 0;          // bytes per CTA
+  // per subtree: sched offset (nodes), node count, rec offset and length (int16 entries),
+  // rectangle x0, y0, width, height (vertices), factor range start (lo, hi) and length,
+  // y_g range start and length (elements of the subtree's precision), 3 unused
+  std::vector<int32_t> subs;
+  // per node, pre-order (root first): node, kind | m << 2 | b << 8 | nf << 20, rec offset
+  // within the subtree's records, y_off, factor and y_g offsets within the subtree's
+  // ranges, b of son 0, b of son 1
+  std::vector<int32_t> sched;
+  // per node: local index of each front row in the rectangle [nf-1]; then, for fathers,
+  // the row's position in each son's condensed right-hand side [nf-1] x 2 (-1: none); for
+  // condensed leaves, the interior row coupled to each boundary row [b]; each padded to even
+  std::vector<int16_t> rec;
+  // down_all_lists without the fused nodes (their own list table)
+  std::vector<ListInfo> top_infos;
+  std::vector<int32_t> top_data;
+  std::vector<std::array<int, 3>> top_lists;
+  int32_t* d_subs = nullptr;
+  int32_t* d_sched = nullptr;
+  int16_t* d_rec = nullptr;
+  int32_t* d_top = nullptr;
+};
+
 struct Plan {
   // problem
   int N = 0, leaf = 0, n_z = 0, n_obs = 0, n_t = 0, device = -1;
@@ -127,6 +168,10 @@ struct Plan {
   std::vector<int32_t> fuse_soff;   // per node
   int32_t* d_fuse_soff = nullptr;
 
+  // fused bottom subtrees of the sweeps (hdd_set_sweep_fusion)
+  SweepSub sweep;
+  int sweep_max_height = kSweepDefaultHeight;
+
   // node lists concatenated (host copy of d_lists) and their descriptors
   std::vector<int32_t> list_data;
   std::vector<ListInfo> lists;
@@ -176,6 +221,11 @@ constexpr int kLeafInvMaxB = 63;
 
 // Build the host plan; returns an empty string on success, else an error text.
 std::string build_plan(const hdd_plan_desc& d, Plan& p);
+// The fused sweep subtrees of a built plan for subtree heights up to max_height (0: none);
+// host tables only (the caller uploads them).
+void build_sweep(Plan& p, int max_height);
+// A node list's descriptor (sizes and algorithmic flops), its nodes appended to data.
+ListInfo make_list(const Plan& p, const std::vector<int>& v, std::vector<int32_t>& data);
 
 // Workspace layout for a batch (byte offsets, 256-byte aligned).
 struct Layout {

@@ -25,7 +25,7 @@ EXPORTED = [
     "hdd_node_indices", "hdd_status_string", "hdd_last_error", "hdd_evaluate_static",
     "hdd_profile_begin", "hdd_profile_end", "hdd_kappa", "hdd_solve_loads", "hdd_subdomain_means",
     "hdd_set_wait_bound", "hdd_mean_functionals", "hdd_multi_create", "hdd_multi_destroy", "hdd_multi_upsweep",
-    "hdd_multi_evaluate", "hdd_multi_info", "hdd_data_scratch_size", "hdd_solve_data",
+    "hdd_multi_evaluate", "hdd_multi_info", "hdd_data_scratch_size", "hdd_solve_data", "hdd_set_sweep_fusion",
 ]
 STATIC_WORKSPACE_BYTES = 32 << 20
 
@@ -54,6 +54,7 @@ class PlanInfo(C.Structure):
         ("bytes_descent_all", C.c_double), ("bytes_descent_visited", C.c_double),
         ("bytes_residual", C.c_double), ("bytes_assemble", C.c_double), ("bytes_kl_basis", C.c_double),
         ("bytes_upsweep_leaf", C.c_double), ("n_condensed_leaves", C.c_int32),
+        ("sweep_fuse_height", C.c_int32),
     ]
 
 
@@ -92,6 +93,7 @@ def load_library() -> C.CDLL:
     lib.hdd_solve_loads.argtypes = [vp, i32, vp, vp, i32, vp, vp, vp]
     lib.hdd_subdomain_means.argtypes = [vp, i32, vp, C.c_int64, vp, vp]
     lib.hdd_set_wait_bound.argtypes = [vp, C.c_uint32, i32, i32]
+    lib.hdd_set_sweep_fusion.argtypes = [vp, i32]
     lib.hdd_mean_functionals.argtypes = [vp, i32, vp, vp, vp, vp]
     lib.hdd_multi_create.argtypes = [C.POINTER(vp), i32, pi32, C.POINTER(vp), C.POINTER(vp)]
     lib.hdd_multi_destroy.argtypes = [vp]
@@ -215,6 +217,11 @@ class Plan:
         """hdd_set_wait_bound: polls of each bounded device wait; (stall_node, stall_sample)
         is the test hook that makes one wait run out (-1: off)."""
         _check(self.lib.hdd_set_wait_bound(self._h, polls, stall_node, stall_sample), "hdd_set_wait_bound")
+
+    def set_sweep_fusion(self, max_height: int = 2):
+        """hdd_set_sweep_fusion: full sweeps over bottom subtrees of height <= max_height in
+        one kernel (0: level by level); info()["sweep_fuse_height"] is the height in use."""
+        _check(self.lib.hdd_set_sweep_fusion(self._h, max_height), "hdd_set_sweep_fusion")
 
     # ---- per-kernel timing ---------------------------------------------
     def profile_begin(self):
