@@ -765,6 +765,128 @@ __global__ void __launch_bounds__(256) k_trsm(StepArgs a) {   // R rows per CTA
     write_tc_tiles(reinterpret_cast<const float*>(X), ldx, nd, a.arenas, s, blockIdx.x * R, nr, r0 + nr == nf);
 }
 
+// TRSM of the large FP32 fronts, X = K_Bg L_gg^-T over the rows below gamma (the
+// bordered row included), the same blocked arithmetic as k_trsm with wider trailing
+// updates: 32 rows per CTA with their m columns in shared memory; per 32-column panel
+// X_p <- X_p inv(L_pp)^T (the inverted diagonal block that POTRF wrote), then the
+// columns to its right in 128-column chunks, X_c -= X_p L_cp^T, each thread a 4 x 4
+// register tile (two 16-byte shared loads per 16 multiply-adds; the 4 x 2 tile of
+// k_trsm spent six scalar loads per eight).  The next chunk of L (32 x 128, 16 values
+// per thread) is loaded into registers while the current one is applied, the next
+// inverted block during the panel.
+constexpr int kTrwR = 32, kTrwC = 128, kTrwCap = 760;
+
+__global__ void __launch_bounds__(256, 3) k_trsm_wide(StepArgs a) {
+  const int node = a.list[blockIdx.y];
+  const int s = blockIdx.z;
+  bind_plan(a, node);
+  if (s >= a.batch) return;
+  const NodeDev nd = a.nodes[node];
+  const int nf = nd.nf, m = nd.m;
+  const int r0 = m + blockIdx.x * kTrwR;
+  if (r0 >= nf || m == 0) return;
+  const int nr = min(kTrwR, nf - r0);
+  float* A = node_F<float>(a.arenas, nd, s);
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float* L = reinterpret_cast<float*>(smem_raw);   // [32][36]: L[l][c] = inv(L_pp)[c][l]
+  float* Lc = L + 32 * 36;                         // [32][kTrwC] the panel's columns right of it
+  float* X = Lc + 32 * kTrwC;                      // [m][32] the CTA's rows
+  const int tid = threadIdx.x;
+  for (int idx = tid; idx < m * kTrwR; idx += blockDim.x) {
+    const int c = idx >> 5, r = idx & 31;
+    X[idx] = (r < nr) ? A[(int64_t)c * nf + r0 + r] : 0.0f;
+  }
+  const float* G0 = reinterpret_cast<const float*>(a.arenas.inv + (int64_t)s * a.arenas.inv_stride + nd.inv_off);
+  float gin[4], pre[16];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) gin[k] = G0[tid + k * 256];
+  // chunk (j0, c0): Lc[l][cc] = L[c0 + cc][j0 + l] = A[(j0 + l) nf + c0 + cc]; thread t
+  // loads column cc = t & 127 of rows l = 2 k + (t >> 7)
+  const int fc = tid & (kTrwC - 1), fl = tid >> 7;
+  auto fetch = [&](int j0, int c0) {
+#pragma unroll
+    for (int k = 0; k < 16; ++k)
+      pre[k] = (c0 + fc < m) ? A[(int64_t)(j0 + 2 * k + fl) * nf + c0 + fc] : 0.0f;
+  };
+  const int rg = tid & 7, cg = tid >> 3;   // update tile: rows 4 rg .. 4 rg + 3, columns 4 cg .. 4 cg + 3
+  for (int j0 = 0; j0 < m; j0 += 32) {
+    const int jb = min(32, m - j0);
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {   // G0[l * 32 + c] = inv[c][l] -> L[l][c], zero where c < l
+      const int idx = tid + k * 256, l = idx >> 5, c = idx & 31;
+      L[l * 36 + c] = l <= c ? gin[k] : 0.0f;
+    }
+    __syncthreads();
+    if (j0 + 32 < m)
+#pragma unroll
+      for (int k = 0; k < 4; ++k) gin[k] = G0[(j0 / 32 + 1) * 1024 + tid + k * 256];
+    if (j0 + jb < m) fetch(j0, j0 + jb);   // a full panel (jb = 32) precedes any chunk
+    {   // X_p <- X_p inv(L_pp)^T: x_c = sum_{l <= c} x_l inv[c][l]; one row, four columns per
+        // thread, over l <= the last of them only (the inverse is lower triangular)
+      const int r = tid & 31, cb = (tid >> 5) * 4;
+      float acc[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+      const int lend = min(jb, cb + 4);
+      for (int l = 0; l < lend; ++l) {
+        const float x = X[(j0 + l) * kTrwR + r];
+        const float4 g = *reinterpret_cast<const float4*>(L + l * 36 + cb);
+        acc[0] += x * g.x;
+        acc[1] += x * g.y;
+        acc[2] += x * g.z;
+        acc[3] += x * g.w;
+      }
+      __syncthreads();
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+        if (cb + q < jb) X[(j0 + cb + q) * kTrwR + r] = acc[q];
+    }
+    for (int c0 = j0 + jb; c0 < m; c0 += kTrwC) {
+      __syncthreads();
+#pragma unroll
+      for (int k = 0; k < 16; ++k) Lc[(2 * k + fl) * kTrwC + fc] = pre[k];
+      __syncthreads();
+      if (c0 + kTrwC < m) fetch(j0, c0 + kTrwC);
+      if (c0 + 4 * cg >= m) continue;   // no column of this thread's tile in the chunk
+      float acc[4][4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+#pragma unroll
+        for (int w = 0; w < 4; ++w) acc[q][w] = 0.0f;
+#pragma unroll 8
+      for (int l = 0; l < 32; ++l) {
+        const float4 x = *reinterpret_cast<const float4*>(X + (j0 + l) * kTrwR + 4 * rg);
+        const float4 y = *reinterpret_cast<const float4*>(Lc + l * kTrwC + 4 * cg);
+        const float xv[4] = {x.x, x.y, x.z, x.w};
+        const float yv[4] = {y.x, y.y, y.z, y.w};
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+#pragma unroll
+          for (int w = 0; w < 4; ++w) acc[q][w] += xv[q] * yv[w];
+      }
+#pragma unroll
+      for (int w = 0; w < 4; ++w) {
+        const int c = c0 + 4 * cg + w;
+        if (c < m) {
+          float4* xc = reinterpret_cast<float4*>(X + c * kTrwR + 4 * rg);
+          float4 v = *xc;
+          v.x -= acc[0][w]; v.y -= acc[1][w]; v.z -= acc[2][w]; v.w -= acc[3][w];
+          *xc = v;
+        }
+      }
+    }
+  }
+  __syncthreads();
+  for (int idx = tid; idx < m * kTrwR; idx += blockDim.x) {
+    const int c = idx >> 5, r = idx & 31;
+    if (r < nr) A[(int64_t)c * nf + r0 + r] = X[idx];
+  }
+  if (r0 + nr == nf) {   // this block holds the bordered row: y_g
+    float* Y = node_Y<float>(a.arenas, nd, s);
+    for (int c = tid; c < m; c += blockDim.x) Y[c] = X[c * kTrwR + (nr - 1)];
+  }
+  if (nd.tc_off >= 0) write_tc_tiles(X, kTrwR, nd, a.arenas, s, blockIdx.x * kTrwR, nr, r0 + nr == nf);
+}
+
 // SYRK: S -= X X^T with X = F[m:nf, 0:m] (b+1 rows incl. the right-hand side).
 // One CTA per (64 x 64 lower tile pair, node, sample), 4 x 4 per thread.
 constexpr int kSyrkTile = 64, kSyrkK = 16;
@@ -895,7 +1017,13 @@ cudaError_t launch_front_large(const StepArgs& a, cudaStream_t st) {
     }
     if (a.prof) a.prof->end(st);
   }
-  if (!fused_pt) {
+  if (!fused_pt && std::is_same<T, float>::value && a.max_m <= kTrwCap) {
+    const size_t smem = ((size_t)a.max_m * kTrwR + 32 * 36 + 32 * kTrwC) * sizeof(float);
+    dim3 grid((a.max_b + 1 + kTrwR - 1) / kTrwR, a.nlist, a.batch);
+    if (a.prof) a.prof->begin(kProfTrsm, a.fl_trsm, st);
+    k_trsm_wide<<<grid, 256, smem, st>>>(a);
+    if (a.prof) a.prof->end(st);
+  } else if (!fused_pt) {
     constexpr int R = TrsmShape<T>::rows;
     const size_t xrows = (size_t)min(a.max_m, TrsmShape<T>::cap);
     const size_t smem = (xrows * R + 32 * 33 + 3 + 32 * 64) * sizeof(T) + 16;
@@ -941,6 +1069,7 @@ cudaError_t configure_front_kernels() {
   if ((e = cudaFuncSetAttribute(k_chol_trsm<double, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
   if ((e = cudaFuncSetAttribute(k_trsm<double, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
   if ((e = cudaFuncSetAttribute(k_trsm<float, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
+  if ((e = cudaFuncSetAttribute(k_trsm_wide, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
   return cudaSuccess;
 }
 

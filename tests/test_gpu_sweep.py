@@ -35,8 +35,8 @@ def run(hdd, plan, Z, c):
     return u.cpu().numpy(), uo.cpu().numpy(), st.cpu().numpy(), st2.cpu().numpy()
 
 
-@pytest.mark.parametrize("N,leaf,prec,heights", [(65, 4, 1, (1, 2, 3)), (129, 4, 1, (2, 3)), (50, 5, 1, (2, 4)),
-                                                 (33, 4, 0, (1, 2)), (65, 3, 0, (3, 5))])
+@pytest.mark.parametrize("N,leaf,prec,heights", [(65, 4, 1, (1, 2, 3)), (129, 4, 1, (2, 3)), (50, 5, 1, (1, 2, 6)),
+                                                 (33, 4, 0, (1, 2)), (65, 3, 0, (1, 3, 6))])
 def test_fused_equals_level_by_level(hdd, N, leaf, prec, heights):
     phi, Z = small_problem(N, n_z=20, corr_len=0.2, variance=2.0, batch=11, seed=N + 7 * leaf)
     plan = hdd.Plan(N, leaf, phi, w.obs_vertices(N, 4), 0.01, precision=prec, ir_max_iter=2 if prec else 0,
@@ -45,9 +45,14 @@ def test_fused_equals_level_by_level(hdd, N, leaf, prec, heights):
     plan.set_sweep_fusion(0)
     assert plan.info()["sweep_fuse_height"] == 0
     ref = run(hdd, plan, Z, c)
+    used = set()
     for h in heights:
         plan.set_sweep_fusion(h)
-        assert plan.info()["sweep_fuse_height"] == h
+        hu = plan.info()["sweep_fuse_height"]
+        assert 1 <= hu <= h   # the largest height <= h whose subtrees fit
+        if hu in used:
+            continue
+        used.add(hu)
         got = run(hdd, plan, Z, c)
         assert (got[2] == 0).all() and (got[3] == 0).all()
         assert rel_err_field(got[0].reshape(-1, N * N), ref[0].reshape(-1, N * N)).max() <= 1e-13
@@ -58,8 +63,8 @@ def test_fused_loads_match_the_oracle(hdd):
     N = 129
     phi, Z = small_problem(N, n_z=20, corr_len=0.2, variance=2.0, batch=3, seed=5)
     plan = hdd.Plan(N, 4, phi, w.obs_vertices(N, 4), 0.01)
-    plan.set_sweep_fusion(3)
-    assert plan.info()["sweep_fuse_height"] == 3
+    plan.set_sweep_fusion(6)
+    assert plan.info()["sweep_fuse_height"] >= 2   # FP64 subtrees: height 2 fits the shared-memory budget
     c = np.random.default_rng(2).standard_normal((3, 1, N * N)) / (N - 1) ** 2
     u, _, st, _ = run(hdd, plan, Z, c)
     assert (st == 0).all()
