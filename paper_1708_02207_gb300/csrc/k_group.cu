@@ -73,29 +73,34 @@ struct Group {
 };
 
 // Adds a son's lower Schur triangle ((b+1) x (b+1), column-major) into the front
-// through its up map ups (son row -> front row).  The lower entries are walked
-// in packed column order: a thread starts at its rank and advances by the group
-// size, carrying its (row, column) along (no division); four entries per pass,
-// loads first.
+// through its up map ups (son row -> front row).  The triangle of n = b + 1 columns
+// is walked as ceil(n / 2) folded columns of n + 1 entries (column c followed by
+// column n - 1 - c, which together hold n + 1 entries; for odd n the middle column
+// stands alone), so entry e of the walk maps to its (row, column) without a loop;
+// four entries per pass, loads first.
 template <typename T, class Grp>
 __device__ __forceinline__ void add_son(T* K, int ld, const NodeDev& ch, const int* ups, const Arenas& A, int s,
                                         const Grp& g) {
-  const int ldc = ch.b + 1;
-  const int total = ldc * (ldc + 1) / 2;
+  const int n = ch.b + 1;
+  const int total = n * (n + 1) / 2;
   const int64_t base = (int64_t)s * (ch.fp64 ? A.s64_stride : A.s32_stride) + ch.s_off;
-  int c = 0, off = g.t;   // entry = (c + off, c)
-  while (c < ldc && off >= ldc - c) { off -= ldc - c; ++c; }
+  const float inv_w = 1.0f / (float)(n + 1);
   for (int i0 = g.t; i0 < total; i0 += 4 * g.size) {
     T v[4];
     int rr[4], cc[4];
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-      const bool use = i0 + q * g.size < total;
-      rr[q] = c + off;
-      cc[q] = c;
-      v[q] = use ? (ch.fp64 ? (T)A.s64[base + c * ldc + c + off] : (T)A.s32[base + c * ldc + c + off]) : (T)0;
-      off += g.size;
-      while (c < ldc && off >= ldc - c) { off -= ldc - c; ++c; }
+      const int e = i0 + q * g.size;
+      int f = (int)((float)e * inv_w);   // folded column, corrected for rounding
+      if (f * (n + 1) > e) --f;
+      if ((f + 1) * (n + 1) <= e) ++f;
+      const int p = e - f * (n + 1);
+      const bool first = p < n - f;      // in column f, else in column n - 1 - f
+      cc[q] = first ? f : n - 1 - f;
+      rr[q] = first ? f + p : cc[q] + (p - (n - f));
+      const bool use = e < total;
+      const int64_t at = base + (int64_t)cc[q] * n + rr[q];
+      v[q] = use ? (ch.fp64 ? (T)A.s64[at] : (T)A.s32[at]) : (T)0;
     }
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
@@ -183,31 +188,56 @@ __global__ void __launch_bounds__(256) k_front_group(StepArgs a, int ld, int fr_
   }
   g.sync();
 
-  // 2. left-looking Cholesky of the gamma columns; rows of a column are spread
-  // over the group
+  // 2. left-looking Cholesky of the gamma columns in blocks of four; rows are spread
+  // over the group.  A block's columns first take the products with every column to
+  // its left (one 16-byte load of the four columns' entries per row entry), then, one
+  // by one, the products within the block, each column's products summed before they
+  // are subtracted from its entries: the entry is usually much larger than what is
+  // left of it, and few roundings at its magnitude are enough.
   bool bad = false;
-  for (int k = 0; k < m; ++k) {
-    const T* rowk = K + k;   // entries (k, l) = K[l * ld + k]
-    for (int r = k + g.t; r < nf; r += g.size) {
-      T acc = K[k * ld + r];
-      if (r == nf - 1 && !nd.leaf) acc += (T)a.rhs(s, map[k]);   // father: load of its gamma vertex
-      // the products are summed first and subtracted once: the entry is usually much
-      // larger than what is left of it, and one rounding at its magnitude is enough
-      T dot = (T)0;
-#pragma unroll 4
-      for (int l = 0; l < k; ++l) dot += K[l * ld + r] * rowk[l * ld];
-      K[k * ld + r] = acc - dot;
+  for (int kb = 0; kb < m; kb += 4) {
+    const int nbk = min(4, m - kb);
+    for (int r = kb + g.t; r < nf; r += g.size) {
+      T dot[4] = {(T)0, (T)0, (T)0, (T)0};
+#pragma unroll 2
+      for (int l = 0; l < kb; ++l) {
+        const T x = K[l * ld + r];
+        T y[4];
+        ld4(K + l * ld + kb, y);   // entries (kb .. kb + 3, l)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) dot[q] += x * y[q];
+      }
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int k = kb + q;
+        if (q < nbk && r >= k) {
+          T acc = K[k * ld + r];
+          if (r == nf - 1 && !nd.leaf) acc += (T)a.rhs(s, map[k]);   // father: load of its gamma vertex
+          K[k * ld + r] = acc - dot[q];
+        }
+      }
     }
     g.sync();
-    T p = K[k * ld + k];
-    if (!(p > (T)0) || !isfinite(p)) {   // not SPD: record, continue with a unit pivot
-      bad = true;
-      p = (T)1;
+    for (int q = 0; q < nbk; ++q) {
+      const int k = kb + q;
+      if (q > 0) {   // products with the block's earlier columns
+        for (int r = k + g.t; r < nf; r += g.size) {
+          T dot = (T)0;
+          for (int l = kb; l < k; ++l) dot += K[l * ld + r] * K[l * ld + k];
+          K[k * ld + r] -= dot;
+        }
+        g.sync();
+      }
+      T p = K[k * ld + k];
+      if (!(p > (T)0) || !isfinite(p)) {   // not SPD: record, continue with a unit pivot
+        bad = true;
+        p = (T)1;
+      }
+      const T d = sqrt(p), inv = (T)1 / d;
+      for (int r = k + 1 + g.t; r < nf; r += g.size) K[k * ld + r] *= inv;
+      if (g.t == 0) dg[k] = d;
+      g.sync();
     }
-    const T d = sqrt(p), inv = (T)1 / d;
-    for (int r = k + 1 + g.t; r < nf; r += g.size) K[k * ld + r] *= inv;
-    if (g.t == 0) dg[k] = d;
-    g.sync();
   }
   if (bad && g.t == 0) flag_status(a.status, s, -HDD_ENOTSPD, node);
 
