@@ -35,6 +35,13 @@ thread_local std::string g_err;
 // Sweeps over nodes whose interface has at least this many vertices use one CTA
 // per (node, sample) with blocked substitution; smaller nodes one warp each.
 constexpr int kSweepCtaMinM = 16;
+// right-hand-side sweeps of lists whose fronts have 16..32 eliminated vertices and at
+// most 256 rows: one warp per (node, sample) with the rows in registers (measured faster
+// there than the CTA kernel; below 16 the staged warp kernel stays faster, and for the
+// descent the CTA kernel)
+bool mid_list(const hdd::ListInfo& li) {
+  return li.max_m >= kSweepCtaMinM && li.max_m <= 32 && li.max_nf - 1 <= hdd::kMidMaxRows;
+}
 
 hdd_status fail_cuda(cudaError_t e, const char* where) {
   g_err = std::string(where) + ": " + cudaGetErrorString(e);
@@ -430,6 +437,9 @@ cudaError_t run_forward(const hdd::Plan& p, int batch, void* ws, const hdd::Rhs&
       if (li.max_nf <= hdd::kTinyMax)
         e = k == 0 ? hdd::launch_forward_tiny<double>(p.d_nodes, p.d_maps, p.d_lists + li.off, li.n, batch, A, rhs, st)
                    : hdd::launch_forward_tiny<float>(p.d_nodes, p.d_maps, p.d_lists + li.off, li.n, batch, A, rhs, st);
+      else if (mid_list(li))
+        e = k == 0 ? hdd::launch_forward_mid<double>(p.d_nodes, p.d_maps, p.d_lists + li.off, li.n, batch, A, rhs, st)
+                   : hdd::launch_forward_mid<float>(p.d_nodes, p.d_maps, p.d_lists + li.off, li.n, batch, A, rhs, st);
       else if (cta)
         e = k == 0 ? hdd::launch_forward<double>(p.d_nodes, p.d_maps, p.d_lists + li.off, li.n, batch, A, rhs,
                                                  li.max_nf, st)

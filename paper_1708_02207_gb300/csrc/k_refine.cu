@@ -62,14 +62,28 @@ __global__ void k_forward(const NodeDev* __restrict__ nodes, const int32_t* __re
     }
   }
   T* Ld = z + ((nf + 3) & ~3);   // [32][33] diagonal block of L_gg, staged per block
+  // the next block's diagonal block is loaded into registers (four entries per thread)
+  // while the current block is solved and folded
+  T dpre[4];
+  auto fetch_diag = [&](int cb) {
+    const int jb = min(32, m - cb);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const int idx = threadIdx.x + k * 256, c = idx >> 5, l = idx & 31;
+      dpre[k] = (c < jb && l < jb) ? F[(int64_t)(cb + c) * nf + cb + l] : (T)0;
+    }
+  };
+  if (m > 0) fetch_diag(0);
   for (int cb = 0; cb < m; cb += 32) {
     const int jb = min(32, m - cb);
     __syncthreads();
-    for (int idx = threadIdx.x; idx < 32 * jb; idx += blockDim.x) {
-      const int c = idx >> 5, l = idx & 31;
-      Ld[c * 33 + l] = (l < jb) ? F[(int64_t)(cb + c) * nf + cb + l] : (T)0;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const int idx = threadIdx.x + k * 256;
+      Ld[(idx >> 5) * 33 + (idx & 31)] = dpre[k];
     }
     __syncthreads();
+    if (cb + 32 < m) fetch_diag(cb + 32);
     if (warp == 0) {
       T x = (lane < jb) ? z[cb + lane] : (T)0;
       for (int c = 0; c < jb; ++c) {
@@ -83,7 +97,15 @@ __global__ void k_forward(const NodeDev* __restrict__ nodes, const int32_t* __re
     __syncthreads();
     for (int i = cb + jb + threadIdx.x; i < nf - 1; i += blockDim.x) {
       T acc = (T)0;
-      for (int c = 0; c < jb; ++c) acc += F[(int64_t)(cb + c) * nf + i] * z[cb + c];
+      if (jb == 32) {   // the block's 32 entries of row i, all loads in flight first
+        T f[32];
+#pragma unroll
+        for (int c = 0; c < 32; ++c) f[c] = F[(int64_t)(cb + c) * nf + i];
+#pragma unroll
+        for (int c = 0; c < 32; ++c) acc += f[c] * z[cb + c];
+      } else {
+        for (int c = 0; c < jb; ++c) acc += F[(int64_t)(cb + c) * nf + i] * z[cb + c];
+      }
       z[i] -= acc;
     }
   }

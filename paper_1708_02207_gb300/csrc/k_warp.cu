@@ -313,6 +313,94 @@ template cudaError_t launch_descent_tiny<double>(const NodeDev*, const int32_t*,
 template cudaError_t launch_descent_tiny<float>(const NodeDev*, const int32_t*, const int32_t*, int, int,
                                                 const Arenas&, double*, int64_t, cudaStream_t);
 
+// ---------------------------------------------------------------------------
+// Right-hand-side sweep over fronts of 16..32 eliminated vertices and at most 256 rows
+// (the middle levels of the tree), one warp per (node, sample), eight samples of a node
+// per CTA.  Lane l owns rows l + 32 j of the front (j < kMidJ) in registers: z = load at
+// gamma + sons' condensed loads; for each column c, y_c = z_c / F[c, c] and the column
+// folded into the rows below it, the next column's entries loaded while the current
+// one is applied, so no front is staged whole.
+constexpr int kMidJ = 8;   // rows per lane: fronts of up to 256 rows
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_forward_mid(const NodeDev* __restrict__ nodes,
+                                                     const int32_t* __restrict__ maps,
+                                                     const int32_t* __restrict__ list, int batch, Arenas A,
+                                                     Rhs rhs) {
+  const int node = list[blockIdx.x];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int s = blockIdx.y * 8 + warp;
+  if (s >= batch) return;
+  const NodeDev nd = nodes[node];
+  const int m = nd.m, nr = nd.nf - 1, nf = nd.nf;
+  const int32_t* vid = maps + nd.map_off;
+  const T* F = warp_F<T>(A, nd, s);
+  T z[kMidJ];
+  {
+    const NodeDev c0 = nd.leaf ? nd : nodes[nd.child0], c1 = nd.leaf ? nd : nodes[nd.child1];
+    const int32_t* pos0 = vid + nr;
+    const int32_t* pos1 = pos0 + nf;
+#pragma unroll
+    for (int j = 0; j < kMidJ; ++j) {
+      const int r = lane + 32 * j;
+      T v = (T)0;
+      if (r < nr) {
+        if (r < m) v = (T)rhs(s, vid[r]);
+        if (!nd.leaf) {
+          const int q0 = pos0[r], q1 = pos1[r];
+          if (q0 >= 0) v += son_cond<T>(A, c0, s, q0);
+          if (q1 >= 0) v += son_cond<T>(A, c1, s, q1);
+        }
+      }
+      z[j] = v;
+    }
+  }
+  T f[kMidJ];   // column c of F at this lane's rows
+#pragma unroll
+  for (int j = 0; j < kMidJ; ++j) {
+    const int r = lane + 32 * j;
+    f[j] = r < nr ? F[r] : (T)0;
+  }
+  for (int c = 0; c < m; ++c) {
+    T fn[kMidJ];   // the next column, in flight while this one is applied
+#pragma unroll
+    for (int j = 0; j < kMidJ; ++j) {
+      const int r = lane + 32 * j;
+      fn[j] = (c + 1 < m && r < nr) ? F[(int64_t)(c + 1) * nf + r] : (T)0;
+    }
+    if (lane == c) z[0] = z[0] / f[0];   // F[c, c] at lane c
+    const T yc = __shfl_sync(kFull, z[0], c);
+#pragma unroll
+    for (int j = 0; j < kMidJ; ++j) {
+      const int r = lane + 32 * j;
+      if (r > c && r < nr) z[j] -= f[j] * yc;
+    }
+#pragma unroll
+    for (int j = 0; j < kMidJ; ++j) f[j] = fn[j];
+  }
+  if (lane < m) node_Y<T>(A, nd, s)[lane] = z[0];
+  if (nd.b > 0) {
+    T* S = warp_S<T>(A, nd, s);
+#pragma unroll
+    for (int j = 0; j < kMidJ; ++j) {
+      const int r = lane + 32 * j;
+      if (r >= m && r < nr) S[r - m] = z[j];
+    }
+  }
+}
+
+template <typename T>
+cudaError_t launch_forward_mid(const NodeDev* nodes, const int32_t* maps, const int32_t* list, int nlist, int batch,
+                               const Arenas& A, const Rhs& rhs, cudaStream_t st) {
+  if (nlist == 0) return cudaSuccess;
+  k_forward_mid<T><<<dim3(nlist, (batch + 7) / 8), 256, 0, st>>>(nodes, maps, list, batch, A, rhs);
+  return cudaGetLastError();
+}
+template cudaError_t launch_forward_mid<double>(const NodeDev*, const int32_t*, const int32_t*, int, int,
+                                                const Arenas&, const Rhs&, cudaStream_t);
+template cudaError_t launch_forward_mid<float>(const NodeDev*, const int32_t*, const int32_t*, int, int,
+                                               const Arenas&, const Rhs&, cudaStream_t);
+
 }  // namespace hdd
 
 namespace hdd {

@@ -181,6 +181,12 @@ template <typename T>
 cudaError_t launch_descent_warp(const NodeDev* nodes, const int32_t* maps, const int32_t* list, int nlist, int batch,
                                 const Arenas& A, double* u, int64_t u_stride, int max_nf, int max_m,
                                 cudaStream_t st);
+// right-hand-side sweep over fronts of 16..32 eliminated vertices and at most 256 rows,
+// rows in registers
+constexpr int kMidMaxRows = 256;
+template <typename T>
+cudaError_t launch_forward_mid(const NodeDev* nodes, const int32_t* maps, const int32_t* list, int nlist, int batch,
+                               const Arenas& A, const Rhs& rhs, cudaStream_t st);
 // sweeps over fronts of at most 32 rows, factor rows in registers
 template <typename T>
 cudaError_t launch_forward_tiny(const NodeDev* nodes, const int32_t* maps, const int32_t* list, int nlist, int batch,
