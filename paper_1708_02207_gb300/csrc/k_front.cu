@@ -976,7 +976,15 @@ __global__ void k_syrk_rhs(StepArgs a) {
   __syncthreads();
   for (int j = threadIdx.x; j <= b; j += blockDim.x) {
     float acc = 0.0f;
-    for (int k = 0; k < m; ++k) acc += y[k] * X[(int64_t)k * nf + j];
+    int k = 0;
+    for (; k + 16 <= m; k += 16) {   // sixteen column loads in flight, then the products
+      float x[16];
+#pragma unroll
+      for (int q = 0; q < 16; ++q) x[q] = X[(int64_t)(k + q) * nf + j];
+#pragma unroll
+      for (int q = 0; q < 16; ++q) acc += y[k + q] * x[q];
+    }
+    for (; k < m; ++k) acc += y[k] * X[(int64_t)k * nf + j];
     const float g = nd.leaf ? S[(int64_t)j * nb + b]
                             : father_entry<float>(nf - 1, m + j, s, nd, map, c0, c1, a.arenas, a.rhs);
     S[(int64_t)j * nb + b] = g - acc;
