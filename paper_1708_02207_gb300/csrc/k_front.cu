@@ -412,9 +412,29 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) k_potrf_smem(Step
   T* P = dinv + 32;                         // the lower triangle, 16-byte aligned 4-row groups
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarp = blockDim.x >> 5;
   auto at = [&](int i, int j) -> T& { return P[tri_off(j, m4) + i - (j & ~3)]; };
-  // load: column by column, one warp per column, zeros above the diagonal and below m
-  for (int j = warp; j < m; j += nwarp)
-    for (int i = (j & ~3) + lane; i < m4; i += 32) at(i, j) = (i >= j && i < m) ? A[(int64_t)j * nf + i] : (T)0;
+  // load: column by column, one warp per column, zeros above the diagonal and below m;
+  // two columns' rows per pass, all loads in flight before the stores
+  for (int j0 = warp; j0 < m; j0 += 2 * nwarp) {
+    T v[2][8];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int j = j0 + h * nwarp;
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        const int i = (j & ~3) + lane + 32 * k;
+        v[h][k] = (j < m && i >= j && i < m) ? A[(int64_t)j * nf + i] : (T)0;
+      }
+    }
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int j = j0 + h * nwarp;
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        const int i = (j & ~3) + lane + 32 * k;
+        if (j < m && i < m4) at(i, j) = v[h][k];
+      }
+    }
+  }
   bool bad = false;
   for (int k0 = 0; k0 < m; k0 += kPanel) {
     const int kb = min(kPanel, m - k0);
@@ -792,9 +812,16 @@ __global__ void __launch_bounds__(256, 3) k_trsm_wide(StepArgs a) {
   float* Lc = L + 32 * 36;                         // [32][kTrwC] the panel's columns right of it
   float* X = Lc + 32 * kTrwC;                      // [m][32] the CTA's rows
   const int tid = threadIdx.x;
-  for (int idx = tid; idx < m * kTrwR; idx += blockDim.x) {
-    const int c = idx >> 5, r = idx & 31;
-    X[idx] = (r < nr) ? A[(int64_t)c * nf + r0 + r] : 0.0f;
+  for (int i0 = tid; i0 < m * kTrwR; i0 += 8 * 256) {   // eight loads in flight, then the stores
+    float v[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const int idx = i0 + q * 256, c = idx >> 5, r = idx & 31;
+      v[q] = (idx < m * kTrwR && r < nr) ? A[(int64_t)c * nf + r0 + r] : 0.0f;
+    }
+#pragma unroll
+    for (int q = 0; q < 8; ++q)
+      if (i0 + q * 256 < m * kTrwR) X[i0 + q * 256] = v[q];
   }
   const float* G0 = reinterpret_cast<const float*>(a.arenas.inv + (int64_t)s * a.arenas.inv_stride + nd.inv_off);
   float gin[4], pre[16];

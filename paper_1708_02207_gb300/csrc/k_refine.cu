@@ -138,8 +138,8 @@ template cudaError_t launch_forward<float>(const NodeDev*, const int32_t*, const
 // when it is not null.
 // A thread owns one column i of vertices over kResRows consecutive rows and
 // slides up them, so that every row of u and of the cells' kappa is loaded once
-// per thread (the left and right neighbours come from the adjacent threads'
-// loads through L1).
+// per thread (the right neighbour comes from the adjacent thread's loads through
+// L1, the left one's edge terms by a shuffle).
 constexpr int kResRows = 8;
 
 __global__ void __launch_bounds__(128) k_residual(const double* __restrict__ kappa, int64_t kap_stride,
@@ -148,8 +148,9 @@ __global__ void __launch_bounds__(128) k_residual(const double* __restrict__ kap
                                                   int64_t load_stride, double* __restrict__ r, int64_t r_stride) {
   const int s = blockIdx.z;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int lane = threadIdx.x & 31;
   const int j0 = blockIdx.y * kResRows;
-  if (i >= N) return;
+  const bool live = i < N;   // every lane stays for the shuffles
   const double* ks = kappa + (int64_t)s * kap_stride;
   const double* us = u + (int64_t)s * u_stride;
   double* rs = r + (int64_t)s * r_stride;
@@ -163,27 +164,46 @@ __global__ void __launch_bounds__(128) k_residual(const double* __restrict__ kap
   auto kc = [&](int ci, int j, int t) {
     return (ci >= 0 && ci <= N - 2 && j >= 0 && j <= N - 2) ? ks[2 * ((int64_t)j * (N - 1) + ci) + t] : 0.0;
   };
-  double u_c = urow(j0, 0), u_s = urow(j0 - 1, 0);
-  double kb0 = kc(i, j0 - 1, 1), kb1 = kc(i - 1, j0 - 1, 0), kb2 = kc(i - 1, j0 - 1, 1);   // cells of row j - 1
+  // Each edge's weight sum (twice its weight) and the difference of u along it are
+  // formed once: a thread forms those of its east and north edges; its west edge is
+  // the east edge of the lane to its left (a shuffle; lane 0 forms it itself), its
+  // south edge the north edge of the row below (carried).  Au = sum over the four
+  // edges of (weight sum) x (difference) / 2, and r = b - Au is one FMA.
+  double u_c = live ? urow(j0, 0) : 0.0;
+  double kb0 = live ? kc(i, j0 - 1, 1) : 0.0;                  // upper-left of (i, j-1)
+  double sum_d = live ? kb0 + kc(i - 1, j0 - 1, 0) : 0.0;      // edge (i, j-1)-(i, j)
+  double d_s = live ? u_c - urow(j0 - 1, 0) : 0.0;             // u_c - u south
   for (int j = j0; j < min(j0 + kResRows, N); ++j) {
-    const double u_n = urow(j + 1, 0);
-    const double ka0 = kc(i, j, 0), ka1 = kc(i, j, 1), ka2 = kc(i - 1, j, 0);       // cells of row j
-    if (!col_in || j < 1 || j > N - 2) {
-      rs[(int64_t)j * N + i] = 0.0;
-    } else {
-      const double ue = urow(j, 1), uw = urow(j, -1);
-      const double wr = 0.5 * (ka0 + kb0);   // (i,j)-(i+1,j): lower-right of (i,j), upper-left of (i,j-1)
-      const double wl = 0.5 * (ka2 + kb2);   // (i-1,j)-(i,j): lower-right of (i-1,j), upper-left of (i-1,j-1)
-      const double wu = 0.5 * (ka1 + ka2);   // (i,j)-(i,j+1): upper-left of (i,j), lower-right of (i-1,j)
-      const double wd = 0.5 * (kb0 + kb1);   // (i,j-1)-(i,j): upper-left of (i,j-1), lower-right of (i-1,j-1)
-      const double Au = wr * (u_c - ue) + wl * (u_c - uw) + wu * (u_c - u_n) + wd * (u_c - u_s);
-      rs[(int64_t)j * N + i] = (bs ? bs[(int64_t)j * N + i] : load) - Au;
+    double u_n = 0.0, ue = 0.0, ka0 = 0.0, ka1 = 0.0, ka2 = 0.0;
+    if (live) {
+      u_n = urow(j + 1, 0);
+      ue = urow(j, 1);
+      ka0 = kc(i, j, 0);
+      ka1 = kc(i, j, 1);
+      ka2 = kc(i - 1, j, 0);
     }
-    u_s = u_c;
+    const double sum_r = ka0 + kb0;   // edge (i, j)-(i+1, j): lower-right of (i, j), upper-left of (i, j-1)
+    const double sum_u = ka1 + ka2;   // edge (i, j)-(i, j+1): upper-left of (i, j), lower-right of (i-1, j)
+    const double d_e = u_c - ue, d_n = u_c - u_n;
+    // west edge: the left neighbour's east edge, with the difference's sign turned
+    double sum_l = __shfl_up_sync(0xffffffffu, sum_r, 1);
+    double d_w = -__shfl_up_sync(0xffffffffu, d_e, 1);
+    if (lane == 0 && live) {
+      sum_l = ka2 + kc(i - 1, j - 1, 1);   // lower-right of (i-1, j), upper-left of (i-1, j-1)
+      d_w = u_c - urow(j, -1);
+    }
+    if (live) {
+      if (!col_in || j < 1 || j > N - 2) {
+        rs[(int64_t)j * N + i] = 0.0;
+      } else {
+        const double Au2 = sum_r * d_e + sum_l * d_w + sum_u * d_n + sum_d * d_s;
+        rs[(int64_t)j * N + i] = fma(-0.5, Au2, bs ? bs[(int64_t)j * N + i] : load);
+      }
+    }
+    sum_d = sum_u;
+    d_s = -d_n;
     u_c = u_n;
     kb0 = ka1;
-    kb1 = ka2;
-    kb2 = kc(i - 1, j, 1);
   }
 }
 
