@@ -291,11 +291,19 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) k_potrf(StepArgs 
     T* P = in_smem ? Ps : A + (int64_t)k0 * nf + k0;
     const int ld = in_smem ? ((rows + 3) & ~3) : nf;
     __syncthreads();
-    if (in_smem)
-      for (int idx = threadIdx.x; idx < kb * rows; idx += blockDim.x) {
-        const int l = idx / rows, i = idx - l * rows;
-        Ps[l * ld + i] = A[(int64_t)(k0 + l) * nf + k0 + i];
-      }
+    if (in_smem)   // one warp per panel column, eight rows per lane in flight
+      for (int l = warp; l < kb; l += nwarp)
+        for (int i0 = lane; i0 < rows; i0 += 256) {
+          T v[8];
+#pragma unroll
+          for (int q = 0; q < 8; ++q) {
+            const int i = i0 + 32 * q;
+            v[q] = i < rows ? A[(int64_t)(k0 + l) * nf + k0 + i] : (T)0;
+          }
+#pragma unroll
+          for (int q = 0; q < 8; ++q)
+            if (i0 + 32 * q < rows) Ps[l * ld + i0 + 32 * q] = v[q];
+        }
     __syncthreads();
     if (warp == 0) {   // the diagonal block, lane r holding row r
       T row[32];
@@ -323,10 +331,8 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) k_potrf(StepArgs 
     }
     __syncthreads();
     if (in_smem)
-      for (int idx = threadIdx.x; idx < kb * rows; idx += blockDim.x) {
-        const int l = idx / rows, i = idx - l * rows;
-        if (i >= l) A[(int64_t)(k0 + l) * nf + k0 + i] = Ps[l * ld + i];
-      }
+      for (int l = warp; l < kb; l += nwarp)
+        for (int i = l + lane; i < rows; i += 32) A[(int64_t)(k0 + l) * nf + k0 + i] = Ps[l * ld + i];
     // trailing update of K_gg[k0+kb:m, k0+kb:m] (lower): 4 x 4 register tiles,
     // one warp per column of tiles, lanes down the rows (coalesced in global memory)
     const int n = rows - kb;
@@ -676,9 +682,16 @@ __global__ void __launch_bounds__(256) k_trsm(StepArgs a) {   // R rows per CTA
   T* X = in_smem ? Xs : A + r0;
   const int64_t ldx = in_smem ? R : nf;
   if (in_smem)
-    for (int idx = threadIdx.x; idx < m * R; idx += blockDim.x) {
-      const int c = idx / R, r = idx - c * R;
-      Xs[idx] = (r < nr) ? A[(int64_t)c * nf + r0 + r] : (T)0;
+    for (int i0 = threadIdx.x; i0 < m * R; i0 += 8 * 256) {   // eight loads in flight, then the stores
+      T v[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const int idx = i0 + q * 256, c = idx / R, r = idx - c * R;
+        v[q] = (idx < m * R && r < nr) ? A[(int64_t)c * nf + r0 + r] : (T)0;
+      }
+#pragma unroll
+      for (int q = 0; q < 8; ++q)
+        if (i0 + q * 256 < m * R) Xs[i0 + q * 256] = v[q];
     }
   const int rg = threadIdx.x % RG, cg = threadIdx.x / RG;
   // Global loads are issued ahead of their use, into registers: the inverse of the
