@@ -38,8 +38,16 @@ template <> __device__ __forceinline__ float* leaf_S<float>(const Arenas& A, con
 }
 
 // per-sample shared buffers of the leaf front (elements of T, then ints)
-constexpr int kSampElems = kLeafInvMax * kLd + 4 * (kLeafInvMaxB + 1) + kLeafInvMax;
-constexpr int kSampInts = 2 * (kLeafInvMaxB + 1);
+// The two samples of a warp (its half-warps) sit one stride apart: a stride of 16 words
+// modulo the 32 shared-memory banks puts their rows in disjoint banks
+constexpr int kSampBase = kLeafInvMax * kLd + 4 * (kLeafInvMaxB + 1) + kLeafInvMax;
+template <typename T>
+__host__ __device__ constexpr int samp_elems() {
+  constexpr int words = sizeof(T) == 4 ? 16 : 8;   // elements that make 16 words
+  constexpr int period = sizeof(T) == 4 ? 32 : 16;
+  return (kSampBase + period - words - 1) / period * period + words;
+}
+constexpr int kSampInts = 2 * (kLeafInvMaxB + 1) + 16;
 constexpr int kLeafSamples = 16;   // samples per CTA: two per warp, one per half-warp
 
 }  // namespace
@@ -60,6 +68,7 @@ __global__ void __launch_bounds__(256) k_leaf_front(StepArgs a) {
   const int hw = threadIdx.x >> 4, r = threadIdx.x & 15;   // half-warp = sample, lane r = row
   const int s = blockIdx.y * kLeafSamples + hw;
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  constexpr int kSampElems = samp_elems<T>();
   T* Gs = reinterpret_cast<T*>(smem_raw) + hw * kSampElems;   // K_gg rows, then G (ld kLd)
   T* wv = Gs + kLeafInvMax * kLd;                               // couplings w [b]
   T* dB = wv + kLeafInvMaxB + 1;                                // K_BB diagonal [b]
@@ -290,7 +299,7 @@ __global__ void __launch_bounds__(256) k_leaf_descent(const NodeDev* __restrict_
 template <typename T>
 cudaError_t launch_leaf_front(const StepArgs& a, cudaStream_t st) {
   if (a.nlist == 0) return cudaSuccess;
-  const size_t smem = (size_t)kLeafSamples * (kSampElems * sizeof(T) + kSampInts * sizeof(int)) +
+  const size_t smem = (size_t)kLeafSamples * (samp_elems<T>() * sizeof(T) + kSampInts * sizeof(int)) +
                       (size_t)(a.max_rect + a.max_nf) * sizeof(int);
   if (a.prof) a.prof->begin(kProfLeaf, a.fl_chol + a.fl_trsm + a.fl_syrk + a.fl_rhs, st);
   k_leaf_front<T><<<dim3(a.nlist, (a.batch + kLeafSamples - 1) / kLeafSamples), 256, smem, st>>>(a);
