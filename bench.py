@@ -258,6 +258,16 @@ def run_uneven(args, hdd, torch, dev, stream, local):
 
     t_multi = timed(multi, args.uneven_steps)
     t_alone = timed(alone, args.uneven_steps)
+    # the same chunks as captured CUDA graphs (hdd_multi_capture), one replay per chunk
+    graphs = [mp.capture(Zs[c], ys) for c in range(chunks)]
+
+    def replay():
+        for g in graphs:
+            g.launch(stream)
+
+    t_graph = timed(replay, args.uneven_steps)
+    for g in graphs:
+        g.close()
     evaluated = sum(batches) * chunks
     info = mp.info()
     out = {"samples": args.uneven_samples, "evaluated_per_step": evaluated, "plans": len(plans), "chunks": chunks,
@@ -265,6 +275,7 @@ def run_uneven(args, hdd, torch, dev, stream, local):
            "precision": prec_name, "tuned": {str(N): tuned[N] for N in grids},
            "ms_per_step": t_multi, "evals_per_s": args.uneven_samples / (t_multi / 1e3),
            "ms_per_step_plans_alone": t_alone, "evals_per_s_plans_alone": args.uneven_samples / (t_alone / 1e3),
+           "ms_per_step_graph": t_graph, "evals_per_s_graph": args.uneven_samples / (t_graph / 1e3),
            "launches_per_chunk": info["launches_evaluate"],
            "launches_per_chunk_plans_alone": sum(p.info()["launches_evaluate"] for p in plans),
            "failed_samples": failed,

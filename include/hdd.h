@@ -362,6 +362,25 @@ hdd_status hdd_multi_upsweep(hdd_multi_t multi, void* stream);
 hdd_status hdd_multi_evaluate(hdd_multi_t multi, const double* const* Z, const double* const* y,
                               const int32_t* y_per_sample, double* const* loglik, double* const* u_obs,
                               int32_t* const* sample_status, void* stream);
+/* The whole hdd_multi_evaluate of these buffers recorded once as a CUDA graph (stream
+ * capture of the call: its assembly, one launch per height and front class of the
+ * upsweep, the per-plan point solves and likelihoods, and the fork and join of the
+ * plan streams) and instantiated, so that later evaluations of the same batch shape
+ * replay it with one hdd_graph_launch instead of issuing each launch from the host.
+ * The graph keeps the pointers it was captured with: new parameters are written into
+ * the same Z[q] (and y[q]) buffers before a launch, and the results appear in the same
+ * loglik[q], u_obs[q] and sample_status[q].  Arguments as for hdd_multi_evaluate; the
+ * multi handle and its workspaces must outlive the graph, and no other work of the
+ * multi handle may run while a launch of the graph is in flight.  Nothing runs during
+ * the capture itself.  Errors: those of hdd_multi_evaluate, HDD_ENOMEM, HDD_ECUDA
+ * (capture or instantiation refused). */
+typedef struct hdd_graph_s* hdd_graph_t;
+hdd_status hdd_multi_capture(hdd_multi_t multi, const double* const* Z, const double* const* y,
+                             const int32_t* y_per_sample, double* const* loglik, double* const* u_obs,
+                             int32_t* const* sample_status, hdd_graph_t* out);
+/* One replay of a captured evaluation, ordered on `stream`.  Errors: HDD_EINVAL, HDD_ECUDA. */
+hdd_status hdd_graph_launch(hdd_graph_t graph, void* stream);
+hdd_status hdd_graph_destroy(hdd_graph_t graph);
 /* Kernel launches of one hdd_multi_upsweep and of one hdd_multi_evaluate. */
 hdd_status hdd_multi_info(hdd_multi_t multi, int32_t* launches_upsweep, int32_t* launches_evaluate);
 

@@ -323,6 +323,68 @@ hdd_status hdd_multi_evaluate(hdd_multi_t multi, const double* const* Z, const d
   return HDD_OK;
 }
 
+// A captured evaluation: the instantiated CUDA graph of one hdd_multi_evaluate.
+struct hdd_graph_s {
+  int device = -1;
+  cudaGraphExec_t exec = nullptr;
+};
+
+hdd_status hdd_multi_capture(hdd_multi_t multi, const double* const* Z, const double* const* y,
+                             const int32_t* y_per_sample, double* const* loglik, double* const* u_obs,
+                             int32_t* const* sample_status, hdd_graph_t* out) {
+  if (!multi || !out) return hdd::set_error(HDD_EINVAL, "multi and out must not be NULL");
+  *out = nullptr;
+  DevScope ds(multi->device);
+  if (ds.err != cudaSuccess) return cuda_fail(ds.err, "cudaSetDevice");
+  cudaStream_t cs = nullptr;
+  cudaError_t e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+  if (e != cudaSuccess) return cuda_fail(e, "hdd_multi_capture stream");
+  e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) {
+    cudaStreamDestroy(cs);
+    return cuda_fail(e, "hdd_multi_capture begin");
+  }
+  // the plan streams join the capture through the fork event and leave it through the
+  // join events, exactly as they order a direct call after the caller's stream
+  const hdd_status s = hdd_multi_evaluate(multi, Z, y, y_per_sample, loglik, u_obs, sample_status, cs);
+  cudaGraph_t graph = nullptr;
+  const cudaError_t ee = cudaStreamEndCapture(cs, &graph);   // ended whatever happened inside
+  cudaGraphExec_t exec = nullptr;
+  if (s == HDD_OK && ee == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
+  if (graph) cudaGraphDestroy(graph);
+  cudaStreamDestroy(cs);
+  if (s != HDD_OK) return s;
+  if (ee != cudaSuccess) return cuda_fail(ee, "hdd_multi_capture end");
+  if (e != cudaSuccess) return cuda_fail(e, "hdd_multi_capture instantiate");
+  hdd_graph_s* g = new (std::nothrow) hdd_graph_s;
+  if (!g) {
+    cudaGraphExecDestroy(exec);
+    return hdd::set_error(HDD_ENOMEM, "host allocation failed");
+  }
+  g->device = multi->device;
+  g->exec = exec;
+  *out = g;
+  return HDD_OK;
+}
+
+hdd_status hdd_graph_launch(hdd_graph_t graph, void* stream) {
+  if (!graph) return hdd::set_error(HDD_EINVAL, "graph is NULL");
+  DevScope ds(graph->device);
+  if (ds.err != cudaSuccess) return cuda_fail(ds.err, "cudaSetDevice");
+  const cudaError_t e = cudaGraphLaunch(graph->exec, static_cast<cudaStream_t>(stream));
+  return e == cudaSuccess ? HDD_OK : cuda_fail(e, "hdd_graph_launch");
+}
+
+hdd_status hdd_graph_destroy(hdd_graph_t graph) {
+  if (!graph) return HDD_OK;
+  {
+    DevScope ds(graph->device);
+    cudaGraphExecDestroy(graph->exec);
+  }
+  delete graph;
+  return HDD_OK;
+}
+
 hdd_status hdd_multi_info(hdd_multi_t multi, int32_t* launches_upsweep, int32_t* launches_evaluate) {
   if (!multi) return hdd::set_error(HDD_EINVAL, "multi is NULL");
   if (launches_upsweep) *launches_upsweep = multi->launches_upsweep;

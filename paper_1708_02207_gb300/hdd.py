@@ -26,6 +26,7 @@ EXPORTED = [
     "hdd_profile_begin", "hdd_profile_end", "hdd_kappa", "hdd_solve_loads", "hdd_subdomain_means",
     "hdd_set_wait_bound", "hdd_mean_functionals", "hdd_multi_create", "hdd_multi_destroy", "hdd_multi_upsweep",
     "hdd_multi_evaluate", "hdd_multi_info", "hdd_data_scratch_size", "hdd_solve_data", "hdd_set_sweep_fusion",
+    "hdd_multi_capture", "hdd_graph_launch", "hdd_graph_destroy",
 ]
 STATIC_WORKSPACE_BYTES = 32 << 20
 
@@ -97,6 +98,10 @@ def load_library() -> C.CDLL:
     lib.hdd_mean_functionals.argtypes = [vp, i32, vp, vp, vp, vp]
     lib.hdd_multi_create.argtypes = [C.POINTER(vp), i32, pi32, C.POINTER(vp), C.POINTER(vp)]
     lib.hdd_multi_destroy.argtypes = [vp]
+    lib.hdd_multi_capture.argtypes = [vp, C.POINTER(vp), C.POINTER(vp), pi32, C.POINTER(vp), C.POINTER(vp),
+                                      C.POINTER(vp), C.POINTER(vp)]
+    lib.hdd_graph_launch.argtypes = [vp, vp]
+    lib.hdd_graph_destroy.argtypes = [vp]
     lib.hdd_multi_upsweep.argtypes = [vp, vp]
     lib.hdd_multi_evaluate.argtypes = [vp, C.POINTER(vp), C.POINTER(vp), pi32, C.POINTER(vp), C.POINTER(vp),
                                        C.POINTER(vp), vp]
@@ -495,3 +500,45 @@ class MultiPlan:
         _check(self.lib.hdd_multi_evaluate(self._h, P(*[Z.data_ptr() for Z in Zs]), P(*[y.data_ptr() for y in ys]),
                                            yps, ll, uo, st, _stream_ptr(stream)), "hdd_multi_evaluate")
         return self.outputs
+
+    def capture(self, Zs: list, ys: list):
+        """hdd_multi_capture: the evaluation of these Z and y tensors (kept alive by the
+        returned graph; write new parameters into them before a launch) as one CUDA graph
+        whose results land in self.outputs."""
+        n = len(self.plans)
+        if len(Zs) != n or len(ys) != n:
+            raise ValueError("one Z and one y per plan")
+        for p, b, Z, y in zip(self.plans, self.batches, Zs, ys):
+            _need(Z, "Z", "f64", (b, p.n_z), p._dev())
+            p._check_y(y, b)
+        P = C.c_void_p * n
+        ll = P(*[o[0].data_ptr() for o in self.outputs])
+        uo = P(*[o[1].data_ptr() for o in self.outputs])
+        st = P(*[o[2].data_ptr() for o in self.outputs])
+        yps = (C.c_int32 * n)(*[1 if y.dim() == 2 else 0 for y in ys])
+        h = C.c_void_p()
+        _check(self.lib.hdd_multi_capture(self._h, P(*[Z.data_ptr() for Z in Zs]), P(*[y.data_ptr() for y in ys]),
+                                          yps, ll, uo, st, C.byref(h)), "hdd_multi_capture")
+        return CapturedEvaluation(self, h, list(Zs), list(ys))
+
+
+class CapturedEvaluation:
+    """A captured hdd_multi_evaluate (hdd_multi_capture); launch() replays it on a stream."""
+
+    def __init__(self, multi: "MultiPlan", handle, Zs: list, ys: list):
+        self.lib, self.multi, self._h, self.Zs, self.ys = multi.lib, multi, handle, Zs, ys
+
+    def launch(self, stream=None):
+        _check(self.lib.hdd_graph_launch(self._h, _stream_ptr(stream)), "hdd_graph_launch")
+        return self.multi.outputs
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self.lib.hdd_graph_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -81,3 +81,49 @@ def test_uneven_batch_mixed_precisions(hdd):
     for q, p in enumerate(plans):
         ll, u, st = (t.cpu().numpy() for t in p.evaluate(Zs[q], ys[q]))
         assert np.array_equal(outs[q][1], u) and np.array_equal(outs[q][0], ll) and (st == 0).all()
+
+
+def test_captured_graph_replays_the_evaluation_bit_for_bit(hdd):
+    # hdd_multi_capture records one whole uneven evaluation as a CUDA graph; replays with the
+    # same and with new parameters (written into the captured Z buffers) equal direct calls
+    rng = np.random.default_rng(31)
+    specs = [(65, 4, 3, 10, hdd.HDD_MIXED_FP32, 2), (33, 4, 2, 10, hdd.HDD_FP64, 0),
+             (129, 4, 2, 20, hdd.HDD_MIXED_FP32, 2)]
+    plans, Zs, ys = [], [], []
+    for N, leaf, B, nz, prec, K in specs:
+        phi = w.kl_basis(N, nz, 0.2, 1.0)
+        obs = w.obs_vertices(N, 3)
+        plans.append(hdd.Plan(N, leaf, phi, obs, 0.01, precision=prec, ir_max_iter=K))
+        Zs.append(torch.from_numpy(rng.standard_normal((B, nz))).cuda())
+        ys.append(torch.from_numpy(0.01 * rng.standard_normal(obs.size)).cuda())
+    mp = hdd.MultiPlan(plans, [s[2] for s in specs])
+    stream = torch.cuda.Stream()
+
+    def direct():
+        with torch.cuda.stream(stream):
+            out = [tuple(t.clone() for t in o) for o in mp.evaluate(Zs, ys, stream)]
+        stream.synchronize()
+        return [tuple(t.cpu().numpy() for t in o) for o in out]
+
+    def replay(g):
+        with torch.cuda.stream(stream):
+            out = [tuple(t.clone() for t in o) for o in g.launch(stream)]
+        stream.synchronize()
+        return [tuple(t.cpu().numpy() for t in o) for o in out]
+
+    ref = direct()
+    g = mp.capture(Zs, ys)
+    for _ in range(2):
+        got = replay(g)
+        for a, b in zip(got, ref):
+            assert (a[2] == 0).all() and all(np.array_equal(x, y) for x, y in zip(a, b))
+    for Z in Zs:   # new parameters in the captured buffers
+        Z.copy_(torch.from_numpy(rng.standard_normal(tuple(Z.shape))))
+    torch.cuda.synchronize()
+    got = replay(g)
+    ref2 = direct()
+    for a, b, c in zip(got, ref2, ref):
+        assert all(np.array_equal(x, y) for x, y in zip(a, b))
+        assert not np.array_equal(a[0], c[0])
+    g.close()
+    del mp
