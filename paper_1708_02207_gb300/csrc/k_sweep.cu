@@ -115,11 +115,12 @@ __device__ __forceinline__ void descent_front(const SNode& q, const T* F, const 
                                               int lane) {
   const int m = q.m, nr = q.nf - 1, ld = q.nf;
   if (m == 0) return;
+  const int J = (nr + 31) >> 5;   // 32-row blocks of the front (at most 4)
   T w[4];
 #pragma unroll
   for (int j = 0; j < 4; ++j) {
     const int r = lane + 32 * j;
-    w[j] = (r >= m && r < nr) ? region[lm[r]] : (T)0;
+    w[j] = (j < J && r >= m && r < nr) ? region[lm[r]] : (T)0;
   }
   T t = (T)0;   // lane c: (L_Bg^T u_B)_c
   for (int c0 = 0; c0 < m; c0 += 4) {
@@ -131,6 +132,7 @@ __device__ __forceinline__ void descent_front(const SNode& q, const T* F, const 
       if (c < m) {
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
+          if (j >= J) break;   // uniform over the warp
           const int r = lane + 32 * j;
           if (r >= m && r < nr) acc[k] += F[c * ld + r] * w[j];
         }
@@ -150,18 +152,34 @@ __device__ __forceinline__ void descent_front(const SNode& q, const T* F, const 
   if (lane < m) region[lm[lane]] = t;
 }
 
-// Descent at a condensed leaf: half-warp h sums the boundary rows i = h, h + 2, ...
+// Descent at a condensed leaf: lanes i < b first form w_i u_B,i and the coupled row c_i
+// (shuffled to the others below); half-warp h then sums the boundary rows i = h, h + 2,
+// ... for interior row r = lane & 15, reading G[r, c_i] through a column start that
+// each lane keeps for its own row (the other one by a shuffle).
 template <typename T>
 __device__ __forceinline__ void descent_leaf(const SNode& q, const T* G, const T* Y, const int16_t* lm,
                                              const int16_t* cpl, T* region, int lane) {
   const int m = q.m, b = q.b;
   const T* wts = G + m * (m + 1) / 2;
   const int r = lane & 15;
+  T twl[2];
+  int cil[2];
+#pragma unroll
+  for (int k = 0; k < 2; ++k) {   // b <= 63: boundary rows lane and lane + 32
+    const int i = lane + 32 * k;
+    twl[k] = i < b ? wts[i] * region[lm[m + i]] : (T)0;
+    cil[k] = i < b ? cpl[i] : -1;
+  }
+  const int cs = r * m - r * (r - 1) / 2 - r;   // packed index of (i, r), i >= r: cs + i
   T acc = (T)0;
-  for (int i = lane >> 4; i < b; i += 2) {
-    const int ci = cpl[i];
-    const T tw = wts[i] * region[lm[m + i]];
-    if (r < m && ci >= 0) acc += tw * G[r >= ci ? pk(r, ci, m) : pk(ci, r, m)];
+  for (int i0 = 0; i0 < b; i0 += 2) {   // same trip count in both halves (the shuffles)
+    const int i = i0 + (lane >> 4);       // i0 is even: i and i0 lie on the same side of 32
+    const int src = i & 31;
+    const T tw = __shfl_sync(kAll, i0 < 32 ? twl[0] : twl[1], src);
+    const int cix = __shfl_sync(kAll, i0 < 32 ? cil[0] : cil[1], src);
+    const int ci = i < b ? cix : -1;
+    const int csc = __shfl_sync(kAll, cs, ci >= 0 ? ci : 0);
+    if (r < m && ci >= 0) acc += tw * G[r >= ci ? csc + r : cs + ci];
   }
   acc += __shfl_xor_sync(kAll, acc, 16);
   __syncwarp();
@@ -179,12 +197,13 @@ __device__ __forceinline__ void sweep_front(const SNode& q, const T* F, const in
   const T* cond1 = cond0 - q.b1;
   const int16_t* p0 = lm + pad2(nr);
   const int16_t* p1 = p0 + pad2(nr);
+  const int J = (nr + 31) >> 5;   // 32-row blocks of the front (at most 4)
   T z[4];
 #pragma unroll
   for (int j = 0; j < 4; ++j) {
     const int r = lane + 32 * j;
     T v = (T)0;
-    if (r < nr) {
+    if (j < J && r < nr) {
       if (r < m) v = region[lm[r]];
       if (q.kind == 0) {
         const int a = p0[r], c = p1[r];
@@ -200,6 +219,7 @@ __device__ __forceinline__ void sweep_front(const SNode& q, const T* F, const in
     const T yc = __shfl_sync(kAll, z[0], c);
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
+      if (j >= J) break;   // uniform over the warp
       const int r = lane + 32 * j;
       if (r > c && r < nr) z[j] -= F[c * ld + r] * yc;
     }
@@ -211,7 +231,7 @@ __device__ __forceinline__ void sweep_front(const SNode& q, const T* F, const in
 #pragma unroll
   for (int j = 0; j < 4; ++j) {
     const int r = lane + 32 * j;
-    if (r >= m && r < nr) out[r - m] = z[j];
+    if (j < J && r >= m && r < nr) out[r - m] = z[j];
   }
   sp = Sroot ? base : base + q.b;
 }
