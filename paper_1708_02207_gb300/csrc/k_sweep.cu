@@ -242,12 +242,21 @@ __device__ __forceinline__ void sweep_leaf(const SNode& q, const T* G, const int
                                            const T* region, T* stack, int& sp, T* Yg, T* Sroot, int lane) {
   const int m = q.m, b = q.b;
   const T* wts = G + m * (m + 1) / 2;
+  // y = G z: half-warp h sums the columns j = h, h + 2, ... for row r = lane & 15, reading
+  // G[r, j] through a column start that each lane keeps for its own row (the other by a
+  // shuffle); the halves' sums are then added
+  const int r = lane & 15;
   const T zr = lane < m ? region[lm[lane]] : (T)0;
+  const int cs = r * m - r * (r - 1) / 2 - r;   // packed index of (i, r), i >= r: cs + i
   T y = (T)0;
-  for (int j = 0; j < m; ++j) {
-    const T zj = __shfl_sync(kAll, zr, j);
-    if (lane < m) y += G[lane >= j ? pk(lane, j, m) : pk(j, lane, m)] * zj;
+  for (int j0 = 0; j0 < m; j0 += 2) {   // same trip count in both halves (the shuffles)
+    const int j = j0 + (lane >> 4);
+    const int jj = j < m ? j : 0;
+    const T zj = __shfl_sync(kAll, zr, jj);
+    const int csj = __shfl_sync(kAll, cs, jj);
+    if (r < m && j < m) y += G[r >= j ? csj + r : cs + j] * zj;
   }
+  y += __shfl_xor_sync(kAll, y, 16);   // lanes r and r + 16 both hold row r's sum
   if (lane < m) Yg[q.y_off + lane] = y;
   T* out = Sroot ? Sroot : stack + sp;
   for (int i0 = 0; i0 < b; i0 += 32) {
