@@ -51,11 +51,14 @@ __global__ void k_kappa(const double* __restrict__ phi, const double* __restrict
 // Assembly for mixed-precision plans without the FP64 pipe: q = sum_k Phi Z and
 // kappa = exp(q) in double-float arithmetic (pairs of FP32 values, hi + lo, ~48
 // significant bits), with the error-free transformations TwoSum (Knuth) and
-// TwoProduct via FMA (Dekker's product).  exp uses the additive range reduction
-// q = k ln2 + r (ln2 as a hi/lo pair, the product k ln2 formed exactly) and the
-// Taylor series of e^r to degree 12 (|r| <= ln2/2, remainder < 2e-16) in
-// Horner form; e^q = 2^k e^r.  Outputs the FP64 kappa (residual) and its FP32
-// copy (factorisation).
+// TwoProduct via FMA (Dekker's product).  exp follows Tang's table-driven method
+// (ACM TOMS 15, 1989): q = (16 m + j) ln2/16 + r with |r| <= ln2/32 (ln2/16 as a
+// hi/lo pair, the product with the integer formed exactly), e^q = 2^m 2^(j/16) e^r,
+// 2^(j/16) from a table of hi/lo pairs and e^r from its Taylor series to degree 6
+// (remainder < 2^-51), the terms of degree 5 and 6 in FP32 and the rest by
+// double-float Horner steps.  Outputs the FP64 kappa (residual), built from the
+// hi/lo pair and 2^m by integer operations (the FP64 pipe is the slowest on this
+// part), and its FP32 copy (factorisation).
 namespace {
 struct dflt { float hi, lo; };
 __device__ __forceinline__ dflt qsum(float a, float b) { const float s = a + b; return {s, b - (s - a)}; }
@@ -74,37 +77,88 @@ __device__ __forceinline__ dflt df_mul(dflt a, dflt b) {
   e = fmaf(a.hi, b.lo, fmaf(a.lo, b.hi, e));
   return qsum(p, e);
 }
-// 1/n! as hi + lo pairs (the FP32 value nearest to 1/n!, then the nearest to the rest)
-__constant__ float kInvFact[13][2] = {
-    {1.0f, 0.0f}, {1.0f, 0.0f}, {0.5f, 0.0f},
-    {0.1666666716337204f, -4.967053879312289e-09f}, {0.0416666679084301f, -1.2417634698280722e-09f},
-    {0.008333333767950535f, -4.34617203337595e-10f}, {0.0013888889225199819f, -3.3631094437103215e-11f},
-    {0.00019841270113829523f, -2.725596874933456e-12f}, {2.4801587642286904e-05f, -3.40699609366682e-13f},
-    {2.7557318844628753e-06f, 3.793571224297229e-14f}, {2.755731998149713e-07f, -7.575112209051195e-15f},
-    {2.5052107943679403e-08f, 4.4176230446483665e-16f}, {2.0876755879584152e-09f, 1.1082839147459852e-16f}};
-// ln 2 as hi + lo
+__device__ __forceinline__ dflt df_mul_f(dflt a, float b) {   // double-float times an FP32 value
+  const float p = a.hi * b;
+  const float e = fmaf(a.lo, b, fmaf(a.hi, b, -p));
+  return qsum(p, e);
+}
+// 1/n! for n = 0..4 as hi + lo pairs (the FP32 value nearest to 1/n!, then the
+// nearest to the rest); 1/5!, 1/6! in FP32
+__constant__ float kInvFact[5][2] = {{1.0f, 0.0f}, {1.0f, 0.0f}, {0.5f, 0.0f},
+                                     {0.1666666716337204f, -4.967053879312289e-09f},
+                                     {0.0416666679084301f, -1.2417634698280722e-09f}};
+constexpr float kInv120 = 0.008333333767950535f, kInv720 = 0.0013888889225199819f;
+// 2^(j/16), j = 0..15, as hi + lo pairs (computed to 200 bits, then rounded as above)
+__constant__ float kExp2J16[16][2] = {
+    {1.0f, 0.0f}, {1.0442737340927124f, 4.8334701574503924e-08f},
+    {1.0905077457427979f, -1.3077539939843064e-08f}, {1.1387885808944702f, 5.386222312608879e-08f},
+    {1.1892070770263672f, 3.797635272917432e-08f}, {1.2418577671051025f, 4.496838101886169e-08f},
+    {1.2968395948410034f, -4.018999533172973e-08f}, {1.3542555570602417f, -1.0123349269974824e-08f},
+    {1.4142135381698608f, 2.4203234971764687e-08f}, {1.4768261909484863f, -4.500898853621038e-08f},
+    {1.5422108173370361f, 8.070904833346049e-09f}, {1.610490322113037f, 9.836217174097328e-09f},
+    {1.6817928552627563f, -2.4755326677450284e-08f}, {1.7562521696090698f, -9.235770370707996e-09f},
+    {1.8340080976486206f, -1.1239277952768134e-08f}, {1.9152065515518188f, 9.845328108326612e-09f}};
+// ln 2 as hi + lo; 16 / ln 2 rounded to FP32 (only chooses the reduction's integer)
 constexpr float kLn2Hi = 0.6931471824645996f, kLn2Lo = -1.9046542121259336e-09f;
+constexpr float kSixteenOverLn2 = 23.083120346069336f;
 
-__device__ __forceinline__ dflt df_exp(dflt q, int* k_out) {
-  const float kf = rintf(q.hi * 1.4426950408889634f);
-  dflt kl = {kf * kLn2Hi, 0.0f};
-  kl.lo = fmaf(kf, kLn2Hi, -kl.hi);          // k ln2_hi exactly, as hi + lo
-  kl.lo = fmaf(kf, kLn2Lo, kl.lo);
+// e^q = 2^m (hi + lo) with hi in [0.97, 2.04)
+__device__ __forceinline__ dflt df_exp(dflt q, int* m_out) {
+  const float kf = rintf(q.hi * kSixteenOverLn2);
+  const float c_hi = kLn2Hi * 0.0625f, c_lo = kLn2Lo * 0.0625f;   // ln2 / 16, exactly scaled
+  dflt kl = {kf * c_hi, 0.0f};
+  kl.lo = fmaf(kf, c_hi, -kl.hi);          // k ln2_hi / 16 exactly, as hi + lo
+  kl.lo = fmaf(kf, c_lo, kl.lo);
   const dflt r = df_add(q, dflt{-kl.hi, -kl.lo});
-  dflt p = {kInvFact[12][0], kInvFact[12][1]};
+  const float t = fmaf(r.hi, kInv720, kInv120);               // 1/5! + r/6!
+  dflt p = df_add(df_mul_f(r, t), dflt{kInvFact[4][0], kInvFact[4][1]});
 #pragma unroll
-  for (int n = 11; n >= 0; --n) p = df_add(df_mul(p, r), dflt{kInvFact[n][0], kInvFact[n][1]});
-  *k_out = (int)kf;
-  return p;
+  for (int n = 3; n >= 0; --n) p = df_add(df_mul(p, r), dflt{kInvFact[n][0], kInvFact[n][1]});
+  const int k = (int)kf;
+  *m_out = k >> 4;                                           // floor(k / 16)
+  const int j = k & 15;
+  return df_mul(p, dflt{kExp2J16[j][0], kExp2J16[j][1]});
+}
+
+// The double nearest to 2^m (x.hi + x.lo), for x.hi a normal positive FP32 value and
+// |x.lo| <= ulp(x.hi) / 2: the 53-bit significand is x.hi's 24 bits shifted up plus x.lo
+// in units of the double's last place (rounded to nearest); 0 below the normal range,
+// +inf above it.
+__device__ __forceinline__ double df_to_double_scaled(dflt x, int m) {
+  const uint32_t hb = __float_as_uint(x.hi);
+  int e = (int)(hb >> 23) - 127;                             // x.hi = mant 2^(e-23)
+  const long long mant = (long long)((hb & 0x7FFFFFu) | 0x800000u);
+  const float unit = __int_as_float((127 + 52 - e) << 23);   // 2^(52-e): x.lo in units of 2^(e-52)
+  long long M = (mant << 29) + (long long)__float2int_rn(x.lo * unit);
+  if (M < (1LL << 52)) {   // x.lo < 0 took x.hi = 2^e below it
+    M <<= 1;
+    --e;
+  }
+  const int ef = e + m + 1023;
+  if (ef >= 2047) return __longlong_as_double(0x7FF0000000000000LL);
+  if (ef <= 0) return 0.0;
+  return __longlong_as_double(((long long)ef << 52) | (M & ((1LL << 52) - 1)));
+}
+
+// 2^m x for a normal positive FP32 x: the exponent field moved by m, or ldexpf
+// where the result leaves the normal range
+__device__ __forceinline__ float scale_pow2(float x, int m) {
+  const int e = (int)(__float_as_uint(x) >> 23) + m;
+  return (e >= 1 && e <= 254) ? __int_as_float((int)__float_as_uint(x) + (m << 23)) : ldexpf(x, m);
 }
 }  // namespace
 
+// CTA = 128 triangles x 8 samples; the sample groups of one triangle block are
+// consecutive CTAs (blockIdx.x = triangle block x groups + group), so the block's
+// Phi rows are read from HBM once and from L2 by the other groups.  Z is staged
+// with the samples innermost: a column's eight samples are two 16-byte loads.
 __global__ void k_kappa_df(const float* __restrict__ phi_hi, const float* __restrict__ phi_lo,
                            const double* __restrict__ Z, int n_t, int n_z, int batch, double* __restrict__ kappa,
                            float* __restrict__ kappa32, int64_t kap_stride) {
   __shared__ float ph[kKapK][kKapT + 1], pl[kKapK][kKapT + 1];
-  __shared__ float zh[kKapS][kKapK], zl[kKapS][kKapK];
-  const int t0 = blockIdx.x * kKapT, s0 = blockIdx.y * kKapS;
+  __shared__ __align__(16) float zh[kKapK][kKapS], zl[kKapK][kKapS];
+  const int n_groups = (batch + kKapS - 1) / kKapS;
+  const int t0 = (blockIdx.x / n_groups) * kKapT, s0 = (blockIdx.x % n_groups) * kKapS;
   const int t = t0 + threadIdx.x;
   float ah[kKapS], al[kKapS];
 #pragma unroll
@@ -122,18 +176,25 @@ __global__ void k_kappa_df(const float* __restrict__ phi_hi, const float* __rest
       const int ss = e / kc, kk = e - ss * kc;
       const double z = (s0 + ss < batch) ? Z[(int64_t)(s0 + ss) * n_z + k0 + kk] : 0.0;
       const float h = (float)z;
-      zh[ss][kk] = h;
-      zl[ss][kk] = (float)(z - (double)h);
+      zh[kk][ss] = h;
+      zl[kk][ss] = (float)(z - (double)h);
     }
     __syncthreads();
     for (int kk = 0; kk < kc; ++kk) {
       const float a = ph[kk][threadIdx.x], b = pl[kk][threadIdx.x];
+      float zq[kKapS], zr[kKapS];
+#pragma unroll
+      for (int q4 = 0; q4 < kKapS; q4 += 4) {
+        const float4 u = *reinterpret_cast<const float4*>(&zh[kk][q4]);
+        const float4 v = *reinterpret_cast<const float4*>(&zl[kk][q4]);
+        zq[q4] = u.x; zq[q4 + 1] = u.y; zq[q4 + 2] = u.z; zq[q4 + 3] = u.w;
+        zr[q4] = v.x; zr[q4 + 1] = v.y; zr[q4 + 2] = v.z; zr[q4 + 3] = v.w;
+      }
 #pragma unroll
       for (int q = 0; q < kKapS; ++q) {
-        const float zq = zh[q][kk];
-        const float p = a * zq;
-        float e = fmaf(a, zq, -p);
-        e = fmaf(a, zl[q][kk], fmaf(b, zq, e));
+        const float p = a * zq[q];
+        float e = fmaf(a, zq[q], -p);
+        e = fmaf(a, zr[q], fmaf(b, zq[q], e));
         const dflt s = tsum(ah[q], p);     // (ah, al) += (p, e)
         ah[q] = s.hi;
         al[q] += s.lo + e;
@@ -144,20 +205,19 @@ __global__ void k_kappa_df(const float* __restrict__ phi_hi, const float* __rest
 #pragma unroll
     for (int q = 0; q < kKapS; ++q) {
       if (s0 + q >= batch) continue;
-      int k;
-      const dflt ex = df_exp(qsum(ah[q], al[q]), &k);
-      const double scale = k > 1023 ? (double)INFINITY
-                                    : (k < -1022 ? 0.0 : __longlong_as_double((long long)(1023 + k) << 52));   // 2^k
-      kappa[(int64_t)(s0 + q) * kap_stride + t] = ((double)ex.hi + (double)ex.lo) * scale;
-      kappa32[(int64_t)(s0 + q) * kap_stride + t] = ldexpf(ex.hi, k);
+      int m;
+      const dflt ex = df_exp(qsum(ah[q], al[q]), &m);
+      kappa[(int64_t)(s0 + q) * kap_stride + t] = df_to_double_scaled(ex, m);
+      kappa32[(int64_t)(s0 + q) * kap_stride + t] = scale_pow2(ex.hi, m);
     }
   }
 }
 
 cudaError_t launch_kappa_df(const float* phi_hi, const float* phi_lo, const double* Z, int n_t, int n_z, int batch,
                             double* kappa, float* kappa32, int64_t kap_stride, cudaStream_t st) {
-  dim3 grid((n_t + kKapT - 1) / kKapT, (batch + kKapS - 1) / kKapS);
-  k_kappa_df<<<grid, kKapT, 0, st>>>(phi_hi, phi_lo, Z, n_t, n_z, batch, kappa, kappa32, kap_stride);
+  const int64_t blocks = (int64_t)((n_t + kKapT - 1) / kKapT) * ((batch + kKapS - 1) / kKapS);
+  if (blocks > INT32_MAX) return cudaErrorInvalidConfiguration;
+  k_kappa_df<<<(unsigned)blocks, kKapT, 0, st>>>(phi_hi, phi_lo, Z, n_t, n_z, batch, kappa, kappa32, kap_stride);
   return cudaGetLastError();
 }
 
