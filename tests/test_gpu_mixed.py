@@ -123,7 +123,8 @@ def test_double_float_assembly_matches_fp64_exp(hdd):
     k64, kdf = ks
     # double-float arithmetic carries ~48 bits (unit 2^-48 = 3.6e-15).  The error of
     # q is bounded by ~2 n_z 2^-48 sum_k |Phi_tk Z_k|, which is also the relative error
-    # it causes in exp(q); the Horner evaluation of exp adds ~13 units.
+    # it causes in exp(q); the table-driven exp (2^(j/16) pairs, a degree-6 series, the
+    # product of the two) adds a few units more.
     u = 2.0 ** -48
     for s in range(3):
         q = phi @ Z[s]
