@@ -55,8 +55,8 @@ __global__ void k_kappa(const double* __restrict__ phi, const double* __restrict
 // (ACM TOMS 15, 1989): q = (16 m + j) ln2/16 + r with |r| <= ln2/32 (ln2/16 as a
 // hi/lo pair, the product with the integer formed exactly), e^q = 2^m 2^(j/16) e^r,
 // 2^(j/16) from a table of hi/lo pairs and e^r from its Taylor series to degree 6
-// (remainder < 2^-51), the terms of degree 5 and 6 in FP32 and the rest by
-// double-float Horner steps.  Outputs the FP64 kappa (residual), built from the
+// (remainder about 2^-51 at |r| = ln2/32), the terms of degree 5 and 6 in FP32 and
+// the rest by double-float Horner steps.  Outputs the FP64 kappa (residual), built from the
 // hi/lo pair and 2^m by integer operations (the FP64 pipe is the slowest on this
 // part), and its FP32 copy (factorisation).
 namespace {
