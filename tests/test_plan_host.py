@@ -206,3 +206,33 @@ def test_data_scratch_size_is_two_groups_of_four_vectors(hdd):
     plan = hdd.Plan(33, 8, None, w.obs_vertices(33, 3), 0.1, device=-1)
     for B in (1, 7, 256):
         assert plan.data_scratch_size(B) == (2 * 4 * B * 33 * 33 + 4 * B) * 8
+
+
+def test_multi_and_graph_calls_refuse_bad_arguments(hdd):
+    # The uneven-batch and graph calls check their arguments before any CUDA call:
+    # NULL handles and host-only plans are refused with HDD_EINVAL, destroying NULL is a
+    # no-op, and no handle is left behind.
+    import ctypes as C
+    lib = hdd.load_library()
+    out = C.c_void_p(1)
+    one = (C.c_int32 * 1)(4)
+    ws = (C.c_void_p * 1)(256)
+    assert lib.hdd_multi_create(None, 1, one, ws, C.byref(out)) == hdd.HDD_EINVAL
+    assert out.value is None
+    plan = hdd.Plan(33, 8, None, w.obs_vertices(33, 3), 0.01, device=-1)
+    plans = (C.c_void_p * 1)(plan._h.value)
+    out = C.c_void_p(1)
+    assert lib.hdd_multi_create(plans, 1, one, ws, C.byref(out)) == hdd.HDD_EINVAL
+    assert out.value is None
+    assert "host-only" in lib.hdd_last_error().decode()
+    assert lib.hdd_multi_create(plans, 0, one, ws, C.byref(out)) == hdd.HDD_EINVAL
+    assert lib.hdd_multi_create(plans, 1, one, ws, None) == hdd.HDD_EINVAL
+    g = C.c_void_p(1)
+    assert lib.hdd_multi_capture(None, None, None, None, None, None, None, C.byref(g)) == hdd.HDD_EINVAL
+    assert lib.hdd_graph_launch(None, None) == hdd.HDD_EINVAL
+    assert lib.hdd_graph_destroy(None) == hdd.HDD_OK
+    assert lib.hdd_multi_destroy(None) == hdd.HDD_OK
+    assert lib.hdd_multi_upsweep(None, None) == hdd.HDD_EINVAL
+    assert lib.hdd_multi_evaluate(None, None, None, None, None, None, None, None) == hdd.HDD_EINVAL
+    up = C.c_int32()
+    assert lib.hdd_multi_info(None, C.byref(up), None) == hdd.HDD_EINVAL
