@@ -185,7 +185,7 @@ def run_reference(args, cfg):
     return 0
 
 
-# Uneven batch (the north-star's batching workload): samples over four grids, 40/30/20/10 %
+# Uneven batch (many grids in one batch): samples over four grids, 40/30/20/10 %
 # by count, n_Z uniform in {10, 20, 40}, per plan an m x m observation lattice with m
 # uniform in 4..32 (16 to 1024 points); KL field with correlation length 0.2, variance 1.
 UNEVEN_MIX = ((129, 0.4), (257, 0.3), (513, 0.2), (1025, 0.1))
@@ -287,7 +287,7 @@ def run_uneven(args, hdd, torch, dev, stream, local):
 
 
 def run_policy(args, cfg, hdd, torch, dev, stream, local, prob, Z, y):
-    """North-star precision split (FP64 Cholesky of the top two tree levels) beside the
+    """The precision split with FP64 Cholesky of the top two tree levels beside the
     benched all-FP32 factorisation: per setting the fewest refinement steps with no sample
     flagged HDD_ENOCONV at the tolerance, and its speed."""
     B = Z.shape[0]

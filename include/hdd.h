@@ -333,7 +333,7 @@ hdd_status hdd_mean_functionals(hdd_plan_t plan, int32_t batch, void* workspace,
                                 void* stream);
 
 /* Uneven batches: several plans evaluated together, "Leaves to Root" as one launch
- * per tree height and front class over the nodes of all of them.  The north-star
+ * per tree height and front class over the nodes of all of them.  An uneven
  * workload mixes grids of 129^2 to 1025^2 with different KL bases and observation
  * sets; run one plan at a time, the upper tree levels of each leave most of the GPU
  * idle, while one launch per height over every plan fills it.  The paper has no
