@@ -55,7 +55,8 @@ MEASURED = _measured_peaks()
 # (taken on the kernel versions of this tree; a stage whose kernels change gets null).
 MEASURED_TRAFFIC = {
     "large_fronts": {"workload": "grid513", "leaf": 4, "precision": "mixed", "bytes_per_sample": 4.3483e9 / 16,
-                     "source": "profiles/large_fronts_dram_grid513_b16.md"},
+                     "source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of k_front_fill, k_potrf*, "
+                               "k_trsm*, k_chol_trsm, k_syrk_tc, k_syrk_rhs over one 16-sample evaluation"},
 }
 
 
